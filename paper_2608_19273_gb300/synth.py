@@ -1,0 +1,241 @@
+"""Seeded synthetic inputs for the batched patch update.
+
+This module holds no arithmetic of the method itself (no flux, no update, no
+conversion between conserved and primitive variables).  It only builds
+
+* patch tables: periodic boxes tiled by equal patches, one box per
+  refinement level, with face-neighbour ids and SoA-arena offsets
+  (the paper's list of K patches, Sec. II Eq. 2, and its typical patch sizes,
+  Sec. IV);
+* smooth random fields: sums of 4 random Fourier modes with integer wave
+  numbers in {-4..4}^d, so that every field is periodic on its box;
+* Gaussian pulses and i.i.d. samples;
+* the workload descriptions (pde, dimension, patch mix, halo, time stepping).
+
+Both the CUDA path and the oracle take their inputs from here.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Same field order and sizes as the library's patch descriptor (72 bytes).
+PATCH_DTYPE = np.dtype([("p", "<i4"), ("level", "<i4"), ("dx", "<f8"), ("x0", "<f8", (3,)),
+                        ("offset", "<i8"), ("nbr", "<i4", (6,))])
+assert PATCH_DTYPE.itemsize == 72
+
+PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE_GW59 = range(7)
+SCHEME_FV, SCHEME_FD = 0, 1
+PDE_NQ = {0: 1, 1: 1, 2: 4, 3: 5, 4: 5, 5: 5, 6: 59}
+PDE_NM = {0: 3, 1: 3, 2: 0, 3: 0, 4: 1, 5: 5, 6: 0}
+
+SEED_BASE = 260819273
+
+
+@dataclasses.dataclass
+class Level:
+    """A periodic box of nx x ny x nz patches of p^d voxels each."""
+    n: tuple          # patches per axis (nz = 1 in 2D)
+    p: int
+    dx: float
+    level: int = 0
+
+
+@dataclasses.dataclass
+class Mesh:
+    dim: int
+    patches: np.ndarray       # PATCH_DTYPE records
+    var_stride: int           # elements between two variables of the arena
+    levels: list
+    level_ranges: list        # [first, last) patch index per level
+
+    @property
+    def K(self):
+        return len(self.patches)
+
+    @property
+    def nvox(self):
+        return int(sum(int(p) ** self.dim for p in self.patches["p"]))
+
+
+def _round_up(x, m):
+    return (x + m - 1) // m * m
+
+
+def make_mesh(levels, dim, align=16):
+    """Tile each level's periodic box by patches (x fastest), assign arena offsets."""
+    recs, ranges = [], []
+    off = 0
+    for lev in levels:
+        nx, ny, nz = lev.n if dim == 3 else (lev.n[0], lev.n[1], 1)
+        first = len(recs)
+        ranges.append((first, first + nx * ny * nz))
+        for k in range(nz):
+            for j in range(ny):
+                for i in range(nx):
+                    def pid(a, b, c):
+                        return first + ((c % nz) * ny + (b % ny)) * nx + (a % nx)
+                    nbr = [pid(i - 1, j, k), pid(i + 1, j, k), pid(i, j - 1, k), pid(i, j + 1, k), -1, -1]
+                    if dim == 3:
+                        nbr[4], nbr[5] = pid(i, j, k - 1), pid(i, j, k + 1)
+                    x0 = (i * lev.p * lev.dx, j * lev.p * lev.dx, k * lev.p * lev.dx if dim == 3 else 0.0)
+                    recs.append((lev.p, lev.level, lev.dx, x0, off, nbr))
+                    off += _round_up(lev.p ** dim, align)
+    patches = np.array(recs, dtype=PATCH_DTYPE)
+    return Mesh(dim=dim, patches=patches, var_stride=_round_up(off, 32), levels=list(levels), level_ranges=ranges)
+
+
+def voxel_centres(mesh):
+    """Coordinates (3, var_stride) of every voxel centre (padding stays 0)."""
+    X = np.zeros((3, mesh.var_stride))
+    for pt in mesh.patches:
+        p = int(pt["p"])
+        pz = p if mesh.dim == 3 else 1
+        z, y, x = np.meshgrid(np.arange(pz), np.arange(p), np.arange(p), indexing="ij")
+        sl = slice(int(pt["offset"]), int(pt["offset"]) + p * p * pz)
+        X[0, sl] = pt["x0"][0] + (x.ravel() + 0.5) * pt["dx"]
+        X[1, sl] = pt["x0"][1] + (y.ravel() + 0.5) * pt["dx"]
+        X[2, sl] = pt["x0"][2] + (z.ravel() + 0.5) * pt["dx"] if mesh.dim == 3 else 0.0
+    return X
+
+
+def level_extent(mesh, li):
+    lev = mesh.levels[li]
+    L = [lev.n[a] * lev.p * lev.dx for a in range(mesh.dim)]
+    return L
+
+
+def level_slices(mesh, li):
+    """Arena index array of all voxels of level li."""
+    a, b = mesh.level_ranges[li]
+    idx = []
+    for pt in mesh.patches[a:b]:
+        n = int(pt["p"]) ** mesh.dim
+        idx.append(np.arange(int(pt["offset"]), int(pt["offset"]) + n))
+    return np.concatenate(idx)
+
+
+def fourier_field(rng, X, L, dim, mid, amp, modes=4, kmax=4):
+    """mid + amp * sum_m a_m sin(2 pi k_m.x/L + phi_m) / sum_m a_m (periodic on the box L)."""
+    a = rng.uniform(0.0, 1.0, modes)
+    phi = rng.uniform(0.0, 2 * math.pi, modes)
+    ks = []
+    while len(ks) < modes:
+        k = rng.integers(-kmax, kmax + 1, dim)
+        if np.any(k != 0):
+            ks.append(k)
+    f = np.zeros(X.shape[1])
+    for m in range(modes):
+        arg = phi[m]
+        for ax in range(dim):
+            arg = arg + 2 * math.pi * ks[m][ax] * X[ax] / L[ax]
+        f += a[m] * np.sin(arg)
+    return mid + amp * f / a.sum()
+
+
+def fill_fields(mesh, rng, specs):
+    """Arena (len(specs), var_stride) of Fourier fields; specs = [(mid, amp), ...] per variable."""
+    X = voxel_centres(mesh)
+    out = np.zeros((len(specs), mesh.var_stride))
+    for li in range(len(mesh.levels)):
+        idx = level_slices(mesh, li)
+        L = level_extent(mesh, li)
+        for v, (mid, amp) in enumerate(specs):
+            out[v, idx] = fourier_field(rng, X[:, idx], L, mesh.dim, mid, amp)
+    return out
+
+
+# ------------------------------------------------------------------ workloads
+@dataclasses.dataclass
+class Workload:
+    name: str
+    pde: int
+    scheme: int
+    mesh: Mesh
+    halo: int
+    rk: int
+    steps: int
+    cfl: float
+    sigma: float
+    seed: int
+    params: np.ndarray | None = None
+
+    @property
+    def nq(self):
+        return PDE_NQ[self.pde]
+
+    @property
+    def nm(self):
+        return PDE_NM[self.pde]
+
+
+def euler2d_mesh(n=8, p=16, dx=1.0 / 128):
+    return make_mesh([Level((n, n, 1), p, dx, 0)], dim=2)
+
+
+def euler3d_amr_mesh(scale=1):
+    """The AMR-like mix: 4096 x 8^3 + 1024 x 16^3 + 128 x 32^3 patches, dx = 1/128.
+
+    Each level is its own periodic box.  ``scale`` > 1 divides the patch
+    counts per axis (small cases for tests)."""
+    s = scale
+    return make_mesh([Level((16 // s, 16 // s, 16 // s), 8, 1.0 / 128, 0),
+                      Level((16 // s, 8 // s, 8 // s), 16, 1.0 / 128, 1),
+                      Level((max(8 // s, 1), max(4 // s, 1), max(4 // s, 1)), 32, 1.0 / 128, 2)], dim=3)
+
+
+def euler_prims(mesh, seed):
+    """rho, p in [0.5, 1.5]; velocities in [-0.5, 0.5]; rows (rho, u.., p)."""
+    rng = np.random.default_rng(seed)
+    specs = [(1.0, 0.5)] + [(0.0, 0.5)] * mesh.dim + [(1.0, 0.5)]
+    return fill_fields(mesh, rng, specs)
+
+
+def workload(name, scale=1):
+    """Workload descriptions.
+
+    euler2d : 2D Euler, 64 patches of 16^2, FV Rusanov, forward Euler, 10 steps, CFL 0.4.
+    euler3d : 3D Euler, AMR-like patch mix, FV Rusanov, SSP-RK3, CFL 0.4.
+    wave3d  : first-order wave system with c(x), FD4 + KO, RK4, 2048 patches of 16^3.
+    srhd3d  : special-relativistic hydro, FV Rusanov + con2prim, SSP-RK3, 4096 patches of 16^3.
+    gw59    : 59-unknown gravitational-wave stand-in, FD4 + KO, RK4, 3 levels of 24^3/16^3 patches.
+    """
+    if name == "euler2d":
+        return Workload(name, PDE_EULER2D, SCHEME_FV, euler2d_mesh(), 1, 1, 10, 0.4, 0.0, SEED_BASE + 0)
+    if name == "euler3d":
+        return Workload(name, PDE_EULER3D, SCHEME_FV, euler3d_amr_mesh(scale), 1, 3, 100, 0.4, 0.0,
+                        SEED_BASE + 1)
+    if name == "wave3d":
+        s = scale
+        mesh = make_mesh([Level((16 // s, 16 // s, 8 // s), 16, 1.0 / 128, 0)], dim=3)
+        return Workload(name, PDE_WAVE3D, SCHEME_FD, mesh, 3, 4, 10, 0.25, 0.1, SEED_BASE + 2,
+                        np.array([0.1]))
+    if name == "srhd3d":
+        s = scale
+        mesh = make_mesh([Level((16 // s, 16 // s, 16 // s), 16, 1.0 / 256, 0)], dim=3)
+        return Workload(name, PDE_SRHD3D, SCHEME_FV, mesh, 1, 3, 10, 0.4, 0.0, SEED_BASE + 3,
+                        np.array([5.0 / 3.0]))
+    if name == "gw59":
+        s = scale
+        mesh = make_mesh([Level((8 // s, 8 // s, 8 // s), 24, 1.0 / 192, 0),
+                          Level((12 // s, 12 // s, 12 // s), 16, 1.0 / 192, 1),
+                          Level((16 // s, 16 // s, 16 // s), 16, 1.0 / 256, 2)], dim=3)
+        rng = np.random.default_rng(SEED_BASE + 4)
+        C = rng.uniform(-0.1, 0.1, (11, 11))
+        params = np.concatenate([[0.1], C.ravel()])
+        return Workload(name, PDE_GW59, SCHEME_FD, mesh, 3, 4, 5, 0.25, 0.1, SEED_BASE + 4, params)
+    raise KeyError(name)
+
+
+def dyadic_field(rng, shape, bits=10, lo=-64, hi=64):
+    """Values k / 2^bits with small integers k: sums, halves and differences stay exact."""
+    return rng.integers(lo, hi + 1, shape).astype(np.float64) / float(2 ** bits)
+
+
+def gaussian(X, centre, width, dim):
+    r2 = np.zeros(X.shape[1])
+    for a in range(dim):
+        r2 = r2 + (X[a] - centre[a]) ** 2
+    return np.exp(-r2 / (2 * width * width))
