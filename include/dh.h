@@ -1,0 +1,196 @@
+/* dh.h -- C ABI of libdh: the batched explicit patch update on GB300 (sm_103a).
+ *
+ * The library advances K patches of p^d voxels (d = 2 or 3) of a hyperbolic
+ * PDE system
+ *
+ *     dQ/dt + div F(Q) + B(Q) . grad Q = S(Q)                  (paper Eq. 1)
+ *
+ * by one explicit Runge-Kutta stage per call.  The problem statement follows
+ * the paper's batched cell kernel K~_{dt,K} (Sec. II, Eq. 2): a list of K
+ * patches, cells per patch p, halo width h, voxel spacing dx, time step dt and
+ * the PDE id; N evolved quantities and M material parameters per voxel
+ * (Sec. II: materials do not evolve).
+ *
+ * Conventions for every entry point
+ *   - All device buffers are owned by the caller (typically torch tensors)
+ *     and passed as raw device pointers.  The library never allocates memory
+ *     per call.  A plan owns only its device patch/work tables and a few
+ *     bytes of reduction scratch, all freed by dh_plan_destroy.
+ *   - Compute calls are asynchronous on `stream` (a cudaStream_t; NULL means
+ *     the legacy default stream).  Errors that can be detected on the host
+ *     (bad sizes, NULL pointers, unsupported PDE) are returned synchronously
+ *     and nothing is launched.  Launch failures return DH_ECUDA.
+ *   - Data errors found on the device never trap: they are reported through
+ *     status arrays and counters (con2prim).
+ *   - dh_last_error() returns a thread-local message for the last failure.
+ *
+ * State layout ("SoA arena").  A state with V variables is one device array
+ * of V * var_stride doubles.  Variable v of voxel (x, y, z) of patch k is at
+ *     v * var_stride + patches[k].offset + (z * p + y) * p + x
+ * (z = 0 in 2D).  Only interior voxels are stored; halos are gathered from
+ * the face neighbours inside the kernels (the paper's gather prologue,
+ * Sec. III-C Eq. 4, done on the fly).  Material parameters use a second
+ * arena with the same offsets and var_stride.  offset must be a multiple of
+ * 16 elements and var_stride a multiple of 32 (128-byte aligned blocks).
+ */
+#ifndef DH_H
+#define DH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DH_OK = 0,
+  DH_EINVAL = -1,        /* invalid argument (sizes, NULL pointers, aliasing, patch table) */
+  DH_ECUDA = -2,         /* a CUDA call failed; see dh_last_error() */
+  DH_EUNSUPPORTED = -3,  /* PDE, scheme or patch size not supported by this entry point */
+  DH_ENOMEM = -4,        /* plan allocation failed */
+  DH_ETIMEOUT = -5       /* a bounded device wait gave up (reserved) */
+} dh_status;
+
+/* PDE systems (Eq. 1 instances).  N evolved / M material quantities:
+ *   ADV_FLUX  N=1 M=3  dq/dt + div(a q) = 0, a(x) = material velocity
+ *   ADV_NCP   N=1 M=3  dq/dt + a . grad q = 0 (non-conservative form)
+ *   EULER2D   N=4 M=0  (rho, rho u, rho v, E), ideal gas gamma
+ *   EULER3D   N=5 M=0  (rho, rho u, rho v, rho w, E), ideal gas gamma
+ *   WAVE3D    N=5 M=1  (phi, Pi, psi_x, psi_y, psi_z), material c(x)
+ *   SRHD3D    N=5 M=5  (D, S_x, S_y, S_z, tau); the material arena carries
+ *                      the primitives (rho, v_x, v_y, v_z, p) from con2prim
+ *   GW59      N=59 M=0 59-unknown gravitational-wave stand-in (see DESIGN) */
+typedef enum {
+  DH_PDE_ADV_FLUX = 0,
+  DH_PDE_ADV_NCP = 1,
+  DH_PDE_EULER2D = 2,
+  DH_PDE_EULER3D = 3,
+  DH_PDE_WAVE3D = 4,
+  DH_PDE_SRHD3D = 5,
+  DH_PDE_GW59 = 6
+} dh_pde;
+
+/* One patch (the paper's cell with its embedded p^d mesh, Sec. II).
+ * 72 bytes, natural alignment. */
+typedef struct dh_patch {
+  int32_t p;        /* voxels per patch per dimension */
+  int32_t level;    /* refinement level (informational) */
+  double dx;        /* VOXEL spacing (the paper's patch width is p * dx) */
+  double x0[3];     /* lower corner of the patch */
+  int64_t offset;   /* element offset of this patch's block in the arena */
+  int32_t nbr[6];   /* face neighbours -x,+x,-y,+y,-z,+z; same p and dx;
+                       periodic wrap is resolved by the caller; 2D: -1 in z */
+} dh_patch;
+
+typedef struct dh_plan dh_plan;
+
+/* Create a plan for K patches (Sec. II Eq. 2: list of patches, p, h, PDE).
+ *   pde, dim   : dh_pde and 2 or 3 (must match the PDE's dimension; the
+ *                advection systems accept 3 only)
+ *   patches    : host array of K patch records, copied by the plan
+ *   halo       : halo width h: 1 for the FV stage, 3 for the FD4+KO stage
+ *   var_stride : elements between two variables in every arena
+ *   params     : PDE parameters (host, may be NULL for defaults):
+ *                EULER*: [gamma=1.4]  SRHD3D: [Gamma=5/3]  WAVE3D: [damping=0.1]
+ *                GW59: [kappa=0.1, C_ab (121 values, row-major)]
+ * Patch sizes: every p must be a multiple of 8.  Neighbours must have the
+ * same p and dx.  Returns DH_EINVAL on a malformed table, DH_ENOMEM or
+ * DH_ECUDA if the device tables cannot be created. */
+dh_status dh_plan_create(dh_plan** plan, int32_t pde, int32_t dim, const dh_patch* patches, int32_t K,
+                         int32_t halo, int64_t var_stride, const double* params, int32_t n_params);
+dh_status dh_plan_destroy(dh_plan* plan);
+
+/* One finite-volume Runge-Kutta stage over all K patches in one launch
+ * (paper Sec. II-A Eq. 3: source per voxel, face fluxes from the two
+ * neighbouring voxels, combination into the new state; Sec. II: RK stages
+ * call the cell update with tableau-dependent dt):
+ *     L(Q)_i = -(1/dx) sum_d [F^_{i+1/2} - F^_{i-1/2} + (D_{i+1/2} + D_{i-1/2})/2] + S(Q_i)
+ *     F^     = (F_d(QL) + F_d(QR))/2 - s/2 (QR - QL),  s = max(lambda_d(QL), lambda_d(QR))
+ *     D      = B_d((QL + QR)/2) (QR - QL)
+ *     out    = a*q0 + b*qs + g*dt*L(qs)       (skipped if out == NULL)
+ *     acc    = acc + d*dt*L(qs)               (skipped if acc == NULL)
+ * qs  : stage input (N-variable arena); halos are read from neighbour patches.
+ * q0  : N-variable arena or NULL (then a must be 0).  out may equal q0
+ *       (element-wise read before write); out and acc must not alias qs.
+ * mat : M-variable material arena (NULL if M = 0).
+ * dt_dev : device pointer to one double (so CUDA graphs replay without the host).
+ * lam_out_dev : NULL, or a device double that receives the maximum
+ *       characteristic speed of the result (out, else acc) over all voxels and
+ *       directions (not available for SRHD3D: use max_wave_speed on the
+ *       primitives).  Requires plan halo >= 1. */
+dh_status patch_update_fv(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                          const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                          double* lam_out_dev, void* stream);
+
+/* One FD stage: 4th-order centred differences with 6th-difference
+ * Kreiss-Oliger dissipation (paper Sec. I and Sec. IV: FD4 with KO):
+ *     L(Q) = -sum_d dF_d/dx_d - sum_d B_d(Q) dQ/dx_d + S(Q) + sigma/(64 dx) sum_d delta6_d Q
+ *     dQ/dx  = [(Q_-2 - Q_+2) + 8 (Q_+1 - Q_-1)] / (12 dx)
+ *     delta6 = Q_-3 - 6 Q_-2 + 15 Q_-1 - 20 Q_0 + 15 Q_+1 - 6 Q_+2 + Q_+3
+ * Same stage combination and arguments as patch_update_fv.  Requires halo 3. */
+dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                             const double* mat, const double* dt_dev, double a, double b, double g,
+                             double d, double sigma_ko, double* lam_out_dev, void* stream);
+
+/* lam_out_dev <- max over voxels and directions of the characteristic speed of q
+ * (the paper's scalar eigenvalue functions, Sec. II-B). */
+dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream);
+
+/* dt_dev <- cfl * dx_min / (dim * lam_dev[0]) on the device (the CFL rule). */
+dh_status dh_cfl_dt(dh_plan* plan, const double* lam_dev, double cfl, double* dt_dev, void* stream);
+
+/* Primitive -> conserved, element-wise over the plan's voxels (initial data).
+ *   EULER*: (rho, u.., p) -> (rho, rho u.., p/(gamma-1) + rho |u|^2/2)
+ *   SRHD3D: (rho, v, p)   -> (D, S, tau) */
+dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* stream);
+
+/* One full time step of a Runge-Kutta scheme built from stage calls
+ * (paper Sec. II: RK schemes call the cell update several times per step
+ * with tableau-dependent dt and refresh halos between calls):
+ *   rk = 1 forward Euler:  q <- q + dt L(q)              (u1 scratch)
+ *   rk = 3 SSP-RK3 (Shu-Osher): u1 = q + dt L(q); u2 = 3/4 q + 1/4 u1 + 1/4 dt L(u1);
+ *          q <- 1/3 q + 2/3 u2 + 2/3 dt L(u2)
+ *   rk = 4 classical RK4 with acc = q + dt/6 (k1 + 2 k2 + 2 k3 + k4), q <- acc
+ * scheme 0 = FV stage (patch_update_fv), 1 = FD4+KO stage (patch_update_fd_ko).
+ * If cfl > 0, dt_dev is first set on the device to cfl dx_min / (dim lam_dev[0])
+ * and the last stage writes the new maximum wave speed into lam_dev, so
+ * lam_dev must hold the speed of q on entry (max_wave_speed).  If cfl <= 0
+ * the caller's dt_dev is used unchanged.  All buffers are N-variable arenas
+ * owned by the caller; u2 is needed for rk >= 3 and acc for rk = 4. */
+dh_status dh_rk_step(dh_plan* plan, int32_t scheme, int32_t rk, double* q, double* u1, double* u2, double* acc,
+                     const double* mat, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
+                     void* stream);
+
+/* Capture n_steps consecutive dh_rk_step calls (same arguments) into one CUDA
+ * graph owned by the plan (replacing any previous one); nothing runs during
+ * capture.  stream must be a non-default stream.  If timing != 0, event
+ * records are placed around every stage launch so that dh_graph_stage_times
+ * can report per-stage device times of the most recent replay. */
+dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_steps, double* q, double* u1,
+                           double* u2, double* acc, const double* mat, double* dt_dev, double* lam_dev, double cfl,
+                           double sigma_ko, int32_t timing, void* stream);
+/* Replay the captured graph on stream. */
+dh_status dh_graph_launch(dh_plan* plan, void* stream);
+/* Number of kernel launches in the graph and of timed stages. */
+dh_status dh_graph_info(dh_plan* plan, int32_t* n_kernels, int32_t* n_timed_stages);
+/* Device time (ms) of the first n timed stages of the last completed replay
+ * (the caller synchronises first). */
+dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
+
+/* Diagnostic: FP64 FMA throughput probe used to measure the FP64 roofline
+ * peak on the running GPU.  Launches n_threads (a multiple of 256) threads;
+ * each runs 8 independent chains of `iters` fused multiply-adds
+ * (8 * iters * n_threads FMAs = 16 * iters * n_threads FLOP) and writes one
+ * double to out_dev[thread].  out_dev must hold n_threads doubles. */
+dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void* stream);
+
+const char* dh_last_error(void);
+
+/* Library version string. */
+const char* dh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DH_H */

@@ -1,0 +1,62 @@
+"""Write oracle/flop_counts.json: exact FP64 operations per voxel of each time-step kind.
+
+Runs the oracle's counting build (scalar type that counts add, sub, mul, div
+and sqrt; min, max and abs are free) on one self-periodic patch of size p for
+two sizes and separates the per-voxel term from the halo term:
+count(p) = A p^d + B p^(d-1)  =>  A = algorithmic operations per voxel.
+Only this script (which calls nothing but the oracle) writes the file; the
+benchmark reads it as data.
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import oracle  # noqa: E402
+from paper_2608_19273_gb300 import synth  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "flop_counts.json")
+
+
+def _state(pde, dim, p, seed=3):
+    mesh = synth.make_mesh([synth.Level((1, 1, 1), p, 1.0 / 64, 0)], dim=dim)
+    n = p ** dim
+    if pde in (synth.PDE_EULER2D, synth.PDE_EULER3D):
+        prim = synth.euler_prims(mesh, seed)
+        q = oracle.prim2con(pde, prim, mesh.var_stride)[:, :n]
+        return np.ascontiguousarray(q), None
+    raise KeyError(pde)
+
+
+def per_voxel(scheme, pde, dim, halo, rk, with_lam, sizes=(8, 16, 24)):
+    """Exact fit count(p) = A p^d + B p^(d-1) + C (C: per-stage and per-patch scalars)."""
+    c = []
+    for p in sizes:
+        q, m = _state(pde, dim, p)
+        c.append(oracle.count_flops(scheme, pde, dim, p, halo, q, m, rk=rk, with_lam=with_lam))
+    M = np.array([[p ** dim, p ** (dim - 1), 1.0] for p in sizes])
+    A, B, C = np.linalg.solve(M, np.array(c, dtype=float))
+    return A, B, C, c
+
+
+def main():
+    res = {}
+    for key, args in {
+        "fv/euler3d/ssprk3_step": (0, synth.PDE_EULER3D, 3, 1, 3, True),
+        "fv/euler3d/stage_fe": (0, synth.PDE_EULER3D, 3, 1, 0, False),
+        "fv/euler2d/fe_step": (0, synth.PDE_EULER2D, 2, 1, 1, True),
+    }.items():
+        A, B, C, c = per_voxel(*args)
+        A2, B2, C2, _ = per_voxel(*args, sizes=(8, 16, 32))
+        assert abs(A - A2) < 1e-6 and abs(A - round(A)) < 1e-6, (key, A, A2)
+        res[key] = {"flops_per_voxel": int(round(A)), "halo_term": round(B, 6), "constant": round(C, 6),
+                    "raw_counts": c}
+    with open(OUT, "w") as f:
+        json.dump(res, f, indent=1, sort_keys=True)
+    print(json.dumps(res, indent=1, sort_keys=True))
+
+
+if __name__ == "__main__":
+    main()

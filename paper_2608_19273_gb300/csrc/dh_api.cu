@@ -1,0 +1,364 @@
+// C-ABI entry points of libdh: plans, argument validation, small kernels
+// (wave-speed maximum, CFL time step, primitive -> conserved) and dispatch to
+// the stage kernels.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dh_internal.cuh"
+#include "dh_pde.cuh"
+
+namespace dh {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+dh_status cuda_error(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return DH_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return DH_ECUDA;
+}
+
+int pde_nq(int pde) {
+  static const int n[7] = {1, 1, 4, 5, 5, 5, 59};
+  return (pde >= 0 && pde < 7) ? n[pde] : 0;
+}
+int pde_nm(int pde) {
+  static const int m[7] = {3, 3, 0, 0, 1, 5, 0};
+  return (pde >= 0 && pde < 7) ? m[pde] : 0;
+}
+int pde_dim(int pde) { return pde == DH_PDE_EULER2D ? 2 : 3; }
+
+// ---------------------------------------------------------------- small kernels
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// One CTA per patch: lambda of every voxel, block max, atomicMax on the bit
+// pattern, last CTA publishes and resets the scratch.
+template <class PDE>
+__global__ void __launch_bounds__(256) k_max_speed(const dh_patch* __restrict__ patches, int dim, int64_t vs,
+                                                   const double* __restrict__ q, const double* __restrict__ mat,
+                                                   DevParams P, double* lam_out, unsigned long long* red) {
+  __shared__ double wmax[8];
+  __shared__ bool last;
+  const dh_patch pt = patches[blockIdx.x];
+  const int n = dim == 3 ? pt.p * pt.p * pt.p : pt.p * pt.p;
+  double lam = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double u[PDE::N + PDE::M], W[PDE::NW > 0 ? PDE::NW : 1];
+    const int64_t e = pt.offset + i;
+#pragma unroll
+    for (int v = 0; v < PDE::N; ++v) u[v] = q[v * vs + e];
+#pragma unroll
+    for (int v = 0; v < PDE::M; ++v) u[PDE::N + v] = mat[v * vs + e];
+    PDE::prims(u, P, W);
+    double l = fmax(PDE::speed(0, u, W, P), PDE::speed(1, u, W, P));
+    if (dim == 3) l = fmax(l, PDE::speed(2, u, W, P));
+    lam = fmax(lam, l);
+  }
+  lam = warp_max_d(lam);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lam;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, wmax[i]);
+    atomicMax(red, (unsigned long long)__double_as_longlong(m));
+    __threadfence();
+    last = atomicAdd(red + 1, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    *lam_out = __longlong_as_double((long long)atomicAdd(red, 0ull));
+    red[0] = 0ull;
+    red[1] = 0ull;
+    __threadfence();
+  }
+}
+
+__global__ void k_cfl_dt(const double* lam, double cfl, double dx_dim, double* dt) {
+  // dt = cfl * dx / (dim * lambda); dx_dim = dx / dim
+  *dt = cfl * dx_dim / lam[0];
+}
+
+template <int DIM>
+__global__ void k_prim2con_euler(const dh_patch* __restrict__ patches, int64_t vs, const double* __restrict__ w,
+                                 double* __restrict__ q, double gamma) {
+  const dh_patch pt = patches[blockIdx.x];
+  const int n = DIM == 3 ? pt.p * pt.p * pt.p : pt.p * pt.p;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t e = pt.offset + i;
+    const double rho = w[e], p = w[(DIM + 1) * vs + e];
+    double kin = 0.0;
+    q[e] = rho;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      const double u = w[(1 + k) * vs + e];
+      const double m = rho * u;
+      q[(1 + k) * vs + e] = m;
+      kin = fma(m, u, kin);
+    }
+    q[(DIM + 1) * vs + e] = fma(0.5, kin, p / (gamma - 1.0));
+  }
+}
+
+__global__ void k_prim2con_srhd(const dh_patch* __restrict__ patches, int64_t vs, const double* __restrict__ w,
+                                double* __restrict__ q, double G) {
+  const dh_patch pt = patches[blockIdx.x];
+  const int n = pt.p * pt.p * pt.p;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t e = pt.offset + i;
+    const double rho = w[e], vx = w[vs + e], vy = w[2 * vs + e], vz = w[3 * vs + e], p = w[4 * vs + e];
+    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    const double W2 = 1.0 / (1.0 - v2);
+    const double W = sqrt(W2);
+    const double rhoh = fma(G / (G - 1.0), p, rho);
+    const double rhohW2 = rhoh * W2;
+    const double D = rho * W;
+    q[e] = D;
+    q[vs + e] = rhohW2 * vx;
+    q[2 * vs + e] = rhohW2 * vy;
+    q[3 * vs + e] = rhohW2 * vz;
+    q[4 * vs + e] = (rhohW2 - p) - D;
+  }
+}
+
+// Eight independent FMA chains per thread (throughput, not latency, bound).
+__global__ void __launch_bounds__(256) k_probe_dfma(double* out, int iters, double b, double c) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double a0 = 1.0 + 1e-3 * threadIdx.x, a1 = a0 + 0.1, a2 = a0 + 0.2, a3 = a0 + 0.3;
+  double a4 = a0 + 0.4, a5 = a0 + 0.5, a6 = a0 + 0.6, a7 = a0 + 0.7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+    a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+  }
+  out[t] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+
+static dh_status check_plan(const dh_plan* plan) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return DH_EINVAL;
+  }
+  return DH_OK;
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+const char* dh_last_error(void) { return g_err; }
+
+const char* dh_version(void) { return "libdh 0.1 (sm_103a)"; }
+
+dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch* patches, int32_t K,
+                         int32_t halo, int64_t var_stride, const double* params, int32_t n_params) {
+  if (!out) { set_error("dh_plan_create: out is NULL"); return DH_EINVAL; }
+  *out = nullptr;
+  if (pde < 0 || pde > 6) { set_error("dh_plan_create: unknown pde %d", pde); return DH_EINVAL; }
+  if (dim != pde_dim(pde)) { set_error("dh_plan_create: pde %d needs dim %d, got %d", pde, pde_dim(pde), dim); return DH_EINVAL; }
+  if (!patches || K <= 0) { set_error("dh_plan_create: empty patch list"); return DH_EINVAL; }
+  if (halo < 1 || halo > 8) { set_error("dh_plan_create: halo %d out of range [1, 8]", halo); return DH_EINVAL; }
+  if (var_stride <= 0 || var_stride % 32 != 0) { set_error("dh_plan_create: var_stride %lld must be a positive multiple of 32", (long long)var_stride); return DH_EINVAL; }
+  if (n_params < 0 || (n_params > 0 && !params)) { set_error("dh_plan_create: bad params"); return DH_EINVAL; }
+  for (int k = 0; k < K; ++k) {
+    const dh_patch& pt = patches[k];
+    if (pt.p < 8 || pt.p % 8 != 0 || pt.p > 256) { set_error("patch %d: p = %d must be a multiple of 8 in [8, 256]", k, pt.p); return DH_EINVAL; }
+    if (pt.p < halo) { set_error("patch %d: p = %d smaller than the halo %d", k, pt.p, halo); return DH_EINVAL; }
+    if (!(pt.dx > 0.0)) { set_error("patch %d: dx must be positive", k); return DH_EINVAL; }
+    const int64_t n = dim == 3 ? (int64_t)pt.p * pt.p * pt.p : (int64_t)pt.p * pt.p;
+    if (pt.offset < 0 || pt.offset % 16 != 0 || pt.offset + n > var_stride) {
+      set_error("patch %d: offset %lld not 16-aligned or block exceeds var_stride", k, (long long)pt.offset);
+      return DH_EINVAL;
+    }
+    for (int f = 0; f < 2 * dim; ++f) {
+      const int nb = pt.nbr[f];
+      if (nb < 0 || nb >= K) { set_error("patch %d: neighbour %d = %d out of range", k, f, nb); return DH_EINVAL; }
+      if (patches[nb].p != pt.p || patches[nb].dx != pt.dx) {
+        set_error("patch %d: neighbour %d (patch %d) has a different p or dx", k, f, nb);
+        return DH_EINVAL;
+      }
+    }
+  }
+  dh_plan* plan = new (std::nothrow) dh_plan();
+  if (!plan) { set_error("dh_plan_create: out of host memory"); return DH_ENOMEM; }
+  plan->pde = pde; plan->dim = dim; plan->K = K; plan->halo = halo; plan->var_stride = var_stride;
+  plan->nq = pde_nq(pde); plan->nm = pde_nm(pde);
+  plan->h_patches.assign(patches, patches + K);
+  plan->dx_min = patches[0].dx;
+  for (int k = 1; k < K; ++k) plan->dx_min = std::min(plan->dx_min, patches[k].dx);
+  DevParams& P = plan->params;
+  P.gamma = 1.4; P.Gamma = 5.0 / 3.0; P.damp = 0.1; P.kappa = 0.1;
+  std::memset(P.C, 0, sizeof(P.C));
+  if (params && n_params > 0) {
+    if (pde == DH_PDE_EULER2D || pde == DH_PDE_EULER3D) P.gamma = params[0];
+    if (pde == DH_PDE_SRHD3D) P.Gamma = params[0];
+    if (pde == DH_PDE_WAVE3D) P.damp = params[0];
+    if (pde == DH_PDE_GW59) {
+      P.kappa = params[0];
+      for (int i = 0; i < 121 && 1 + i < n_params; ++i) P.C[i] = params[1 + i];
+    }
+  }
+  // Tile work list: 16x16 columns for p % 16 == 0, groups of four 8x8 columns
+  // (same p) otherwise; largest work first.
+  std::vector<Work> work;
+  std::vector<std::vector<std::pair<int, std::pair<int, int>>>> pending(257);
+  for (int k = 0; k < K; ++k) {
+    const int p = patches[k].p, pz = dim == 3 ? p : 1;
+    if (p % 16 == 0) {
+      for (int yy = 0; yy < p; yy += 16)
+        for (int xx = 0; xx < p; xx += 16) {
+          Work w{};
+          w.cls = 0; w.pz = pz;
+          for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
+          w.patch[0] = k; w.x0[0] = (int16_t)xx; w.y0[0] = (int16_t)yy;
+          work.push_back(w);
+        }
+    } else {
+      for (int yy = 0; yy < p; yy += 8)
+        for (int xx = 0; xx < p; xx += 8) pending[p].push_back({k, {xx, yy}});
+    }
+  }
+  for (int p = 8; p <= 256; p += 8) {
+    auto& v = pending[p];
+    for (size_t i = 0; i < v.size(); i += 4) {
+      Work w{};
+      w.cls = 1; w.pz = dim == 3 ? p : 1;
+      for (int j = 0; j < 4; ++j) {
+        if (i + j < v.size()) { w.patch[j] = v[i + j].first; w.x0[j] = (int16_t)v[i + j].second.first; w.y0[j] = (int16_t)v[i + j].second.second; }
+        else { w.patch[j] = -1; w.x0[j] = 0; w.y0[j] = 0; }
+      }
+      work.push_back(w);
+    }
+  }
+  auto cost = [](const Work& w) {
+    int ng = 0;
+    for (int j = 0; j < 4; ++j) ng += w.patch[j] >= 0;
+    return (long long)(w.cls == 0 ? 256 : 64 * ng) * w.pz;
+  };
+  std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
+  for (const Work& w : work) plan->has_cls[w.cls] = true;
+  plan->h_work = work;
+  plan->n_work = (int)work.size();
+
+  cudaError_t e = cudaGetDevice(&plan->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_patches, sizeof(dh_patch) * K);
+  if (e == cudaSuccess) e = cudaMemcpy(plan->d_patches, patches, sizeof(dh_patch) * K, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_work, sizeof(Work) * std::max<size_t>(1, work.size()));
+  if (e == cudaSuccess && !work.empty())
+    e = cudaMemcpy(plan->d_work, work.data(), sizeof(Work) * work.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    dh_status st = cuda_error(e, "dh_plan_create");
+    dh_plan_destroy(plan);
+    return e == cudaErrorMemoryAllocation ? DH_ENOMEM : st;
+  }
+  *out = plan;
+  return DH_OK;
+}
+
+dh_status dh_plan_destroy(dh_plan* plan) {
+  if (!plan) return DH_OK;
+  if (plan->d_patches) cudaFree(plan->d_patches);
+  if (plan->d_work) cudaFree(plan->d_work);
+  if (plan->d_red) cudaFree(plan->d_red);
+  if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
+  for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
+  for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);
+  delete plan;
+  return DH_OK;
+}
+
+dh_status patch_update_fv(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                          const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                          double* lam_out_dev, void* stream) {
+  dh_status st = check_plan(plan);
+  if (st != DH_OK) return st;
+  if (!qs || !dt_dev) { set_error("patch_update_fv: qs and dt_dev are required"); return DH_EINVAL; }
+  if (!out && !acc) { set_error("patch_update_fv: nothing to write (out and acc are NULL)"); return DH_EINVAL; }
+  if (plan->nm > 0 && !mat) { set_error("patch_update_fv: PDE needs the material arena"); return DH_EINVAL; }
+  if (!q0 && a != 0.0) { set_error("patch_update_fv: q0 is NULL but a != 0"); return DH_EINVAL; }
+  if (out == qs || acc == qs || (out && out == acc)) { set_error("patch_update_fv: out/acc must not alias qs or each other"); return DH_EINVAL; }
+  if (plan->pde == DH_PDE_SRHD3D && lam_out_dev) { set_error("patch_update_fv: lam_out is not available for SRHD3D"); return DH_EUNSUPPORTED; }
+  if (plan->pde == DH_PDE_WAVE3D || plan->pde == DH_PDE_GW59) {
+    set_error("patch_update_fv: PDE %d is evolved with patch_update_fd_ko", plan->pde);
+    return DH_EUNSUPPORTED;
+  }
+  return launch_fv_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev, (cudaStream_t)stream);
+}
+
+dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                             const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                             double sigma_ko, double* lam_out_dev, void* stream) {
+  dh_status st = check_plan(plan);
+  if (st != DH_OK) return st;
+  (void)qs; (void)q0; (void)out; (void)acc; (void)mat; (void)dt_dev; (void)a; (void)b; (void)g; (void)d;
+  (void)sigma_ko; (void)lam_out_dev; (void)stream;
+  set_error("patch_update_fd_ko: not built yet");
+  return DH_EUNSUPPORTED;
+}
+
+dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream) {
+  dh_status st = check_plan(plan);
+  if (st != DH_OK) return st;
+  if (!q || !lam_out_dev) { set_error("max_wave_speed: q and lam_out_dev are required"); return DH_EINVAL; }
+  if (plan->nm > 0 && !mat) { set_error("max_wave_speed: PDE needs the material arena"); return DH_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  const dh_patch* P = plan->d_patches;
+  switch (plan->pde) {
+    case DH_PDE_ADV_FLUX: k_max_speed<PdeAdvFlux><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_ADV_NCP: k_max_speed<PdeAdvNcp><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_EULER2D: k_max_speed<PdeEuler2><<<plan->K, 256, 0, s>>>(P, 2, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_EULER3D: k_max_speed<PdeEuler3><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    default:
+      set_error("max_wave_speed: PDE %d not supported yet", plan->pde);
+      return DH_EUNSUPPORTED;
+  }
+  return cuda_error(cudaGetLastError(), "max_wave_speed launch");
+}
+
+dh_status dh_cfl_dt(dh_plan* plan, const double* lam_dev, double cfl, double* dt_dev, void* stream) {
+  dh_status st = check_plan(plan);
+  if (st != DH_OK) return st;
+  if (!lam_dev || !dt_dev || !(cfl > 0.0)) { set_error("dh_cfl_dt: bad arguments"); return DH_EINVAL; }
+  k_cfl_dt<<<1, 1, 0, (cudaStream_t)stream>>>(lam_dev, cfl, plan->dx_min / plan->dim, dt_dev);
+  return cuda_error(cudaGetLastError(), "dh_cfl_dt launch");
+}
+
+dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* stream) {
+  dh_status st = check_plan(plan);
+  if (st != DH_OK) return st;
+  if (!prim || !cons || prim == cons) { set_error("dh_prim2con: bad buffers"); return DH_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (plan->pde == DH_PDE_EULER2D) k_prim2con_euler<2><<<plan->K, 256, 0, s>>>(plan->d_patches, plan->var_stride, prim, cons, plan->params.gamma);
+  else if (plan->pde == DH_PDE_EULER3D) k_prim2con_euler<3><<<plan->K, 256, 0, s>>>(plan->d_patches, plan->var_stride, prim, cons, plan->params.gamma);
+  else if (plan->pde == DH_PDE_SRHD3D) k_prim2con_srhd<<<plan->K, 256, 0, s>>>(plan->d_patches, plan->var_stride, prim, cons, plan->params.Gamma);
+  else { set_error("dh_prim2con: PDE %d has no primitive form", plan->pde); return DH_EUNSUPPORTED; }
+  return cuda_error(cudaGetLastError(), "dh_prim2con launch");
+}
+
+dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void* stream) {
+  if (!out_dev || n_threads <= 0 || n_threads % 256 != 0 || n_threads / 256 > (1ll << 30) || iters <= 0) {
+    set_error("dh_probe_dfma: out_dev must be non-NULL, n_threads a positive multiple of 256, iters > 0");
+    return DH_EINVAL;
+  }
+  k_probe_dfma<<<(unsigned)(n_threads / 256), 256, 0, (cudaStream_t)stream>>>(out_dev, iters, 0.999999, 1e-7);
+  return cuda_error(cudaGetLastError(), "dh_probe_dfma launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,424 @@
+// Finite-volume Runge-Kutta stage over all patches in one launch.
+//
+// Scheme (paper Sec. II-A Eq. 3; Rusanov flux and midpoint path-conservative
+// product as the readings of the unspecified face flux):
+//   L(Q)_i = -(1/dx) sum_d [F^_{i+1/2} - F^_{i-1/2} + (D_{i+1/2} + D_{i-1/2})/2] + S(Q_i)
+//   out = a q0 + b qs + g dt L ; acc += d dt L
+//
+// Kernel design (GB300: the FP64 pipe, ~2 FMA/clk/SM, is the bottleneck, so
+// every FP64 operation is done once and only by full warps):
+//   * A CTA owns a (TX x TY) column of one patch (or four 8x8 columns of four
+//     8^3 patches) and marches it through all z-planes of the patch.
+//   * Per voxel, the derived quantities W (one reciprocal, one square root for
+//     Euler), the three directional fluxes F_d and speeds lambda_d are computed
+//     exactly once.  x/y neighbours exchange them through shared memory; the
+//     z neighbour is the same thread one plane later (registers).
+//   * The ring of halo voxels around the column (neighbour patches or the
+//     rest of the same patch) is computed by the first 2(TX+TY)G threads;
+//     ring voxels only need the one direction that crosses into the column.
+//   * Every face flux is computed once: each voxel thread computes its -x and
+//     -y faces, the +x/+y boundary faces are computed by ring threads; the
+//     factor 1/2 of the Rusanov average is folded into the final -1/(2dx).
+//   * The maximum characteristic speed of the result is reduced with warp
+//     shuffles, then one atomicMax per CTA on the bit pattern (valid for
+//     non-negative doubles), and the last CTA publishes it (no spin waits).
+#include <algorithm>
+
+#include "dh_internal.cuh"
+#include "dh_pde.cuh"
+
+namespace dh {
+
+struct FvArgs {
+  const dh_patch* patches;
+  const Work* work;
+  const double* qs;
+  const double* q0;
+  double* out;
+  double* acc;
+  const double* mat;
+  const double* dt_dev;
+  double a, b, g, d;
+  double* lam_out;
+  unsigned long long* red;
+  int64_t vs;  // var stride
+  DevParams P;
+};
+
+// Arena index of voxel (x, y, z) of patch k; at most one coordinate may lie
+// outside [0, p): it is then taken from the face neighbour (periodic wrap is
+// encoded in the neighbour table).
+__device__ __forceinline__ int64_t vox_index(const dh_patch* __restrict__ P, int k, int p, int x, int y, int z) {
+  if (x < 0) { k = P[k].nbr[0]; x += p; }
+  else if (x >= p) { k = P[k].nbr[1]; x -= p; }
+  else if (y < 0) { k = P[k].nbr[2]; y += p; }
+  else if (y >= p) { k = P[k].nbr[3]; y -= p; }
+  else if (z < 0) { k = P[k].nbr[4]; z += p; }
+  else if (z >= p) { k = P[k].nbr[5]; z -= p; }
+  return P[k].offset + ((int64_t)z * p + y) * p + x;
+}
+
+template <class PDE>
+__device__ __forceinline__ void load_q(const FvArgs& A, int64_t e, double* q) {
+#pragma unroll
+  for (int v = 0; v < PDE::N; ++v) q[v] = __ldg(A.qs + v * A.vs + e);
+#pragma unroll
+  for (int v = 0; v < PDE::M; ++v) q[PDE::N + v] = __ldg(A.mat + v * A.vs + e);
+}
+
+template <class PDE, int TX, int TY, int G>
+struct FvTile {
+  static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW, DIM = PDE::DIM;
+  static constexpr int NT = TX * TY * G;
+  static constexpr int RG = TX + TY;           // ring voxels per group and half
+  static constexpr int HALF = G * RG;          // face-computing ring voxels (+x, +y)
+  static constexpr int NR = 2 * HALF;
+  static constexpr int NS = NT + NR;
+  static constexpr int FXG = (TX + 1) * TY, FYG = TX * (TY + 1);
+  static constexpr int FX = G * FXG, FY = G * FYG;
+  static constexpr int NF = PDE::NCP ? 2 : 1;
+  static constexpr size_t SMEM = sizeof(double) * ((size_t)NV * NS + 2 * (size_t)N * NS + 2 * NS +
+                                                   (size_t)NF * N * (FX + FY));
+  static_assert(NT == 256, "tile classes use 256 threads");
+
+  struct Smem {
+    double *Q, *Fx, *Fy, *Lx, *Ly, *Hx, *Hy, *Dx, *Dy;
+  };
+  __device__ static Smem carve(double* s) {
+    Smem S;
+    S.Q = s; s += NV * NS;
+    S.Fx = s; s += N * NS;
+    S.Fy = s; s += N * NS;
+    S.Lx = s; s += NS;
+    S.Ly = s; s += NS;
+    S.Hx = s; s += N * FX;
+    S.Hy = s; s += N * FY;
+    S.Dx = s; if (PDE::NCP) s += N * FX;
+    S.Dy = s;
+    return S;
+  }
+
+  // Face value F^' = (FL + FR) - s (QR - QL)  (twice the Rusanov flux) and,
+  // for non-conservative systems, D = B_d((QL+QR)/2)(QR - QL).
+  __device__ static void face(const Smem& S, const DevParams& P, int d, int Ls, int Rs, double* H, double* D,
+                              int fidx, int fstride) {
+    const double* F = d == 0 ? S.Fx : S.Fy;
+    const double* L = d == 0 ? S.Lx : S.Ly;
+    const double s = fmax(L[Ls], L[Rs]);
+    double dq[N];
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      const double qL = S.Q[v * NS + Ls], qR = S.Q[v * NS + Rs];
+      dq[v] = qR - qL;
+      double h = -s * dq[v];
+      if (PDE::FLUX) h = fma(-s, dq[v], F[v * NS + Ls] + F[v * NS + Rs]);
+      H[v * fstride + fidx] = h;
+    }
+    if (PDE::NCP) {
+      double qb[NV], Dv[N];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) qb[v] = 0.5 * (S.Q[v * NS + Ls] + S.Q[v * NS + Rs]);
+      PDE::ncp(d, qb, dq, P, Dv);
+#pragma unroll
+      for (int v = 0; v < N; ++v) D[v * fstride + fidx] = Dv[v];
+    }
+  }
+
+  // Ring voxel r of plane z: load, derive, flux and speed in its one direction.
+  __device__ static void ring_voxel(const FvArgs& A, const Smem& S, const Work& w, int r, int p, int z) {
+    const int h = r < HALF ? 0 : 1;
+    const int rr = r - h * HALF;
+    const int g = rr / RG, j = rr % RG;
+    const int k = w.patch[g];
+    if (k < 0) return;
+    const int x0 = w.x0[g], y0 = w.y0[g];
+    int x, y, d;
+    if (j < TY) { d = 0; y = y0 + j; x = h == 0 ? x0 + TX : x0 - 1; }
+    else { d = 1; x = x0 + (j - TY); y = h == 0 ? y0 + TY : y0 - 1; }
+    const int64_t e = vox_index(A.patches, k, p, x, y, z);
+    double q[NV], W[NW > 0 ? NW : 1], F[N];
+    load_q<PDE>(A, e, q);
+    PDE::prims(q, A.P, W);
+    const int s = NT + r;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) S.Q[v * NS + s] = q[v];
+    double* Fd = d == 0 ? S.Fx : S.Fy;
+    double* Ld = d == 0 ? S.Lx : S.Ly;
+    if (PDE::FLUX) {
+      PDE::flux(d, q, W, A.P, F);
+#pragma unroll
+      for (int v = 0; v < N; ++v) Fd[v * NS + s] = F[v];
+    }
+    Ld[s] = PDE::speed(d, q, W, A.P);
+  }
+
+  __device__ static void run(const FvArgs& A, const Work& w, double* smem, double& lam_thread) {
+    const Smem S = carve(smem);
+    const int tid = threadIdx.x;
+    const int g = tid / (TX * TY), lxy = tid % (TX * TY), lx = lxy % TX, ly = lxy / TX;
+    const int k = w.patch[g];
+    const bool act = k >= 0;
+    const int pz = w.pz;
+    // the patch size of every group in this CTA is the same (pz in 3D; 2D: from the table)
+    const int kk = act ? k : w.patch[0];
+    const int p = A.patches[kk].p;
+    const double dxk = A.patches[kk].dx;
+    const int x = (act ? w.x0[g] : 0) + lx, y = (act ? w.y0[g] : 0) + ly;
+    const int64_t off = act ? A.patches[k].offset : 0;
+    const double dt = *A.dt_dev;
+    const double gdt = A.g * dt, ddt = A.d * dt;
+    const double cL = -0.5 / dxk;  // -1/(2 dx): faces hold twice the flux
+    const bool ring = tid < NR;
+
+    // smem slots of this voxel and of its -x / -y neighbours
+    const int me = tid;
+    const int xm = lx > 0 ? me - 1 : NT + HALF + g * RG + ly;
+    const int ym = ly > 0 ? me - TX : NT + HALF + g * RG + TY + lx;
+    // face indices
+    const int fxl = g * FXG + ly * (TX + 1) + lx, fxr = fxl + 1;
+    const int fyl = g * FYG + ly * TX + lx, fyu = fyl + TX;
+
+    double Qk[NV];                 // this voxel, current plane
+    double Fzk[N > 0 ? N : 1];     // its z flux (3D)
+    double Lzk = 0.0;              // its z speed
+    double Hzlo[N], Dzlo[N];       // face below the current plane
+#pragma unroll
+    for (int v = 0; v < N; ++v) { Hzlo[v] = 0.0; Dzlo[v] = 0.0; Fzk[v] = 0.0; }
+
+    // ---- prologue: plane 0 (and plane -1 for the first z face)
+    if (act) {
+      double Wk[NW > 0 ? NW : 1], F[N];
+      load_q<PDE>(A, off + ((int64_t)0 * p + y) * p + x, Qk);
+      PDE::prims(Qk, A.P, Wk);
+      if (PDE::FLUX) {
+        PDE::flux(0, Qk, Wk, A.P, F);
+#pragma unroll
+        for (int v = 0; v < N; ++v) S.Fx[v * NS + me] = F[v];
+        PDE::flux(1, Qk, Wk, A.P, F);
+#pragma unroll
+        for (int v = 0; v < N; ++v) S.Fy[v * NS + me] = F[v];
+      }
+      S.Lx[me] = PDE::speed(0, Qk, Wk, A.P);
+      S.Ly[me] = PDE::speed(1, Qk, Wk, A.P);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) S.Q[v * NS + me] = Qk[v];
+      if (DIM == 3) {
+        if (PDE::FLUX) PDE::flux(2, Qk, Wk, A.P, Fzk);
+        Lzk = PDE::speed(2, Qk, Wk, A.P);
+        // plane -1 from the -z neighbour
+        double Qm[NV], Wm[NW > 0 ? NW : 1], Fzm[N];
+        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, -1), Qm);
+        PDE::prims(Qm, A.P, Wm);
+        if (PDE::FLUX) PDE::flux(2, Qm, Wm, A.P, Fzm);
+        const double s = fmax(PDE::speed(2, Qm, Wm, A.P), Lzk);
+        double dq[N];
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          dq[v] = Qk[v] - Qm[v];
+          Hzlo[v] = PDE::FLUX ? fma(-s, dq[v], Fzm[v] + Fzk[v]) : -s * dq[v];
+        }
+        if (PDE::NCP) {
+          double qb[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) qb[v] = 0.5 * (Qm[v] + Qk[v]);
+          PDE::ncp(2, qb, dq, A.P, Dzlo);
+        }
+      }
+    }
+    if (ring) ring_voxel(A, S, w, tid, p, 0);
+    __syncthreads();
+
+    for (int kz = 0; kz < pz; ++kz) {
+      // ---- faces of plane kz inside the plane
+      if (act) {
+        face(S, A.P, 0, xm, me, S.Hx, S.Dx, fxl, FX);
+        face(S, A.P, 1, ym, me, S.Hy, S.Dy, fyl, FY);
+      }
+      if (tid < HALF) {
+        // +x and +y boundary faces of the column: one call with a run-time
+        // direction so that a warp holding both kinds does not diverge
+        const int gg = tid / RG, j = tid % RG;
+        if (w.patch[gg] >= 0) {
+          const bool isx = j < TY;
+          const int Ls = isx ? gg * TX * TY + j * TX + (TX - 1) : gg * TX * TY + (TY - 1) * TX + (j - TY);
+          const int fidx = isx ? gg * FXG + j * (TX + 1) + TX : gg * FYG + TY * TX + (j - TY);
+          face(S, A.P, isx ? 0 : 1, Ls, NT + tid, isx ? S.Hx : S.Hy, isx ? S.Dx : S.Dy, fidx, isx ? FX : FY);
+        }
+      }
+      // ---- next plane's own voxel (3D): derived quantities, z flux, z face
+      double Qn[NV], Wn[NW > 0 ? NW : 1], Fzn[N], Lzn = 0.0, Hzhi[N], Dzhi[N];
+#pragma unroll
+      for (int v = 0; v < N; ++v) { Hzhi[v] = 0.0; Dzhi[v] = 0.0; Fzn[v] = 0.0; }
+      if (DIM == 3 && act) {
+        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, kz + 1), Qn);
+        PDE::prims(Qn, A.P, Wn);
+        if (PDE::FLUX) PDE::flux(2, Qn, Wn, A.P, Fzn);
+        Lzn = PDE::speed(2, Qn, Wn, A.P);
+        const double s = fmax(Lzk, Lzn);
+        double dq[N];
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          dq[v] = Qn[v] - Qk[v];
+          Hzhi[v] = PDE::FLUX ? fma(-s, dq[v], Fzk[v] + Fzn[v]) : -s * dq[v];
+        }
+        if (PDE::NCP) {
+          double qb[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) qb[v] = 0.5 * (Qk[v] + Qn[v]);
+          PDE::ncp(2, qb, dq, A.P, Dzhi);
+        }
+      }
+      __syncthreads();
+      // ---- update of plane kz
+      if (act) {
+        double Sv[N];
+        if (PDE::SRC) {
+          double Wk[NW > 0 ? NW : 1];
+          PDE::prims(Qk, A.P, Wk);
+          PDE::source(Qk, Wk, A.P, Sv);
+        }
+        const int64_t e = off + ((int64_t)kz * p + y) * p + x;
+        double res[NV];
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          double sum = (S.Hx[v * FX + fxr] - S.Hx[v * FX + fxl]) + (S.Hy[v * FY + fyu] - S.Hy[v * FY + fyl]);
+          if (DIM == 3) sum += Hzhi[v] - Hzlo[v];
+          if (PDE::NCP) {
+            double dsum = (S.Dx[v * FX + fxr] + S.Dx[v * FX + fxl]) + (S.Dy[v * FY + fyu] + S.Dy[v * FY + fyl]);
+            if (DIM == 3) dsum += Dzhi[v] + Dzlo[v];
+            sum += dsum;
+          }
+          double L = cL * sum;
+          if (PDE::SRC) L += Sv[v];
+          const int64_t ev = v * A.vs + e;
+          if (A.out) {
+            double base = A.b * Qk[v];
+            if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
+            res[v] = fma(gdt, L, base);
+          }
+          if (A.acc) {
+            const double r = fma(ddt, L, A.acc[ev]);
+            A.acc[ev] = r;
+            if (!A.out) res[v] = r;
+          }
+          if (A.out) A.out[ev] = res[v];
+        }
+        if (A.lam_out) {
+#pragma unroll
+          for (int v = N; v < NV; ++v) res[v] = Qk[v];
+          double Wr[NW > 0 ? NW : 1];
+          PDE::prims(res, A.P, Wr);
+          double l = fmax(PDE::speed(0, res, Wr, A.P), PDE::speed(1, res, Wr, A.P));
+          if (DIM == 3) l = fmax(l, PDE::speed(2, res, Wr, A.P));
+          lam_thread = fmax(lam_thread, l);
+        }
+      }
+      // ---- publish plane kz+1 (3D)
+      if (DIM == 3 && kz + 1 < pz) {
+        if (act) {
+          double F[N];
+          if (PDE::FLUX) {
+            PDE::flux(0, Qn, Wn, A.P, F);
+#pragma unroll
+            for (int v = 0; v < N; ++v) S.Fx[v * NS + me] = F[v];
+            PDE::flux(1, Qn, Wn, A.P, F);
+#pragma unroll
+            for (int v = 0; v < N; ++v) S.Fy[v * NS + me] = F[v];
+          }
+          S.Lx[me] = PDE::speed(0, Qn, Wn, A.P);
+          S.Ly[me] = PDE::speed(1, Qn, Wn, A.P);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) { S.Q[v * NS + me] = Qn[v]; Qk[v] = Qn[v]; }
+#pragma unroll
+          for (int v = 0; v < N; ++v) { Fzk[v] = Fzn[v]; Hzlo[v] = Hzhi[v]; Dzlo[v] = Dzhi[v]; }
+          Lzk = Lzn;
+        }
+        if (ring) ring_voxel(A, S, w, tid, p, kz + 1);
+        __syncthreads();
+      }
+    }
+  }
+};
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide max, then one atomicMax per CTA and last-CTA publication.
+__device__ void publish_lambda(double lam, double* lam_out, unsigned long long* red) {
+  __shared__ double wmax[32];
+  __shared__ bool last;
+  lam = warp_max(lam);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wmax[wid] = lam;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, wmax[i]);
+    atomicMax(red, (unsigned long long)__double_as_longlong(m));
+    __threadfence();
+    const unsigned long long t = atomicAdd(red + 1, 1ull);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long bits = atomicAdd(red, 0ull);
+    *lam_out = __longlong_as_double((long long)bits);
+    red[0] = 0ull;
+    red[1] = 0ull;
+    __threadfence();
+  }
+}
+
+template <class PDE>
+__global__ void __launch_bounds__(256) k_fv_stage(const __grid_constant__ FvArgs A) {
+  extern __shared__ __align__(16) double smem[];
+  const Work w = A.work[blockIdx.x];
+  double lam = 0.0;
+  if (w.cls == 0) FvTile<PDE, 16, 16, 1>::run(A, w, smem, lam);
+  else FvTile<PDE, 8, 8, 4>::run(A, w, smem, lam);
+  if (A.lam_out) publish_lambda(lam, A.lam_out, A.red);
+}
+
+template <class PDE>
+static dh_status launch(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
+  const size_t smem = std::max(plan->has_cls[0] ? FvTile<PDE, 16, 16, 1>::SMEM : 0,
+                               plan->has_cls[1] ? FvTile<PDE, 8, 8, 4>::SMEM : 0);
+  static int configured_device = -1;  // attribute is per device function; set once per process and device
+  if (configured_device != plan->device) {
+    const size_t mx = std::max(FvTile<PDE, 16, 16, 1>::SMEM, FvTile<PDE, 8, 8, 4>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_fv_stage<PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv_stage)");
+    configured_device = plan->device;
+  }
+  k_fv_stage<PDE><<<plan->n_work, 256, smem, stream>>>(A);
+  return cuda_error(cudaGetLastError(), "k_fv_stage launch");
+}
+
+dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                          const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                          double* lam_out, cudaStream_t stream) {
+  FvArgs A;
+  A.patches = plan->d_patches;
+  A.work = plan->d_work;
+  A.qs = qs; A.q0 = q0; A.out = out; A.acc = acc; A.mat = mat; A.dt_dev = dt_dev;
+  A.a = a; A.b = b; A.g = g; A.d = d;
+  A.lam_out = lam_out;
+  A.red = plan->d_red;
+  A.vs = plan->var_stride;
+  A.P = plan->params;
+  switch (plan->pde) {
+    case DH_PDE_ADV_FLUX: return launch<PdeAdvFlux>(plan, A, stream);
+    case DH_PDE_ADV_NCP: return launch<PdeAdvNcp>(plan, A, stream);
+    case DH_PDE_EULER2D: return launch<PdeEuler2>(plan, A, stream);
+    case DH_PDE_EULER3D: return launch<PdeEuler3>(plan, A, stream);
+    default:
+      set_error("patch_update_fv: PDE %d not supported by the FV stage", plan->pde);
+      return DH_EUNSUPPORTED;
+  }
+}
+
+}  // namespace dh

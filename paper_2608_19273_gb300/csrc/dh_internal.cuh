@@ -1,0 +1,72 @@
+// Internal declarations shared by the CUDA translation units of libdh.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dh.h"
+
+namespace dh {
+
+// PDE parameters passed by value to every kernel.
+struct DevParams {
+  double gamma;   // Euler ratio of specific heats
+  double Gamma;   // SRHD adiabatic index
+  double damp;    // wave-system damping
+  double kappa;   // GW59 lapse coupling
+  double C[121];  // GW59 coupling matrix, row-major
+};
+
+// One CTA's worth of FV/FD work: up to 4 groups, each a (TX x TY) column of
+// one patch that the CTA marches through all z-planes of that patch.
+struct Work {
+  int32_t cls;    // tile class: 0 = 16x16 columns, 1 face group; 1 = 8x8 columns, 4 groups
+  int32_t pz;     // planes to march (p in 3D, 1 in 2D)
+  int32_t patch[4];
+  int16_t x0[4];
+  int16_t y0[4];
+};
+
+struct PlanLaunch;  // forward
+
+}  // namespace dh
+
+struct dh_plan {
+  int pde = 0, dim = 3, K = 0, halo = 1;
+  int64_t var_stride = 0;
+  int nq = 0, nm = 0;
+  int device = 0;
+  double dx_min = 0;
+  dh::DevParams params{};
+  std::vector<dh_patch> h_patches;
+  dh_patch* d_patches = nullptr;
+  // FV / FD tile work list (cost-descending)
+  std::vector<dh::Work> h_work;
+  dh::Work* d_work = nullptr;
+  int n_work = 0;
+  bool has_cls[2] = {false, false};
+  // reduction scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter
+  unsigned long long* d_red = nullptr;
+  int num_sms = 0;
+  // captured multi-step graph and optional per-stage timing events
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<cudaEvent_t> ev_start, ev_stop;
+  int graph_stages = 0, graph_kernels = 0;
+};
+
+namespace dh {
+
+void set_error(const char* fmt, ...);
+dh_status cuda_error(cudaError_t e, const char* what);
+int pde_nq(int pde);
+int pde_nm(int pde);
+int pde_dim(int pde);
+
+dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                          const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                          double* lam_out, cudaStream_t stream);
+
+}  // namespace dh

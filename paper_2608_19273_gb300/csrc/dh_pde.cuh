@@ -1,0 +1,90 @@
+// PDE terms of Eq. 1 (dQ/dt + div F(Q) + B(Q).grad Q = S(Q)) as device functors.
+//
+// Each system provides, per voxel, the derived quantities W (computed once per
+// voxel and shared by all directions), the flux F_d, the largest
+// characteristic speed lambda_d, the non-conservative product B_d(Qb).dQ and
+// the source S.  The direction d may be a run-time value: it is only used in
+// selects, never to index a register array, so the same code serves interior
+// voxels (d unrolled) and halo voxels of either direction without divergence.
+#pragma once
+
+#include "dh_internal.cuh"
+
+namespace dh {
+
+__device__ __forceinline__ double sel3(int d, double a, double b, double c) {
+  return d == 0 ? a : (d == 1 ? b : c);
+}
+
+// ---------------------------------------------------------------- advection
+// dq/dt + div(a q) = 0 with material velocity a (M = 3).  F_d = a_d q, lambda_d = |a_d|.
+struct PdeAdvFlux {
+  static constexpr int N = 1, M = 3, NW = 1, DIM = 3;
+  static constexpr bool FLUX = true, NCP = false, SRC = false;
+  __device__ static void prims(const double*, const DevParams&, double*) {}
+  __device__ static void flux(int d, const double* q, const double*, const DevParams&, double* F) {
+    F[0] = sel3(d, q[1], q[2], q[3]) * q[0];
+  }
+  __device__ static double speed(int d, const double* q, const double*, const DevParams&) {
+    return fabs(sel3(d, q[1], q[2], q[3]));
+  }
+  __device__ static void ncp(int, const double*, const double*, const DevParams&, double*) {}
+  __device__ static void source(const double*, const double*, const DevParams&, double*) {}
+};
+
+// dq/dt + a . grad q = 0 (non-conservative form, F = 0): B_d = a_d.
+struct PdeAdvNcp {
+  static constexpr int N = 1, M = 3, NW = 1, DIM = 3;
+  static constexpr bool FLUX = false, NCP = true, SRC = false;
+  __device__ static void prims(const double*, const DevParams&, double*) {}
+  __device__ static void flux(int, const double*, const double*, const DevParams&, double*) {}
+  __device__ static double speed(int d, const double* q, const double*, const DevParams&) {
+    return fabs(sel3(d, q[1], q[2], q[3]));
+  }
+  // qb holds N + M midpoint values (evolved then material).
+  __device__ static void ncp(int d, const double* qb, const double* dq, const DevParams&, double* D) {
+    D[0] = sel3(d, qb[1], qb[2], qb[3]) * dq[0];
+  }
+  __device__ static void source(const double*, const double*, const DevParams&, double*) {}
+};
+
+// ---------------------------------------------------------------- Euler
+// Ideal-gas Euler equations in DIM dimensions: Q = (rho, rho u_k, E).
+// W = (u_0 .. u_{DIM-1}, p, c, H = E + p): one reciprocal and one square root per voxel.
+template <int D_>
+struct PdeEuler {
+  static constexpr int DIM = D_, N = D_ + 2, M = 0, NW = D_ + 3;
+  static constexpr bool FLUX = true, NCP = false, SRC = false;
+  __device__ static void prims(const double* q, const DevParams& P, double* w) {
+    const double r = 1.0 / q[0];
+    double kin = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+      w[k] = q[1 + k] * r;
+      kin = fma(q[1 + k], w[k], kin);
+    }
+    const double p = (P.gamma - 1.0) * fma(-0.5, kin, q[DIM + 1]);
+    w[DIM] = p;
+    w[DIM + 1] = sqrt(P.gamma * p * r);
+    w[DIM + 2] = q[DIM + 1] + p;
+  }
+  __device__ static void flux(int d, const double* q, const double* w, const DevParams&, double* F) {
+    const double u = (DIM == 3) ? sel3(d, w[0], w[1], w[DIM == 3 ? 2 : 0]) : (d == 0 ? w[0] : w[1]);
+    const double p = w[DIM];
+    F[0] = (DIM == 3) ? sel3(d, q[1], q[2], q[DIM == 3 ? 3 : 1]) : (d == 0 ? q[1] : q[2]);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) F[1 + k] = fma(q[1 + k], u, d == k ? p : 0.0);
+    F[DIM + 1] = w[DIM + 2] * u;
+  }
+  __device__ static double speed(int d, const double*, const double* w, const DevParams&) {
+    const double u = (DIM == 3) ? sel3(d, w[0], w[1], w[DIM == 3 ? 2 : 0]) : (d == 0 ? w[0] : w[1]);
+    return fabs(u) + w[DIM + 1];
+  }
+  __device__ static void ncp(int, const double*, const double*, const DevParams&, double*) {}
+  __device__ static void source(const double*, const double*, const DevParams&, double*) {}
+};
+
+using PdeEuler2 = PdeEuler<2>;
+using PdeEuler3 = PdeEuler<3>;
+
+}  // namespace dh

@@ -1,0 +1,180 @@
+// Time-stepping runtime: whole Runge-Kutta steps built from stage calls, and
+// their capture into a CUDA graph owned by the plan.
+//
+// A Runge-Kutta scheme calls the cell update several times per time step with
+// tableau-dependent dt, with a face-neighbour synchronisation (halo refresh)
+// between calls (paper Sec. II).  Here every stage is one batched launch over
+// all patches; the halo refresh is implicit because each stage reads its halos
+// from the previous stage's output in global memory.  dt lives in device
+// memory and is recomputed on the device from the maximum wave speed that the
+// last stage of the previous step produced, so a graph of many steps replays
+// without any host round trip.
+#include <cstring>
+
+#include "dh_internal.cuh"
+
+namespace dh {
+
+static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
+                            double* acc, const double* mat, const double* dt, double a, double b, double g,
+                            double d, double sigma, double* lam, cudaStream_t s) {
+  if (scheme == 0) return patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s);
+  return patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s);
+}
+
+struct Timer {
+  dh_plan* plan;
+  bool on;
+  cudaStream_t s;
+  int next = 0;
+  dh_status begin() {
+    if (!on) return DH_OK;
+    if (next >= (int)plan->ev_start.size()) { set_error("graph timing: too many stages"); return DH_EINVAL; }
+    return cuda_error(cudaEventRecordWithFlags(plan->ev_start[next], s, cudaEventRecordExternal), "event record");
+  }
+  dh_status end() {
+    if (!on) return DH_OK;
+    dh_status st = cuda_error(cudaEventRecordWithFlags(plan->ev_stop[next], s, cudaEventRecordExternal), "event record");
+    ++next;
+    return st;
+  }
+};
+
+#define DH_TRY(x) do { dh_status _st = (x); if (_st != DH_OK) return _st; } while (0)
+
+// One time step.  bufs: q (state, in/out), u1, u2 (stage buffers), acc (RK4).
+static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
+                         const double* mat, double* dt, double* lam, double cfl, double sigma, Timer& T,
+                         cudaStream_t s) {
+  const size_t bytes = sizeof(double) * (size_t)plan->nq * (size_t)plan->var_stride;
+  double* lam_last = cfl > 0 ? lam : nullptr;
+  if (cfl > 0) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
+  if (rk == 1) {
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, s));
+    DH_TRY(T.end());
+    DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
+  } else if (rk == 3) {
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, s));
+    DH_TRY(T.end());
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, s));
+    DH_TRY(T.end());
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, u2, q, q, nullptr, mat, dt, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, sigma, lam_last, s));
+    DH_TRY(T.end());
+  } else if (rk == 4) {
+    DH_TRY(cuda_error(cudaMemcpyAsync(acc, q, bytes, cudaMemcpyDeviceToDevice, s), "copy q -> acc"));
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, q, q, u1, acc, mat, dt, 1, 0, 0.5, 1.0 / 6.0, sigma, nullptr, s));
+    DH_TRY(T.end());
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 1, 0, 0.5, 1.0 / 3.0, sigma, nullptr, s));
+    DH_TRY(T.end());
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, u2, q, u1, acc, mat, dt, 1, 0, 1.0, 1.0 / 3.0, sigma, nullptr, s));
+    DH_TRY(T.end());
+    DH_TRY(T.begin());
+    DH_TRY(stage_call(plan, scheme, u1, nullptr, nullptr, acc, mat, dt, 0, 0, 0, 1.0 / 6.0, sigma, lam_last, s));
+    DH_TRY(T.end());
+    DH_TRY(cuda_error(cudaMemcpyAsync(q, acc, bytes, cudaMemcpyDeviceToDevice, s), "copy acc -> q"));
+  } else {
+    set_error("dh_rk_step: rk must be 1, 3 or 4");
+    return DH_EINVAL;
+  }
+  return DH_OK;
+}
+
+static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
+                          double* dt, double* lam, double cfl) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (scheme != 0 && scheme != 1) { set_error("scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
+  if (!q || !u1 || !dt || (rk == 3 && !u2) || (rk == 4 && (!u2 || !acc))) {
+    set_error("dh_rk_step: missing state or stage buffer");
+    return DH_EINVAL;
+  }
+  if (cfl > 0 && !lam) { set_error("dh_rk_step: cfl > 0 needs lam_dev"); return DH_EINVAL; }
+  if (rk != 1 && rk != 3 && rk != 4) { set_error("dh_rk_step: rk must be 1, 3 or 4"); return DH_EINVAL; }
+  return DH_OK;
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+dh_status dh_rk_step(dh_plan* plan, int32_t scheme, int32_t rk, double* q, double* u1, double* u2, double* acc,
+                     const double* mat, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
+                     void* stream) {
+  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, dt_dev, lam_dev, cfl));
+  Timer T{plan, false, (cudaStream_t)stream};
+  return rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, (cudaStream_t)stream);
+}
+
+dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_steps, double* q, double* u1,
+                           double* u2, double* acc, const double* mat, double* dt_dev, double* lam_dev, double cfl,
+                           double sigma_ko, int32_t timing, void* stream) {
+  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, dt_dev, lam_dev, cfl));
+  if (n_steps <= 0 || n_steps > 100000) { set_error("dh_graph_capture: n_steps out of range"); return DH_EINVAL; }
+  if (!stream) { set_error("dh_graph_capture: needs a non-default stream"); return DH_EINVAL; }
+  cudaStream_t s = (cudaStream_t)stream;
+  // release a previous graph and timing events
+  if (plan->graph_exec) { cudaGraphExecDestroy(plan->graph_exec); plan->graph_exec = nullptr; }
+  for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
+  for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);
+  plan->ev_start.clear();
+  plan->ev_stop.clear();
+  const int stages = (rk == 1 ? 1 : rk) * n_steps;
+  if (timing) {
+    for (int i = 0; i < stages; ++i) {
+      cudaEvent_t a, b;
+      DH_TRY(cuda_error(cudaEventCreate(&a), "cudaEventCreate"));
+      DH_TRY(cuda_error(cudaEventCreate(&b), "cudaEventCreate"));
+      plan->ev_start.push_back(a);
+      plan->ev_stop.push_back(b);
+    }
+  }
+  DH_TRY(cuda_error(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"));
+  Timer T{plan, timing != 0, s};
+  dh_status st = DH_OK;
+  for (int i = 0; i < n_steps && st == DH_OK; ++i)
+    st = rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (st != DH_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&plan->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) { plan->graph_exec = nullptr; return cuda_error(e, "cudaGraphInstantiate"); }
+  plan->graph_stages = timing ? stages : 0;
+  plan->graph_kernels = n_steps * ((rk == 1 ? 1 : rk) + (cfl > 0 ? 1 : 0));
+  return DH_OK;
+}
+
+dh_status dh_graph_launch(dh_plan* plan, void* stream) {
+  if (!plan || !plan->graph_exec) { set_error("dh_graph_launch: no captured graph"); return DH_EINVAL; }
+  return cuda_error(cudaGraphLaunch(plan->graph_exec, (cudaStream_t)stream), "cudaGraphLaunch");
+}
+
+dh_status dh_graph_info(dh_plan* plan, int32_t* n_kernels, int32_t* n_timed_stages) {
+  if (!plan || !plan->graph_exec) { set_error("dh_graph_info: no captured graph"); return DH_EINVAL; }
+  if (n_kernels) *n_kernels = plan->graph_kernels;
+  if (n_timed_stages) *n_timed_stages = plan->graph_stages;
+  return DH_OK;
+}
+
+dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n) {
+  if (!plan || !ms_out || n < 0 || n > plan->graph_stages) {
+    set_error("dh_graph_stage_times: bad arguments or graph captured without timing");
+    return DH_EINVAL;
+  }
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = cudaEventElapsedTime(&ms_out[i], plan->ev_start[i], plan->ev_stop[i]);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventElapsedTime");
+  }
+  return DH_OK;
+}
+
+}  // extern "C"

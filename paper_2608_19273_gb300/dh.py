@@ -1,0 +1,201 @@
+"""Thin ctypes binding of libdh (include/dh.h).
+
+Argument marshalling only: every step of the patch update runs in the CUDA
+kernels of libdh.so.  Device buffers are torch tensors (float64, contiguous,
+on the GPU) or raw device pointers (int); streams are torch streams or raw
+cudaStream_t values.  There is no CPU fallback: if libdh.so is missing or the
+tensors are not on a CUDA device, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import synth
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdh.so")
+_lib = None
+
+DH_OK, DH_EINVAL, DH_ECUDA, DH_EUNSUPPORTED, DH_ENOMEM, DH_ETIMEOUT = 0, -1, -2, -3, -4, -5
+PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE_GW59 = range(7)
+
+# Every symbol that include/dh.h declares (checked by the CPU tests).
+EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
+           "dh_cfl_dt", "dh_prim2con", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_last_error", "dh_version"]
+
+
+class DhError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().dh_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libdh.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(paper_2608_19273_gb300/build.py); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, d, i32, i64 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int32, ctypes.c_int64
+        L.dh_plan_create.argtypes = [ctypes.POINTER(vp), i32, i32, vp, i32, i32, i64, vp, i32]
+        L.dh_plan_destroy.argtypes = [vp]
+        L.patch_update_fv.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, d, vp, vp]
+        L.patch_update_fd_ko.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, d, d, vp, vp]
+        L.max_wave_speed.argtypes = [vp, vp, vp, vp, vp]
+        L.dh_cfl_dt.argtypes = [vp, vp, d, vp, vp]
+        L.dh_prim2con.argtypes = [vp, vp, vp, vp]
+        L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
+        L.dh_rk_step.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, vp]
+        L.dh_graph_capture.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, vp]
+        L.dh_graph_launch.argtypes = [vp, vp]
+        L.dh_graph_info.argtypes = [vp, vp, vp]
+        L.dh_graph_stage_times.argtypes = [vp, vp, i32]
+        L.dh_last_error.restype = ctypes.c_char_p
+        L.dh_version.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _ptr(x, what="buffer"):
+    """Device pointer of a CUDA float64/float32/uint8/int32 tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not getattr(x, "is_cuda", False):
+        raise TypeError(f"{what} must be a CUDA tensor (no CPU fallback)")
+    if not x.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st, where):
+    if st != DH_OK:
+        raise DhError(st, where)
+
+
+class Plan:
+    """Owns a dh_plan: device patch table, tile work list, reduction scratch."""
+
+    def __init__(self, pde, dim, patches, halo, var_stride, params=None):
+        patches = np.ascontiguousarray(patches, dtype=synth.PATCH_DTYPE)
+        prm = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = lib().dh_plan_create(ctypes.byref(h), int(pde), int(dim), patches.ctypes.data, len(patches), int(halo),
+                                  int(var_stride), None if prm is None else prm.ctypes.data,
+                                  0 if prm is None else len(prm))
+        _check(st, "dh_plan_create")
+        self.handle = h.value
+        self.pde, self.dim, self.halo, self.var_stride = pde, dim, halo, var_stride
+        self.patches = patches
+        self.nq = synth.PDE_NQ[pde]
+        self.nm = synth.PDE_NM[pde]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dh_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def dh_plan_create(pde, dim, patches, halo, var_stride, params=None):
+    return Plan(pde, dim, patches, halo, var_stride, params)
+
+
+def dh_plan_destroy(plan):
+    plan.close()
+
+
+def patch_update_fv(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev=None, stream=None):
+    st = lib().patch_update_fv(plan.handle, _ptr(qs, "qs"), _ptr(q0, "q0"), _ptr(out, "out"), _ptr(acc, "acc"),
+                               _ptr(mat, "mat"), _ptr(dt_dev, "dt_dev"), float(a), float(b), float(g), float(d),
+                               _ptr(lam_out_dev, "lam_out_dev"), _stream(stream))
+    _check(st, "patch_update_fv")
+
+
+def patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, sigma_ko=0.1, lam_out_dev=None,
+                       stream=None):
+    st = lib().patch_update_fd_ko(plan.handle, _ptr(qs, "qs"), _ptr(q0, "q0"), _ptr(out, "out"),
+                                  _ptr(acc, "acc"), _ptr(mat, "mat"), _ptr(dt_dev, "dt_dev"), float(a), float(b),
+                                  float(g), float(d), float(sigma_ko), _ptr(lam_out_dev, "lam_out_dev"),
+                                  _stream(stream))
+    _check(st, "patch_update_fd_ko")
+
+
+def max_wave_speed(plan, q, mat, lam_out_dev, stream=None):
+    _check(lib().max_wave_speed(plan.handle, _ptr(q, "q"), _ptr(mat, "mat"), _ptr(lam_out_dev, "lam"),
+                                _stream(stream)), "max_wave_speed")
+
+
+def dh_cfl_dt(plan, lam_dev, cfl, dt_dev, stream=None):
+    _check(lib().dh_cfl_dt(plan.handle, _ptr(lam_dev, "lam"), float(cfl), _ptr(dt_dev, "dt"), _stream(stream)),
+           "dh_cfl_dt")
+
+
+def dh_prim2con(plan, prim, cons, stream=None):
+    _check(lib().dh_prim2con(plan.handle, _ptr(prim, "prim"), _ptr(cons, "cons"), _stream(stream)), "dh_prim2con")
+
+
+def dh_rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko=0.1, stream=None):
+    _check(lib().dh_rk_step(plan.handle, int(scheme), int(rk), _ptr(q, "q"), _ptr(u1, "u1"), _ptr(u2, "u2"),
+                            _ptr(acc, "acc"), _ptr(mat, "mat"), _ptr(dt_dev, "dt"), _ptr(lam_dev, "lam"),
+                            float(cfl), float(sigma_ko), _stream(stream)), "dh_rk_step")
+
+
+def dh_graph_capture(plan, scheme, rk, n_steps, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko=0.1,
+                     timing=False, stream=None):
+    _check(lib().dh_graph_capture(plan.handle, int(scheme), int(rk), int(n_steps), _ptr(q, "q"), _ptr(u1, "u1"),
+                                  _ptr(u2, "u2"), _ptr(acc, "acc"), _ptr(mat, "mat"), _ptr(dt_dev, "dt"),
+                                  _ptr(lam_dev, "lam"), float(cfl), float(sigma_ko), int(bool(timing)),
+                                  _stream(stream)), "dh_graph_capture")
+
+
+def dh_graph_launch(plan, stream=None):
+    _check(lib().dh_graph_launch(plan.handle, _stream(stream)), "dh_graph_launch")
+
+
+def dh_graph_info(plan):
+    nk, nt = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().dh_graph_info(plan.handle, ctypes.byref(nk), ctypes.byref(nt)), "dh_graph_info")
+    return nk.value, nt.value
+
+
+def dh_graph_stage_times(plan, n):
+    out = (ctypes.c_float * n)()
+    _check(lib().dh_graph_stage_times(plan.handle, out, int(n)), "dh_graph_stage_times")
+    return np.array(out[:], dtype=np.float64)
+
+
+def dh_probe_dfma(out_dev, n_threads, iters, stream=None):
+    _check(lib().dh_probe_dfma(_ptr(out_dev, "out"), int(n_threads), int(iters), _stream(stream)), "dh_probe_dfma")
+
+
+def version():
+    return lib().dh_version().decode()

@@ -87,17 +87,31 @@ def make_mesh(levels, dim, align=16):
     return Mesh(dim=dim, patches=patches, var_stride=_round_up(off, 32), levels=list(levels), level_ranges=ranges)
 
 
+def _level_block(mesh, li):
+    """(first offset, patches, voxels per patch, contiguous?) of level li."""
+    a, b = mesh.level_ranges[li]
+    sel = mesh.patches[a:b]
+    n = int(sel["p"][0]) ** mesh.dim
+    off = sel["offset"]
+    contiguous = bool(np.all(off == off[0] + n * np.arange(len(sel))))
+    return int(off[0]), sel, n, contiguous
+
+
 def voxel_centres(mesh):
     """Coordinates (3, var_stride) of every voxel centre (padding stays 0)."""
     X = np.zeros((3, mesh.var_stride))
-    for pt in mesh.patches:
-        p = int(pt["p"])
+    for li in range(len(mesh.levels)):
+        first, sel, n, contiguous = _level_block(mesh, li)
+        p = int(sel["p"][0])
         pz = p if mesh.dim == 3 else 1
         z, y, x = np.meshgrid(np.arange(pz), np.arange(p), np.arange(p), indexing="ij")
-        sl = slice(int(pt["offset"]), int(pt["offset"]) + p * p * pz)
-        X[0, sl] = pt["x0"][0] + (x.ravel() + 0.5) * pt["dx"]
-        X[1, sl] = pt["x0"][1] + (y.ravel() + 0.5) * pt["dx"]
-        X[2, sl] = pt["x0"][2] + (z.ravel() + 0.5) * pt["dx"] if mesh.dim == 3 else 0.0
+        loc = [x.ravel(), y.ravel(), z.ravel()]
+        for a in range(mesh.dim):
+            vals = sel["x0"][:, a][:, None] + (loc[a][None, :] + 0.5) * sel["dx"][:, None]
+            if contiguous:
+                X[a, first:first + n * len(sel)] = vals.ravel()
+            else:
+                X[a, (sel["offset"][:, None] + np.arange(n)[None, :]).ravel()] = vals.ravel()
     return X
 
 
@@ -108,13 +122,11 @@ def level_extent(mesh, li):
 
 
 def level_slices(mesh, li):
-    """Arena index array of all voxels of level li."""
-    a, b = mesh.level_ranges[li]
-    idx = []
-    for pt in mesh.patches[a:b]:
-        n = int(pt["p"]) ** mesh.dim
-        idx.append(np.arange(int(pt["offset"]), int(pt["offset"]) + n))
-    return np.concatenate(idx)
+    """Arena indices of all voxels of level li (a slice when the level is contiguous)."""
+    first, sel, n, contiguous = _level_block(mesh, li)
+    if contiguous:
+        return slice(first, first + n * len(sel))
+    return (sel["offset"][:, None] + np.arange(n)[None, :]).ravel()
 
 
 def fourier_field(rng, X, L, dim, mid, amp, modes=4, kmax=4):
@@ -128,10 +140,8 @@ def fourier_field(rng, X, L, dim, mid, amp, modes=4, kmax=4):
             ks.append(k)
     f = np.zeros(X.shape[1])
     for m in range(modes):
-        arg = phi[m]
-        for ax in range(dim):
-            arg = arg + 2 * math.pi * ks[m][ax] * X[ax] / L[ax]
-        f += a[m] * np.sin(arg)
+        w = np.array([2 * math.pi * ks[m][ax] / L[ax] for ax in range(dim)])
+        f += a[m] * np.sin(w @ X[:dim] + phi[m])
     return mid + amp * f / a.sum()
 
 
@@ -142,8 +152,9 @@ def fill_fields(mesh, rng, specs):
     for li in range(len(mesh.levels)):
         idx = level_slices(mesh, li)
         L = level_extent(mesh, li)
+        Xl = X[:, idx]
         for v, (mid, amp) in enumerate(specs):
-            out[v, idx] = fourier_field(rng, X[:, idx], L, mesh.dim, mid, amp)
+            out[v, idx] = fourier_field(rng, Xl, L, mesh.dim, mid, amp)
     return out
 
 

@@ -1,0 +1,77 @@
+"""The C-ABI library loads and exports every symbol that include/dh.h declares,
+and rejects malformed plans on the host (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2608_19273_gb300 import build as dhbuild
+from paper_2608_19273_gb300 import dh, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libdh():
+    dhbuild.build()
+    return dh.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "dh.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:dh_status|const char\*)\s+(\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_symbols_exported(libdh):
+    names = _declared()
+    assert "patch_update_fv" in names and "max_wave_speed" in names
+    for n in names:
+        assert hasattr(libdh, n), f"{n} declared in dh.h but not exported"
+    assert set(names) <= set(dh.EXPORTS) | set(names)
+    assert set(dh.EXPORTS) == set(names), "binding EXPORTS list out of sync with dh.h"
+
+
+def test_version(libdh):
+    assert "sm_103a" in dh.version()
+
+
+def _create(patches, pde=3, dim=3, halo=1, vs=None):
+    vs = vs if vs is not None else 1 << 20
+    h = ctypes.c_void_p()
+    st = dh.lib().dh_plan_create(ctypes.byref(h), pde, dim, patches.ctypes.data, len(patches), halo, vs, None, 0)
+    return st
+
+
+@pytest.mark.parametrize("mutate,code", [
+    (lambda P: P.__setitem__("p", 12), dh.DH_EINVAL),         # not a multiple of 8
+    (lambda P: P["nbr"].__setitem__((0, 1), 99), dh.DH_EINVAL),  # neighbour out of range
+    (lambda P: P.__setitem__("offset", P["offset"] + 3), dh.DH_EINVAL),  # misaligned block
+    (lambda P: P["dx"].__setitem__(0, -1.0), dh.DH_EINVAL),   # negative spacing
+])
+def test_plan_validation_rejects(libdh, mutate, code):
+    mesh = synth.euler3d_amr_mesh(scale=8)
+    P = mesh.patches.copy()
+    mutate(P)
+    assert _create(P, vs=mesh.var_stride) == code
+    assert len(dh.lib().dh_last_error()) > 0
+
+
+def test_plan_validation_dim_and_pde(libdh):
+    mesh = synth.euler3d_amr_mesh(scale=8)
+    assert _create(mesh.patches.copy(), pde=2, dim=3, vs=mesh.var_stride) == dh.DH_EINVAL
+    assert _create(mesh.patches.copy(), pde=9, dim=3, vs=mesh.var_stride) == dh.DH_EINVAL
+    assert _create(mesh.patches.copy(), vs=mesh.var_stride + 1) == dh.DH_EINVAL
+
+
+def test_binding_refuses_cpu_tensors(libdh):
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        dh._ptr(torch.zeros(4, dtype=torch.float64), "q")
+
+
+def test_null_plan_rejected(libdh):
+    L = dh.lib()
+    assert L.patch_update_fv(None, None, None, None, None, None, None, 0.0, 1.0, 1.0, 0.0, None, None) == dh.DH_EINVAL

@@ -1,0 +1,146 @@
+"""GPU parity of the FV stage (patch_update_fv) against the FP64 oracle.
+
+Tolerance: 1e-12 relative per voxel, relative to max(|r|, s_v) with s_v the
+largest magnitude of variable v over the workload (values that cross zero)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_parity, dev, host, require_cuda
+from helpers import arena, from_grid, single_level, to_grid, voxel_mask
+from paper_2608_19273_gb300 import dh, synth
+
+pytestmark = pytest.mark.gpu
+FV = 0
+
+
+def _euler_cons(orc, mesh, seed, pde=synth.PDE_EULER3D):
+    return orc.prim2con(pde, synth.euler_prims(mesh, seed), mesh.var_stride)
+
+
+@pytest.mark.parametrize("scale", [8, 4])
+@pytest.mark.parametrize("coef", [(0.0, 1.0, 1.0), (0.75, 0.25, 0.25), (1 / 3, 2 / 3, 2 / 3)])
+def test_euler3d_single_stage(orc, scale, coef):
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=scale)
+    q0 = _euler_cons(orc, mesh, 21)
+    qs = _euler_cons(orc, mesh, 22)
+    a, b, g = coef
+    dt = 1.7e-3
+    ref = np.zeros_like(qs)
+    lam_ref = orc.stage(FV, 3, 3, mesh.patches, 1, mesh.var_stride, qs, q0=q0 if a else None, out=ref, dt=dt,
+                        a=a, b=b, g=g, want_lam=True)
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        d_qs, d_q0 = dev(torch, qs), dev(torch, q0)
+        d_out = torch.zeros_like(d_qs)
+        d_dt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        d_lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.patch_update_fv(plan, d_qs, d_q0 if a else None, d_out, None, None, d_dt, a, b, g, 0.0, d_lam)
+        torch.cuda.synchronize()
+        out = host(d_out)
+        lam = float(host(d_lam)[0])
+    m = voxel_mask(mesh)
+    assert_parity(out, ref, m, what="euler3d stage")
+    assert abs(lam - lam_ref) <= 1e-14 * lam_ref
+
+
+@pytest.mark.parametrize("pde", [synth.PDE_ADV_FLUX, synth.PDE_ADV_NCP])
+@pytest.mark.parametrize("axis,sign", [(0, 1), (1, -1), (2, 1)])
+@pytest.mark.parametrize("p", [8, 16])
+def test_advection_exact_shift(orc, pde, axis, sign, p):
+    """|a| dt/dx = 1: the GPU stage moves dyadic data by exactly one voxel (bitwise)."""
+    torch = require_cuda()
+    mesh = single_level((2, 2, 2), p, 1.0 / 128)
+    rng = np.random.default_rng(5)
+    G = synth.dyadic_field(rng, (2 * p,) * 3)
+    q = from_grid(mesh, G, arena(mesh, 1)[0])[None].copy()
+    mat = arena(mesh, 3)
+    mat[axis] = sign * 1.0
+    with dh.Plan(pde, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        d_out = torch.zeros(q.shape, dtype=torch.float64, device="cuda")
+        d_dt = torch.tensor([1.0 / 128], dtype=torch.float64, device="cuda")
+        dh.patch_update_fv(plan, dev(torch, q), None, d_out, None, dev(torch, mat), d_dt, 0, 1, 1, 0)
+        out = host(d_out)
+    assert np.array_equal(to_grid(mesh, out[0]), np.roll(G, sign, axis=2 - axis))
+
+
+def test_free_stream_bitwise_gpu(orc):
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=4)
+    q = arena(mesh, 5)
+    for v, c in enumerate([1.3, 0.37, -0.21, 0.11, 2.9]):
+        q[v] = c
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        d_out = torch.zeros(q.shape, dtype=torch.float64, device="cuda")
+        d_dt = torch.tensor([0.37], dtype=torch.float64, device="cuda")
+        dh.patch_update_fv(plan, dev(torch, q), None, d_out, None, None, d_dt, 0, 1, 1, 0)
+        out = host(d_out)
+    m = voxel_mask(mesh)
+    assert np.array_equal(out[:, m], q[:, m])
+
+
+def test_euler2d_workload_10_steps(orc):
+    """The full 2D workload: 64 patches of 16^2, 10 forward-Euler steps with device-side CFL dt."""
+    torch = require_cuda()
+    w = synth.workload("euler2d")
+    mesh = w.mesh
+    q = _euler_cons(orc, mesh, w.seed, synth.PDE_EULER2D)
+    ref = q.copy()
+    dts = orc.rk_steps(FV, 2, 2, mesh.patches, 1, mesh.var_stride, ref, rk=1, steps=10, cfl=0.4)
+    with dh.Plan(2, 2, mesh.patches, 1, mesh.var_stride) as plan:
+        a = dev(torch, q)
+        b = torch.zeros_like(a)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, a, None, lam)
+        got_dt = []
+        for s in range(10):
+            dh.dh_cfl_dt(plan, lam, 0.4, dt)
+            got_dt.append(float(host(dt)[0]))
+            dh.patch_update_fv(plan, a, None, b, None, None, dt, 0, 1, 1, 0, lam)
+            a, b = b, a
+        out = host(a)
+    m = voxel_mask(mesh)
+    assert_parity(out, ref, m, what="euler2d 10 steps")
+    assert np.max(np.abs(np.array(got_dt) - dts) / dts) < 1e-14
+
+
+def test_euler3d_ssprk3_steps(orc):
+    """Three SSP-RK3 steps (9 stages) on the AMR-like mix at reduced patch counts."""
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=4)
+    q = _euler_cons(orc, mesh, 31)
+    ref = q.copy()
+    dts = orc.rk_steps(FV, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=3, cfl=0.4)
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        Q = dev(torch, q)
+        U1, U2 = torch.zeros_like(Q), torch.zeros_like(Q)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, Q, None, lam)
+        for s in range(3):
+            dh.dh_cfl_dt(plan, lam, 0.4, dt)
+            dh.patch_update_fv(plan, Q, None, U1, None, None, dt, 0, 1, 1, 0)
+            dh.patch_update_fv(plan, U1, Q, U2, None, None, dt, 0.75, 0.25, 0.25, 0)
+            dh.patch_update_fv(plan, U2, Q, Q, None, None, dt, 1 / 3, 2 / 3, 2 / 3, 0, lam)
+        out = host(Q)
+        dt_last = float(host(dt)[0])
+    m = voxel_mask(mesh)
+    assert_parity(out, ref, m, what="euler3d 3 SSP-RK3 steps")
+    assert abs(dt_last - dts[-1]) <= 1e-14 * dts[-1]
+
+
+@pytest.mark.parametrize("p", [8, 16, 32])
+def test_single_self_periodic_patch(orc, p):
+    """K = 1: a patch that is its own neighbour in every direction."""
+    torch = require_cuda()
+    mesh = single_level((1, 1, 1), p, 1.0 / 64)
+    q = _euler_cons(orc, mesh, 40 + p)
+    ref = np.zeros_like(q)
+    orc.stage(FV, 3, 3, mesh.patches, 1, mesh.var_stride, q, out=ref, dt=1e-3)
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        d_out = torch.zeros(q.shape, dtype=torch.float64, device="cuda")
+        d_dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
+        dh.patch_update_fv(plan, dev(torch, q), None, d_out, None, None, d_dt, 0, 1, 1, 0)
+        out = host(d_out)
+    assert_parity(out, ref, voxel_mask(mesh), what=f"self-periodic p={p}")
