@@ -624,9 +624,11 @@ void srhd_prim2con(double Gamma, const T* w, T* q) {
 // Newton iteration on the pressure:
 //   f(p)  = ((G-1)/G) [ (E+p) - S^2/(E+p) - D sqrt(1 - S^2/(E+p)^2) ] - p
 //   f'(p) = ((G-1)/G) [ 1 + S^2/(E+p)^2 - D S^2 / ((E+p)^3 sqrt(1 - S^2/(E+p)^2)) ] - 1
-// Stops when |p_new - p| <= tol p_new; fails when p leaves (p_lo, inf), on NaN,
-// or when max_iter iterations did not converge.  Returns iterations used (>0)
-// on success, -iterations on failure.
+// Stops when |p_new - p| <= tol p_new.  A step that would leave the bracket
+// (p_lo, inf) is replaced by the midpoint between the current iterate and
+// p_lo (safeguard: plain Newton from a cold seed overshoots below zero for
+// fast flows).  Fails on NaN or when max_iter iterations did not converge.
+// Returns iterations used (>0) on success, -iterations on failure.
 int srhd_newton(double G, double D, double S2, double E, double p_lo, double p0, double tol,
                 int max_iter, double* p_out) {
   double p = p0;
@@ -638,8 +640,13 @@ int srhd_newton(double G, double D, double S2, double E, double p_lo, double p0,
     double f = gf * (Ep - S2 / Ep - D * rt) - p;
     double fp = gf * (1.0 + s2e - D * S2 / (Ep * Ep * Ep * rt)) - 1.0;
     double pn = p - f / fp;
-    if (!(pn == pn) || pn <= p_lo) { *p_out = pn; return -it; }
-    if (std::fabs(pn - p) <= tol * pn) { *p_out = pn; return it; }
+    if (!(pn == pn)) { *p_out = pn; return -it; }
+    if (pn <= p_lo) {
+      pn = 0.5 * (p + p_lo);  // safeguard step: never counts as convergence
+    } else if (std::fabs(pn - p) <= tol * pn) {
+      *p_out = pn;
+      return it;
+    }
     p = pn;
   }
   *p_out = p;

@@ -1,0 +1,142 @@
+"""Pins of the SRHD oracle: prim2con / con2prim (Newton on p) and the MLP seed maths (CPU only).
+
+Special-relativistic hydro is not in the paper; the system, the Newton
+iteration and the learned seed follow textbook definitions (see DESIGN)."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import arena, single_level, voxel_mask
+from paper_2608_19273_gb300 import synth
+
+G = 5.0 / 3.0
+
+
+def iid_prims(n, seed, wmax=10.0):
+    """rho, p log-uniform on [0.1, 10]; Lorentz factor uniform in [1, wmax]; random direction."""
+    rng = np.random.default_rng(seed)
+    rho = np.exp(rng.uniform(math.log(0.1), math.log(10), n))
+    p = np.exp(rng.uniform(math.log(0.1), math.log(10), n))
+    W = rng.uniform(1.0, wmax, n)
+    v = np.sqrt(1 - 1 / W ** 2)
+    nd = rng.normal(size=(3, n))
+    nd /= np.linalg.norm(nd, axis=0)
+    w = np.zeros((5, n))
+    w[0], w[4] = rho, p
+    w[1:4] = v * nd
+    return w
+
+
+def test_round_trip_iid(orc):
+    w = iid_prims(20000, 1)
+    n = w.shape[1]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    got, status, iters, fails = orc.con2prim(q, n)
+    assert fails == 0 and np.all(status == 0)
+    assert np.max(np.abs(got[4] - w[4]) / w[4]) < 1e-10
+    assert np.max(np.abs(got[0] - w[0]) / w[0]) < 1e-10
+    assert np.max(np.abs(got[1:4] - w[1:4])) < 1e-10
+    assert iters.max() <= 50
+
+
+def test_at_rest_closed_form(orc):
+    """v = 0: p = (Gamma - 1) tau, which the cold seed hits, so Newton stops after one step."""
+    w = np.zeros((5, 4))
+    w[0] = [0.3, 1.0, 2.0, 7.0]
+    w[4] = [0.1, 1.0, 3.0, 9.5]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, 4)
+    assert np.allclose(q[0], w[0], rtol=0, atol=0)
+    assert np.max(np.abs(q[4] - w[4] / (G - 1)) / q[4]) < 1e-15
+    got, status, iters, _ = orc.con2prim(q, 4)
+    assert np.max(np.abs(got[4] - w[4]) / w[4]) < 1e-15
+    assert np.all(iters == 1)
+
+
+def test_warm_seed_converges_fast(orc):
+    w = iid_prims(5000, 2)
+    n = w.shape[1]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    _, _, it_cold, _ = orc.con2prim(q, n)
+    _, status, it_warm, _ = orc.con2prim(q, n, p_prev=w[4] * (1 + 1e-6))
+    assert np.all(status == 0)
+    assert it_warm.mean() < it_cold.mean()
+
+
+def test_unphysical_state_reports_failure(orc):
+    """|S| > E + large margin has no physical pressure: status 2, counted, no exception."""
+    q = np.zeros((5, 3))
+    q[:, 0] = [1.0, 50.0, 0.0, 0.0, 0.1]     # |S| >> tau + D
+    q[:, 1] = [1.0, 0.1, 0.0, 0.0, 2.0]      # physical
+    q[:, 2] = [1.0, 0.0, 0.0, 0.0, -5.0]     # negative energy
+    prim, status, iters, fails = orc.con2prim(q, 3)
+    assert status[1] == 0
+    assert status[0] == 2 and status[2] == 2
+    assert fails == 2
+
+
+def test_sound_speed_at_rest(orc):
+    """v = 0: the characteristic speeds are +-cs, cs^2 = Gamma p / (rho h)."""
+    mesh = single_level((1, 1, 1), 8, 1.0 / 8)
+    prim = arena(mesh, 5)
+    prim[0], prim[4] = 2.0, 3.0
+    q = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
+    lam = orc.max_wave_speed(synth.PDE_SRHD3D, 3, mesh.patches, mesh.var_stride, q, mat=prim)
+    h = 1 + G * 3.0 / ((G - 1) * 2.0)
+    assert abs(lam - math.sqrt(G * 3.0 / (2.0 * h))) < 1e-15
+
+
+def test_light_speed_limit(orc):
+    """Every characteristic speed stays below c = 1 even at W = 10."""
+    mesh = single_level((1, 1, 1), 8, 1.0 / 8)
+    w = iid_prims(512, 3)
+    prim = arena(mesh, 5)
+    prim[:, :512] = w
+    q = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
+    lam = orc.max_wave_speed(synth.PDE_SRHD3D, 3, mesh.patches, mesh.var_stride, q, mat=prim)
+    assert 0.5 < lam < 1.0
+
+
+def test_srhd_fv_free_stream_and_conservation(orc):
+    mesh = single_level((2, 2, 2), 8, 1.0 / 16)
+    prim = arena(mesh, 5)
+    prim[0], prim[1], prim[2], prim[3], prim[4] = 1.5, 0.3, -0.4, 0.2, 2.0
+    q = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
+    out = np.zeros_like(q)
+    orc.stage(0, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, q, out=out, mat=prim, dt=0.01)
+    m = voxel_mask(mesh)
+    assert np.array_equal(out[:, m], q[:, m])
+    rng = np.random.default_rng(4)
+    X = synth.voxel_centres(mesh)
+    prim[0] = synth.fourier_field(rng, X, [1, 1, 1], 3, 1.0, 0.5)
+    prim[4] = synth.fourier_field(rng, X, [1, 1, 1], 3, 1.0, 0.5)
+    q = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
+    orc.stage(0, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, q, out=out, mat=prim, dt=0.005)
+    for v in range(5):
+        assert abs(out[v, m].sum() - q[v, m].sum()) <= 1e-13 * np.abs(q[v, m]).sum()
+
+
+def test_mlp_gradient_matches_finite_differences(orc):
+    rng = np.random.default_rng(5)
+    w = rng.normal(scale=0.3, size=1217)
+    x = rng.normal(size=(64, 3))
+    t = rng.normal(size=64)
+    loss, g = orc.mlp_loss_grad(w, x, t)
+    h = 1e-6
+    idx = rng.choice(1217, 60, replace=False).tolist() + [0, 95, 96, 127, 128, 1151, 1152, 1183, 1184, 1215, 1216]
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (orc.mlp_loss_grad(wp, x, t)[0] - orc.mlp_loss_grad(wm, x, t)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-7 * max(1.0, abs(fd)), (i, fd, g[i])
+    assert abs(loss - np.mean((orc.mlp_forward(w, x) - t) ** 2)) < 1e-14
+
+
+def test_adam_first_step_closed_form(orc):
+    """After one step from zero moments, Adam moves each weight by lr g / (|g| + eps)."""
+    g = np.array([0.5, -2.0, 1e-3, 0.0])
+    w = np.zeros(4)
+    m, v = np.zeros(4), np.zeros(4)
+    orc.adam(w, m, v, g, 1, lr=1e-3)
+    assert np.max(np.abs(w + 1e-3 * g / (np.abs(g) + 1e-8))) < 1e-18
