@@ -184,6 +184,31 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  * double to out_dev[thread].  out_dev must hold n_threads doubles. */
 dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void* stream);
 
+/* The FV stage for callers that cannot allocate device memory (a host
+ * framework whose pool owns the device, a plugin host that forbids
+ * allocations after start-up, a real-time loop that must not block in the
+ * allocator).  The paper has no counterpart: it is a deployment variant of
+ * patch_update_fv.  It takes the plan-creation arguments (host patch table,
+ * K, var_stride, params) together with the stage arguments of
+ * patch_update_fv, and keeps the patch table, the work list and the two
+ * reduction slots in one file-scope device array of 1,376,512 bytes that
+ * every GPU loading the library holds until exit.  Limits: K <= 8192 patches
+ * and at most 16384 tile work items (a 16x16 column of a patch, or four 8x8
+ * columns); larger inputs return DH_EINVAL.  PDEs: ADV_FLUX, ADV_NCP,
+ * EULER2D, EULER3D; halo 1.  Each call uploads the tables with
+ * cudaMemcpyAsync from host memory (staged before the call returns), clears
+ * the reduction slots, then launches the stage on `stream`; it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  All calls share the one
+ * array and overwrite the previous call's contents, so calls that overlap on
+ * the GPU race.  The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture. */
+dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_patch* patches, int32_t K,
+                                  int64_t var_stride, const double* params, int32_t n_params,
+                                  const double* qs, const double* q0, double* out, double* acc,
+                                  const double* mat, const double* dt_dev, double a, double b, double g,
+                                  double d, double* lam_out_dev, void* stream);
+
 const char* dh_last_error(void);
 
 /* Library version string. */

@@ -25,7 +25,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "dh_last_error", "dh_version"]
+           "dh_graph_stage_times", "dh_probe_dfma", "patch_update_fv_noalloc", "dh_last_error", "dh_version"]
 
 
 class DhError(RuntimeError):
@@ -52,6 +52,8 @@ def lib():
         L.dh_cfl_dt.argtypes = [vp, vp, d, vp, vp]
         L.dh_prim2con.argtypes = [vp, vp, vp, vp]
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
+        L.patch_update_fv_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp, vp, d, d, d, d,
+                                              vp, vp]
         L.dh_rk_step.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, vp]
         L.dh_graph_capture.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, vp]
         L.dh_graph_launch.argtypes = [vp, vp]
@@ -147,6 +149,19 @@ def patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, sigma_ko
                                   float(g), float(d), float(sigma_ko), _ptr(lam_out_dev, "lam_out_dev"),
                                   _stream(stream))
     _check(st, "patch_update_fd_ko")
+
+
+def patch_update_fv_noalloc(pde, dim, patches, var_stride, params, qs, q0, out, acc, mat, dt_dev, a, b, g, d,
+                            lam_out_dev=None, stream=None):
+    """FV stage without a plan and without any device allocation (static device scratch; see dh.h)."""
+    patches = np.ascontiguousarray(patches, dtype=synth.PATCH_DTYPE)
+    prm = None if params is None else np.ascontiguousarray(params, dtype=np.float64)
+    st = lib().patch_update_fv_noalloc(int(pde), int(dim), patches.ctypes.data, len(patches), int(var_stride),
+                                       None if prm is None else prm.ctypes.data, 0 if prm is None else len(prm),
+                                       _ptr(qs, "qs"), _ptr(q0, "q0"), _ptr(out, "out"), _ptr(acc, "acc"),
+                                       _ptr(mat, "mat"), _ptr(dt_dev, "dt_dev"), float(a), float(b), float(g),
+                                       float(d), _ptr(lam_out_dev, "lam_out_dev"), _stream(stream))
+    _check(st, "patch_update_fv_noalloc")
 
 
 def max_wave_speed(plan, q, mat, lam_out_dev, stream=None):
