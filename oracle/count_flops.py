@@ -27,7 +27,17 @@ def _state(pde, dim, p, seed=3):
         prim = synth.euler_prims(mesh, seed)
         q = oracle.prim2con(pde, prim, mesh.var_stride)[:, :n]
         return np.ascontiguousarray(q), None
+    rng = np.random.default_rng(seed)
+    if pde == synth.PDE_WAVE3D:
+        return rng.normal(size=(5, n)), np.full((1, n), 1.3)
+    if pde == synth.PDE_GW59:
+        q = 1e-3 * rng.normal(size=(59, n))
+        q[55] += 1.0
+        return q, None
     raise KeyError(pde)
+
+
+PARAMS = {synth.PDE_GW59: synth.workload("gw59", scale=8).params, synth.PDE_WAVE3D: np.array([0.1])}
 
 
 def per_voxel(scheme, pde, dim, halo, rk, with_lam, sizes=(8, 16, 24)):
@@ -35,7 +45,8 @@ def per_voxel(scheme, pde, dim, halo, rk, with_lam, sizes=(8, 16, 24)):
     c = []
     for p in sizes:
         q, m = _state(pde, dim, p)
-        c.append(oracle.count_flops(scheme, pde, dim, p, halo, q, m, rk=rk, with_lam=with_lam))
+        c.append(oracle.count_flops(scheme, pde, dim, p, halo, q, m, rk=rk, with_lam=with_lam,
+                                    params=PARAMS.get(pde)))
     M = np.array([[p ** dim, p ** (dim - 1), 1.0] for p in sizes])
     A, B, C = np.linalg.solve(M, np.array(c, dtype=float))
     return A, B, C, c
@@ -47,6 +58,8 @@ def main():
         "fv/euler3d/ssprk3_step": (0, synth.PDE_EULER3D, 3, 1, 3, True),
         "fv/euler3d/stage_fe": (0, synth.PDE_EULER3D, 3, 1, 0, False),
         "fv/euler2d/fe_step": (0, synth.PDE_EULER2D, 2, 1, 1, True),
+        "fd/wave3d/rk4_step": (1, synth.PDE_WAVE3D, 3, 3, 4, True),
+        "fd/gw59/rk4_step": (1, synth.PDE_GW59, 3, 3, 4, True),
     }.items():
         A, B, C, c = per_voxel(*args)
         A2, B2, C2, _ = per_voxel(*args, sizes=(8, 16, 32))

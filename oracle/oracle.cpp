@@ -265,6 +265,17 @@ void ncp(int pde, const Params& P, int d, const T* qb, const T* dq, T* out) {
   }
 }
 
+// Whether the non-conservative product in direction d reads dQ_v/dx_d, i.e.
+// whether column v of B_d is non-zero (only those derivatives are computed).
+bool needs_grad(int pde, int d, int v) {
+  switch (pde) {
+    case ADV_NCP: return v == 0;
+    case WAVE3D: return v == 1 || v == 2 + d;
+    case GW59: return v == 55 || (v < 55 && v % 5 != 0);  // Pi_a, psi_a, alpha
+  }
+  return false;
+}
+
 // Source S(Q).
 template <class T>
 void source(int pde, const Params& P, const T* q, const T* m, T* S) {
@@ -531,7 +542,7 @@ void fd_operator(int pde, const Params& P, Block<T>& B, double dxd, double sigma
           }
           if (I.ncp) {
             for (int v = 0; v < N; ++v)
-              dq[v] = ((q[1][v] - q[5][v]) + T(8.0) * (q[4][v] - q[2][v])) * r12;
+              dq[v] = needs_grad(pde, d, v) ? ((q[1][v] - q[5][v]) + T(8.0) * (q[4][v] - q[2][v])) * r12 : T(0.0);
             ncp(pde, P, d, u0, dq.data(), bq.data());
             for (int v = 0; v < N; ++v) Lv[v] = Lv[v] - bq[v];
           }

@@ -254,6 +254,18 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   plan->h_work = work;
   plan->n_work = (int)work.size();
 
+  // FD tiles: 8x8x4 blocks (p is a multiple of 8)
+  std::vector<FdWork> fdw;
+  if (dim == 3) {
+    for (int k = 0; k < K; ++k) {
+      const int p = patches[k].p;
+      for (int zz = 0; zz < p; zz += 4)
+        for (int yy = 0; yy < p; yy += 8)
+          for (int xx = 0; xx < p; xx += 8) fdw.push_back(FdWork{k, (int16_t)xx, (int16_t)yy, (int16_t)zz, 0});
+    }
+  }
+  plan->n_fdwork = (int)fdw.size();
+
   cudaError_t e = cudaGetDevice(&plan->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_patches, sizeof(dh_patch) * K);
@@ -261,6 +273,9 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_work, sizeof(Work) * std::max<size_t>(1, work.size()));
   if (e == cudaSuccess && !work.empty())
     e = cudaMemcpy(plan->d_work, work.data(), sizeof(Work) * work.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !fdw.empty()) e = cudaMalloc(&plan->d_fdwork, sizeof(FdWork) * fdw.size());
+  if (e == cudaSuccess && !fdw.empty())
+    e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 2 * sizeof(unsigned long long));
   if (e != cudaSuccess) {
@@ -277,6 +292,7 @@ dh_status dh_plan_destroy(dh_plan* plan) {
   if (plan->d_patches) cudaFree(plan->d_patches);
   if (plan->d_work) cudaFree(plan->d_work);
   if (plan->d_red) cudaFree(plan->d_red);
+  if (plan->d_fdwork) cudaFree(plan->d_fdwork);
   if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
   for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);
@@ -307,10 +323,15 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
                              double sigma_ko, double* lam_out_dev, void* stream) {
   dh_status st = check_plan(plan);
   if (st != DH_OK) return st;
-  (void)qs; (void)q0; (void)out; (void)acc; (void)mat; (void)dt_dev; (void)a; (void)b; (void)g; (void)d;
-  (void)sigma_ko; (void)lam_out_dev; (void)stream;
-  set_error("patch_update_fd_ko: not built yet");
-  return DH_EUNSUPPORTED;
+  if (!qs || !dt_dev) { set_error("patch_update_fd_ko: qs and dt_dev are required"); return DH_EINVAL; }
+  if (!out && !acc) { set_error("patch_update_fd_ko: nothing to write (out and acc are NULL)"); return DH_EINVAL; }
+  if (plan->nm > 0 && !mat) { set_error("patch_update_fd_ko: PDE needs the material arena"); return DH_EINVAL; }
+  if (!q0 && a != 0.0) { set_error("patch_update_fd_ko: q0 is NULL but a != 0"); return DH_EINVAL; }
+  if (out == qs || acc == qs || (out && out == acc)) { set_error("patch_update_fd_ko: out/acc must not alias qs or each other"); return DH_EINVAL; }
+  if (plan->halo < 3) { set_error("patch_update_fd_ko: the plan needs halo >= 3 (it has %d)", plan->halo); return DH_EINVAL; }
+  if (plan->dim != 3) { set_error("patch_update_fd_ko: 3D only"); return DH_EUNSUPPORTED; }
+  if (!(sigma_ko >= 0.0)) { set_error("patch_update_fd_ko: sigma must be >= 0"); return DH_EINVAL; }
+  return launch_fd_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, sigma_ko, lam_out_dev, (cudaStream_t)stream);
 }
 
 dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream) {
@@ -325,6 +346,8 @@ dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, doub
     case DH_PDE_ADV_NCP: k_max_speed<PdeAdvNcp><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     case DH_PDE_EULER2D: k_max_speed<PdeEuler2><<<plan->K, 256, 0, s>>>(P, 2, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     case DH_PDE_EULER3D: k_max_speed<PdeEuler3><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_WAVE3D: k_max_speed<PdeWave><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_GW59: k_max_speed<PdeGW59><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     default:
       set_error("max_wave_speed: PDE %d not supported yet", plan->pde);
       return DH_EUNSUPPORTED;

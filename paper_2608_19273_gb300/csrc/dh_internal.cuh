@@ -30,7 +30,11 @@ struct Work {
   int16_t y0[4];
 };
 
-struct PlanLaunch;  // forward
+// One FD tile: an 8x8x4 block of one patch.
+struct FdWork {
+  int32_t patch;
+  int16_t x0, y0, z0, pad;
+};
 
 }  // namespace dh
 
@@ -48,6 +52,9 @@ struct dh_plan {
   dh::Work* d_work = nullptr;
   int n_work = 0;
   bool has_cls[2] = {false, false};
+  // FD tile list (8x8x4 tiles)
+  dh::FdWork* d_fdwork = nullptr;
+  int n_fdwork = 0;
   // reduction scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter
   unsigned long long* d_red = nullptr;
   int num_sms = 0;
@@ -64,6 +71,10 @@ dh_status cuda_error(cudaError_t e, const char* what);
 int pde_nq(int pde);
 int pde_nm(int pde);
 int pde_dim(int pde);
+
+dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                          const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                          double sigma, double* lam_out, cudaStream_t stream);
 
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,

@@ -36,6 +36,7 @@ struct PdeAdvFlux {
 struct PdeAdvNcp {
   static constexpr int N = 1, M = 3, NW = 1, DIM = 3;
   static constexpr bool FLUX = false, NCP = true, SRC = false;
+  __device__ static constexpr bool needs_grad(int, int v) { return v == 0; }
   __device__ static void prims(const double*, const DevParams&, double*) {}
   __device__ static void flux(int, const double*, const double*, const DevParams&, double*) {}
   __device__ static double speed(int d, const double* q, const double*, const DevParams&) {
@@ -86,5 +87,51 @@ struct PdeEuler {
 
 using PdeEuler2 = PdeEuler<2>;
 using PdeEuler3 = PdeEuler<3>;
+
+// ---------------------------------------------------------------- wave system
+// First-order reduction of the damped scalar wave equation with speed c(x):
+//   d_t phi = Pi,  d_t Pi = c^2 div psi - gamma Pi,  d_t psi_i = d_i Pi
+// as Eq. 1: F = 0; B_d has (row Pi, col psi_d) = -c^2 and (row psi_d, col Pi) = -1;
+// S = (Pi, -gamma Pi, 0, 0, 0).  Material: c (M = 1).  lambda_d = c.
+struct PdeWave {
+  static constexpr int N = 5, M = 1, NW = 1, DIM = 3;
+  static constexpr bool FLUX = false, NCP = true, SRC = true;
+  __device__ static constexpr bool needs_grad(int d, int v) { return v == 1 || v == 2 + d; }
+  __device__ static void prims(const double*, const DevParams&, double*) {}
+  __device__ static void flux(int, const double*, const double*, const DevParams&, double*) {}
+  __device__ static double speed(int, const double* q, const double*, const DevParams&) { return q[5]; }
+  __device__ static void ncp(int d, const double* qb, const double* dq, const DevParams&, double* D) {
+    const double c2 = qb[5] * qb[5];
+    D[0] = 0.0;
+    D[1] = -c2 * sel3(d, dq[2], dq[3], dq[4]);
+    D[2] = d == 0 ? -dq[1] : 0.0;
+    D[3] = d == 1 ? -dq[1] : 0.0;
+    D[4] = d == 2 ? -dq[1] : 0.0;
+  }
+  __device__ static void source(const double* q, const double*, const DevParams& P, double* S) {
+    S[0] = q[1];
+    S[1] = -P.damp * q[1];
+    S[2] = 0.0; S[3] = 0.0; S[4] = 0.0;
+  }
+};
+
+// ---------------------------------------------------------------- GW59 stand-in
+// 11 first-order scalar waves (phi_a, Pi_a, psi_a,xyz) coupled to a lapse alpha
+// and shift beta (59 unknowns):
+//   d_t phi_a   = alpha Pi_a + beta^k psi_a,k
+//   d_t Pi_a    = alpha d_k psi_a,k + beta^k d_k Pi_a + alpha sum_b C_ab phi_b Pi_b
+//   d_t psi_a,i = alpha d_i Pi_a + Pi_a d_i alpha + beta^k d_k psi_a,i
+//   d_t alpha   = -kappa alpha^2 sum_a Pi_a^2
+//   d_t beta^i  = 3/4 sum_a psi_a,i Pi_a
+// F = 0; every gradient term is part of B(Q).grad Q.  Layout: field a at 5a..5a+4,
+// alpha at 55, beta at 56..58.  lambda_d = alpha + |beta^d|.
+struct PdeGW59 {
+  static constexpr int N = 59, M = 0, NW = 1, DIM = 3;
+  static constexpr bool FLUX = false, NCP = true, SRC = true;
+  __device__ static void prims(const double*, const DevParams&, double*) {}
+  __device__ static double speed(int d, const double* q, const double*, const DevParams&) {
+    return q[55] + fabs(sel3(d, q[56], q[57], q[58]));
+  }
+};
 
 }  // namespace dh

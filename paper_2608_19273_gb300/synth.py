@@ -250,3 +250,45 @@ def gaussian(X, centre, width, dim):
     for a in range(dim):
         r2 = r2 + (X[a] - centre[a]) ** 2
     return np.exp(-r2 / (2 * width * width))
+
+
+def wave_initial(mesh, seed, width=0.05):
+    """Wave system: Gaussian pulse phi, Pi = 0, psi = grad phi (analytic); material
+    c(x) = 1.25 + 0.75 sin(2 pi x/Lx) sin(2 pi y/Ly) sin(2 pi z/Lz) in [0.5, 2]."""
+    rng = np.random.default_rng(seed)
+    X = voxel_centres(mesh)
+    q = np.zeros((5, mesh.var_stride))
+    mat = np.zeros((1, mesh.var_stride))
+    for li in range(len(mesh.levels)):
+        idx = level_slices(mesh, li)
+        L = level_extent(mesh, li)
+        Xl = X[:, idx]
+        x0 = [rng.uniform(0.25, 0.75) * L[a] for a in range(3)]
+        g = gaussian(Xl, x0, width, 3)
+        q[0, idx] = g
+        for a in range(3):
+            q[2 + a, idx] = -(Xl[a] - x0[a]) / (width * width) * g
+        mat[0, idx] = 1.25 + 0.75 * (np.sin(2 * math.pi * Xl[0] / L[0]) * np.sin(2 * math.pi * Xl[1] / L[1])
+                                     * np.sin(2 * math.pi * Xl[2] / L[2]))
+    return q, mat
+
+
+def gw59_initial(mesh, seed, amp=1e-6, width=0.05, noise=0.0):
+    """Flat state (alpha = 1, everything else 0) plus a Gaussian of amplitude amp in alpha
+    and phi_1 with a seeded centre per level; optional smooth noise of amplitude `noise`
+    in every variable (test data that exercises the nonlinear terms)."""
+    rng = np.random.default_rng(seed)
+    X = voxel_centres(mesh)
+    q = np.zeros((59, mesh.var_stride))
+    for li in range(len(mesh.levels)):
+        idx = level_slices(mesh, li)
+        L = level_extent(mesh, li)
+        Xl = X[:, idx]
+        x0 = [rng.uniform(0.25, 0.75) * L[a] for a in range(3)]
+        g = gaussian(Xl, x0, width, 3)
+        q[55, idx] = 1.0 + amp * g
+        q[0, idx] = amp * g
+        if noise:
+            for v in range(59):
+                q[v, idx] += fourier_field(rng, Xl, L, 3, 0.0, noise)
+    return q
