@@ -136,6 +136,61 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
  * (the paper's scalar eigenvalue functions, Sec. II-B). */
 dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream);
 
+/* Conservative -> primitive recovery for SRHD3D over the plan's voxels
+ * (relativistic hydro is not in the paper; textbook definitions):
+ * per voxel, FP64 Newton iteration on the pressure
+ *   f(p) = ((G-1)/G) [(E+p) - S^2/(E+p) - D sqrt(1 - S^2/(E+p)^2)] - p,  E = tau + D,
+ * within the bracket p > max(0, |S| - E) (a step leaving it is replaced by the
+ * midpoint to the bound), stopping when |p_new - p| <= tol p_new, at most
+ * max_iter steps; then v = S/(E+p), rho = D sqrt(1 - v^2).
+ *   cons   : 5-variable arena (D, S_x, S_y, S_z, tau)
+ *   prim   : 5-variable arena (rho, v_x, v_y, v_z, p), written
+ *   p_prev : NULL or a pressure array (arena layout, one variable): the plain seed
+ *   mlp_w  : NULL or 1224 floats (device): FP32 MLP seed p = E exp(mlp(x)),
+ *            x = z-scored (|S|/E, D/E, ln(E/D)); then p_prev (or the cold seed
+ *            max((1+1e-8) p_lo + 1e-300, (G-1) tau)) is the fallback
+ *   status : NULL or one byte per voxel: 0 first seed converged, 1 fallback
+ *            converged, 2 both failed (pressure = p_prev or the cold seed)
+ *   iters  : NULL or Newton iterations per voxel (int32)
+ *   fail_count_dev : NULL or a device int32 incremented by the number of status-2 voxels
+ * Never traps on unphysical input. */
+dh_status con2prim(dh_plan* plan, const double* cons, double* prim, const double* p_prev, const float* mlp_w,
+                   double tol, int32_t max_iter, uint8_t* status, int32_t* iters, int32_t* fail_count_dev,
+                   void* stream);
+/* Same recovery on a flat array of n voxels (variable v of voxel i at v*stride + i). */
+dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t stride, const double* p_prev,
+                        const float* mlp_w, double Gamma, double tol, int32_t max_iter, uint8_t* status,
+                        int32_t* iters, int32_t* fail_count_dev, void* stream);
+
+/* MLP pressure seed (3 -> 32 tanh -> 32 tanh -> 1, FP32; not in the paper).
+ * Weight vector: 1224 floats = W1[32][3], b1[32], W2[32][32], b2[32], W3[32],
+ * b3, input mean[3], input std[3], pad.  Loss: mean of (y - ln(p/E))^2.
+ * dh_mlp_features : raw inputs x (n x 3 floats) and, if p != NULL, targets
+ *                   y = ln(p/E) (n floats) from a flat conserved array.
+ * dh_mlp_standardize : writes the mean/std of x into w[1217..1222]
+ *                   (scratch: >= 6 doubles; more allows more parallel partial sums).
+ * dh_mlp_forward  : y = mlp(x) for raw inputs (z-scored inside).
+ * dh_mlp_grad     : grad[0..1216] = d loss / d w over samples [offset, offset+B),
+ *                   grad[1217] = loss; partials: ceil(B/64) * 1224 floats.
+ *                   Deterministic (fixed-order sums, no atomics).
+ * dh_mlp_adam     : one Adam step (Kingma & Ba) at step count t.
+ * dh_mlp_train    : `steps` steps of grad + Adam (lr, beta 0.9/0.999, eps 1e-8)
+ *                   over consecutive batches of the (pre-shuffled) data; step
+ *                   counter starts at t0 + 1; loss_log (optional) gets one
+ *                   float per step. */
+dh_status dh_mlp_features(const double* cons, const double* p, int64_t n, int64_t stride, float* x, float* y,
+                          void* stream);
+dh_status dh_mlp_standardize(const float* x, int64_t n, float* w, double* scratch, int32_t scratch_len,
+                             void* stream);
+dh_status dh_mlp_forward(const float* w, const float* x, int64_t n, float* y, void* stream);
+dh_status dh_mlp_grad(const float* w, const float* x, const float* t, int64_t offset, int32_t B, float* partials,
+                      float* grad, void* stream);
+dh_status dh_mlp_adam(float* w, float* m, float* v, const float* g, int32_t t, float lr, float b1, float b2,
+                      float eps, void* stream);
+dh_status dh_mlp_train(float* w, float* m, float* v, const float* x, const float* t, int64_t n, int32_t batch,
+                       int32_t steps, int32_t t0, float lr, float* partials, float* grad, float* loss_log,
+                       void* stream);
+
 /* dt_dev <- cfl * dx_min / (dim * lam_dev[0]) on the device (the CFL rule). */
 dh_status dh_cfl_dt(dh_plan* plan, const double* lam_dev, double cfl, double* dt_dev, void* stream);
 
@@ -176,6 +231,11 @@ dh_status dh_graph_info(dh_plan* plan, int32_t* n_kernels, int32_t* n_timed_stag
 /* Device time (ms) of the first n timed stages of the last completed replay
  * (the caller synchronises first). */
 dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
+
+/* Diagnostic: for n doubles x, y_nr[i] = the kernels' Newton-Raphson
+ * reciprocal of x[i] and y_div[i] = 1.0 / x[i] (IEEE division), so that a test
+ * can bound the reciprocal's error.  All three arrays are device arrays of n. */
+dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n, void* stream);
 
 /* Diagnostic: FP64 FMA throughput probe used to measure the FP64 roofline
  * peak on the running GPU.  Launches n_threads (a multiple of 256) threads;

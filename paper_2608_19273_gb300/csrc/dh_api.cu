@@ -146,6 +146,15 @@ __global__ void __launch_bounds__(256) k_probe_dfma(double* out, int iters, doub
   out[t] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
 }
 
+// recip_nr next to the IEEE division, for the accuracy test.
+__global__ void k_check_recip(const double* x, double* y_nr, double* y_div, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    y_nr[i] = recip_nr(x[i]);
+    y_div[i] = 1.0 / x[i];
+  }
+}
+
 static dh_status check_plan(const dh_plan* plan) {
   if (!plan) {
     set_error("plan is NULL");
@@ -346,6 +355,7 @@ dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, doub
     case DH_PDE_ADV_NCP: k_max_speed<PdeAdvNcp><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     case DH_PDE_EULER2D: k_max_speed<PdeEuler2><<<plan->K, 256, 0, s>>>(P, 2, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     case DH_PDE_EULER3D: k_max_speed<PdeEuler3><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_SRHD3D: k_max_speed<PdeSRHD><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     case DH_PDE_WAVE3D: k_max_speed<PdeWave><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     case DH_PDE_GW59: k_max_speed<PdeGW59><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, q, mat, plan->params, lam_out_dev, plan->d_red); break;
     default:
@@ -373,6 +383,12 @@ dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* str
   else if (plan->pde == DH_PDE_SRHD3D) k_prim2con_srhd<<<plan->K, 256, 0, s>>>(plan->d_patches, plan->var_stride, prim, cons, plan->params.Gamma);
   else { set_error("dh_prim2con: PDE %d has no primitive form", plan->pde); return DH_EUNSUPPORTED; }
   return cuda_error(cudaGetLastError(), "dh_prim2con launch");
+}
+
+dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n, void* stream) {
+  if (!x || !y_nr || !y_div || n <= 0 || n > (1ll << 40)) { set_error("dh_check_recip: bad arguments"); return DH_EINVAL; }
+  k_check_recip<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y_nr, y_div, n);
+  return cuda_error(cudaGetLastError(), "dh_check_recip launch");
 }
 
 dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void* stream) {

@@ -168,6 +168,8 @@ struct FvTile {
     const double dt = *A.dt_dev;
     const double gdt = A.g * dt, ddt = A.d * dt;
     const double cL = -0.5 / dxk;  // -1/(2 dx): faces hold twice the flux
+    const double cS = gdt * cL, cA = ddt * cL;  // stage scalars folded with -1/(2 dx)
+    const bool b1 = A.b == 1.0;
     const bool ring = tid < NR;
 
     // smem slots of this voxel and of its -x / -y neighbours
@@ -288,16 +290,14 @@ struct FvTile {
             if (DIM == 3) dsum += Dzhi[v] + Dzlo[v];
             sum += dsum;
           }
-          double L = cL * sum;
-          if (PDE::SRC) L += Sv[v];
           const int64_t ev = v * A.vs + e;
           if (A.out) {
-            double base = A.b * Qk[v];
+            double base = b1 ? Qk[v] : A.b * Qk[v];
             if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
-            res[v] = fma(gdt, L, base);
+            res[v] = PDE::SRC ? fma(gdt, fma(cL, sum, Sv[v]), base) : fma(cS, sum, base);
           }
           if (A.acc) {
-            const double r = fma(ddt, L, A.acc[ev]);
+            const double r = PDE::SRC ? fma(ddt, fma(cL, sum, Sv[v]), A.acc[ev]) : fma(cA, sum, A.acc[ev]);
             A.acc[ev] = r;
             if (!A.out) res[v] = r;
           }
@@ -415,6 +415,7 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
     case DH_PDE_ADV_NCP: return launch<PdeAdvNcp>(plan, A, stream);
     case DH_PDE_EULER2D: return launch<PdeEuler2>(plan, A, stream);
     case DH_PDE_EULER3D: return launch<PdeEuler3>(plan, A, stream);
+    case DH_PDE_SRHD3D: return launch<PdeSRHD>(plan, A, stream);
     default:
       set_error("patch_update_fv: PDE %d not supported by the FV stage", plan->pde);
       return DH_EUNSUPPORTED;

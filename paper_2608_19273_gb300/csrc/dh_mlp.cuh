@@ -1,0 +1,56 @@
+// Small FP32 MLP (3 -> 32 tanh -> 32 tanh -> 1) that seeds the SRHD pressure
+// Newton iteration.  Weight vector layout (floats), shared by inference and
+// training:
+//   W1[32][3] (0..95), b1[32] (96..127), W2[32][32] (128..1151), b2[32]
+//   (1152..1183), W3[32] (1184..1215), b3 (1216), then the z-score
+//   statistics of the inputs: mean[3] (1217..1219), std[3] (1220..1222), pad.
+// Inputs: x = (|S|/E, D/E, ln(E/D)) with E = tau + D; target y = ln(p/E).
+// tanh is CUDA's tanhf.
+#pragma once
+
+#include "dh_internal.cuh"
+
+namespace dh {
+
+constexpr int MLP_NW = 1217;       // trainable parameters
+constexpr int MLP_LEN = 1224;      // parameters + statistics + pad
+constexpr int MLP_W1 = 0, MLP_B1 = 96, MLP_W2 = 128, MLP_B2 = 1152, MLP_W3 = 1184, MLP_B3 = 1216;
+constexpr int MLP_MEAN = 1217, MLP_STD = 1220;
+
+// Invariants of a conserved SRHD state in FP64.
+__device__ __forceinline__ void srhd_invariants(const double* q, double* x) {
+  const double D = q[0], E = q[4] + q[0];
+  const double S = sqrt(fma(q[1], q[1], fma(q[2], q[2], q[3] * q[3])));
+  x[0] = S / E;
+  x[1] = D / E;
+  x[2] = log(E / D);
+}
+
+// z-scored FP32 input from FP64 invariants (statistics in the weight vector).
+__device__ __forceinline__ void mlp_normalize(const float* w, const double* xd, float* x) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) x[j] = (float)((xd[j] - (double)w[MLP_MEAN + j]) / (double)w[MLP_STD + j]);
+}
+
+// Forward pass; h1/h2 receive the hidden activations.
+__device__ __forceinline__ float mlp_forward(const float* w, const float* x, float* h1, float* h2) {
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    float s = w[MLP_B1 + i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s = fmaf(w[MLP_W1 + 3 * i + j], x[j], s);
+    h1[i] = tanhf(s);
+  }
+  float y = w[MLP_B3];
+#pragma unroll 4
+  for (int i = 0; i < 32; ++i) {
+    float s = w[MLP_B2 + i];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) s = fmaf(w[MLP_W2 + 32 * i + j], h1[j], s);
+    h2[i] = tanhf(s);
+    y = fmaf(w[MLP_W3 + i], h2[i], y);
+  }
+  return y;
+}
+
+}  // namespace dh

@@ -1,0 +1,202 @@
+// Conservative -> primitive recovery for special-relativistic hydrodynamics:
+// per voxel, FP64 Newton iteration on the pressure, seeded either by the
+// previous pressure (plain) or by the FP32 MLP guess, with the plain seed as
+// fallback.  (The paper has no SRHD; definitions are the textbook ones.)
+//
+//   E = tau + D, S^2 = |S|^2, bracket p > p_lo = max(0, |S| - E)
+//   f(p)  = ((G-1)/G) [ (E+p) - S^2/(E+p) - D sqrt(1 - S^2/(E+p)^2) ] - p
+//   f'(p) = ((G-1)/G) [ 1 + S^2/(E+p)^2 - D S^2 / ((E+p)^3 sqrt(1 - S^2/(E+p)^2)) ] - 1
+//   p <- p - f/f'; a step that leaves the bracket is replaced by the midpoint
+//   between the current iterate and p_lo and never counts as convergence;
+//   converged when |p_new - p| <= tol p_new; at most max_iter steps.
+//   Seeds: MLP (if weights given) -> p_prev (if given) -> cold seed
+//   max((1 + 1e-8) p_lo + 1e-300, (G-1) tau); the first seed is tried, the
+//   second only if the first fails.  status: 0 first seed converged, 1 second
+//   seed converged, 2 both failed (p = p_prev or the cold seed, counted in
+//   fail_count).  Recovery: v = S/(E+p), W = 1/sqrt(1 - v^2), rho = D/W.
+// Failures never trap: they are reported through status and the counter.
+#include "dh_internal.cuh"
+#include "dh_mlp.cuh"
+
+namespace dh {
+
+// Returns iterations used (> 0) on convergence, -iterations on failure.
+__device__ int srhd_newton_dev(double G, double D, double S2, double E, double p_lo, double p0, double tol,
+                               int max_iter, double* p_out) {
+  const double gf = (G - 1.0) / G;
+  double p = p0;
+  for (int it = 1; it <= max_iter; ++it) {
+    const double Ep = E + p;
+    const double rEp = 1.0 / Ep;
+    const double t = S2 * rEp;          // S^2/(E+p)
+    const double s2e = t * rEp;         // S^2/(E+p)^2
+    const double om = 1.0 - s2e;
+    const double rrt = rsqrt(om);       // 1/sqrt(1 - S^2/(E+p)^2)
+    const double rt = om * rrt;
+    const double f = fma(gf, (Ep - t) - D * rt, -p);
+    const double fp = fma(gf, 1.0 + s2e - D * s2e * rEp * rrt, -1.0);
+    double pn = p - f / fp;
+    if (!(pn == pn)) { *p_out = pn; return -it; }
+    if (pn <= p_lo) {
+      pn = 0.5 * (p + p_lo);
+    } else if (fabs(pn - p) <= tol * pn) {
+      *p_out = pn;
+      return it;
+    }
+    p = pn;
+  }
+  *p_out = p;
+  return -max_iter;
+}
+
+struct C2PArgs {
+  const double* cons;
+  double* prim;
+  const double* p_prev;
+  const float* mlp;
+  double tol;
+  int max_iter;
+  uint8_t* status;
+  int32_t* iters;
+  int32_t* fail_count;
+  int64_t vs;
+  double G;
+};
+
+__device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64_t e) {
+  const int64_t vs = A.vs;
+  double q[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) q[v] = A.cons[v * vs + e];
+  const double G = A.G;
+  const double D = q[0], E = q[4] + q[0];
+  const double S2 = fma(q[1], q[1], fma(q[2], q[2], q[3] * q[3]));
+  const double S = sqrt(S2);
+  const double p_lo = fmax(0.0, S - E);
+  const double cold = fmax(fma(1.0 + 1e-8, p_lo, 1e-300), (G - 1.0) * q[4]);
+  const bool have_prev = A.p_prev != nullptr;
+  double s1, s2;
+  bool have2;
+  if (w) {
+    double xd[3];
+    float x[3], h1[32], h2[32];
+    srhd_invariants(q, xd);
+    mlp_normalize(w, xd, x);
+    const float y = mlp_forward(w, x, h1, h2);
+    const double ps = E * exp((double)y);
+    const double lo = p_lo * (1.0 + 1e-12);
+    s1 = ps > lo ? ps : cold;
+    s2 = have_prev ? A.p_prev[e] : cold;
+    have2 = true;
+  } else {
+    s1 = have_prev ? A.p_prev[e] : cold;
+    s2 = cold;
+    have2 = have_prev;
+  }
+  double p;
+  int it1 = srhd_newton_dev(G, D, S2, E, p_lo, s1, A.tol, A.max_iter, &p);
+  int total = it1 > 0 ? it1 : -it1;
+  uint8_t st = 0;
+  if (it1 <= 0) {
+    int it2 = 0;
+    if (have2) {
+      it2 = srhd_newton_dev(G, D, S2, E, p_lo, s2, A.tol, A.max_iter, &p);
+      total += it2 > 0 ? it2 : -it2;
+    }
+    if (have2 && it2 > 0) st = 1;
+    else { st = 2; p = have_prev ? A.p_prev[e] : cold; }
+  }
+  const double rEp = 1.0 / (E + p);
+  const double vx = q[1] * rEp, vy = q[2] * rEp, vz = q[3] * rEp;
+  const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+  // rho = D / W = D sqrt(1 - v^2)
+  A.prim[e] = D * sqrt(1.0 - v2);
+  A.prim[vs + e] = vx;
+  A.prim[2 * vs + e] = vy;
+  A.prim[3 * vs + e] = vz;
+  A.prim[4 * vs + e] = p;
+  if (A.status) A.status[e] = st;
+  if (A.iters) A.iters[e] = total;
+  return st == 2 ? 1 : 0;
+}
+
+__device__ __forceinline__ void load_mlp_smem(const float* src, float* dst) {
+  for (int i = threadIdx.x; i < MLP_LEN; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ void count_failures(int nfail, int32_t* fail_count) {
+  // warp-aggregated counter update (order-independent integer sum)
+  const unsigned m = __ballot_sync(0xffffffffu, nfail != 0);
+  if (fail_count && (threadIdx.x & 31) == 0 && m) atomicAdd(fail_count, __popc(m));
+}
+
+// One CTA per patch.
+__global__ void __launch_bounds__(256) k_con2prim_patches(const dh_patch* __restrict__ patches, int dim,
+                                                          const __grid_constant__ C2PArgs A) {
+  __shared__ float w[MLP_LEN];
+  if (A.mlp) load_mlp_smem(A.mlp, w);
+  const dh_patch pt = patches[blockIdx.x];
+  const int n = dim == 3 ? pt.p * pt.p * pt.p : pt.p * pt.p;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    int f = 0;
+    if (i < n) f = c2p_voxel(A, A.mlp ? w : nullptr, pt.offset + i);
+    count_failures(f, A.fail_count);
+  }
+}
+
+// Flat array of n voxels (element i of variable v at v * stride + i).
+__global__ void __launch_bounds__(256) k_con2prim_flat(int64_t n, const __grid_constant__ C2PArgs A) {
+  __shared__ float w[MLP_LEN];
+  if (A.mlp) load_mlp_smem(A.mlp, w);
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int f = 0;
+    if (i < n) f = c2p_voxel(A, A.mlp ? w : nullptr, i);
+    count_failures(f, A.fail_count);
+  }
+}
+
+static dh_status c2p_check(const double* cons, double* prim, double tol, int32_t max_iter) {
+  if (!cons || !prim || cons == prim) { set_error("con2prim: cons and prim are required and distinct"); return DH_EINVAL; }
+  if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000) { set_error("con2prim: tol > 0 and 1 <= max_iter <= 1000 required"); return DH_EINVAL; }
+  return DH_OK;
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+dh_status con2prim(dh_plan* plan, const double* cons, double* prim, const double* p_prev, const float* mlp_w,
+                   double tol, int32_t max_iter, uint8_t* status, int32_t* iters, int32_t* fail_count_dev,
+                   void* stream) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (plan->pde != DH_PDE_SRHD3D) { set_error("con2prim: the plan's PDE is not SRHD3D"); return DH_EUNSUPPORTED; }
+  dh_status st = c2p_check(cons, prim, tol, max_iter);
+  if (st != DH_OK) return st;
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, plan->var_stride, plan->params.Gamma};
+  k_con2prim_patches<<<plan->K, 256, 0, (cudaStream_t)stream>>>(plan->d_patches, plan->dim, A);
+  return cuda_error(cudaGetLastError(), "con2prim launch");
+}
+
+dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t stride, const double* p_prev,
+                        const float* mlp_w, double Gamma, double tol, int32_t max_iter, uint8_t* status,
+                        int32_t* iters, int32_t* fail_count_dev, void* stream) {
+  dh_status st = c2p_check(cons, prim, tol, max_iter);
+  if (st != DH_OK) return st;
+  if (n <= 0 || stride < n) { set_error("con2prim_flat: need 0 < n <= stride"); return DH_EINVAL; }
+  if (!(Gamma > 1.0)) { set_error("con2prim_flat: Gamma must exceed 1"); return DH_EINVAL; }
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, stride, Gamma};
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 8);
+  k_con2prim_flat<<<grid, 256, 0, (cudaStream_t)stream>>>(n, A);
+  return cuda_error(cudaGetLastError(), "con2prim_flat launch");
+}
+
+}  // extern "C"

@@ -25,7 +25,9 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "patch_update_fv_noalloc", "dh_last_error", "dh_version"]
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
+           "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
+           "dh_last_error", "dh_version"]
 
 
 class DhError(RuntimeError):
@@ -52,8 +54,18 @@ def lib():
         L.dh_cfl_dt.argtypes = [vp, vp, d, vp, vp]
         L.dh_prim2con.argtypes = [vp, vp, vp, vp]
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
+        L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
         L.patch_update_fv_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp, vp, d, d, d, d,
                                               vp, vp]
+        L.con2prim.argtypes = [vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp]
+        L.con2prim_flat.argtypes = [vp, vp, i64, i64, vp, vp, d, d, i32, vp, vp, vp, vp]
+        f32 = ctypes.c_float
+        L.dh_mlp_features.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+        L.dh_mlp_standardize.argtypes = [vp, i64, vp, vp, i32, vp]
+        L.dh_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.dh_mlp_grad.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
+        L.dh_mlp_adam.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]
+        L.dh_mlp_train.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, f32, vp, vp, vp, vp]
         L.dh_rk_step.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, vp]
         L.dh_graph_capture.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, vp]
         L.dh_graph_launch.argtypes = [vp, vp]
@@ -164,6 +176,54 @@ def patch_update_fv_noalloc(pde, dim, patches, var_stride, params, qs, q0, out, 
     _check(st, "patch_update_fv_noalloc")
 
 
+def con2prim(plan, cons, prim, p_prev=None, mlp_w=None, tol=1e-12, max_iter=50, status=None, iters=None,
+             fail_count_dev=None, stream=None):
+    _check(lib().con2prim(plan.handle, _ptr(cons, "cons"), _ptr(prim, "prim"), _ptr(p_prev, "p_prev"),
+                          _ptr(mlp_w, "mlp_w"), float(tol), int(max_iter), _ptr(status, "status"),
+                          _ptr(iters, "iters"), _ptr(fail_count_dev, "fail_count"), _stream(stream)), "con2prim")
+
+
+def con2prim_flat(cons, prim, n, stride, p_prev=None, mlp_w=None, Gamma=5.0 / 3.0, tol=1e-12, max_iter=50,
+                  status=None, iters=None, fail_count_dev=None, stream=None):
+    _check(lib().con2prim_flat(_ptr(cons, "cons"), _ptr(prim, "prim"), int(n), int(stride), _ptr(p_prev, "p_prev"),
+                               _ptr(mlp_w, "mlp_w"), float(Gamma), float(tol), int(max_iter),
+                               _ptr(status, "status"), _ptr(iters, "iters"), _ptr(fail_count_dev, "fail_count"),
+                               _stream(stream)), "con2prim_flat")
+
+
+MLP_NW, MLP_LEN = 1217, 1224
+
+
+def dh_mlp_features(cons, p, n, stride, x, y=None, stream=None):
+    _check(lib().dh_mlp_features(_ptr(cons, "cons"), _ptr(p, "p"), int(n), int(stride), _ptr(x, "x"), _ptr(y, "y"),
+                                 _stream(stream)), "dh_mlp_features")
+
+
+def dh_mlp_standardize(x, n, w, scratch, stream=None):
+    _check(lib().dh_mlp_standardize(_ptr(x, "x"), int(n), _ptr(w, "w"), _ptr(scratch, "scratch"),
+                                    int(scratch.numel()), _stream(stream)), "dh_mlp_standardize")
+
+
+def dh_mlp_forward(w, x, n, y, stream=None):
+    _check(lib().dh_mlp_forward(_ptr(w, "w"), _ptr(x, "x"), int(n), _ptr(y, "y"), _stream(stream)), "dh_mlp_forward")
+
+
+def dh_mlp_grad(w, x, t, offset, B, partials, grad, stream=None):
+    _check(lib().dh_mlp_grad(_ptr(w, "w"), _ptr(x, "x"), _ptr(t, "t"), int(offset), int(B),
+                             _ptr(partials, "partials"), _ptr(grad, "grad"), _stream(stream)), "dh_mlp_grad")
+
+
+def dh_mlp_adam(w, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    _check(lib().dh_mlp_adam(_ptr(w, "w"), _ptr(m, "m"), _ptr(v, "v"), _ptr(g, "g"), int(t), float(lr), float(b1),
+                             float(b2), float(eps), _stream(stream)), "dh_mlp_adam")
+
+
+def dh_mlp_train(w, m, v, x, t, n, batch, steps, t0, lr, partials, grad, loss_log=None, stream=None):
+    _check(lib().dh_mlp_train(_ptr(w, "w"), _ptr(m, "m"), _ptr(v, "v"), _ptr(x, "x"), _ptr(t, "t"), int(n),
+                              int(batch), int(steps), int(t0), float(lr), _ptr(partials, "partials"),
+                              _ptr(grad, "grad"), _ptr(loss_log, "loss_log"), _stream(stream)), "dh_mlp_train")
+
+
 def max_wave_speed(plan, q, mat, lam_out_dev, stream=None):
     _check(lib().max_wave_speed(plan.handle, _ptr(q, "q"), _ptr(mat, "mat"), _ptr(lam_out_dev, "lam"),
                                 _stream(stream)), "max_wave_speed")
@@ -210,6 +270,11 @@ def dh_graph_stage_times(plan, n):
 
 def dh_probe_dfma(out_dev, n_threads, iters, stream=None):
     _check(lib().dh_probe_dfma(_ptr(out_dev, "out"), int(n_threads), int(iters), _stream(stream)), "dh_probe_dfma")
+
+
+def dh_check_recip(x, y_nr, y_div, stream=None):
+    _check(lib().dh_check_recip(_ptr(x, "x"), _ptr(y_nr, "y_nr"), _ptr(y_div, "y_div"), int(x.numel()),
+                                _stream(stream)), "dh_check_recip")
 
 
 def version():

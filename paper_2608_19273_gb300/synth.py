@@ -292,3 +292,37 @@ def gw59_initial(mesh, seed, amp=1e-6, width=0.05, noise=0.0):
             for v in range(59):
                 q[v, idx] += fourier_field(rng, Xl, L, 3, 0.0, noise)
     return q
+
+
+def srhd_iid_prims(n, seed, wmax=10.0):
+    """i.i.d. SRHD primitives (rows rho, v_x, v_y, v_z, p): rho, p log-uniform on
+    [0.1, 10]; Lorentz factor uniform on [1, wmax]; isotropic direction."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros((5, n))
+    w[0] = np.exp(rng.uniform(math.log(0.1), math.log(10.0), n))
+    w[4] = np.exp(rng.uniform(math.log(0.1), math.log(10.0), n))
+    W = rng.uniform(1.0, wmax, n)
+    speed = np.sqrt(1.0 - 1.0 / (W * W))
+    nd = rng.normal(size=(3, n))
+    nd /= np.linalg.norm(nd, axis=0)
+    w[1:4] = speed * nd
+    return w
+
+
+def srhd_initial(mesh, seed, wmax=10.0):
+    """Smooth SRHD primitives: ln rho and ln p are Fourier fields mapped onto
+    [ln 0.1, ln 10]; W = 1 + (wmax - 1) s(x) with s a Fourier field in [0, 1];
+    v = sqrt(1 - 1/W^2) n(x), n a normalised Fourier vector field."""
+    rng = np.random.default_rng(seed)
+    lo, hi = math.log(0.1), math.log(10.0)
+    f = fill_fields(mesh, rng, [(0.5 * (lo + hi), 0.5 * (hi - lo))] * 2 + [(0.5, 0.5)] + [(0.0, 1.0)] * 3)
+    w = np.zeros((5, mesh.var_stride))
+    w[0] = np.exp(f[0])
+    w[4] = np.exp(f[1])
+    W = 1.0 + (wmax - 1.0) * f[2]
+    nrm = np.sqrt(f[3] ** 2 + f[4] ** 2 + f[5] ** 2)
+    nrm = np.where(nrm < 1e-12, 1.0, nrm)
+    speed = np.sqrt(np.maximum(1.0 - 1.0 / (W * W), 0.0))
+    for a in range(3):
+        w[1 + a] = speed * f[3 + a] / nrm
+    return w

@@ -144,3 +144,18 @@ def test_single_self_periodic_patch(orc, p):
         dh.patch_update_fv(plan, dev(torch, q), None, d_out, None, None, d_dt, 0, 1, 1, 0)
         out = host(d_out)
     assert_parity(out, ref, voxel_mask(mesh), what=f"self-periodic p={p}")
+
+
+def test_newton_reciprocal_within_one_ulp():
+    """The kernels' reciprocal (hardware estimate + two Newton-Raphson steps) against IEEE 1.0/x."""
+    torch = require_cuda()
+    rng = np.random.default_rng(17)
+    x = np.concatenate([np.exp(rng.uniform(-30, 30, 400000)), -np.exp(rng.uniform(-30, 30, 100000)),
+                        np.array([1.0, 2.0, 0.5, 3.0, 1e-300, 1e300, 0.1, 7.0])])
+    d_x = dev(torch, x)
+    y_nr, y_div = torch.zeros_like(d_x), torch.zeros_like(d_x)
+    dh.dh_check_recip(d_x, y_nr, y_div)
+    a, b = host(y_nr), host(y_div)
+    ulp = np.abs(a.view(np.int64) - b.view(np.int64))
+    assert ulp.max() <= 1, ulp.max()
+    assert np.array_equal(b, 1.0 / x)

@@ -1,0 +1,230 @@
+"""GPU parity of the SRHD path: prim2con, con2prim (plain and MLP-seeded Newton),
+the FV stage with SRHD fluxes, and the MLP forward/backward/Adam kernels, against
+the FP64 oracle.  con2prim tolerance: 1e-10 relative; status arrays bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import assert_parity, dev, host, require_cuda
+from helpers import arena, single_level, voxel_mask
+from paper_2608_19273_gb300 import dh, synth
+from test_oracle_srhd import iid_prims
+
+pytestmark = pytest.mark.gpu
+G = 5.0 / 3.0
+
+
+def _flat_c2p(torch, cons, p_prev=None, mlp=None):
+    n = cons.shape[1]
+    d_cons = dev(torch, cons)
+    prim = torch.zeros_like(d_cons)
+    status = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    iters = torch.zeros(n, dtype=torch.int32, device="cuda")
+    fails = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dh.con2prim_flat(d_cons, prim, n, n, dev(torch, p_prev) if p_prev is not None else None,
+                     dev(torch, mlp) if mlp is not None else None, G, 1e-12, 50, status, iters, fails)
+    torch.cuda.synchronize()
+    return host(prim), host(status), host(iters), int(host(fails)[0])
+
+
+def test_prim2con_gpu_matches_oracle(orc):
+    torch = require_cuda()
+    for pde, mesh in ((synth.PDE_SRHD3D, single_level((2, 2, 2), 8, 1 / 16)),
+                      (synth.PDE_EULER3D, synth.euler3d_amr_mesh(scale=8))):
+        if pde == synth.PDE_SRHD3D:
+            prim = arena(mesh, 5)
+            m = voxel_mask(mesh)
+            prim[:, m] = iid_prims(int(m.sum()), 11)
+        else:
+            prim = synth.euler_prims(mesh, 3)
+        ref = orc.prim2con(pde, prim, mesh.var_stride)
+        with dh.Plan(pde, 3, mesh.patches, 1, mesh.var_stride) as plan:
+            out = torch.zeros(ref.shape, dtype=torch.float64, device="cuda")
+            dh.dh_prim2con(plan, dev(torch, prim), out)
+            got = host(out)
+        assert_parity(got, ref, voxel_mask(mesh), tol=1e-14, what=f"prim2con pde {pde}")
+
+
+@pytest.mark.parametrize("warm", [False, True])
+def test_con2prim_plain(orc, warm):
+    torch = require_cuda()
+    w = iid_prims(50000, 21)
+    n = w.shape[1]
+    cons = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    p_prev = w[4] * (1 + 1e-6) if warm else None
+    ref, st_ref, it_ref, f_ref = orc.con2prim(cons, n, p_prev=p_prev)
+    got, st, it, f = _flat_c2p(torch, cons, p_prev)
+    assert np.array_equal(st, st_ref) and f == f_ref == 0
+    assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what="con2prim")
+    assert_parity(got, w, np.ones(n, dtype=bool), tol=1e-10, what="round trip")
+    assert abs(it.mean() - it_ref.mean()) < 0.05 * it_ref.mean()
+
+
+def test_con2prim_unphysical_reports(orc):
+    torch = require_cuda()
+    cons = np.zeros((5, 4))
+    cons[:, 0] = [1.0, 50.0, 0.0, 0.0, 0.1]
+    cons[:, 1] = [1.0, 0.1, 0.0, 0.0, 2.0]
+    cons[:, 2] = [1.0, 0.0, 0.0, 0.0, -5.0]
+    cons[:, 3] = [1.0, 0.0, 0.0, 0.0, float("nan")]
+    _, st_ref, _, f_ref = orc.con2prim(cons, 4)
+    _, st, _, f = _flat_c2p(torch, cons)
+    assert np.array_equal(st, st_ref)
+    assert f == f_ref and f >= 2 and st[1] == 0
+
+
+def _random_mlp(rng):
+    w = np.zeros(1224, dtype=np.float32)
+    w[:1217] = rng.normal(scale=0.4, size=1217)
+    w[1217:1220] = [0.3, 0.4, 0.8]
+    w[1220:1223] = [0.2, 0.25, 0.6]
+    return w
+
+
+def test_mlp_forward_and_gradient_vs_oracle(orc):
+    torch = require_cuda()
+    rng = np.random.default_rng(7)
+    w = _random_mlp(rng)
+    n = 4000
+    xraw = rng.uniform([0.0, 0.05, 0.0], [1.0, 1.0, 2.5], size=(n, 3)).astype(np.float32)
+    t = rng.normal(size=n).astype(np.float32)
+    xn = (xraw.astype(np.float64) - w[1217:1220].astype(np.float64)) / w[1220:1223].astype(np.float64)
+    xn = xn.astype(np.float32).astype(np.float64)
+    y_ref = orc.mlp_forward(w[:1217].astype(np.float64), xn)
+    d_w, d_x, d_t = dev(torch, w), dev(torch, xraw), dev(torch, t)
+    y = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dh.dh_mlp_forward(d_w, d_x, n, y)
+    assert np.max(np.abs(host(y) - y_ref)) < 2e-5 * max(1.0, np.max(np.abs(y_ref)))
+    loss_ref, g_ref = orc.mlp_loss_grad(w[:1217].astype(np.float64), xn, t.astype(np.float64))
+    part = torch.zeros(((n + 63) // 64) * 1224, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(1224, dtype=torch.float32, device="cuda")
+    dh.dh_mlp_grad(d_w, d_x, d_t, 0, n, part, grad)
+    g = host(grad)
+    assert abs(g[1217] - loss_ref) <= 1e-5 * loss_ref
+    for lo, hi in ((0, 96), (96, 128), (128, 1152), (1152, 1184), (1184, 1216), (1216, 1217)):
+        err = np.linalg.norm(g[lo:hi] - g_ref[lo:hi]) / max(np.linalg.norm(g_ref[lo:hi]), 1e-30)
+        assert err <= 1e-4, (lo, hi, err)
+    # determinism: the same call gives bitwise the same gradient
+    grad2 = torch.zeros_like(grad)
+    dh.dh_mlp_grad(d_w, d_x, d_t, 0, n, part, grad2)
+    assert torch.equal(grad, grad2)
+
+
+def test_mlp_adam_vs_oracle(orc):
+    torch = require_cuda()
+    rng = np.random.default_rng(8)
+    w = rng.normal(size=1224).astype(np.float32)
+    g = rng.normal(size=1224).astype(np.float32)
+    m = (0.1 * rng.normal(size=1224)).astype(np.float32)
+    v = np.abs(0.1 * rng.normal(size=1224)).astype(np.float32)
+    wr, mr, vr = w[:1217].astype(np.float64), m[:1217].astype(np.float64), v[:1217].astype(np.float64)
+    orc.adam(wr, mr, vr, g[:1217].astype(np.float64), 5)
+    d_w, d_m, d_v = dev(torch, w), dev(torch, m), dev(torch, v)
+    dh.dh_mlp_adam(d_w, d_m, d_v, dev(torch, g), 5)
+    assert np.max(np.abs(host(d_w)[:1217] - wr)) < 1e-6
+    assert np.max(np.abs(host(d_m)[:1217] - mr)) < 1e-6
+
+
+def train_seed_mlp(torch, orc, n=1_000_000, steps=6000, seed=260819276):
+    """Train the seed network on n oracle prim2con pairs with the library kernels."""
+    w_prim = iid_prims(n, seed)
+    cons = orc.prim2con(synth.PDE_SRHD3D, w_prim, n)
+    d_cons = dev(torch, cons)
+    d_p = dev(torch, np.ascontiguousarray(w_prim[4]))
+    x = torch.zeros(n * 3, dtype=torch.float32, device="cuda")
+    y = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dh.dh_mlp_features(d_cons, d_p, n, n, x, y)
+    rng = np.random.default_rng(seed)
+    w = np.zeros(1224, dtype=np.float32)
+    # Xavier (Glorot) uniform initial weights, zero biases
+    for off, fan_in, fan_out in ((0, 3, 32), (128, 32, 32), (1184, 32, 1)):
+        lim = math.sqrt(6.0 / (fan_in + fan_out))
+        w[off:off + fan_in * fan_out] = rng.uniform(-lim, lim, fan_in * fan_out)
+    d_w = dev(torch, w)
+    scratch = torch.zeros(6 * 1024, dtype=torch.float64, device="cuda")
+    dh.dh_mlp_standardize(x, n, d_w, scratch)
+    m = torch.zeros(1224, dtype=torch.float32, device="cuda")
+    v = torch.zeros(1224, dtype=torch.float32, device="cuda")
+    B = 4096
+    part = torch.zeros((B // 64) * 1224, dtype=torch.float32, device="cuda")
+    grad = torch.zeros(1224, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    dh.dh_mlp_train(d_w, m, v, x, y, n, B, steps, 0, 1e-3, part, grad, loss)
+    torch.cuda.synchronize()
+    return host(d_w), host(loss)
+
+
+def test_mlp_training_and_seeded_newton(orc):
+    """Train on oracle pairs; the learned seed must converge to the oracle's answer and
+    need fewer Newton iterations than the cold plain seed on i.i.d. states."""
+    torch = require_cuda()
+    w, loss = train_seed_mlp(torch, orc, n=200_000, steps=3000)
+    assert loss[-100:].mean() < 0.1 * loss[:20].mean()
+    held = iid_prims(20000, 99)
+    n = held.shape[1]
+    cons = orc.prim2con(synth.PDE_SRHD3D, held, n)
+    ref, st_ref, it_ref, _ = orc.con2prim(cons, n, mlp=w)
+    got, st, it, f = _flat_c2p(torch, cons, mlp=w)
+    assert f == 0
+    assert np.array_equal(st, st_ref)
+    assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what="mlp-seeded con2prim")
+    _, _, it_cold, _ = _flat_c2p(torch, cons)
+    assert it.mean() < it_cold.mean()
+
+
+def test_srhd_fv_stage_and_rk3(orc):
+    torch = require_cuda()
+    w = synth.workload("srhd3d", scale=8)
+    mesh = w.mesh
+    m = voxel_mask(mesh)
+    prim = arena(mesh, 5)
+    prim[:, m] = iid_prims(int(m.sum()), 5, wmax=3.0)  # rough data exercises every flux term
+    X = synth.voxel_centres(mesh)
+    rng = np.random.default_rng(6)
+    prim[0] = np.exp(synth.fourier_field(rng, X, [1, 1, 1], 3, 0.0, 1.0))
+    prim[4] = np.exp(synth.fourier_field(rng, X, [1, 1, 1], 3, 0.0, 1.0))
+    for a in range(3):
+        prim[1 + a] = synth.fourier_field(rng, X, [1, 1, 1], 3, 0.0, 0.5)
+    cons = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
+    dt = 1e-3
+    ref = np.zeros_like(cons)
+    orc.stage(0, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, cons, out=ref, mat=prim, dt=dt,
+              params=w.params)
+    lam_ref = orc.max_wave_speed(synth.PDE_SRHD3D, 3, mesh.patches, mesh.var_stride, cons, mat=prim,
+                                 params=w.params)
+    with dh.Plan(synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, w.params) as plan:
+        d_cons, d_prim = dev(torch, cons), dev(torch, prim)
+        out = torch.zeros_like(d_cons)
+        d_dt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dh.patch_update_fv(plan, d_cons, None, out, None, d_prim, d_dt, 0, 1, 1, 0)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, d_cons, d_prim, lam)
+        got = host(out)
+        assert_parity(got, ref, m, what="srhd stage")
+        assert abs(float(host(lam)[0]) - lam_ref) <= 1e-14 * lam_ref
+        # one SSP-RK3 step with con2prim (warm seed) before every stage, both sides
+        q_o = cons.copy()
+        u1_o, u2_o = np.zeros_like(cons), np.zeros_like(cons)
+        pr_o = prim.copy()
+
+        def c2p_o(q, pr):
+            p2, st, _, fl = orc.con2prim(q, mesh.var_stride, n=mesh.var_stride, p_prev=np.ascontiguousarray(pr[4]))
+            assert np.all(st[m] == 0)
+            return p2
+        for (qs, q0, out_o, a, b, g) in ((q_o, None, u1_o, 0, 1, 1), (u1_o, q_o, u2_o, 0.75, 0.25, 0.25),
+                                         (u2_o, q_o, q_o, 1 / 3, 2 / 3, 2 / 3)):
+            pr_o[:, m] = c2p_o(qs, pr_o)[:, m]
+            orc.stage(0, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, qs, q0=q0, out=out_o, mat=pr_o,
+                      dt=dt, a=a, b=b, g=g, params=w.params)
+        Q = dev(torch, cons)
+        U1, U2, PR, PR2 = torch.zeros_like(Q), torch.zeros_like(Q), dev(torch, prim), torch.zeros_like(Q)
+        fails = torch.zeros(1, dtype=torch.int32, device="cuda")
+        for (qs, q0, o, a, b, g) in ((Q, None, U1, 0, 1, 1), (U1, Q, U2, 0.75, 0.25, 0.25),
+                                     (U2, Q, Q, 1 / 3, 2 / 3, 2 / 3)):
+            dh.con2prim(plan, qs, PR2, PR[4], None, 1e-12, 50, None, None, fails)
+            PR.copy_(PR2)
+            dh.patch_update_fv(plan, qs, q0, o, None, PR, d_dt, a, b, g, 0)
+        got = host(Q)
+        assert int(host(fails)[0]) == 0
+    assert_parity(got, q_o, m, tol=1e-10, what="srhd SSP-RK3 step")
