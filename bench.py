@@ -1,25 +1,30 @@
 #!/usr/bin/env python3
 """Benchmark of the batched explicit patch update on GB300.
 
-Workload: 3D compressible Euler (5 variables, gamma = 1.4), first-order FV
-with the Rusanov flux and SSP-RK3, on the AMR-like patch mix
-4096 x 8^3 + 1024 x 16^3 + 128 x 32^3 voxels (10,485,760 voxels, halo 1),
+Default workload (the headline line): 3D compressible Euler (5 variables,
+gamma = 1.4), first-order FV with the Rusanov flux and SSP-RK3 on the AMR-like
+patch mix 4096 x 8^3 + 1024 x 16^3 + 128 x 32^3 (10,485,760 voxels, halo 1),
 seeded smooth Fourier-mode initial data.  One benchmark step is one replay of
-a CUDA graph of 100 time steps; each time step is the device-side CFL time
-step (CFL 0.4) followed by three batched stage launches (one per SSP-RK3
-stage).  Metric: FP64 cell-updates per second (voxels x time steps / s).
+a CUDA graph of 100 time steps; a time step is the device-side CFL time step
+(CFL 0.4) plus three batched stage launches (one per SSP-RK3 stage).
+Metric: FP64 cell-updates per second (voxels x time steps / s).  The line
+also carries the learned-seed vs plain con2prim comparison at 1e-12.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload euler3d|euler2d|wave3d|srhd3d|gw59]
 
---impl reference times the FP64 CPU oracle (the plain C++ implementation the
-CUDA path is checked against) on the host cores: a deliberately slow
-baseline, not a target.  Under torchrun every rank runs an independent
-replica (the patch update of one rank needs no data from another).
+The other workloads (2D Euler forward Euler; wave system FD4+KO RK4; SRHD
+FV + con2prim SSP-RK3; 59-unknown GW59 FD4+KO RK4) print the same line for
+their own configuration.  --impl reference times the FP64 CPU oracle (the
+plain C++ implementation the CUDA path is checked against) on the host
+cores: a deliberately slow baseline, not a target.  Under torchrun every rank
+runs an independent replica of the workload.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -36,9 +41,32 @@ from paper_2608_19273_gb300 import synth  # noqa: E402
 
 METRIC = "FP64 cell-updates/s + % of roofline; learned-seed vs plain con2prim at 1e-12"
 UNIT = "cell-updates/s"
-INNER_STEPS = 100
-CFL = 0.4
 FLOPS_FILE = os.path.join(ROOT, "oracle", "flop_counts.json")
+
+# name: pde, scheme (0 FV, 1 FD), rk, time steps per graph replay, CFL, flop-count key,
+# algorithmic bytes per voxel-step (state reads and writes of all stages, materials,
+# RK4 accumulator copies, SRHD primitive reads/writes), description
+WORKLOADS = {
+    "euler3d": dict(pde=3, scheme=0, rk=3, inner=100, cfl=0.4, flops="fv/euler3d/ssprk3_step", bytes=320,
+                    kernel="k_fv_stage<Euler3D>",
+                    desc="3D Euler (5 vars, gamma 1.4), FV Rusanov, SSP-RK3; 4096x8^3 + 1024x16^3 + 128x32^3 "
+                         "patches, halo 1"),
+    "euler2d": dict(pde=2, scheme=0, rk=1, inner=10, cfl=0.4, flops="fv/euler2d/fe_step", bytes=128,
+                    kernel="k_fv_stage<Euler2D>",
+                    desc="2D Euler (4 vars), FV Rusanov, forward Euler; 64 patches of 16^2, halo 1"),
+    "wave3d": dict(pde=4, scheme=1, rk=4, inner=10, cfl=0.25, flops="fd/wave3d/rk4_step", bytes=872,
+                   kernel="k_fd_stage<Wave>",
+                   desc="first-order wave system with c(x) in [0.5, 2], FD4 + KO sigma 0.1, RK4; 2048 patches of "
+                        "16^3, halo 3"),
+    "srhd3d": dict(pde=5, scheme=0, rk=3, inner=10, cfl=0.4, flops="fv/srhd3d/ssprk3_step", bytes=1040,
+                   kernel="k_fv_stage<SRHD> + k_con2prim",
+                   desc="3D SRHD (Gamma 5/3), FV Rusanov + per-voxel con2prim Newton (tol 1e-12), SSP-RK3; "
+                        "4096 patches of 16^3, halo 1"),
+    "gw59": dict(pde=6, scheme=1, rk=4, inner=5, cfl=0.25, flops="fd/gw59/rk4_step", bytes=9912,
+                 kernel="k_fd_stage<GW59>",
+                 desc="59-unknown GW stand-in, FD4 + KO sigma 0.1, RK4; 512x24^3 + 1728x16^3 + 4096x16^3 patches "
+                      "(3 levels), halo 3"),
+}
 
 
 def parse_args():
@@ -47,8 +75,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="euler3d")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-con2prim", action="store_true", help="skip the con2prim seed comparison")
     return ap.parse_args()
 
 
@@ -56,12 +86,29 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload_config(mesh):
-    return {"workload": "euler3d_fv_rusanov_ssprk3_amr_mix", "pde": "3D Euler (5 vars, gamma 1.4)",
-            "patches": "4096x8^3 + 1024x16^3 + 128x32^3", "voxels": mesh.nvox, "halo": 1,
-            "time_steps_per_step": INNER_STEPS, "rk": "SSP-RK3", "cfl": CFL, "cuda_graph": True,
-            "l2": "no flush: each state array (420 MB) is larger than L2 (129 MB)",
-            "seed": synth.SEED_BASE + 1}
+def workload_config(name, w, mesh):
+    spec = WORKLOADS[name]
+    return {"workload": name, "description": spec["desc"], "voxels": mesh.nvox, "patches": int(mesh.K),
+            "time_steps_per_step": spec["inner"], "cfl": spec["cfl"], "cuda_graph": True,
+            "l2": "no flush: every state array is larger than L2 (129 MB)" if mesh.nvox * 40 > 129e6
+            else "state fits in L2 (small workload)",
+            "seed": int(w.seed)}
+
+
+# ------------------------------------------------------------------ inputs
+def host_inputs(name, w):
+    """(prim or cons on host, material on host or None, kind) of the workload."""
+    mesh = w.mesh
+    if name in ("euler3d", "euler2d"):
+        return synth.euler_prims(mesh, w.seed), None, "prim"
+    if name == "wave3d":
+        q, mat = synth.wave_initial(mesh, w.seed)
+        return q, mat, "cons"
+    if name == "srhd3d":
+        return synth.srhd_initial(mesh, w.seed), None, "prim"
+    if name == "gw59":
+        return synth.gw59_initial(mesh, w.seed), None, "cons"
+    raise KeyError(name)
 
 
 # ------------------------------------------------------------------ clocks
@@ -122,56 +169,95 @@ class ClockSampler:
 
 def gpu_id_for_smi(torch, dev):
     try:
-        u = torch.cuda.get_device_properties(dev).uuid
-        s = str(u)
+        s = str(torch.cuda.get_device_properties(dev).uuid)
         return s if s.startswith("GPU-") else "GPU-" + s
     except Exception:
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-        first = vis.split(",")[dev] if vis else str(dev)
-        return first
+        return vis.split(",")[dev] if vis else str(dev)
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_rate(mesh, prim, budget_s, threads=0):
-    """Oracle SSP-RK3 steps on the full workload for about budget_s seconds (at least one step)."""
+def oracle_step(name, w, mesh, q, mat, prim):
+    """One time step of the oracle on the given mesh (q, prim updated in place)."""
     import oracle
-    cores = oracle.num_threads(threads)
-    q = oracle.prim2con(synth.PDE_EULER3D, prim, mesh.var_stride)
+    spec = WORKLOADS[name]
+    if name == "srhd3d":
+        # con2prim before every stage, warm-started from the previous primitives
+        vs = mesh.var_stride
+        pr, _, _, _ = oracle.con2prim(q, vs, p_prev=np.ascontiguousarray(prim[4]))
+        prim[:] = pr
+        lam = oracle.max_wave_speed(5, 3, mesh.patches, vs, q, mat=prim, params=w.params)
+        dt = oracle.cfl_dt(spec["cfl"], float(mesh.patches["dx"].min()), 3, lam)
+        u1, u2 = np.zeros_like(q), np.zeros_like(q)
+        for qs, q0, out, a, b, g in ((q, None, u1, 0, 1, 1), (u1, q, u2, 0.75, 0.25, 0.25),
+                                     (u2, q, q, 1 / 3, 2 / 3, 2 / 3)):
+            if qs is not q:
+                pr, _, _, _ = oracle.con2prim(qs, vs, p_prev=np.ascontiguousarray(prim[4]))
+                prim[:] = pr
+            oracle.stage(0, 5, 3, mesh.patches, 1, vs, qs, q0=q0, out=out, mat=prim, dt=dt, a=a, b=b, g=g,
+                         params=w.params)
+        return
+    oracle.rk_steps(spec["scheme"], spec["pde"], mesh.dim, mesh.patches, w.halo, mesh.var_stride, q, mat=mat,
+                    rk=spec["rk"], steps=1, cfl=spec["cfl"], sigma=0.1, params=w.params)
+
+
+def oracle_sample(name, budget_s):
+    """The oracle on a bounded sample of the workload: the full mesh when it is small enough,
+    else the same patch sizes with fewer patches per level (scaled box)."""
+    import oracle
+    cores = oracle.num_threads(0)
+    scale = {"euler3d": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
+    w = synth.workload(name, scale=scale)
+    mesh = w.mesh
+    h, mat, kind = host_inputs(name, w)
+    prim = None
+    if name == "srhd3d":
+        prim = h.copy()
+        q = oracle.prim2con(5, h, mesh.var_stride, params=w.params)
+    elif kind == "prim":
+        q = oracle.prim2con(WORKLOADS[name]["pde"], h, mesh.var_stride, params=w.params)
+    else:
+        q = h
     steps, t0 = 0, time.perf_counter()
     while True:
-        oracle.rk_steps(0, synth.PDE_EULER3D, 3, mesh.patches, 1, mesh.var_stride, q, rk=3, steps=1, cfl=CFL)
+        oracle_step(name, w, mesh, q, mat, prim)
         steps += 1
         el = time.perf_counter() - t0
         if el >= budget_s or el / steps * (steps + 1) > 2.5 * budget_s:
             break
-    return mesh.nvox * steps / el, cores, steps, el
+    sample = (f"{steps} full time step(s) of the {'whole' if scale == 1 else f'1/{scale**3} (box scaled 1/{scale} per axis)'} "
+              f"workload ({mesh.nvox} voxels) in {el:.1f} s, OpenMP over patches")
+    return mesh.nvox * steps / el, cores, sample, el / steps
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
-    w = synth.workload("euler3d")
-    mesh = w.mesh
-    prim = synth.euler_prims(mesh, w.seed)
+    name = args.workload
     import oracle
     cores = oracle.num_threads(0)
-    q = oracle.prim2con(synth.PDE_EULER3D, prim, mesh.var_stride)
+    scale = {"euler3d": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
+    w = synth.workload(name, scale=scale)
+    mesh = w.mesh
+    h, mat, kind = host_inputs(name, w)
+    prim = h.copy() if name == "srhd3d" else None
+    q = oracle.prim2con(WORKLOADS[name]["pde"], h, mesh.var_stride, params=w.params) if kind == "prim" else h
     for _ in range(args.warmup):
-        oracle.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, q, rk=3, steps=1, cfl=CFL)
+        oracle_step(name, w, mesh, q, mat, prim)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, q, rk=3, steps=1, cfl=CFL)
+        oracle_step(name, w, mesh, q, mat, prim)
     el = time.perf_counter() - t0
     value = mesh.nvox * args.steps / el
-    cfg = workload_config(mesh)
+    cfg = workload_config(name, w, mesh)
     cfg["time_steps_per_step"] = 1
+    sample = (f"one full time step per bench step of the {'whole' if scale == 1 else f'1/{scale**3}'} workload "
+              f"({mesh.nvox} voxels), OpenMP over patches")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": cfg,
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"one full SSP-RK3 time step of the whole workload per bench step "
-                                       f"({mesh.nvox} voxels), OpenMP over patches"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -194,6 +280,103 @@ def measure_fp64_peak(torch, dh, stream, sms):
     return 16.0 * iters * n / (best * 1e-3) / 1e12  # TFLOP/s
 
 
+def train_seed(torch, dh, stream, n=1 << 20, steps=6000, seed=synth.SEED_BASE + 3):
+    """Train the con2prim seed MLP on n (conserved, pressure) pairs with the library's kernels.
+    The pairs come from the library's prim2con kernel on i.i.d. primitives (the tests pin that
+    kernel, and the training itself, to the oracle's prim2con)."""
+    from paper_2608_19273_gb300 import dh as _dh  # noqa: F401
+    mesh = synth.make_mesh([synth.Level((8, 8, 4), 16, 1.0 / 256, 0)], dim=3)
+    prim = synth.srhd_iid_prims(mesh.var_stride, seed)
+    plan = dh.Plan(5, 3, mesh.patches, 1, mesh.var_stride)
+    d_prim = torch.from_numpy(prim).to("cuda")
+    cons = torch.empty_like(d_prim)
+    dh.dh_prim2con(plan, d_prim, cons, stream)
+    n = mesh.var_stride
+    x = torch.empty(n * 3, dtype=torch.float32, device="cuda")
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    dh.dh_mlp_features(cons, d_prim[4], n, n, x, y, stream)
+    rng = np.random.default_rng(seed)
+    w = np.zeros(1224, dtype=np.float32)
+    for off, fi, fo in ((0, 3, 32), (128, 32, 32), (1184, 32, 1)):
+        lim = math.sqrt(6.0 / (fi + fo))
+        w[off:off + fi * fo] = rng.uniform(-lim, lim, fi * fo)
+    d_w = torch.from_numpy(w).to("cuda")
+    scratch = torch.zeros(6 * 1024, dtype=torch.float64, device="cuda")
+    dh.dh_mlp_standardize(x, n, d_w, scratch, stream)
+    m, v = torch.zeros(1224, device="cuda"), torch.zeros(1224, device="cuda")
+    B = 4096
+    part = torch.zeros((B // 64) * 1224, device="cuda")
+    grad = torch.zeros(1224, device="cuda")
+    loss = torch.zeros(steps, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dh.dh_mlp_train(d_w, m, v, x, y, n, B, steps, 0, 1e-3, part, grad, loss, stream)
+    e1.record(stream)
+    e1.synchronize()
+    plan.close()
+    lh = loss.cpu().numpy()
+    return d_w, {"samples": n, "steps": steps, "batch": B, "train_ms": e0.elapsed_time(e1),
+                 "loss_first": float(lh[:20].mean()), "loss_last": float(lh[-100:].mean())}
+
+
+def con2prim_compare(torch, dh, stream):
+    """Plain vs MLP-seeded Newton at tol 1e-12: cold (i.i.d. states, no previous pressure)
+    and warm (the first SSP-RK3 stage of the SRHD workload, seeded by the previous pressure)."""
+    d_w, train = train_seed(torch, dh, stream)
+    res = {"tol": 1e-12, "max_iter": 50, "training": train}
+    w = synth.workload("srhd3d")
+    mesh = w.mesh
+    n = mesh.var_stride
+    plan = dh.Plan(5, 3, mesh.patches, 1, mesh.var_stride, w.params)
+
+    def run(cons, p_prev, mlp):
+        prim = torch.empty_like(cons)
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        fails = torch.zeros(1, dtype=torch.int32, device="cuda")
+        dh.con2prim(plan, cons, prim, p_prev, mlp, 1e-12, 50, None, it, fails, stream)  # warm-up
+        fails.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps = 5
+        for _ in range(reps):
+            dh.con2prim(plan, cons, prim, p_prev, mlp, 1e-12, 50, None, it, fails, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return prim, {"ns_per_voxel": ms * 1e6 / mesh.nvox, "iters_mean": float(it.double().mean().item()),
+                      "fails": int(fails.item()) // reps}
+
+    with torch.cuda.stream(stream):
+        # cold: i.i.d. primitives (rho, p log-uniform on [0.1, 10], W uniform on [1, 10])
+        prim_iid = torch.from_numpy(synth.srhd_iid_prims(n, synth.SEED_BASE + 13)).to("cuda")
+        cons = torch.empty_like(prim_iid)
+        dh.dh_prim2con(plan, prim_iid, cons, stream)
+        _, plain = run(cons, None, None)
+        _, mlp = run(cons, None, d_w)
+        res["cold_iid"] = {"voxels": mesh.nvox, "plain": plain, "mlp": mlp,
+                           "speedup": plain["ns_per_voxel"] / mlp["ns_per_voxel"]}
+        del prim_iid
+        # warm: smooth workload state after one FV stage; seed = previous pressure
+        prim0 = torch.from_numpy(synth.srhd_initial(mesh, w.seed)).to("cuda")
+        q0 = torch.empty_like(prim0)
+        dh.dh_prim2con(plan, prim0, q0, stream)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, q0, prim0, lam, stream)
+        dh.dh_cfl_dt(plan, lam, 0.4, dt, stream)
+        u1 = torch.empty_like(q0)
+        dh.patch_update_fv(plan, q0, None, u1, None, prim0, dt, 0, 1, 1, 0, None, stream)
+        p_prev = prim0[4].contiguous()
+        _, plain = run(u1, p_prev, None)
+        _, mlp = run(u1, p_prev, d_w)
+        res["warm_stage"] = {"voxels": mesh.nvox, "plain": plain, "mlp": mlp,
+                             "speedup": plain["ns_per_voxel"] / mlp["ns_per_voxel"]}
+    plan.close()
+    res["winner_cold"] = "mlp" if res["cold_iid"]["speedup"] > 1 else "plain"
+    res["winner_warm"] = "mlp" if res["warm_stage"]["speedup"] > 1 else "plain"
+    return res
+
+
 def our_arm(args, rank, world, local_rank):
     import torch
     from paper_2608_19273_gb300 import dh
@@ -204,30 +387,45 @@ def our_arm(args, rank, world, local_rank):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    name = args.workload
+    spec = WORKLOADS[name]
     dev = torch.cuda.current_device()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    w = synth.workload("euler3d")
+    w = synth.workload(name)
     mesh = w.mesh
-    prim = synth.euler_prims(mesh, w.seed)
+    h, h_mat, kind = host_inputs(name, w)
     stream = torch.cuda.Stream()
+    srhd = name == "srhd3d"
     with torch.cuda.stream(stream):
-        plan = dh.Plan(synth.PDE_EULER3D, 3, mesh.patches, 1, mesh.var_stride)
-        d_prim = torch.from_numpy(prim).to("cuda")
-        Q = torch.empty_like(d_prim)
-        dh.dh_prim2con(plan, d_prim, Q, stream)
-        del d_prim
-        U1, U2 = torch.empty_like(Q), torch.empty_like(Q)
+        plan = dh.Plan(spec["pde"], mesh.dim, mesh.patches, w.halo, mesh.var_stride, w.params)
+        d_h = torch.from_numpy(h).to("cuda")
+        if kind == "prim":
+            Q = torch.empty_like(d_h)
+            dh.dh_prim2con(plan, d_h, Q, stream)
+        else:
+            Q = d_h
+        mat = d_h if srhd else (torch.from_numpy(h_mat).to("cuda") if h_mat is not None else None)
+        if not srhd and kind == "prim":
+            del d_h
+        U1 = torch.empty_like(Q)
+        U2 = torch.empty_like(Q) if spec["rk"] >= 3 else None
+        ACC = torch.empty_like(Q) if spec["rk"] == 4 else None
         lam = torch.zeros(1, dtype=torch.float64, device="cuda")
         dt = torch.zeros(1, dtype=torch.float64, device="cuda")
         Q_init = Q.clone()
-        dh.max_wave_speed(plan, Q, None, lam, stream)
+        M_init = mat.clone() if mat is not None else None
+        dh.max_wave_speed(plan, Q, mat, lam, stream)
         lam_init = lam.clone()
         # eager warm-up step (sets kernel attributes outside of capture), then reset
-        dh.dh_rk_step(plan, 0, 3, Q, U1, U2, None, None, dt, lam, CFL, 0.1, stream)
+        dh.dh_rk_step(plan, spec["scheme"], spec["rk"], Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1, stream)
         Q.copy_(Q_init)
         lam.copy_(lam_init)
+        if mat is not None:
+            mat.copy_(M_init)
         stream.synchronize()
-        dh.dh_graph_capture(plan, 0, 3, INNER_STEPS, Q, U1, U2, None, None, dt, lam, CFL, 0.1, True, stream)
+        inner = spec["inner"]
+        dh.dh_graph_capture(plan, spec["scheme"], spec["rk"], inner, Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1,
+                            True, stream)
         n_kernels, n_timed = dh.dh_graph_info(plan)
         peak = measure_fp64_peak(torch, dh, stream, sms)
         for _ in range(args.warmup):
@@ -256,62 +454,72 @@ def our_arm(args, rank, world, local_rank):
             dist.barrier()
         finite = bool(torch.isfinite(Q).all().item())
 
-        # end-to-end through the public API with host buffers: H2D of the state,
-        # one graph replay (100 time steps), D2H of the result, every step
+        # end-to-end through the public API with host buffers: every step copies the
+        # state (and material/primitive arena) in from pinned host memory, replays the
+        # graph, and copies the resulting state back
         h_in = torch.empty(Q.shape, dtype=torch.float64, pin_memory=True)
         h_in.copy_(Q_init)
+        h_m = None
+        if mat is not None:
+            h_m = torch.empty(mat.shape, dtype=torch.float64, pin_memory=True)
+            h_m.copy_(M_init)
         h_out = torch.empty_like(h_in, pin_memory=True)
         n_e2e = max(2, args.steps // 2)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t_host = time.perf_counter()
         f0.record(stream)
         for _ in range(n_e2e):
             Q.copy_(h_in, non_blocking=True)
-            dh.max_wave_speed(plan, Q, None, lam, stream)
+            if mat is not None:
+                mat.copy_(h_m, non_blocking=True)
+            dh.max_wave_speed(plan, Q, mat, lam, stream)
             dh.dh_graph_launch(plan, stream)
             h_out.copy_(Q, non_blocking=True)
         f1.record(stream)
         f1.synchronize()
-        t_host = time.perf_counter() - t_host
         e2e_ms = f0.elapsed_time(f1)
+        h2d = int(Q.numel() * 8 + (mat.numel() * 8 if mat is not None else 0))
 
     nvox = mesh.nvox
-    value = world * nvox * INNER_STEPS * args.steps / (ms * 1e-3)
-    flops_voxel_step = json.load(open(FLOPS_FILE))["fv/euler3d/ssprk3_step"]["flops_per_voxel"]
-    # dominant kernel: the FV stage; average over the 3 x 100 stage launches of the last replay
-    ach = flops_voxel_step * nvox * INNER_STEPS / (float(stage_ms.sum()) * 1e-3) / 1e12
+    value = world * nvox * inner * args.steps / (ms * 1e-3)
+    flops_vs = json.load(open(FLOPS_FILE))[spec["flops"]]["flops_per_voxel"]
+    stage_sum_s = float(stage_ms.sum()) * 1e-3
+    ach = flops_vs * nvox * inner / stage_sum_s / 1e12
     stage_share = float(stage_ms.sum()) / (ms / args.steps)
+    hbm = 6701.5
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        hbm = float(json.load(open(mp)).get("hbm_gbs", hbm))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(mesh), parallelism="replicas" if world > 1 else "single-gpu"),
-        "roofline": {"bound": "alu", "kernel": "k_fv_stage<Euler3D>", "achieved": ach,
-                     "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                     "peak_source": "FP64 FMA peak measured live by dh_probe_dfma on this GPU",
-                     "flops_per_voxel_step": flops_voxel_step,
-                     "stage_ms_mean": float(stage_ms.mean()), "stage_share_of_step": stage_share,
-                     "hbm_bound_frac": None},
-        "e2e": {"value": world * nvox * INNER_STEPS * n_e2e / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(Q.numel() * 8), "d2h_bytes_per_step": int(Q.numel() * 8),
-                "host_wall_s": t_host},
+        "config": dict(workload_config(name, w, mesh), parallelism="replicas" if world > 1 else "single-gpu"),
+        "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": None,
+                     "peak_source": "FP64 FMA peak measured live on this GPU (dh_probe_dfma, 2 FLOP per FMA)",
+                     "flops_per_voxel_step": flops_vs,
+                     "timed_launches": int(n_timed), "stage_ms_mean": float(stage_ms.mean()),
+                     "stage_share_of_step": stage_share,
+                     "hbm": {"bytes_per_voxel_step": spec["bytes"], "peak_gbs": hbm,
+                             "achieved_gbs": spec["bytes"] * nvox * inner / stage_sum_s / 1e9,
+                             "frac": spec["bytes"] * nvox * inner / stage_sum_s / 1e9 / hbm}},
+        "e2e": {"value": world * nvox * inner * n_e2e / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(Q.numel() * 8)},
         "gpu_launches": int(n_kernels * args.steps),
         "clocks": clocks,
         "state_finite": finite,
     }
-    # HBM side of the roofline: 320 algorithmic bytes per voxel-step (see DESIGN)
-    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs") if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6701.5
-    line["roofline"]["hbm_bound_frac"] = (320.0 * nvox * INNER_STEPS / (float(stage_ms.sum()) * 1e-3) / 1e9) / hbm
+    plan.close()
+    del Q, U1, U2, ACC, Q_init, M_init, mat
+    torch.cuda.empty_cache()
+    if rank == 0 and name in ("euler3d", "srhd3d") and not args.no_con2prim:
+        line["con2prim"] = con2prim_compare(torch, dh, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, steps, el = oracle_rate(mesh, prim, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": f"{steps} full SSP-RK3 time step(s) of the whole workload "
-                                          f"({nvox} voxels) in {el:.1f} s, OpenMP over patches"}
+        rate, cores, sample, _ = oracle_sample(name, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0

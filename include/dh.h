@@ -211,10 +211,20 @@ dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* str
  * and the last stage writes the new maximum wave speed into lam_dev, so
  * lam_dev must hold the speed of q on entry (max_wave_speed).  If cfl <= 0
  * the caller's dt_dev is used unchanged.  All buffers are N-variable arenas
- * owned by the caller; u2 is needed for rk >= 3 and acc for rk = 4. */
+ * owned by the caller; u2 is needed for rk >= 3 and acc for rk = 4.
+ * SRHD3D: mat is the primitive arena (rho, v, p) and is updated in place:
+ * before every stage con2prim recovers the primitives of the stage input,
+ * seeded by the current primitives (settings from dh_plan_set_con2prim); with
+ * cfl > 0 the step starts with con2prim(q) and max_wave_speed. */
 dh_status dh_rk_step(dh_plan* plan, int32_t scheme, int32_t rk, double* q, double* u1, double* u2, double* acc,
                      const double* mat, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
                      void* stream);
+
+/* con2prim settings used by dh_rk_step for SRHD3D: MLP seed weights (NULL:
+ * plain Newton from the previous primitives), tolerance, iteration cap and an
+ * optional device failure counter.  Defaults: NULL, 1e-12, 50, NULL. */
+dh_status dh_plan_set_con2prim(dh_plan* plan, const float* mlp_w, double tol, int32_t max_iter,
+                               int32_t* fail_count_dev);
 
 /* Capture n_steps consecutive dh_rk_step calls (same arguments) into one CUDA
  * graph owned by the plan (replacing any previous one); nothing runs during

@@ -28,6 +28,9 @@ def _state(pde, dim, p, seed=3):
         q = oracle.prim2con(pde, prim, mesh.var_stride)[:, :n]
         return np.ascontiguousarray(q), None
     rng = np.random.default_rng(seed)
+    if pde == synth.PDE_SRHD3D:
+        prim = synth.srhd_iid_prims(n, seed, wmax=3.0)
+        return oracle.prim2con(pde, prim, n), prim
     if pde == synth.PDE_WAVE3D:
         return rng.normal(size=(5, n)), np.full((1, n), 1.3)
     if pde == synth.PDE_GW59:
@@ -59,6 +62,7 @@ def main():
         "fv/euler3d/stage_fe": (0, synth.PDE_EULER3D, 3, 1, 0, False),
         "fv/euler2d/fe_step": (0, synth.PDE_EULER2D, 2, 1, 1, True),
         "fd/wave3d/rk4_step": (1, synth.PDE_WAVE3D, 3, 3, 4, True),
+        "fv/srhd3d/ssprk3_step": (0, synth.PDE_SRHD3D, 3, 1, 3, False),
         "fd/gw59/rk4_step": (1, synth.PDE_GW59, 3, 3, 4, True),
     }.items():
         A, B, C, c = per_voxel(*args)

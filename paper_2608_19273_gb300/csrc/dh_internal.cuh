@@ -58,6 +58,11 @@ struct dh_plan {
   // reduction scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter
   unsigned long long* d_red = nullptr;
   int num_sms = 0;
+  // con2prim settings used by dh_rk_step for SRHD3D
+  const float* c2p_mlp = nullptr;
+  double c2p_tol = 1e-12;
+  int c2p_max_iter = 50;
+  int32_t* c2p_fail = nullptr;
   // captured multi-step graph and optional per-stage timing events
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<cudaEvent_t> ev_start, ev_stop;

@@ -18,6 +18,14 @@ namespace dh {
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
                             double d, double sigma, double* lam, cudaStream_t s) {
+  if (plan->pde == DH_PDE_SRHD3D) {
+    // primitives of the stage input, seeded by the previous primitives (in place)
+    double* prim = const_cast<double*>(mat);
+    dh_status st = con2prim(plan, qs, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol,
+                            plan->c2p_max_iter, nullptr, nullptr, plan->c2p_fail, s);
+    if (st != DH_OK) return st;
+    lam = nullptr;
+  }
   if (scheme == 0) return patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s);
   return patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s);
 }
@@ -48,6 +56,13 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
                          cudaStream_t s) {
   const size_t bytes = sizeof(double) * (size_t)plan->nq * (size_t)plan->var_stride;
   double* lam_last = cfl > 0 ? lam : nullptr;
+  if (cfl > 0 && plan->pde == DH_PDE_SRHD3D) {
+    // the wave speed needs the primitives of q: recover them, then take the maximum
+    double* prim = const_cast<double*>(mat);
+    DH_TRY(con2prim(plan, q, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol, plan->c2p_max_iter,
+                    nullptr, nullptr, plan->c2p_fail, s));
+    DH_TRY(max_wave_speed(plan, q, prim, lam, s));
+  }
   if (cfl > 0) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
   if (rk == 1) {
     DH_TRY(T.begin());
@@ -87,7 +102,7 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
 }
 
 static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
-                          double* dt, double* lam, double cfl) {
+                          const double* mat, double* dt, double* lam, double cfl) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
   if (scheme != 0 && scheme != 1) { set_error("scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
   if (!q || !u1 || !dt || (rk == 3 && !u2) || (rk == 4 && (!u2 || !acc))) {
@@ -95,6 +110,7 @@ static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* 
     return DH_EINVAL;
   }
   if (cfl > 0 && !lam) { set_error("dh_rk_step: cfl > 0 needs lam_dev"); return DH_EINVAL; }
+  if (plan->pde == DH_PDE_SRHD3D && !mat) { set_error("dh_rk_step: SRHD3D needs the primitive arena as mat"); return DH_EINVAL; }
   if (rk != 1 && rk != 3 && rk != 4) { set_error("dh_rk_step: rk must be 1, 3 or 4"); return DH_EINVAL; }
   return DH_OK;
 }
@@ -105,10 +121,21 @@ using namespace dh;
 
 extern "C" {
 
+dh_status dh_plan_set_con2prim(dh_plan* plan, const float* mlp_w, double tol, int32_t max_iter,
+                               int32_t* fail_count_dev) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000) { set_error("dh_plan_set_con2prim: bad tol or max_iter"); return DH_EINVAL; }
+  plan->c2p_mlp = mlp_w;
+  plan->c2p_tol = tol;
+  plan->c2p_max_iter = max_iter;
+  plan->c2p_fail = fail_count_dev;
+  return DH_OK;
+}
+
 dh_status dh_rk_step(dh_plan* plan, int32_t scheme, int32_t rk, double* q, double* u1, double* u2, double* acc,
                      const double* mat, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
                      void* stream) {
-  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, dt_dev, lam_dev, cfl));
+  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl));
   Timer T{plan, false, (cudaStream_t)stream};
   return rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, (cudaStream_t)stream);
 }
@@ -116,7 +143,7 @@ dh_status dh_rk_step(dh_plan* plan, int32_t scheme, int32_t rk, double* q, doubl
 dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_steps, double* q, double* u1,
                            double* u2, double* acc, const double* mat, double* dt_dev, double* lam_dev, double cfl,
                            double sigma_ko, int32_t timing, void* stream) {
-  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, dt_dev, lam_dev, cfl));
+  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl));
   if (n_steps <= 0 || n_steps > 100000) { set_error("dh_graph_capture: n_steps out of range"); return DH_EINVAL; }
   if (!stream) { set_error("dh_graph_capture: needs a non-default stream"); return DH_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
@@ -149,7 +176,9 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) { plan->graph_exec = nullptr; return cuda_error(e, "cudaGraphInstantiate"); }
   plan->graph_stages = timing ? stages : 0;
-  plan->graph_kernels = n_steps * ((rk == 1 ? 1 : rk) + (cfl > 0 ? 1 : 0));
+  const int nst = rk == 1 ? 1 : rk;
+  const int srhd = plan->pde == DH_PDE_SRHD3D;
+  plan->graph_kernels = n_steps * (nst * (1 + srhd) + (cfl > 0 ? 1 + 2 * srhd : 0));
   return DH_OK;
 }
 

@@ -24,7 +24,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
-           "dh_cfl_dt", "dh_prim2con", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
+           "dh_cfl_dt", "dh_prim2con", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
            "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
@@ -66,6 +66,7 @@ def lib():
         L.dh_mlp_grad.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
         L.dh_mlp_adam.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]
         L.dh_mlp_train.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, f32, vp, vp, vp, vp]
+        L.dh_plan_set_con2prim.argtypes = [vp, vp, d, i32, vp]
         L.dh_rk_step.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, vp]
         L.dh_graph_capture.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, vp]
         L.dh_graph_launch.argtypes = [vp, vp]
@@ -236,6 +237,11 @@ def dh_cfl_dt(plan, lam_dev, cfl, dt_dev, stream=None):
 
 def dh_prim2con(plan, prim, cons, stream=None):
     _check(lib().dh_prim2con(plan.handle, _ptr(prim, "prim"), _ptr(cons, "cons"), _stream(stream)), "dh_prim2con")
+
+
+def dh_plan_set_con2prim(plan, mlp_w=None, tol=1e-12, max_iter=50, fail_count_dev=None):
+    _check(lib().dh_plan_set_con2prim(plan.handle, _ptr(mlp_w, "mlp_w"), float(tol), int(max_iter),
+                                      _ptr(fail_count_dev, "fail_count")), "dh_plan_set_con2prim")
 
 
 def dh_rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko=0.1, stream=None):
