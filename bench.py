@@ -79,6 +79,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-con2prim", action="store_true", help="skip the con2prim seed comparison")
+    ap.add_argument("--scale", type=int, default=1,
+                    help="divide the patch counts per axis by this factor (small cases for profiling); 1 = full size")
     return ap.parse_args()
 
 
@@ -391,7 +393,7 @@ def our_arm(args, rank, world, local_rank):
     spec = WORKLOADS[name]
     dev = torch.cuda.current_device()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    w = synth.workload(name)
+    w = synth.workload(name, scale=args.scale)
     mesh = w.mesh
     h, h_mat, kind = host_inputs(name, w)
     stream = torch.cuda.Stream()
@@ -494,7 +496,8 @@ def our_arm(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(name, w, mesh), parallelism="replicas" if world > 1 else "single-gpu"),
+        "config": dict(workload_config(name, w, mesh), parallelism="replicas" if world > 1 else "single-gpu",
+                       scale=args.scale),
         "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": ach / peak, "traffic": None,
                      "peak_source": "FP64 FMA peak measured live on this GPU (dh_probe_dfma, 2 FLOP per FMA)",

@@ -15,20 +15,10 @@
 
 namespace dh {
 
+struct Timer;
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
-                            double d, double sigma, double* lam, cudaStream_t s) {
-  if (plan->pde == DH_PDE_SRHD3D) {
-    // primitives of the stage input, seeded by the previous primitives (in place)
-    double* prim = const_cast<double*>(mat);
-    dh_status st = con2prim(plan, qs, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol,
-                            plan->c2p_max_iter, nullptr, nullptr, plan->c2p_fail, s);
-    if (st != DH_OK) return st;
-    lam = nullptr;
-  }
-  if (scheme == 0) return patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s);
-  return patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s);
-}
+                            double d, double sigma, double* lam, Timer& T, cudaStream_t s);
 
 struct Timer {
   dh_plan* plan;
@@ -50,6 +40,23 @@ struct Timer {
 
 #define DH_TRY(x) do { dh_status _st = (x); if (_st != DH_OK) return _st; } while (0)
 
+// One stage launch, timed (when timing is on) around the stage kernel only.
+static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
+                            double* acc, const double* mat, const double* dt, double a, double b, double g,
+                            double d, double sigma, double* lam, Timer& T, cudaStream_t s) {
+  if (plan->pde == DH_PDE_SRHD3D) {
+    // primitives of the stage input, seeded by the previous primitives (in place)
+    double* prim = const_cast<double*>(mat);
+    DH_TRY(con2prim(plan, qs, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol, plan->c2p_max_iter,
+                    nullptr, nullptr, plan->c2p_fail, s));
+    lam = nullptr;
+  }
+  DH_TRY(T.begin());
+  if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
+  else DH_TRY(patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s));
+  return T.end();
+}
+
 // One time step.  bufs: q (state, in/out), u1, u2 (stage buffers), acc (RK4).
 static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
                          const double* mat, double* dt, double* lam, double cfl, double sigma, Timer& T,
@@ -65,34 +72,18 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
   }
   if (cfl > 0) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
   if (rk == 1) {
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, s));
-    DH_TRY(T.end());
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s));
     DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
   } else if (rk == 3) {
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, s));
-    DH_TRY(T.end());
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, s));
-    DH_TRY(T.end());
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, u2, q, q, nullptr, mat, dt, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, sigma, lam_last, s));
-    DH_TRY(T.end());
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, u2, q, q, nullptr, mat, dt, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, sigma, lam_last, T, s));
   } else if (rk == 4) {
     DH_TRY(cuda_error(cudaMemcpyAsync(acc, q, bytes, cudaMemcpyDeviceToDevice, s), "copy q -> acc"));
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, q, q, u1, acc, mat, dt, 1, 0, 0.5, 1.0 / 6.0, sigma, nullptr, s));
-    DH_TRY(T.end());
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 1, 0, 0.5, 1.0 / 3.0, sigma, nullptr, s));
-    DH_TRY(T.end());
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, u2, q, u1, acc, mat, dt, 1, 0, 1.0, 1.0 / 3.0, sigma, nullptr, s));
-    DH_TRY(T.end());
-    DH_TRY(T.begin());
-    DH_TRY(stage_call(plan, scheme, u1, nullptr, nullptr, acc, mat, dt, 0, 0, 0, 1.0 / 6.0, sigma, lam_last, s));
-    DH_TRY(T.end());
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 0.5, 1.0 / 6.0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 1, 0, 0.5, 1.0 / 3.0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, u2, q, u1, acc, mat, dt, 1, 0, 1.0, 1.0 / 3.0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, u1, nullptr, nullptr, acc, mat, dt, 0, 0, 0, 1.0 / 6.0, sigma, lam_last, T, s));
     DH_TRY(cuda_error(cudaMemcpyAsync(q, acc, bytes, cudaMemcpyDeviceToDevice, s), "copy acc -> q"));
   } else {
     set_error("dh_rk_step: rk must be 1, 3 or 4");
