@@ -221,6 +221,7 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
       for (int i = 0; i < 121 && 1 + i < n_params; ++i) P.C[i] = params[1 + i];
     }
   }
+  finish_params(P);
   // Tile work list: 16x16 columns for p % 16 == 0, groups of four 8x8 columns
   // (same p) otherwise; largest work first.
   std::vector<Work> work;

@@ -109,15 +109,16 @@ struct FvTile {
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       const double qL = S.Q[v * NS + Ls], qR = S.Q[v * NS + Rs];
-      dq[v] = qR - qL;
-      double h = -s * dq[v];
-      if (PDE::FLUX) h = fma(-s, dq[v], F[v * NS + Ls] + F[v * NS + Rs]);
+      dq[v] = SUB(P, qR, qL);
+      double h;
+      if (PDE::FLUX) h = fma(-s, dq[v], ADD(P, F[v * NS + Ls], F[v * NS + Rs]));
+      else h = MUL(P, -s, dq[v]);
       H[v * fstride + fidx] = h;
     }
     if (PDE::NCP) {
       double qb[NV], Dv[N];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) qb[v] = 0.5 * (S.Q[v * NS + Ls] + S.Q[v * NS + Rs]);
+      for (int v = 0; v < NV; ++v) qb[v] = MUL(P, 0.5, ADD(P, S.Q[v * NS + Ls], S.Q[v * NS + Rs]));
       PDE::ncp(d, qb, dq, P, Dv);
 #pragma unroll
       for (int v = 0; v < N; ++v) D[v * fstride + fidx] = Dv[v];
@@ -216,13 +217,13 @@ struct FvTile {
         double dq[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-          dq[v] = Qk[v] - Qm[v];
-          Hzlo[v] = PDE::FLUX ? fma(-s, dq[v], Fzm[v] + Fzk[v]) : -s * dq[v];
+          dq[v] = SUB(A.P, Qk[v], Qm[v]);
+          Hzlo[v] = PDE::FLUX ? fma(-s, dq[v], ADD(A.P, Fzm[v], Fzk[v])) : MUL(A.P, -s, dq[v]);
         }
         if (PDE::NCP) {
           double qb[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) qb[v] = 0.5 * (Qm[v] + Qk[v]);
+          for (int v = 0; v < NV; ++v) qb[v] = MUL(A.P, 0.5, ADD(A.P, Qm[v], Qk[v]));
           PDE::ncp(2, qb, dq, A.P, Dzlo);
         }
       }
@@ -260,13 +261,13 @@ struct FvTile {
         double dq[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-          dq[v] = Qn[v] - Qk[v];
-          Hzhi[v] = PDE::FLUX ? fma(-s, dq[v], Fzk[v] + Fzn[v]) : -s * dq[v];
+          dq[v] = SUB(A.P, Qn[v], Qk[v]);
+          Hzhi[v] = PDE::FLUX ? fma(-s, dq[v], ADD(A.P, Fzk[v], Fzn[v])) : MUL(A.P, -s, dq[v]);
         }
         if (PDE::NCP) {
           double qb[NV];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) qb[v] = 0.5 * (Qk[v] + Qn[v]);
+          for (int v = 0; v < NV; ++v) qb[v] = MUL(A.P, 0.5, ADD(A.P, Qk[v], Qn[v]));
           PDE::ncp(2, qb, dq, A.P, Dzhi);
         }
       }
@@ -283,16 +284,19 @@ struct FvTile {
         double res[NV];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-          double sum = (S.Hx[v * FX + fxr] - S.Hx[v * FX + fxl]) + (S.Hy[v * FY + fyu] - S.Hy[v * FY + fyl]);
-          if (DIM == 3) sum += Hzhi[v] - Hzlo[v];
+          const DevParams& P = A.P;
+          double sum = ADD(P, SUB(P, S.Hx[v * FX + fxr], S.Hx[v * FX + fxl]),
+                           SUB(P, S.Hy[v * FY + fyu], S.Hy[v * FY + fyl]));
+          if (DIM == 3) sum = ADD(P, sum, SUB(P, Hzhi[v], Hzlo[v]));
           if (PDE::NCP) {
-            double dsum = (S.Dx[v * FX + fxr] + S.Dx[v * FX + fxl]) + (S.Dy[v * FY + fyu] + S.Dy[v * FY + fyl]);
-            if (DIM == 3) dsum += Dzhi[v] + Dzlo[v];
-            sum += dsum;
+            double dsum = ADD(P, ADD(P, S.Dx[v * FX + fxr], S.Dx[v * FX + fxl]),
+                              ADD(P, S.Dy[v * FY + fyu], S.Dy[v * FY + fyl]));
+            if (DIM == 3) dsum = ADD(P, dsum, ADD(P, Dzhi[v], Dzlo[v]));
+            sum = ADD(P, sum, dsum);
           }
           const int64_t ev = v * A.vs + e;
           if (A.out) {
-            double base = b1 ? Qk[v] : A.b * Qk[v];
+            double base = b1 ? Qk[v] : MUL(P, A.b, Qk[v]);
             if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
             res[v] = PDE::SRC ? fma(gdt, fma(cL, sum, Sv[v]), base) : fma(cS, sum, base);
           }

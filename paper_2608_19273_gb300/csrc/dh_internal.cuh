@@ -11,10 +11,15 @@
 
 namespace dh {
 
-// PDE parameters passed by value to every kernel.
+// PDE parameters passed by value to every kernel.  one/mone/zero hold 1, -1
+// and 0: kernels multiply or add them in fused multiply-adds so that plain
+// adds and multiplies are issued as DFMA (see dh_pde.cuh).
 struct DevParams {
+  double one, mone, zero;
   double gamma;   // Euler ratio of specific heats
+  double gm1;     // gamma - 1
   double Gamma;   // SRHD adiabatic index
+  double Gq;      // Gamma / (Gamma - 1)
   double damp;    // wave-system damping
   double kappa;   // GW59 lapse coupling
   double C[121];  // GW59 coupling matrix, row-major
@@ -76,6 +81,15 @@ dh_status cuda_error(cudaError_t e, const char* what);
 int pde_nq(int pde);
 int pde_nm(int pde);
 int pde_dim(int pde);
+
+// Fill the derived constants of DevParams (call after setting gamma, Gamma, ...).
+inline void finish_params(DevParams& P) {
+  P.one = 1.0;
+  P.mone = -1.0;
+  P.zero = 0.0;
+  P.gm1 = P.gamma - 1.0;
+  P.Gq = P.Gamma / (P.Gamma - 1.0);
+}
 
 dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,

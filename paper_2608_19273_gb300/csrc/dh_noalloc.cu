@@ -162,6 +162,7 @@ extern "C" dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_
   P.gamma = 1.4; P.Gamma = 5.0 / 3.0; P.damp = 0.1; P.kappa = 0.1;
   std::memset(P.C, 0, sizeof(P.C));
   if (params && n_params > 0 && (pde == DH_PDE_EULER2D || pde == DH_PDE_EULER3D)) P.gamma = params[0];
+  finish_params(P);
   view.d_patches = d_patches;
   view.d_work = d_work;
   view.n_work = nw;

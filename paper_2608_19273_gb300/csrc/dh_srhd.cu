@@ -21,25 +21,27 @@
 namespace dh {
 
 // Returns iterations used (> 0) on convergence, -iterations on failure.
+// Adds and products are issued as FMAs with the run-time constants one/mone/zero
+// (GB300 runs DFMA faster than DADD/DMUL; results are bitwise the same).
 __device__ int srhd_newton_dev(double G, double D, double S2, double E, double p_lo, double p0, double tol,
-                               int max_iter, double* p_out) {
+                               int max_iter, double one, double mone, double zero, double* p_out) {
   const double gf = (G - 1.0) / G;
   double p = p0;
   for (int it = 1; it <= max_iter; ++it) {
-    const double Ep = E + p;
+    const double Ep = fma(E, one, p);
     const double rEp = 1.0 / Ep;
-    const double t = S2 * rEp;          // S^2/(E+p)
-    const double s2e = t * rEp;         // S^2/(E+p)^2
-    const double om = 1.0 - s2e;
-    const double rrt = rsqrt(om);       // 1/sqrt(1 - S^2/(E+p)^2)
-    const double rt = om * rrt;
-    const double f = fma(gf, (Ep - t) - D * rt, -p);
-    const double fp = fma(gf, 1.0 + s2e - D * s2e * rEp * rrt, -1.0);
-    double pn = p - f / fp;
+    const double t = fma(S2, rEp, zero);   // S^2/(E+p)
+    const double s2e = fma(t, rEp, zero);  // S^2/(E+p)^2
+    const double om = fma(s2e, mone, one);
+    const double rrt = rsqrt(om);          // 1/sqrt(1 - S^2/(E+p)^2)
+    const double rt = fma(om, rrt, zero);
+    const double f = fma(gf, fma(-D, rt, fma(t, mone, Ep)), -p);
+    const double fp = fma(gf, fma(-D, fma(fma(s2e, rEp, zero), rrt, zero), fma(s2e, one, one)), mone);
+    double pn = fma(-f, 1.0 / fp, p);
     if (!(pn == pn)) { *p_out = pn; return -it; }
     if (pn <= p_lo) {
-      pn = 0.5 * (p + p_lo);
-    } else if (fabs(pn - p) <= tol * pn) {
+      pn = fma(0.5, p, 0.5 * p_lo);
+    } else if (fabs(fma(pn, one, -p)) <= fma(tol, pn, zero)) {
       *p_out = pn;
       return it;
     }
@@ -61,6 +63,7 @@ struct C2PArgs {
   int32_t* fail_count;
   int64_t vs;
   double G;
+  double one, mone, zero;  // 1, -1, 0 for the FMA forms of adds and products
 };
 
 __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64_t e) {
@@ -94,13 +97,13 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
     have2 = have_prev;
   }
   double p;
-  int it1 = srhd_newton_dev(G, D, S2, E, p_lo, s1, A.tol, A.max_iter, &p);
+  int it1 = srhd_newton_dev(G, D, S2, E, p_lo, s1, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
   int total = it1 > 0 ? it1 : -it1;
   uint8_t st = 0;
   if (it1 <= 0) {
     int it2 = 0;
     if (have2) {
-      it2 = srhd_newton_dev(G, D, S2, E, p_lo, s2, A.tol, A.max_iter, &p);
+      it2 = srhd_newton_dev(G, D, S2, E, p_lo, s2, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
       total += it2 > 0 ? it2 : -it2;
     }
     if (have2 && it2 > 0) st = 1;
@@ -177,7 +180,8 @@ dh_status con2prim(dh_plan* plan, const double* cons, double* prim, const double
   if (plan->pde != DH_PDE_SRHD3D) { set_error("con2prim: the plan's PDE is not SRHD3D"); return DH_EUNSUPPORTED; }
   dh_status st = c2p_check(cons, prim, tol, max_iter);
   if (st != DH_OK) return st;
-  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, plan->var_stride, plan->params.Gamma};
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, plan->var_stride, plan->params.Gamma,
+            1.0, -1.0, 0.0};
   k_con2prim_patches<<<plan->K, 256, 0, (cudaStream_t)stream>>>(plan->d_patches, plan->dim, A);
   return cuda_error(cudaGetLastError(), "con2prim launch");
 }
@@ -189,7 +193,7 @@ dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t str
   if (st != DH_OK) return st;
   if (n <= 0 || stride < n) { set_error("con2prim_flat: need 0 < n <= stride"); return DH_EINVAL; }
   if (!(Gamma > 1.0)) { set_error("con2prim_flat: Gamma must exceed 1"); return DH_EINVAL; }
-  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, stride, Gamma};
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, stride, Gamma, 1.0, -1.0, 0.0};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
