@@ -40,6 +40,12 @@ struct FdArgs {
   DevParams P;
 };
 
+// Plain FP64 adds, subtractions and products.  (Issuing them as FMAs with
+// run-time 1/-1/0 operands, as the FV stage does, measured 7% slower here.)
+__device__ __forceinline__ double PADD(const DevParams&, double a, double b) { return a + b; }
+__device__ __forceinline__ double PSUB(const DevParams&, double a, double b) { return a - b; }
+__device__ __forceinline__ double PMUL(const DevParams&, double a, double b) { return a * b; }
+
 constexpr int FTX = 8, FTY = 8, FTZ = 4, FH = 3;
 constexpr int FBX = FTX + 2 * FH, FBY = FTY + 2 * FH, FBZ = FTZ + 2 * FH;
 constexpr int FBOX = FBX * FBY * FBZ;                                               // 1960
@@ -95,18 +101,18 @@ __device__ __forceinline__ void fd_stage_vars(const FdArgs& A, double* box, cons
 
 // 4th-order centred derivative (times 1/(12 dx)) along stride st.
 __device__ __forceinline__ double fd_d1(const DevParams& P, const double* s, int c, int st, double r12) {
-  return MUL(P, fma(8.0, SUB(P, s[c + st], s[c - st]), SUB(P, s[c - 2 * st], s[c + 2 * st])), r12);
+  return PMUL(P, fma(8.0, PSUB(P, s[c + st], s[c - st]), PSUB(P, s[c - 2 * st], s[c + 2 * st])), r12);
 }
 // Bracketed sixth difference (exactly 0 on constants).
 __device__ __forceinline__ double fd_d6(const DevParams& P, const double* s, int c, int st) {
-  const double two = MUL(P, 2.0, s[c]);
-  const double t3 = SUB(P, ADD(P, s[c - 3 * st], s[c + 3 * st]), two);
-  const double t2 = SUB(P, ADD(P, s[c - 2 * st], s[c + 2 * st]), two);
-  const double t1 = SUB(P, ADD(P, s[c - st], s[c + st]), two);
+  const double two = PMUL(P, 2.0, s[c]);
+  const double t3 = PSUB(P, PADD(P, s[c - 3 * st], s[c + 3 * st]), two);
+  const double t2 = PSUB(P, PADD(P, s[c - 2 * st], s[c + 2 * st]), two);
+  const double t1 = PSUB(P, PADD(P, s[c - st], s[c + st]), two);
   return fma(15.0, t1, fma(-6.0, t2, t3));
 }
 __device__ __forceinline__ double fd_ko3(const DevParams& P, const double* s, int c) {
-  return ADD(P, ADD(P, fd_d6(P, s, c, 1), fd_d6(P, s, c, FBX)), fd_d6(P, s, c, FBX * FBY));
+  return PADD(P, PADD(P, fd_d6(P, s, c, 1), fd_d6(P, s, c, FBX)), fd_d6(P, s, c, FBX * FBY));
 }
 
 // out / acc update of one variable; returns the new value of the result.
@@ -114,7 +120,7 @@ __device__ __forceinline__ double fd_combine(const FdArgs& A, int64_t ev, double
                                              double ddt) {
   double res = 0.0;
   if (A.out) {
-    double base = A.b == 1.0 ? qsv : MUL(A.P, A.b, qsv);
+    double base = A.b == 1.0 ? qsv : PMUL(A.P, A.b, qsv);
     if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
     res = fma(gdt, L, base);
   }
@@ -162,7 +168,7 @@ __device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* box, d
     for (int v = 0; v < N; ++v) dq[v] = PDE::needs_grad(d, v) ? fd_d1(A.P, box + v * FBOX, c, st, r12) : 0.0;
     PDE::ncp(d, q, dq, A.P, D);
 #pragma unroll
-    for (int v = 0; v < N; ++v) L[v] = SUB(A.P, L[v], D[v]);
+    for (int v = 0; v < N; ++v) L[v] = PSUB(A.P, L[v], D[v]);
   }
   double res[NV];
 #pragma unroll
@@ -202,11 +208,11 @@ __device__ void fd_tile_gw59(const FdArgs& A, const FdWork& w, double* box, doub
   const double dal0 = fd_d1(P, box, c, X, r12), dal1 = fd_d1(P, box, c, Y, r12), dal2 = fd_d1(P, box, c, Z, r12);
   double ko_ab[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) ko_ab[v] = MUL(P, ko, fd_ko3(P, box + v * FBOX, c));
+  for (int v = 0; v < 4; ++v) ko_ab[v] = PMUL(P, ko, fd_ko3(P, box + v * FBOX, c));
   // phi_b Pi_b at this voxel for the source coupling
   double u[11];
 #pragma unroll
-  for (int bb = 0; bb < 11; ++bb) u[bb] = MUL(P, __ldg(A.qs + (int64_t)(5 * bb) * vs + e), __ldg(A.qs + (int64_t)(5 * bb + 1) * vs + e));
+  for (int bb = 0; bb < 11; ++bb) u[bb] = PMUL(P, __ldg(A.qs + (int64_t)(5 * bb) * vs + e), __ldg(A.qs + (int64_t)(5 * bb + 1) * vs + e));
   double sumPi2 = 0.0, bs0 = 0.0, bs1 = 0.0, bs2 = 0.0;
 
 #pragma unroll 1
@@ -222,20 +228,20 @@ __device__ void fd_tile_gw59(const FdArgs& A, const FdWork& w, double* box, doub
     const double phi = sphi[c], Pi = sPi[c], px = spx[c], py = spy[c], pz = spz[c];
     const double dPi0 = fd_d1(P, sPi, c, X, r12), dPi1 = fd_d1(P, sPi, c, Y, r12), dPi2 = fd_d1(P, sPi, c, Z, r12);
     // coupling sum_b C_ab phi_b Pi_b
-    double cs = MUL(P, A.P.C[11 * a], u[0]);
+    double cs = PMUL(P, A.P.C[11 * a], u[0]);
 #pragma unroll
     for (int bb = 1; bb < 11; ++bb) cs = fma(A.P.C[11 * a + bb], u[bb], cs);
     // phi: alpha Pi + beta . psi
-    const double Lphi = fma(al, Pi, fma(bx, px, fma(by, py, MUL(P, bz, pz))));
+    const double Lphi = fma(al, Pi, fma(bx, px, fma(by, py, PMUL(P, bz, pz))));
     // Pi: alpha div psi + beta . grad Pi + alpha cs
     const double dpx0 = fd_d1(P, spx, c, X, r12), dpx1 = fd_d1(P, spx, c, Y, r12), dpx2 = fd_d1(P, spx, c, Z, r12);
     const double dpy0 = fd_d1(P, spy, c, X, r12), dpy1 = fd_d1(P, spy, c, Y, r12), dpy2 = fd_d1(P, spy, c, Z, r12);
     const double dpz0 = fd_d1(P, spz, c, X, r12), dpz1 = fd_d1(P, spz, c, Y, r12), dpz2 = fd_d1(P, spz, c, Z, r12);
-    const double LPi = fma(al, ADD(P, ADD(P, dpx0, dpy1), dpz2), fma(bx, dPi0, fma(by, dPi1, fma(bz, dPi2, MUL(P, al, cs)))));
+    const double LPi = fma(al, PADD(P, PADD(P, dpx0, dpy1), dpz2), fma(bx, dPi0, fma(by, dPi1, fma(bz, dPi2, PMUL(P, al, cs)))));
     // psi_i: alpha d_i Pi + Pi d_i alpha + beta . grad psi_i
-    const double Lpx = fma(al, dPi0, fma(Pi, dal0, fma(bx, dpx0, fma(by, dpx1, MUL(P, bz, dpx2)))));
-    const double Lpy = fma(al, dPi1, fma(Pi, dal1, fma(bx, dpy0, fma(by, dpy1, MUL(P, bz, dpy2)))));
-    const double Lpz = fma(al, dPi2, fma(Pi, dal2, fma(bx, dpz0, fma(by, dpz1, MUL(P, bz, dpz2)))));
+    const double Lpx = fma(al, dPi0, fma(Pi, dal0, fma(bx, dpx0, fma(by, dpx1, PMUL(P, bz, dpx2)))));
+    const double Lpy = fma(al, dPi1, fma(Pi, dal1, fma(bx, dpy0, fma(by, dpy1, PMUL(P, bz, dpy2)))));
+    const double Lpz = fma(al, dPi2, fma(Pi, dal2, fma(bx, dpz0, fma(by, dpz1, PMUL(P, bz, dpz2)))));
     sumPi2 = fma(Pi, Pi, sumPi2);
     bs0 = fma(px, Pi, bs0);
     bs1 = fma(py, Pi, bs1);
@@ -247,12 +253,12 @@ __device__ void fd_tile_gw59(const FdArgs& A, const FdWork& w, double* box, doub
     fd_combine(A, eb + 3 * vs, py, fma(ko, fd_ko3(P, spy, c), Lpy), gdt, ddt);
     fd_combine(A, eb + 4 * vs, pz, fma(ko, fd_ko3(P, spz, c), Lpz), gdt, ddt);
   }
-  const double Lal = fma(MUL(P, -A.P.kappa, MUL(P, al, al)), sumPi2, ko_ab[0]);
+  const double Lal = fma(PMUL(P, -A.P.kappa, PMUL(P, al, al)), sumPi2, ko_ab[0]);
   const double ra = fd_combine(A, 55 * vs + e, al, Lal, gdt, ddt);
   const double r0 = fd_combine(A, 56 * vs + e, bx, fma(0.75, bs0, ko_ab[1]), gdt, ddt);
   const double r1 = fd_combine(A, 57 * vs + e, by, fma(0.75, bs1, ko_ab[2]), gdt, ddt);
   const double r2 = fd_combine(A, 58 * vs + e, bz, fma(0.75, bs2, ko_ab[3]), gdt, ddt);
-  if (A.lam_out) lam_thread = fmax(lam_thread, ADD(P, ra, fmax(fmax(fabs(r0), fabs(r1)), fabs(r2))));
+  if (A.lam_out) lam_thread = fmax(lam_thread, PADD(P, ra, fmax(fmax(fabs(r0), fabs(r1)), fabs(r2))));
 }
 
 __device__ __forceinline__ double fd_warp_max(double v) {
