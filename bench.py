@@ -418,6 +418,11 @@ def our_arm(args, rank, world, local_rank):
         M_init = mat.clone() if mat is not None else None
         dh.max_wave_speed(plan, Q, mat, lam, stream)
         lam_init = lam.clone()
+        # autotune the stage kernel variant on this workload (U1 is scratch here)
+        dh.dh_cfl_dt(plan, lam, spec["cfl"], dt, stream)
+        tv, tz, tf, _, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3, stream=stream)
+        tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf,
+                "candidate_ms": [round(t, 4) for t in ttimes[:(8 if spec["scheme"] == 0 else 2)]]}
         # eager warm-up step (sets kernel attributes outside of capture), then reset
         dh.dh_rk_step(plan, spec["scheme"], spec["rk"], Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1, stream)
         Q.copy_(Q_init)
@@ -510,6 +515,7 @@ def our_arm(args, rank, world, local_rank):
         "e2e": {"value": world * nvox * inner * n_e2e / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(Q.numel() * 8)},
         "gpu_launches": int(n_kernels * args.steps),
+        "autotune": tune,
         "clocks": clocks,
         "state_finite": finite,
     }

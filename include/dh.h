@@ -242,6 +242,25 @@ dh_status dh_graph_info(dh_plan* plan, int32_t* n_kernels, int32_t* n_timed_stag
  * (the caller synchronises first). */
 dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
 
+/* Autotuner.  Times every compiled variant of the plan's stage kernel on the
+ * caller's buffers (one stage out = qs + dt L(qs), `reps` launches each after a
+ * warm-up, CUDA events on `stream`) and keeps the fastest in the plan:
+ *   FV (scheme 0): halo ring computed before or after the mid-plane barrier
+ *                  x register cap (1 or 2 CTAs per SM) x z-march in whole
+ *                  patches or in chunks of <= 16 planes (8 candidates);
+ *   FD (scheme 1): register cap (2 candidates).
+ * `out` is overwritten.  If cache_path is not NULL the choice is first looked up
+ * there (one JSON object per line, keyed by GPU name, PDE, scheme and patch-size
+ * histogram) and, when timed, appended to it.  choice_out (optional, 4 ints):
+ * fv_var, fv_zs, fd_var, 1 if taken from the cache.  times_out (optional, 8
+ * floats): ms per launch of each candidate. */
+dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* out, const double* mat,
+                      const double* dt_dev, int32_t reps, const char* cache_path, int32_t* choice_out,
+                      float* times_out, void* stream);
+/* Select a variant directly: fv_var 0..3 (bit 0: ring before the barrier,
+ * bit 1: two CTAs per SM), fv_zs 0..1 (z-chunks of <= 16 planes), fd_var 0 or 2. */
+dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var);
+
 /* Diagnostic: for n doubles x, y_nr[i] = the kernels' Newton-Raphson
  * reciprocal of x[i] and y_div[i] = 1.0 / x[i] (IEEE division), so that a test
  * can bound the reciprocal's error.  All three arrays are device arrays of n. */

@@ -222,47 +222,54 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     }
   }
   finish_params(P);
-  // Tile work list: 16x16 columns for p % 16 == 0, groups of four 8x8 columns
-  // (same p) otherwise; largest work first.
-  std::vector<Work> work;
-  std::vector<std::vector<std::pair<int, std::pair<int, int>>>> pending(257);
-  for (int k = 0; k < K; ++k) {
-    const int p = patches[k].p, pz = dim == 3 ? p : 1;
-    if (p % 16 == 0) {
-      for (int yy = 0; yy < p; yy += 16)
-        for (int xx = 0; xx < p; xx += 16) {
-          Work w{};
-          w.cls = 0; w.pz = pz;
-          for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
-          w.patch[0] = k; w.x0[0] = (int16_t)xx; w.y0[0] = (int16_t)yy;
-          work.push_back(w);
-        }
-    } else {
-      for (int yy = 0; yy < p; yy += 8)
-        for (int xx = 0; xx < p; xx += 8) pending[p].push_back({k, {xx, yy}});
-    }
-  }
-  for (int p = 8; p <= 256; p += 8) {
-    auto& v = pending[p];
-    for (size_t i = 0; i < v.size(); i += 4) {
-      Work w{};
-      w.cls = 1; w.pz = dim == 3 ? p : 1;
-      for (int j = 0; j < 4; ++j) {
-        if (i + j < v.size()) { w.patch[j] = v[i + j].first; w.x0[j] = (int16_t)v[i + j].second.first; w.y0[j] = (int16_t)v[i + j].second.second; }
-        else { w.patch[j] = -1; w.x0[j] = 0; w.y0[j] = 0; }
+  // Tile work lists: 16x16 columns for p % 16 == 0, groups of four 8x8 columns
+  // (same p) otherwise; largest work first.  List 1 also splits the z-march of
+  // the 16x16 columns into chunks of at most 16 planes (more, shorter CTAs).
+  std::vector<Work> lists[2];
+  for (int zs = 0; zs < 2; ++zs) {
+    std::vector<Work>& work = lists[zs];
+    std::vector<std::vector<std::pair<int, std::pair<int, int>>>> pending(257);
+    for (int k = 0; k < K; ++k) {
+      const int p = patches[k].p, pz = dim == 3 ? p : 1;
+      if (p % 16 == 0) {
+        const int chunk = (zs == 1 && pz > 16) ? 16 : pz;
+        for (int zz = 0; zz < pz; zz += chunk)
+          for (int yy = 0; yy < p; yy += 16)
+            for (int xx = 0; xx < p; xx += 16) {
+              Work w{};
+              w.cls = 0; w.pz = std::min(chunk, pz - zz); w.z0 = zz;
+              for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
+              w.patch[0] = k; w.x0[0] = (int16_t)xx; w.y0[0] = (int16_t)yy;
+              work.push_back(w);
+            }
+      } else {
+        for (int yy = 0; yy < p; yy += 8)
+          for (int xx = 0; xx < p; xx += 8) pending[p].push_back({k, {xx, yy}});
       }
-      work.push_back(w);
     }
+    for (int p = 8; p <= 256; p += 8) {
+      auto& v = pending[p];
+      for (size_t i = 0; i < v.size(); i += 4) {
+        Work w{};
+        w.cls = 1; w.pz = dim == 3 ? p : 1; w.z0 = 0;
+        for (int j = 0; j < 4; ++j) {
+          if (i + j < v.size()) { w.patch[j] = v[i + j].first; w.x0[j] = (int16_t)v[i + j].second.first; w.y0[j] = (int16_t)v[i + j].second.second; }
+          else { w.patch[j] = -1; w.x0[j] = 0; w.y0[j] = 0; }
+        }
+        work.push_back(w);
+      }
+    }
+    auto cost = [](const Work& w) {
+      int ng = 0;
+      for (int j = 0; j < 4; ++j) ng += w.patch[j] >= 0;
+      return (long long)(w.cls == 0 ? 256 : 64 * ng) * w.pz;
+    };
+    std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
+    for (const Work& w : work) plan->has_cls[w.cls] = true;
+    plan->n_work_z[zs] = (int)work.size();
   }
-  auto cost = [](const Work& w) {
-    int ng = 0;
-    for (int j = 0; j < 4; ++j) ng += w.patch[j] >= 0;
-    return (long long)(w.cls == 0 ? 256 : 64 * ng) * w.pz;
-  };
-  std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
-  for (const Work& w : work) plan->has_cls[w.cls] = true;
-  plan->h_work = work;
-  plan->n_work = (int)work.size();
+  plan->h_work = lists[0];
+  plan->n_work = (int)lists[0].size();
 
   // FD tiles: 8x8x4 blocks (p is a multiple of 8)
   std::vector<FdWork> fdw;
@@ -280,9 +287,12 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_patches, sizeof(dh_patch) * K);
   if (e == cudaSuccess) e = cudaMemcpy(plan->d_patches, patches, sizeof(dh_patch) * K, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&plan->d_work, sizeof(Work) * std::max<size_t>(1, work.size()));
-  if (e == cudaSuccess && !work.empty())
-    e = cudaMemcpy(plan->d_work, work.data(), sizeof(Work) * work.size(), cudaMemcpyHostToDevice);
+  for (int zs = 0; zs < 2 && e == cudaSuccess; ++zs) {
+    e = cudaMalloc(&plan->d_work_z[zs], sizeof(Work) * std::max<size_t>(1, lists[zs].size()));
+    if (e == cudaSuccess && !lists[zs].empty())
+      e = cudaMemcpy(plan->d_work_z[zs], lists[zs].data(), sizeof(Work) * lists[zs].size(), cudaMemcpyHostToDevice);
+  }
+  plan->d_work = plan->d_work_z[0];
   if (e == cudaSuccess && !fdw.empty()) e = cudaMalloc(&plan->d_fdwork, sizeof(FdWork) * fdw.size());
   if (e == cudaSuccess && !fdw.empty())
     e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
@@ -300,7 +310,8 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
 dh_status dh_plan_destroy(dh_plan* plan) {
   if (!plan) return DH_OK;
   if (plan->d_patches) cudaFree(plan->d_patches);
-  if (plan->d_work) cudaFree(plan->d_work);
+  for (int zs = 0; zs < 2; ++zs)
+    if (plan->d_work_z[zs]) cudaFree(plan->d_work_z[zs]);
   if (plan->d_red) cudaFree(plan->d_red);
   if (plan->d_fdwork) cudaFree(plan->d_fdwork);
   if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);

@@ -290,8 +290,10 @@ __device__ void fd_publish_lambda(double lam, double* lam_out, unsigned long lon
   }
 }
 
-template <class PDE>
-__global__ void __launch_bounds__(FNT) k_fd_stage(const __grid_constant__ FdArgs A) {
+// Kernel variants (chosen per plan by the autotuner): VAR bit 1 caps the
+// registers at 128 so that two CTAs fit on an SM.
+template <class PDE, int VAR>
+__global__ void __launch_bounds__(FNT, (VAR & 2) ? 2 : 1) k_fd_stage(const __grid_constant__ FdArgs A) {
   extern __shared__ __align__(16) double box[];
   const FdWork w = A.work[blockIdx.x];
   double lam = 0.0;
@@ -300,18 +302,23 @@ __global__ void __launch_bounds__(FNT) k_fd_stage(const __grid_constant__ FdArgs
   if (A.lam_out) fd_publish_lambda(lam, A.lam_out, A.red);
 }
 
-template <class PDE>
-static dh_status fd_launch(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
+template <class PDE, int VAR>
+static dh_status fd_launch_var(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
   constexpr int NB = PDE::N == 59 ? 5 : PDE::N;
   const size_t smem = sizeof(double) * NB * FBOX;
   static int configured_device = -1;
   if (configured_device != plan->device) {
-    cudaError_t e = cudaFuncSetAttribute(k_fd_stage<PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fd_stage<PDE, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fd_stage)");
     configured_device = plan->device;
   }
-  k_fd_stage<PDE><<<plan->n_fdwork, FNT, smem, stream>>>(A);
+  k_fd_stage<PDE, VAR><<<plan->n_fdwork, FNT, smem, stream>>>(A);
   return cuda_error(cudaGetLastError(), "k_fd_stage launch");
+}
+
+template <class PDE>
+static dh_status fd_launch(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
+  return (plan->fd_var & 2) ? fd_launch_var<PDE, 2>(plan, A, stream) : fd_launch_var<PDE, 0>(plan, A, stream);
 }
 
 dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,

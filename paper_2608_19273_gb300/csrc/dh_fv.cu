@@ -66,14 +66,14 @@ __device__ __forceinline__ void load_q(const FvArgs& A, int64_t e, double* q) {
   for (int v = 0; v < PDE::M; ++v) q[PDE::N + v] = __ldg(A.mat + v * A.vs + e);
 }
 
-template <class PDE, int TX, int TY, int G>
+template <class PDE, int TX, int TY, int G, bool EARLY>
 struct FvTile {
   static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW, DIM = PDE::DIM;
   static constexpr int NT = TX * TY * G;
   static constexpr int RG = TX + TY;           // ring voxels per group and half
   static constexpr int HALF = G * RG;          // face-computing ring voxels (+x, +y)
   static constexpr int NR = 2 * HALF;
-  static constexpr int NS = NT + NR;
+  static constexpr int NS = NT + 2 * NR;        // interior slots + two ring buffers (plane parity)
   static constexpr int FXG = (TX + 1) * TY, FYG = TX * (TY + 1);
   static constexpr int FX = G * FXG, FY = G * FYG;
   static constexpr int NF = PDE::NCP ? 2 : 1;
@@ -125,8 +125,9 @@ struct FvTile {
     }
   }
 
-  // Ring voxel r of plane z: load, derive, flux and speed in its one direction.
-  __device__ static void ring_voxel(const FvArgs& A, const Smem& S, const Work& w, int r, int p, int z) {
+  // Ring voxel r of plane z (into ring buffer buf): load, derive, flux and speed
+  // in its one direction.
+  __device__ static void ring_voxel(const FvArgs& A, const Smem& S, const Work& w, int r, int p, int z, int buf) {
     const int h = r < HALF ? 0 : 1;
     const int rr = r - h * HALF;
     const int g = rr / RG, j = rr % RG;
@@ -140,7 +141,7 @@ struct FvTile {
     double q[NV], W[NW > 0 ? NW : 1], F[N];
     load_q<PDE>(A, e, q);
     PDE::prims(q, A.P, W);
-    const int s = NT + r;
+    const int s = NT + buf * NR + r;
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.Q[v * NS + s] = q[v];
     double* Fd = d == 0 ? S.Fx : S.Fy;
@@ -159,7 +160,7 @@ struct FvTile {
     const int g = tid / (TX * TY), lxy = tid % (TX * TY), lx = lxy % TX, ly = lxy / TX;
     const int k = w.patch[g];
     const bool act = k >= 0;
-    const int pz = w.pz;
+    const int pz = w.pz, z0 = w.z0;
     // the patch size of every group in this CTA is the same (pz in 3D; 2D: from the table)
     const int kk = act ? k : w.patch[0];
     const int p = A.patches[kk].p;
@@ -175,8 +176,10 @@ struct FvTile {
 
     // smem slots of this voxel and of its -x / -y neighbours
     const int me = tid;
-    const int xm = lx > 0 ? me - 1 : NT + HALF + g * RG + ly;
-    const int ym = ly > 0 ? me - TX : NT + HALF + g * RG + TY + lx;
+    const int xm0 = lx > 0 ? me - 1 : NT + HALF + g * RG + ly;       // ring buffer 0
+    const int ym0 = ly > 0 ? me - TX : NT + HALF + g * RG + TY + lx;
+    const int xm1 = lx > 0 ? me - 1 : xm0 + NR;                         // ring buffer 1
+    const int ym1 = ly > 0 ? me - TX : ym0 + NR;
     // face indices
     const int fxl = g * FXG + ly * (TX + 1) + lx, fxr = fxl + 1;
     const int fyl = g * FYG + ly * TX + lx, fyu = fyl + TX;
@@ -191,7 +194,7 @@ struct FvTile {
     // ---- prologue: plane 0 (and plane -1 for the first z face)
     if (act) {
       double Wk[NW > 0 ? NW : 1], F[N];
-      load_q<PDE>(A, off + ((int64_t)0 * p + y) * p + x, Qk);
+      load_q<PDE>(A, off + ((int64_t)z0 * p + y) * p + x, Qk);
       PDE::prims(Qk, A.P, Wk);
       if (PDE::FLUX) {
         PDE::flux(0, Qk, Wk, A.P, F);
@@ -210,7 +213,7 @@ struct FvTile {
         Lzk = PDE::speed(2, Qk, Wk, A.P);
         // plane -1 from the -z neighbour
         double Qm[NV], Wm[NW > 0 ? NW : 1], Fzm[N];
-        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, -1), Qm);
+        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, z0 - 1), Qm);
         PDE::prims(Qm, A.P, Wm);
         if (PDE::FLUX) PDE::flux(2, Qm, Wm, A.P, Fzm);
         const double s = fmax(PDE::speed(2, Qm, Wm, A.P), Lzk);
@@ -228,14 +231,16 @@ struct FvTile {
         }
       }
     }
-    if (ring) ring_voxel(A, S, w, tid, p, 0);
+    if (ring) ring_voxel(A, S, w, tid, p, z0, 0);
     __syncthreads();
 
     for (int kz = 0; kz < pz; ++kz) {
+      const int buf = kz & 1;
+      const int zg = z0 + kz;  // plane index within the patch
       // ---- faces of plane kz inside the plane
       if (act) {
-        face(S, A.P, 0, xm, me, S.Hx, S.Dx, fxl, FX);
-        face(S, A.P, 1, ym, me, S.Hy, S.Dy, fyl, FY);
+        face(S, A.P, 0, buf ? xm1 : xm0, me, S.Hx, S.Dx, fxl, FX);
+        face(S, A.P, 1, buf ? ym1 : ym0, me, S.Hy, S.Dy, fyl, FY);
       }
       if (tid < HALF) {
         // +x and +y boundary faces of the column: one call with a run-time
@@ -245,7 +250,8 @@ struct FvTile {
           const bool isx = j < TY;
           const int Ls = isx ? gg * TX * TY + j * TX + (TX - 1) : gg * TX * TY + (TY - 1) * TX + (j - TY);
           const int fidx = isx ? gg * FXG + j * (TX + 1) + TX : gg * FYG + TY * TX + (j - TY);
-          face(S, A.P, isx ? 0 : 1, Ls, NT + tid, isx ? S.Hx : S.Hy, isx ? S.Dx : S.Dy, fidx, isx ? FX : FY);
+          face(S, A.P, isx ? 0 : 1, Ls, NT + buf * NR + tid, isx ? S.Hx : S.Hy, isx ? S.Dx : S.Dy, fidx,
+               isx ? FX : FY);
         }
       }
       // ---- next plane's own voxel (3D): derived quantities, z flux, z face
@@ -253,7 +259,7 @@ struct FvTile {
 #pragma unroll
       for (int v = 0; v < N; ++v) { Hzhi[v] = 0.0; Dzhi[v] = 0.0; Fzn[v] = 0.0; }
       if (DIM == 3 && act) {
-        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, kz + 1), Qn);
+        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, zg + 1), Qn);
         PDE::prims(Qn, A.P, Wn);
         if (PDE::FLUX) PDE::flux(2, Qn, Wn, A.P, Fzn);
         Lzn = PDE::speed(2, Qn, Wn, A.P);
@@ -271,6 +277,8 @@ struct FvTile {
           PDE::ncp(2, qb, dq, A.P, Dzhi);
         }
       }
+      // EARLY variant: the ring of plane kz+1 (other ring buffer) overlaps this phase
+      if (EARLY && DIM == 3 && kz + 1 < pz && ring) ring_voxel(A, S, w, tid, p, zg + 1, buf ^ 1);
       __syncthreads();
       // ---- update of plane kz
       if (act) {
@@ -280,7 +288,7 @@ struct FvTile {
           PDE::prims(Qk, A.P, Wk);
           PDE::source(Qk, Wk, A.P, Sv);
         }
-        const int64_t e = off + ((int64_t)kz * p + y) * p + x;
+        const int64_t e = off + ((int64_t)zg * p + y) * p + x;
         double res[NV];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
@@ -337,7 +345,7 @@ struct FvTile {
           for (int v = 0; v < N; ++v) { Fzk[v] = Fzn[v]; Hzlo[v] = Hzhi[v]; Dzlo[v] = Dzhi[v]; }
           Lzk = Lzn;
         }
-        if (ring) ring_voxel(A, S, w, tid, p, kz + 1);
+        if (!EARLY && ring) ring_voxel(A, S, w, tid, p, zg + 1, buf ^ 1);
         __syncthreads();
       }
     }
@@ -377,29 +385,48 @@ __device__ void publish_lambda(double lam, double* lam_out, unsigned long long* 
   }
 }
 
-template <class PDE>
-__global__ void __launch_bounds__(256) k_fv_stage(const __grid_constant__ FvArgs A) {
+// Kernel variants (chosen per plan by the autotuner, dh_autotune):
+//   VAR bit 0: EARLY -- the halo ring of the next plane is computed before the
+//              mid-plane barrier instead of after it;
+//   VAR bit 1: at most 128 registers so that two CTAs fit on an SM.
+template <class PDE, int VAR>
+__global__ void __launch_bounds__(256, (VAR & 2) ? 2 : 1) k_fv_stage(const __grid_constant__ FvArgs A) {
   extern __shared__ __align__(16) double smem[];
+  constexpr bool EARLY = (VAR & 1) != 0;
   const Work w = A.work[blockIdx.x];
   double lam = 0.0;
-  if (w.cls == 0) FvTile<PDE, 16, 16, 1>::run(A, w, smem, lam);
-  else FvTile<PDE, 8, 8, 4>::run(A, w, smem, lam);
+  if (w.cls == 0) FvTile<PDE, 16, 16, 1, EARLY>::run(A, w, smem, lam);
+  else FvTile<PDE, 8, 8, 4, EARLY>::run(A, w, smem, lam);
   if (A.lam_out) publish_lambda(lam, A.lam_out, A.red);
+}
+
+template <class PDE, int VAR>
+static dh_status launch_var(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
+  constexpr bool EARLY = (VAR & 1) != 0;
+  const int zs = plan->fv_zs;
+  const size_t smem = std::max(plan->has_cls[0] ? FvTile<PDE, 16, 16, 1, EARLY>::SMEM : 0,
+                               plan->has_cls[1] ? FvTile<PDE, 8, 8, 4, EARLY>::SMEM : 0);
+  static int configured_device = -1;  // attribute is per device function; set once per process and device
+  if (configured_device != plan->device) {
+    const size_t mx = std::max(FvTile<PDE, 16, 16, 1, EARLY>::SMEM, FvTile<PDE, 8, 8, 4, EARLY>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k_fv_stage<PDE, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv_stage)");
+    configured_device = plan->device;
+  }
+  FvArgs B = A;
+  B.work = plan->d_work_z[zs];
+  k_fv_stage<PDE, VAR><<<plan->n_work_z[zs], 256, smem, stream>>>(B);
+  return cuda_error(cudaGetLastError(), "k_fv_stage launch");
 }
 
 template <class PDE>
 static dh_status launch(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
-  const size_t smem = std::max(plan->has_cls[0] ? FvTile<PDE, 16, 16, 1>::SMEM : 0,
-                               plan->has_cls[1] ? FvTile<PDE, 8, 8, 4>::SMEM : 0);
-  static int configured_device = -1;  // attribute is per device function; set once per process and device
-  if (configured_device != plan->device) {
-    const size_t mx = std::max(FvTile<PDE, 16, 16, 1>::SMEM, FvTile<PDE, 8, 8, 4>::SMEM);
-    cudaError_t e = cudaFuncSetAttribute(k_fv_stage<PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
-    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv_stage)");
-    configured_device = plan->device;
+  switch (plan->fv_var & 3) {
+    case 0: return launch_var<PDE, 0>(plan, A, stream);
+    case 1: return launch_var<PDE, 1>(plan, A, stream);
+    case 2: return launch_var<PDE, 2>(plan, A, stream);
+    default: return launch_var<PDE, 3>(plan, A, stream);
   }
-  k_fv_stage<PDE><<<plan->n_work, 256, smem, stream>>>(A);
-  return cuda_error(cudaGetLastError(), "k_fv_stage launch");
 }
 
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,

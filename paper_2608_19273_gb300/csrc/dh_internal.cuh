@@ -28,8 +28,9 @@ struct DevParams {
 // One CTA's worth of FV/FD work: up to 4 groups, each a (TX x TY) column of
 // one patch that the CTA marches through all z-planes of that patch.
 struct Work {
-  int32_t cls;    // tile class: 0 = 16x16 columns, 1 face group; 1 = 8x8 columns, 4 groups
-  int32_t pz;     // planes to march (p in 3D, 1 in 2D)
+  int32_t cls;    // tile class: 0 = 16x16 columns, 1 group; 1 = 8x8 columns, 4 groups
+  int32_t pz;     // planes to march (p in 3D, 1 in 2D) ...
+  int32_t z0;     // ... starting at this plane of the patch
   int32_t patch[4];
   int16_t x0[4];
   int16_t y0[4];
@@ -56,6 +57,11 @@ struct dh_plan {
   std::vector<dh::Work> h_work;
   dh::Work* d_work = nullptr;
   int n_work = 0;
+  // work lists without / with the z-split of 16x16 columns into chunks of <= 16 planes
+  dh::Work* d_work_z[2] = {nullptr, nullptr};
+  int n_work_z[2] = {0, 0};
+  // kernel variants chosen by the autotuner
+  int fv_var = 2, fv_zs = 0, fd_var = 0;
   bool has_cls[2] = {false, false};
   // FD tile list (8x8x4 tiles)
   dh::FdWork* d_fdwork = nullptr;

@@ -72,7 +72,7 @@ int na_build_work(int dim, const dh_patch* patches, int K, int halo, int64_t var
       for (int xx = 0; xx < p; xx += 16) {
         if (nw >= NA_MAX_WORK) { set_error("patch_update_fv_noalloc: more than %d work items", NA_MAX_WORK); return DH_EINVAL; }
         Work& w = g_na_work[nw++];
-        w.cls = 0; w.pz = dim == 3 ? p : 1;
+        w.cls = 0; w.pz = dim == 3 ? p : 1; w.z0 = 0;
         for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
         w.patch[0] = k; w.x0[0] = (int16_t)xx; w.y0[0] = (int16_t)yy;
         has_cls[0] = true;
@@ -87,7 +87,7 @@ int na_build_work(int dim, const dh_patch* patches, int K, int halo, int64_t var
           if (slot == 4) {
             if (nw >= NA_MAX_WORK) { set_error("patch_update_fv_noalloc: more than %d work items", NA_MAX_WORK); return DH_EINVAL; }
             Work& w = g_na_work[nw++];
-            w.cls = 1; w.pz = dim == 3 ? p : 1;
+            w.cls = 1; w.pz = dim == 3 ? p : 1; w.z0 = 0;
             for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
             slot = 0;
             has_cls[1] = true;
@@ -166,6 +166,9 @@ extern "C" dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_
   view.d_patches = d_patches;
   view.d_work = d_work;
   view.n_work = nw;
+  view.d_work_z[0] = d_work;
+  view.n_work_z[0] = nw;
+  view.fv_zs = 0;
   view.has_cls[0] = has_cls[0];
   view.has_cls[1] = has_cls[1];
   view.d_red = red;

@@ -1,0 +1,141 @@
+// Autotuner: picks, per plan (PDE x patch mix x GPU), the fastest compiled
+// variant of the stage kernel by timing every candidate with CUDA events on
+// the caller's own buffers, and remembers the choice in a small JSON-lines
+// cache file.
+//
+// Candidates
+//   FV stage: kernel variant (halo ring before / after the mid-plane barrier)
+//             x register cap (1 or 2 CTAs per SM)
+//             x work list (16x16 columns march whole patches / chunks of <= 16 planes)
+//   FD stage: register cap (1 or 2 CTAs per SM)
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+
+#include "dh_internal.cuh"
+
+namespace dh {
+
+static std::string tune_key(const dh_plan* plan, int scheme) {
+  std::map<int, int> mix;
+  for (const dh_patch& p : plan->h_patches) mix[p.p]++;
+  cudaDeviceProp prop;
+  std::string dev = "gpu";
+  if (cudaGetDeviceProperties(&prop, plan->device) == cudaSuccess) dev = prop.name;
+  std::string k = dev + "|pde=" + std::to_string(plan->pde) + "|scheme=" + std::to_string(scheme) +
+                  "|dim=" + std::to_string(plan->dim) + "|mix=";
+  for (auto& kv : mix) k += std::to_string(kv.first) + "x" + std::to_string(kv.second) + ",";
+  return k;
+}
+
+// Looks for `"key": "<key>"` in the cache and reads the three integers after it.
+static bool cache_lookup(const char* path, const std::string& key, int* fv_var, int* fv_zs, int* fd_var) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[4096];
+  bool found = false;
+  const std::string needle = "\"key\": \"" + key + "\"";
+  while (fgets(line, sizeof(line), f)) {
+    if (!strstr(line, needle.c_str())) continue;
+    const char* a = strstr(line, "\"fv_var\": ");
+    const char* b = strstr(line, "\"fv_zs\": ");
+    const char* c = strstr(line, "\"fd_var\": ");
+    if (a && b && c && sscanf(a, "\"fv_var\": %d", fv_var) == 1 && sscanf(b, "\"fv_zs\": %d", fv_zs) == 1 &&
+        sscanf(c, "\"fd_var\": %d", fd_var) == 1)
+      found = true;  // the last matching line wins
+  }
+  fclose(f);
+  return found;
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (fv_var < 0 || fv_var > 3 || fv_zs < 0 || fv_zs > 1 || (fd_var != 0 && fd_var != 2)) {
+    set_error("dh_plan_set_variant: fv_var in 0..3, fv_zs in 0..1, fd_var in {0, 2}");
+    return DH_EINVAL;
+  }
+  plan->fv_var = fv_var;
+  plan->fv_zs = fv_zs;
+  plan->fd_var = fd_var;
+  return DH_OK;
+}
+
+dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* out, const double* mat,
+                      const double* dt_dev, int32_t reps, const char* cache_path, int32_t* choice_out,
+                      float* times_out, void* stream) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (scheme != 0 && scheme != 1) { set_error("dh_autotune: scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
+  if (!qs || !out || !dt_dev || reps < 1 || reps > 1000) { set_error("dh_autotune: bad arguments"); return DH_EINVAL; }
+  const std::string key = tune_key(plan, scheme);
+  int v = 0, z = 0, f = 0;
+  if (cache_path && cache_lookup(cache_path, key, &v, &z, &f)) {
+    dh_status st = dh_plan_set_variant(plan, v, z, f);
+    if (st == DH_OK && choice_out) { choice_out[0] = v; choice_out[1] = z; choice_out[2] = f; choice_out[3] = 1; }
+    return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  struct Cand { int v, z, f; };
+  Cand cands[8];
+  int nc = 0;
+  if (scheme == 0) {
+    for (int zz = 0; zz < 2; ++zz)
+      for (int vv = 0; vv < 4; ++vv) cands[nc++] = {vv, zz, plan->fd_var};
+  } else {
+    cands[nc++] = {plan->fv_var, plan->fv_zs, 0};
+    cands[nc++] = {plan->fv_var, plan->fv_zs, 2};
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    set_error("dh_autotune: cudaEventCreate failed");
+    return DH_ECUDA;
+  }
+  float best = 1e30f;
+  int bi = 0;
+  dh_status st = DH_OK;
+  for (int i = 0; i < nc && st == DH_OK; ++i) {
+    plan->fv_var = cands[i].v;
+    plan->fv_zs = cands[i].z;
+    plan->fd_var = cands[i].f;
+    auto launch = [&]() {
+      return scheme == 0 ? patch_update_fv(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, nullptr, s)
+                         : patch_update_fd_ko(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, 0.1, nullptr, s);
+    };
+    st = launch();  // warm-up (also sets the kernel's shared-memory attribute)
+    if (st != DH_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == DH_OK; ++r) st = launch();
+    cudaEventRecord(e1, s);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) { st = cuda_error(ce, "dh_autotune"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (times_out) times_out[i] = ms;
+    if (ms < best) { best = ms; bi = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DH_OK) return st;
+  plan->fv_var = cands[bi].v;
+  plan->fv_zs = cands[bi].z;
+  plan->fd_var = cands[bi].f;
+  if (choice_out) { choice_out[0] = cands[bi].v; choice_out[1] = cands[bi].z; choice_out[2] = cands[bi].f; choice_out[3] = 0; }
+  if (cache_path) {
+    FILE* fo = fopen(cache_path, "a");
+    if (fo) {
+      fprintf(fo, "{\"key\": \"%s\", \"fv_var\": %d, \"fv_zs\": %d, \"fd_var\": %d, \"ms\": %.6f, \"candidates\": %d}\n",
+              key.c_str(), cands[bi].v, cands[bi].z, cands[bi].f, best, nc);
+      fclose(fo);
+    }
+  }
+  return DH_OK;
+}
+
+}  // extern "C"

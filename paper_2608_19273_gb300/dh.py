@@ -25,7 +25,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
 
@@ -55,6 +55,8 @@ def lib():
         L.dh_prim2con.argtypes = [vp, vp, vp, vp]
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
         L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
+        L.dh_autotune.argtypes = [vp, i32, vp, vp, vp, vp, i32, ctypes.c_char_p, vp, vp, vp]
+        L.dh_plan_set_variant.argtypes = [vp, i32, i32, i32]
         L.patch_update_fv_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp, vp, d, d, d, d,
                                               vp, vp]
         L.con2prim.argtypes = [vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp]
@@ -276,6 +278,20 @@ def dh_graph_stage_times(plan, n):
 
 def dh_probe_dfma(out_dev, n_threads, iters, stream=None):
     _check(lib().dh_probe_dfma(_ptr(out_dev, "out"), int(n_threads), int(iters), _stream(stream)), "dh_probe_dfma")
+
+
+def dh_autotune(plan, scheme, qs, out, mat, dt_dev, reps=3, cache_path=None, stream=None):
+    """Pick the fastest kernel variant for this plan; returns (fv_var, fv_zs, fd_var, from_cache, times_ms)."""
+    choice = (ctypes.c_int32 * 4)()
+    times = (ctypes.c_float * 8)()
+    _check(lib().dh_autotune(plan.handle, int(scheme), _ptr(qs, "qs"), _ptr(out, "out"), _ptr(mat, "mat"),
+                             _ptr(dt_dev, "dt"), int(reps), None if cache_path is None else cache_path.encode(),
+                             choice, times, _stream(stream)), "dh_autotune")
+    return choice[0], choice[1], choice[2], bool(choice[3]), [float(t) for t in times]
+
+
+def dh_plan_set_variant(plan, fv_var, fv_zs, fd_var):
+    _check(lib().dh_plan_set_variant(plan.handle, int(fv_var), int(fv_zs), int(fd_var)), "dh_plan_set_variant")
 
 
 def dh_check_recip(x, y_nr, y_div, stream=None):
