@@ -48,6 +48,9 @@ def lib():
             L.or_num_threads.restype = i
             L.or_stage.argtypes = [i, i, i, vp, i, i, i64, vp, vp, vp, vp, vp, d, d, d, d, d, d, vp, i, vp]
             L.or_stage.restype = i
+            L.or_stage_subset.argtypes = [i, i, i, vp, i, i, i64, vp, vp, vp, vp, vp, d, d, d, d, d, d, vp, i, vp,
+                                          i]
+            L.or_stage_subset.restype = i
             L.or_max_wave_speed.argtypes = [i, i, vp, i, i64, vp, vp, vp, i]
             L.or_max_wave_speed.restype = d
             L.or_cfl_dt.argtypes = [d, d, i, d]
@@ -100,6 +103,16 @@ def stage(scheme, pde, dim, patches, halo, var_stride, qs, q0=None, out=None, ac
                    _p(out), _p(acc), _p(mat), dt, a, b, g, d, sigma, _p(prm),
                    0 if prm is None else len(prm), _p(lam) if want_lam else None)
     return float(lam[0]) if want_lam else None
+
+
+def stage_subset(scheme, pde, dim, patches, halo, var_stride, qs, only, q0=None, out=None, acc=None, mat=None,
+                 dt=0.0, a=0.0, b=1.0, g=1.0, d=0.0, sigma=0.1, params=None):
+    """One stage on the listed patches only (their halos still come from every patch)."""
+    prm = _f64(params)
+    only = np.ascontiguousarray(only, dtype=np.int32)
+    lib().or_stage_subset(scheme, pde, dim, _p(patches), len(patches), halo, var_stride, _p(qs), _p(q0), _p(out),
+                          _p(acc), _p(mat), dt, a, b, g, d, sigma, _p(prm), 0 if prm is None else len(prm), _p(only),
+                          len(only))
 
 
 def max_wave_speed(pde, dim, patches, var_stride, q, mat=None, params=None):

@@ -566,13 +566,15 @@ template <class T>
 void stage(int scheme, int pde, const Params& P, int dim, const Patch* patches, int K, int h,
            int64_t var_stride, const double* qs, const double* q0, double* out, double* acc,
            const double* mat, double dt, double a, double b, double g, double dd, double sigma,
-           double* lam) {
+           double* lam, const int32_t* only = nullptr, int n_only = 0) {
   const PdeInfo I = pde_info(pde);
   const int N = I.N, M = I.M;
   const T gdt = T(g) * T(dt), ddt = T(dd) * T(dt);  // per-stage scalars g dt and d dt
   double lam_max = 0.0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(max : lam_max) if (K > 1)
-  for (int k = 0; k < K; ++k) {
+  const int n = only ? n_only : K;  // optionally only the listed patches (halos still from all)
+#pragma omp parallel for schedule(dynamic, 1) reduction(max : lam_max) if (n > 1)
+  for (int kk = 0; kk < n; ++kk) {
+    const int k = only ? only[kk] : kk;
     Block<T> B;
     gather_block(B, patches, k, dim, h, N, M, var_stride, qs, mat);
     std::vector<T> L;
@@ -722,6 +724,18 @@ int or_stage(int scheme, int pde, int dim, const void* patches, int K, int halo,
   Params P = make_params(pde, prm, nprm);
   stage<double>(scheme, pde, P, dim, (const Patch*)patches, K, halo, var_stride, qs, q0, out, acc,
                 mat, dt, a, b, g, d, sigma, lam);
+  return 0;
+}
+
+// One stage on the listed patches only (halos still come from every patch):
+// a sample of a workload too large for the whole oracle.
+int or_stage_subset(int scheme, int pde, int dim, const void* patches, int K, int halo, int64_t var_stride,
+                    const double* qs, const double* q0, double* out, double* acc, const double* mat,
+                    double dt, double a, double b, double g, double d, double sigma, const double* prm,
+                    int nprm, const int32_t* only, int n_only) {
+  Params P = make_params(pde, prm, nprm);
+  stage<double>(scheme, pde, P, dim, (const Patch*)patches, K, halo, var_stride, qs, q0, out, acc, mat, dt,
+                a, b, g, d, sigma, nullptr, only, n_only);
   return 0;
 }
 

@@ -1,0 +1,124 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times (autotuned kernel variant, whole time steps through dh_rk_step).
+
+3D Euler (10.5M voxels), the wave system (8.4M) and SRHD (16.7M) are compared
+with the oracle voxel by voxel after one full time step; GW59 (31M voxels x 59
+unknowns, 14.6 GB per state) is compared on a sample of patches from every
+level after one stage (the oracle updates only the sampled patches)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_parity, dev, host, require_cuda
+from helpers import voxel_mask
+from paper_2608_19273_gb300 import dh, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_step(torch, name, w, q, mat, steps=1):
+    spec = {"euler3d": (0, 3, 0.4), "wave3d": (1, 4, 0.25), "srhd3d": (0, 3, 0.4)}[name]
+    scheme, rk, cfl = spec
+    mesh = w.mesh
+    with dh.Plan(w.pde, 3, mesh.patches, w.halo, mesh.var_stride, w.params) as plan:
+        Q = dev(torch, q)
+        M = dev(torch, mat) if mat is not None else None
+        U1, U2 = torch.empty_like(Q), torch.empty_like(Q)
+        ACC = torch.empty_like(Q) if rk == 4 else None
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        if name == "srhd3d":
+            dh.con2prim(plan, Q, U2, M[4], None, 1e-12, 50)
+            M.copy_(U2)
+        dh.max_wave_speed(plan, Q, M, lam)
+        dh.dh_cfl_dt(plan, lam, cfl, dt)
+        dh.dh_autotune(plan, scheme, Q, U1, M, dt, reps=1)
+        for _ in range(steps):
+            dh.dh_rk_step(plan, scheme, rk, Q, U1, U2, ACC, M, dt, lam, cfl, 0.1)
+        torch.cuda.synchronize()
+        return host(Q), float(host(dt)[0])
+
+
+def test_euler3d_full_size_step(orc):
+    torch = require_cuda()
+    w = synth.workload("euler3d")
+    mesh = w.mesh
+    q = orc.prim2con(3, synth.euler_prims(mesh, w.seed), mesh.var_stride)
+    got, dt = _gpu_step(torch, "euler3d", w, q, None)
+    ref = q.copy()
+    dts = orc.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=1, cfl=0.4)
+    assert abs(dt - dts[0]) <= 1e-15 * dts[0]
+    assert_parity(got, ref, voxel_mask(mesh), what="euler3d full size")
+
+
+def test_wave3d_full_size_step(orc):
+    torch = require_cuda()
+    w = synth.workload("wave3d")
+    mesh = w.mesh
+    q, mat = synth.wave_initial(mesh, w.seed)
+    got, dt = _gpu_step(torch, "wave3d", w, q, mat)
+    ref = q.copy()
+    dts = orc.rk_steps(1, 4, 3, mesh.patches, 3, mesh.var_stride, ref, mat=mat, rk=4, steps=1, cfl=0.25,
+                       sigma=0.1, params=w.params)
+    assert abs(dt - dts[0]) <= 1e-15 * dts[0]
+    assert_parity(got, ref, voxel_mask(mesh), what="wave3d full size")
+
+
+def test_srhd3d_full_size_step(orc):
+    torch = require_cuda()
+    w = synth.workload("srhd3d")
+    mesh = w.mesh
+    prim = synth.srhd_initial(mesh, w.seed)
+    q = orc.prim2con(5, prim, mesh.var_stride, params=w.params)
+    got, _ = _gpu_step(torch, "srhd3d", w, q, prim)
+    # oracle: con2prim (warm) before the step and before every stage
+    vs = mesh.var_stride
+    pr = prim.copy()
+    pr[:], st, _, _ = orc.con2prim(q, vs, p_prev=np.ascontiguousarray(pr[4]))
+    lam = orc.max_wave_speed(5, 3, mesh.patches, vs, q, mat=pr, params=w.params)
+    dt = orc.cfl_dt(0.4, float(mesh.patches["dx"].min()), 3, lam)
+    u1, u2 = np.zeros_like(q), np.zeros_like(q)
+    for qs, q0, out, a, b, g in ((q, None, u1, 0, 1, 1), (u1, q, u2, 0.75, 0.25, 0.25), (u2, q, q, 1 / 3, 2 / 3, 2 / 3)):
+        if qs is not q:
+            pr[:], st, _, _ = orc.con2prim(qs, vs, p_prev=np.ascontiguousarray(pr[4]))
+        assert np.all(st == 0)
+        orc.stage(0, 5, 3, mesh.patches, 1, vs, qs, q0=q0, out=out, mat=pr, dt=dt, a=a, b=b, g=g, params=w.params)
+    assert_parity(got, q, voxel_mask(mesh), tol=1e-10, what="srhd3d full size")
+
+
+def test_gw59_full_size_sampled_stage(orc):
+    torch = require_cuda()
+    w = synth.workload("gw59")
+    mesh = w.mesh
+    vs = mesh.var_stride
+    # only alpha and phi_1 are non-zero initially: the host array stays mostly untouched (lazy zero pages)
+    q = np.zeros((59, vs))
+    X = synth.voxel_centres(mesh)
+    rng = np.random.default_rng(w.seed)
+    for li in range(len(mesh.levels)):
+        idx = synth.level_slices(mesh, li)
+        L = synth.level_extent(mesh, li)
+        x0 = [rng.uniform(0.25, 0.75) * L[a] for a in range(3)]
+        g = synth.gaussian(X[:, idx], x0, 0.05, 3)
+        q[55, idx] = 1.0 + 1e-3 * g
+        q[0, idx] = 1e-3 * g
+        q[1, idx] = 2e-3 * g  # Pi_1: makes the nonlinear couplings non-zero
+    del X
+    dt = 1e-3
+    rs = np.random.default_rng(5)
+    sample = np.concatenate([rs.choice(np.arange(a, b), 16, replace=False) for a, b in mesh.level_ranges])
+    with dh.Plan(6, 3, mesh.patches, 3, vs, w.params) as plan:
+        Q = torch.from_numpy(q).cuda()
+        out = torch.zeros_like(Q)
+        d_dt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dh.dh_autotune(plan, 1, Q, out, None, d_dt, reps=1)
+        dh.patch_update_fd_ko(plan, Q, None, out, None, None, d_dt, 0, 1, 1, 0, 0.1)
+        torch.cuda.synchronize()
+        idx = np.concatenate([np.arange(int(mesh.patches[k]["offset"]), int(mesh.patches[k]["offset"]) +
+                                        int(mesh.patches[k]["p"]) ** 3) for k in sample])
+        got = host(out[:, torch.from_numpy(idx).cuda()])
+        del Q, out
+    ref_full = np.zeros_like(q)
+    orc.stage_subset(1, 6, 3, mesh.patches, 3, vs, q, sample, out=ref_full, dt=dt, sigma=0.1, params=w.params)
+    ref = ref_full[:, idx]
+    assert_parity(got, ref, np.ones(len(idx), dtype=bool), what="gw59 full size, sampled patches")
