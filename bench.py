@@ -84,6 +84,21 @@ def parse_args():
     return ap.parse_args()
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """Largest value over all ranks (the timed region of the slowest rank); identity without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, nvox, time_steps, ms):
+    """Cell-updates per second of the whole job: every rank advanced nvox voxels by time_steps in ms."""
+    return world * nvox * time_steps / (ms * 1e-3)
+
+
 def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -455,9 +470,7 @@ def our_arm(args, rank, world, local_rank):
         ms = e0.elapsed_time(e1)
         stage_ms = dh.dh_graph_stage_times(plan, n_timed)
         if dist:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, dist, device="cuda")
             dist.barrier()
         finite = bool(torch.isfinite(Q).all().item())
 
@@ -488,7 +501,7 @@ def our_arm(args, rank, world, local_rank):
         h2d = int(Q.numel() * 8 + (mat.numel() * 8 if mat is not None else 0))
 
     nvox = mesh.nvox
-    value = world * nvox * inner * args.steps / (ms * 1e-3)
+    value = whole_job_rate(world, nvox, inner * args.steps, ms)
     flops_vs = json.load(open(FLOPS_FILE))[spec["flops"]]["flops_per_voxel"]
     stage_sum_s = float(stage_ms.sum()) * 1e-3
     ach = flops_vs * nvox * inner / stage_sum_s / 1e12
