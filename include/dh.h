@@ -248,7 +248,9 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  *   FV (scheme 0): halo ring computed before or after the mid-plane barrier
  *                  x register cap (1 or 2 CTAs per SM) x z-march in whole
  *                  patches or in chunks of <= 16 planes (8 candidates);
- *   FD (scheme 1): register cap (2 candidates).
+ *   FD (scheme 1): register cap x shared-memory staging by plain loads or by
+ *                  TMA tensor copies (4 candidates; TMA only when every level
+ *                  is a run of back-to-back patches, see dh_plan_set_variant).
  * `out` is overwritten.  If cache_path is not NULL the choice is first looked up
  * there (one JSON object per line, keyed by GPU name, PDE, scheme and patch-size
  * histogram) and, when timed, appended to it.  choice_out (optional, 4 ints):
@@ -258,8 +260,21 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
                       const double* dt_dev, int32_t reps, const char* cache_path, int32_t* choice_out,
                       float* times_out, void* stream);
 /* Select a variant directly: fv_var 0..3 (bit 0: ring before the barrier,
- * bit 1: two CTAs per SM), fv_zs 0..1 (z-chunks of <= 16 planes), fd_var 0 or 2. */
+ * bit 1: two CTAs per SM), fv_zs 0..1 (z-chunks of <= 16 planes), fd_var
+ * 0, 2, 4 or 6 (bit 1: two CTAs per SM; bit 2: TMA staging, which needs every
+ * run of equal-size patches to be stored back to back with its face
+ * neighbours inside the run; DH_EUNSUPPORTED otherwise). */
 dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var);
+
+/* Error flags raised on the device by the plan's kernels (bit 0: a bounded
+ * wait for a TMA copy gave up, the tile was skipped).  Synchronous; clear != 0
+ * resets them. */
+dh_status dh_plan_errors(dh_plan* plan, uint32_t* flags, int32_t clear);
+
+/* Test hooks (0 in normal use).  Bit 0: the TMA-staged FD stage arms its
+ * barriers but issues no copy, so that its bounded waits run out and the
+ * error flag path can be exercised without any fault. */
+dh_status dh_plan_set_debug(dh_plan* plan, int32_t flags);
 
 /* Diagnostic: for n doubles x, y_nr[i] = the kernels' Newton-Raphson
  * reciprocal of x[i] and y_div[i] = 1.0 / x[i] (IEEE division), so that a test

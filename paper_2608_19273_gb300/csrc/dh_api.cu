@@ -155,6 +155,8 @@ __global__ void k_check_recip(const double* x, double* y_nr, double* y_div, int6
   }
 }
 
+static inline int pt_nbr(const dh_patch* patches, int k, int f) { return patches[k].nbr[f]; }
+
 static dh_status check_plan(const dh_plan* plan) {
   if (!plan) {
     set_error("plan is NULL");
@@ -283,6 +285,30 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   }
   plan->n_fdwork = (int)fdw.size();
 
+  // Levels for TMA staging (see dh_internal.cuh).
+  std::vector<int2> lvl(K);
+  {
+    bool ok = dim == 3;
+    int nl = 0;
+    for (int k = 0; k < K && ok;) {
+      int e = k + 1;
+      const int64_t step = (int64_t)patches[k].p * patches[k].p * patches[k].p;
+      while (e < K && patches[e].p == patches[k].p && patches[e].offset == patches[e - 1].offset + step) ++e;
+      if (nl >= 8) { ok = false; break; }
+      plan->lvl_p[nl] = patches[k].p;
+      plan->lvl_K[nl] = e - k;
+      plan->lvl_off[nl] = patches[k].offset;
+      for (int j = k; j < e; ++j) lvl[j] = make_int2(nl, j - k);
+      ++nl;
+      k = e;
+    }
+    for (int k = 0; k < K && ok; ++k)
+      for (int f = 0; f < 6; ++f)
+        if (lvl[pt_nbr(patches, k, f)].x != lvl[k].x) ok = false;
+    plan->n_lvl = ok ? nl : 0;
+    plan->tma_ok = ok;
+  }
+
   cudaError_t e = cudaGetDevice(&plan->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_patches, sizeof(dh_patch) * K);
@@ -296,8 +322,10 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   if (e == cudaSuccess && !fdw.empty()) e = cudaMalloc(&plan->d_fdwork, sizeof(FdWork) * fdw.size());
   if (e == cudaSuccess && !fdw.empty())
     e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 2 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 2 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess && plan->tma_ok) e = cudaMalloc(&plan->d_lvl, sizeof(int2) * K);
+  if (e == cudaSuccess && plan->tma_ok) e = cudaMemcpy(plan->d_lvl, lvl.data(), sizeof(int2) * K, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     dh_status st = cuda_error(e, "dh_plan_create");
     dh_plan_destroy(plan);
@@ -314,6 +342,7 @@ dh_status dh_plan_destroy(dh_plan* plan) {
     if (plan->d_work_z[zs]) cudaFree(plan->d_work_z[zs]);
   if (plan->d_red) cudaFree(plan->d_red);
   if (plan->d_fdwork) cudaFree(plan->d_fdwork);
+  if (plan->d_lvl) cudaFree(plan->d_lvl);
   if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
   for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);
@@ -395,6 +424,25 @@ dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* str
   else if (plan->pde == DH_PDE_SRHD3D) k_prim2con_srhd<<<plan->K, 256, 0, s>>>(plan->d_patches, plan->var_stride, prim, cons, plan->params.Gamma);
   else { set_error("dh_prim2con: PDE %d has no primitive form", plan->pde); return DH_EUNSUPPORTED; }
   return cuda_error(cudaGetLastError(), "dh_prim2con launch");
+}
+
+dh_status dh_plan_set_debug(dh_plan* plan, int32_t flags) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  plan->debug_flags = flags;
+  return DH_OK;
+}
+
+dh_status dh_plan_errors(dh_plan* plan, uint32_t* flags, int32_t clear) {
+  if (!plan || !flags) { set_error("dh_plan_errors: bad arguments"); return DH_EINVAL; }
+  unsigned long long v = 0;
+  cudaError_t e = cudaMemcpy(&v, plan->d_red + 2, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "dh_plan_errors");
+  *flags = (uint32_t)v;
+  if (clear) {
+    e = cudaMemset(plan->d_red + 2, 0, sizeof(v));
+    if (e != cudaSuccess) return cuda_error(e, "dh_plan_errors");
+  }
+  return DH_OK;
 }
 
 dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n, void* stream) {

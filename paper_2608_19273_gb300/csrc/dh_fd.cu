@@ -9,23 +9,42 @@
 // states stay bitwise constant).
 //
 // Kernel design: a CTA owns an 8x8x4 tile of one patch (one voxel per
-// thread).  The variables are staged, a group at a time, into a padded
-// 14x14x10 shared-memory box holding the tile and its three-voxel face halos
-// (edges and corners are never read by the axis-aligned stencils and are not
-// loaded).  Halo voxels outside the patch come from the face neighbours.
+// thread).  The variables are staged in groups of at most five into shared
+// memory together with the tile's three-voxel face halos (edges and corners
+// are never read by the axis-aligned stencils and are not loaded); halo
+// voxels outside the patch come from the face neighbours.  Two staging
+// variants exist (the autotuner picks one):
+//   * plain loads: every thread copies voxels into a padded 14x14x10 box;
+//   * TMA: one thread issues seven 5-D tensor copies per group (interior box
+//     and six face slabs, from this patch or its neighbours) that complete on
+//     an mbarrier; groups are double buffered, so the next field group of
+//     GW59 streams in while the current one is computed.
 // Every derivative is taken only for the variables that a column of B_d
-// reads.  Systems with up to 8 unknowns stage all variables at once; the
-// 59-unknown GW59 system is processed field by field (lapse/shift first,
-// then the 11 scalar-wave fields), keeping per voxel only the few coupling
-// quantities (alpha, beta, grad alpha, phi_b Pi_b, source sums) in registers.
+// reads.  GW59 is processed field by field (lapse/shift first, then the 11
+// scalar-wave fields), keeping per voxel only the coupling quantities (alpha,
+// beta, grad alpha, phi_b Pi_b, source sums) in registers.
+#include <cuda.h>
+
+#include <cstring>
+
 #include "dh_internal.cuh"
 #include "dh_pde.cuh"
 
 namespace dh {
 
+// Tensor-map descriptor as a kernel parameter (opaque 128 bytes).
+struct alignas(64) TmaDesc {
+  unsigned long long v[16];
+};
+
+constexpr int FD_MAX_LEVELS = 8;
+enum { TMA_INT = 0, TMA_XS = 1, TMA_YS = 2, TMA_ZS = 3 };
+
 struct FdArgs {
+  TmaDesc maps[FD_MAX_LEVELS][4];  // per level: interior, x-slab, y-slab, z-slab boxes of qs
   const dh_patch* patches;
   const FdWork* work;
+  const int2* lvl;                 // per patch: (level, index within the level)
   const double* qs;
   const double* q0;
   double* out;
@@ -36,6 +55,8 @@ struct FdArgs {
   double sigma;
   double* lam_out;
   unsigned long long* red;
+  unsigned int* err;               // error flags (bit 0: a TMA wait gave up)
+  int debug_no_issue;              // test hook: arm the barrier but issue no copy
   int64_t vs;
   DevParams P;
 };
@@ -51,6 +72,24 @@ constexpr int FBX = FTX + 2 * FH, FBY = FTY + 2 * FH, FBZ = FTZ + 2 * FH;
 constexpr int FBOX = FBX * FBY * FBZ;                                               // 1960
 constexpr int FNSLOT = FTX * FTY * FTZ + 2 * FH * (FTY * FTZ + FTX * FTZ + FTX * FTY);  // 1024
 constexpr int FNT = FTX * FTY * FTZ;                                                // 256 threads
+constexpr int GV = 5;                                                               // variables per group
+
+// TMA staging buffer of one group (doubles): dense boxes, each 128-byte aligned.
+//   interior [5][4][8][8], x-slabs [5][4][8][4] (x rounded out to 16-byte
+//   alignment: the slab starts one voxel further out), y-slabs [5][4][3][8],
+//   z-slabs [5][3][8][8].
+constexpr int TI = 0;
+constexpr int TXM = TI + GV * 4 * 8 * 8;   // 1280
+constexpr int TXP = TXM + GV * 4 * 8 * 4;  // 1920
+constexpr int TYM = TXP + GV * 4 * 8 * 4;  // 2560
+constexpr int TYP = TYM + GV * 4 * 3 * 8;  // 3040
+constexpr int TZM = TYP + GV * 4 * 3 * 8;  // 3520
+constexpr int TZP = TZM + GV * 3 * 8 * 8;  // 4480
+constexpr int TBUF = TZP + GV * 3 * 8 * 8;  // 5440 doubles = 43,520 bytes
+constexpr unsigned TBYTES = TBUF * 8;
+static_assert((TXM * 8) % 128 == 0 && (TXP * 8) % 128 == 0 && (TYM * 8) % 128 == 0 && (TYP * 8) % 128 == 0 &&
+                  (TZM * 8) % 128 == 0 && (TZP * 8) % 128 == 0 && (TBUF * 8) % 128 == 0,
+              "TMA destinations must be 128-byte aligned");
 
 __device__ __forceinline__ int64_t fd_vox_index(const dh_patch* __restrict__ P, int k, int p, int x, int y, int z) {
   if (x < 0) { k = P[k].nbr[0]; x += p; }
@@ -88,7 +127,77 @@ __device__ __forceinline__ void fd_slot(int s, int& x, int& y, int& z) {
 
 __device__ __forceinline__ int fd_box(int x, int y, int z) { return ((z + FH) * FBY + (y + FH)) * FBX + (x + FH); }
 
-// Stage variables [v0, v0 + nv) of qs into smem boxes 0..nv-1.
+// ------------------------------------------------------------- stencils
+// 4th-order centred derivative (times 1/(12 dx)) from the values at -2, -1, +1, +2.
+__device__ __forceinline__ double st_d1(const DevParams& P, double m2, double m1, double p1, double p2, double r12) {
+  return PMUL(P, fma(8.0, PSUB(P, p1, m1), PSUB(P, m2, p2)), r12);
+}
+// Bracketed sixth difference (exactly 0 on constants).
+__device__ __forceinline__ double st_d6(const DevParams& P, double m3, double m2, double m1, double c, double p1,
+                                        double p2, double p3) {
+  const double two = PMUL(P, 2.0, c);
+  const double t3 = PSUB(P, PADD(P, m3, p3), two);
+  const double t2 = PSUB(P, PADD(P, m2, p2), two);
+  const double t1 = PSUB(P, PADD(P, m1, p1), two);
+  return fma(15.0, t1, fma(-6.0, t2, t3));
+}
+
+// Read access to one staged group: the padded box ...
+struct BoxAcc {
+  const double* box;
+  int c;
+  __device__ double val(int v) const { return box[v * FBOX + c]; }
+  template <int D>
+  __device__ double nb(int v, int o) const {
+    constexpr int st = D == 0 ? 1 : (D == 1 ? FBX : FBX * FBY);
+    return box[v * FBOX + c + o * st];
+  }
+};
+
+// ... or the TMA staging buffer (dense interior box plus face slabs).
+struct TmaAcc {
+  const double* b;
+  int lx, ly, lz;
+  __device__ double val(int v) const { return b[TI + ((v * 4 + lz) * 8 + ly) * 8 + lx]; }
+  template <int D>
+  __device__ double nb(int v, int o) const {
+    if (D == 0) {
+      const int x = lx + o;
+      if (x < 0) return b[TXM + ((v * 4 + lz) * 8 + ly) * 4 + (x + 4)];
+      if (x >= 8) return b[TXP + ((v * 4 + lz) * 8 + ly) * 4 + (x - 8)];
+      return b[TI + ((v * 4 + lz) * 8 + ly) * 8 + x];
+    } else if (D == 1) {
+      const int y = ly + o;
+      if (y < 0) return b[TYM + ((v * 4 + lz) * 3 + (y + 3)) * 8 + lx];
+      if (y >= 8) return b[TYP + ((v * 4 + lz) * 3 + (y - 8)) * 8 + lx];
+      return b[TI + ((v * 4 + lz) * 8 + y) * 8 + lx];
+    } else {
+      const int z = lz + o;
+      if (z < 0) return b[TZM + ((v * 3 + (z + 3)) * 8 + ly) * 8 + lx];
+      if (z >= 4) return b[TZP + ((v * 3 + (z - 4)) * 8 + ly) * 8 + lx];
+      return b[TI + ((v * 4 + z) * 8 + ly) * 8 + lx];
+    }
+  }
+};
+
+template <int D, class Acc>
+__device__ __forceinline__ double acc_d1(const DevParams& P, const Acc& S, int v, double r12) {
+  return st_d1(P, S.template nb<D>(v, -2), S.template nb<D>(v, -1), S.template nb<D>(v, 1), S.template nb<D>(v, 2), r12);
+}
+template <class Acc>
+__device__ __forceinline__ double acc_ko3(const DevParams& P, const Acc& S, int v) {
+  const double c = S.val(v);
+  const double dx = st_d6(P, S.template nb<0>(v, -3), S.template nb<0>(v, -2), S.template nb<0>(v, -1), c,
+                          S.template nb<0>(v, 1), S.template nb<0>(v, 2), S.template nb<0>(v, 3));
+  const double dy = st_d6(P, S.template nb<1>(v, -3), S.template nb<1>(v, -2), S.template nb<1>(v, -1), c,
+                          S.template nb<1>(v, 1), S.template nb<1>(v, 2), S.template nb<1>(v, 3));
+  const double dz = st_d6(P, S.template nb<2>(v, -3), S.template nb<2>(v, -2), S.template nb<2>(v, -1), c,
+                          S.template nb<2>(v, 1), S.template nb<2>(v, 2), S.template nb<2>(v, 3));
+  return PADD(P, PADD(P, dx, dy), dz);
+}
+
+// ------------------------------------------------------------- staging
+// Plain loads into the padded box (single buffer; the caller synchronises).
 __device__ __forceinline__ void fd_stage_vars(const FdArgs& A, double* box, const FdWork& w, int p, int v0, int nv) {
   for (int s = threadIdx.x; s < FNSLOT; s += FNT) {
     int x, y, z;
@@ -99,20 +208,72 @@ __device__ __forceinline__ void fd_stage_vars(const FdArgs& A, double* box, cons
   }
 }
 
-// 4th-order centred derivative (times 1/(12 dx)) along stride st.
-__device__ __forceinline__ double fd_d1(const DevParams& P, const double* s, int c, int st, double r12) {
-  return PMUL(P, fma(8.0, PSUB(P, s[c + st], s[c - st]), PSUB(P, s[c - 2 * st], s[c + 2 * st])), r12);
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-// Bracketed sixth difference (exactly 0 on constants).
-__device__ __forceinline__ double fd_d6(const DevParams& P, const double* s, int c, int st) {
-  const double two = PMUL(P, 2.0, s[c]);
-  const double t3 = PSUB(P, PADD(P, s[c - 3 * st], s[c + 3 * st]), two);
-  const double t2 = PSUB(P, PADD(P, s[c - 2 * st], s[c + 2 * st]), two);
-  const double t1 = PSUB(P, PADD(P, s[c - st], s[c + st]), two);
-  return fma(15.0, t1, fma(-6.0, t2, t3));
+
+// One TMA tensor copy (5-D tile) into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load5(void* dst, const TmaDesc* map, int c0, int c1, int c2, int c3, int c4,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::
+          "r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4),
+      "r"(smem_u32(bar))
+      : "memory");
 }
-__device__ __forceinline__ double fd_ko3(const DevParams& P, const double* s, int c) {
-  return PADD(P, PADD(P, fd_d6(P, s, c, 1), fd_d6(P, s, c, FBX)), fd_d6(P, s, c, FBX * FBY));
+
+// Bounded wait for phase `parity` of `bar`: gives up after ~2^27 SM clocks
+// (about 65 ms) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1ll << 27)) return false;
+  }
+}
+
+// Issue the seven copies of group v0 (variables v0..v0+4) of tile w into buffer `buf`.
+__device__ void tma_issue(const FdArgs& A, const FdWork& w, int p, double* buf, uint64_t* bar, int v0) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(TBYTES) : "memory");
+  if (A.debug_no_issue) return;
+  const int2 me = A.lvl[w.patch];
+  const TmaDesc* M = A.maps[me.x];
+  const dh_patch& pt = A.patches[w.patch];
+  const int x0 = w.x0, y0 = w.y0, z0 = w.z0, kl = me.y;
+  tma_load5(buf + TI, &M[TMA_INT], x0, y0, z0, kl, v0, bar);
+  // x slabs (4 wide, 16-byte aligned start), from this patch or the x neighbours
+  if (x0 > 0) tma_load5(buf + TXM, &M[TMA_XS], x0 - 4, y0, z0, kl, v0, bar);
+  else tma_load5(buf + TXM, &M[TMA_XS], p - 4, y0, z0, A.lvl[pt.nbr[0]].y, v0, bar);
+  if (x0 + 8 < p) tma_load5(buf + TXP, &M[TMA_XS], x0 + 8, y0, z0, kl, v0, bar);
+  else tma_load5(buf + TXP, &M[TMA_XS], 0, y0, z0, A.lvl[pt.nbr[1]].y, v0, bar);
+  if (y0 > 0) tma_load5(buf + TYM, &M[TMA_YS], x0, y0 - 3, z0, kl, v0, bar);
+  else tma_load5(buf + TYM, &M[TMA_YS], x0, p - 3, z0, A.lvl[pt.nbr[2]].y, v0, bar);
+  if (y0 + 8 < p) tma_load5(buf + TYP, &M[TMA_YS], x0, y0 + 8, z0, kl, v0, bar);
+  else tma_load5(buf + TYP, &M[TMA_YS], x0, 0, z0, A.lvl[pt.nbr[3]].y, v0, bar);
+  if (z0 > 0) tma_load5(buf + TZM, &M[TMA_ZS], x0, y0, z0 - 3, kl, v0, bar);
+  else tma_load5(buf + TZM, &M[TMA_ZS], x0, y0, p - 3, A.lvl[pt.nbr[4]].y, v0, bar);
+  if (z0 + 4 < p) tma_load5(buf + TZP, &M[TMA_ZS], x0, y0, z0 + 4, kl, v0, bar);
+  else tma_load5(buf + TZP, &M[TMA_ZS], x0, y0, 0, A.lvl[pt.nbr[5]].y, v0, bar);
+}
+
+// CTA-uniform wait; on a timeout every thread records it, waits once more
+// (bounded) for copies still in flight, and the caller abandons the tile.
+__device__ bool tma_wait_all(const FdArgs& A, uint64_t* bar, uint32_t parity) {
+  const bool ok = mbar_wait(bar, parity);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicOr(A.err, 1u);
+    mbar_wait(bar, parity);
+    return false;
+  }
+  return true;
 }
 
 // out / acc update of one variable; returns the new value of the result.
@@ -133,26 +294,17 @@ __device__ __forceinline__ double fd_combine(const FdArgs& A, int64_t ev, double
   return res;
 }
 
-// ------------------------------------------------------------- generic (N <= 8)
-template <class PDE>
-__device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* box, double& lam_thread) {
+// ------------------------------------------------------------- generic (N <= 5)
+template <class PDE, class Acc>
+__device__ void fd_voxel_generic(const FdArgs& A, const Acc& S, int64_t e, double dx, double& lam_thread) {
   constexpr int N = PDE::N, NV = PDE::N + PDE::M;
-  const dh_patch& pt = A.patches[w.patch];
-  const int p = pt.p;
-  fd_stage_vars(A, box, w, p, 0, N);
-  __syncthreads();
-  const int t = threadIdx.x;
-  const int lx = t % FTX, ly = (t / FTX) % FTY, lz = t / (FTX * FTY);
-  const int c = fd_box(lx, ly, lz);
-  const int64_t e = pt.offset + ((int64_t)(w.z0 + lz) * p + (w.y0 + ly)) * p + (w.x0 + lx);
-  const double dx = pt.dx;
   const double r12 = 1.0 / (12.0 * dx);
   const double ko = A.sigma / (64.0 * dx);
   const double dt = *A.dt_dev;
   const double gdt = A.g * dt, ddt = A.d * dt;
   double q[NV], L[N], W[1];
 #pragma unroll
-  for (int v = 0; v < N; ++v) q[v] = box[v * FBOX + c];
+  for (int v = 0; v < N; ++v) q[v] = S.val(v);
 #pragma unroll
   for (int v = 0; v < PDE::M; ++v) q[N + v] = __ldg(A.mat + (int64_t)v * A.vs + e);
   if (PDE::SRC) PDE::source(q, W, A.P, L);
@@ -160,20 +312,26 @@ __device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* box, d
 #pragma unroll
     for (int v = 0; v < N; ++v) L[v] = 0.0;
   }
+  double dq[N], D[N];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int st = d == 0 ? 1 : (d == 1 ? FBX : FBX * FBY);
-    double dq[N], D[N];
+  for (int v = 0; v < N; ++v) dq[v] = PDE::needs_grad(0, v) ? acc_d1<0>(A.P, S, v, r12) : 0.0;
+  PDE::ncp(0, q, dq, A.P, D);
 #pragma unroll
-    for (int v = 0; v < N; ++v) dq[v] = PDE::needs_grad(d, v) ? fd_d1(A.P, box + v * FBOX, c, st, r12) : 0.0;
-    PDE::ncp(d, q, dq, A.P, D);
+  for (int v = 0; v < N; ++v) L[v] = PSUB(A.P, L[v], D[v]);
 #pragma unroll
-    for (int v = 0; v < N; ++v) L[v] = PSUB(A.P, L[v], D[v]);
-  }
+  for (int v = 0; v < N; ++v) dq[v] = PDE::needs_grad(1, v) ? acc_d1<1>(A.P, S, v, r12) : 0.0;
+  PDE::ncp(1, q, dq, A.P, D);
+#pragma unroll
+  for (int v = 0; v < N; ++v) L[v] = PSUB(A.P, L[v], D[v]);
+#pragma unroll
+  for (int v = 0; v < N; ++v) dq[v] = PDE::needs_grad(2, v) ? acc_d1<2>(A.P, S, v, r12) : 0.0;
+  PDE::ncp(2, q, dq, A.P, D);
+#pragma unroll
+  for (int v = 0; v < N; ++v) L[v] = PSUB(A.P, L[v], D[v]);
   double res[NV];
 #pragma unroll
   for (int v = 0; v < N; ++v) {
-    const double Lv = fma(ko, fd_ko3(A.P, box + v * FBOX, c), L[v]);
+    const double Lv = fma(ko, acc_ko3(A.P, S, v), L[v]);
     res[v] = fd_combine(A, (int64_t)v * A.vs + e, q[v], Lv, gdt, ddt);
   }
   if (A.lam_out) {
@@ -184,81 +342,138 @@ __device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* box, d
   }
 }
 
-// ------------------------------------------------------------- GW59
-__device__ void fd_tile_gw59(const FdArgs& A, const FdWork& w, double* box, double& lam_thread) {
+template <class PDE, bool TMA>
+__device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* smem, uint64_t* bars, double& lam_thread) {
+  static_assert(PDE::N <= GV, "generic FD path stages one group of at most five variables");
   const dh_patch& pt = A.patches[w.patch];
   const int p = pt.p;
   const int t = threadIdx.x;
   const int lx = t % FTX, ly = (t / FTX) % FTY, lz = t / (FTX * FTY);
-  const int c = fd_box(lx, ly, lz);
   const int64_t e = pt.offset + ((int64_t)(w.z0 + lz) * p + (w.y0 + ly)) * p + (w.x0 + lx);
+  if (TMA) {
+    if (t == 0) tma_issue(A, w, p, smem, &bars[0], 0);
+    if (!tma_wait_all(A, &bars[0], 0)) return;
+    fd_voxel_generic<PDE>(A, TmaAcc{smem, lx, ly, lz}, e, pt.dx, lam_thread);
+  } else {
+    fd_stage_vars(A, smem, w, p, 0, PDE::N);
+    __syncthreads();
+    fd_voxel_generic<PDE>(A, BoxAcc{smem, fd_box(lx, ly, lz)}, e, pt.dx, lam_thread);
+  }
+}
+
+// ------------------------------------------------------------- GW59
+struct Gw59State {
+  double al, bx, by, bz, dal0, dal1, dal2, ko_ab[4], u[11], sumPi2, bs0, bs1, bs2;
+};
+
+template <class Acc>
+__device__ __forceinline__ void gw59_lapse_shift(const FdArgs& A, const Acc& S, int64_t e, double r12, double ko,
+                                                 Gw59State& G) {
+  const DevParams& P = A.P;
+  G.al = S.val(0); G.bx = S.val(1); G.by = S.val(2); G.bz = S.val(3);
+  G.dal0 = acc_d1<0>(P, S, 0, r12);
+  G.dal1 = acc_d1<1>(P, S, 0, r12);
+  G.dal2 = acc_d1<2>(P, S, 0, r12);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) G.ko_ab[v] = PMUL(P, ko, acc_ko3(P, S, v));
+  // phi_b Pi_b at this voxel for the source coupling
+#pragma unroll
+  for (int bb = 0; bb < 11; ++bb)
+    G.u[bb] = PMUL(P, __ldg(A.qs + (int64_t)(5 * bb) * A.vs + e), __ldg(A.qs + (int64_t)(5 * bb + 1) * A.vs + e));
+  G.sumPi2 = 0.0; G.bs0 = 0.0; G.bs1 = 0.0; G.bs2 = 0.0;
+}
+
+template <class Acc>
+__device__ __forceinline__ void gw59_field(const FdArgs& A, const Acc& S, int a, int64_t e, double r12, double ko,
+                                           double gdt, double ddt, Gw59State& G) {
+  const DevParams& P = A.P;
   const int64_t vs = A.vs;
+  const double al = G.al, bx = G.bx, by = G.by, bz = G.bz;
+  const double phi = S.val(0), Pi = S.val(1), px = S.val(2), py = S.val(3), pz = S.val(4);
+  const double dPi0 = acc_d1<0>(P, S, 1, r12), dPi1 = acc_d1<1>(P, S, 1, r12), dPi2 = acc_d1<2>(P, S, 1, r12);
+  // coupling sum_b C_ab phi_b Pi_b
+  double cs = PMUL(P, P.C[11 * a], G.u[0]);
+#pragma unroll
+  for (int bb = 1; bb < 11; ++bb) cs = fma(P.C[11 * a + bb], G.u[bb], cs);
+  // phi: alpha Pi + beta . psi
+  const double Lphi = fma(al, Pi, fma(bx, px, fma(by, py, PMUL(P, bz, pz))));
+  // Pi: alpha div psi + beta . grad Pi + alpha cs
+  const double dpx0 = acc_d1<0>(P, S, 2, r12), dpx1 = acc_d1<1>(P, S, 2, r12), dpx2 = acc_d1<2>(P, S, 2, r12);
+  const double dpy0 = acc_d1<0>(P, S, 3, r12), dpy1 = acc_d1<1>(P, S, 3, r12), dpy2 = acc_d1<2>(P, S, 3, r12);
+  const double dpz0 = acc_d1<0>(P, S, 4, r12), dpz1 = acc_d1<1>(P, S, 4, r12), dpz2 = acc_d1<2>(P, S, 4, r12);
+  const double LPi = fma(al, PADD(P, PADD(P, dpx0, dpy1), dpz2), fma(bx, dPi0, fma(by, dPi1, fma(bz, dPi2, PMUL(P, al, cs)))));
+  // psi_i: alpha d_i Pi + Pi d_i alpha + beta . grad psi_i
+  const double Lpx = fma(al, dPi0, fma(Pi, G.dal0, fma(bx, dpx0, fma(by, dpx1, PMUL(P, bz, dpx2)))));
+  const double Lpy = fma(al, dPi1, fma(Pi, G.dal1, fma(bx, dpy0, fma(by, dpy1, PMUL(P, bz, dpy2)))));
+  const double Lpz = fma(al, dPi2, fma(Pi, G.dal2, fma(bx, dpz0, fma(by, dpz1, PMUL(P, bz, dpz2)))));
+  G.sumPi2 = fma(Pi, Pi, G.sumPi2);
+  G.bs0 = fma(px, Pi, G.bs0);
+  G.bs1 = fma(py, Pi, G.bs1);
+  G.bs2 = fma(pz, Pi, G.bs2);
+  const int64_t eb = (int64_t)(5 * a) * vs + e;
+  fd_combine(A, eb, phi, fma(ko, acc_ko3(P, S, 0), Lphi), gdt, ddt);
+  fd_combine(A, eb + vs, Pi, fma(ko, acc_ko3(P, S, 1), LPi), gdt, ddt);
+  fd_combine(A, eb + 2 * vs, px, fma(ko, acc_ko3(P, S, 2), Lpx), gdt, ddt);
+  fd_combine(A, eb + 3 * vs, py, fma(ko, acc_ko3(P, S, 3), Lpy), gdt, ddt);
+  fd_combine(A, eb + 4 * vs, pz, fma(ko, acc_ko3(P, S, 4), Lpz), gdt, ddt);
+}
+
+__device__ __forceinline__ void gw59_finish(const FdArgs& A, int64_t e, double gdt, double ddt, const Gw59State& G,
+                                            double& lam_thread) {
+  const DevParams& P = A.P;
+  const int64_t vs = A.vs;
+  const double Lal = fma(PMUL(P, -P.kappa, PMUL(P, G.al, G.al)), G.sumPi2, G.ko_ab[0]);
+  const double ra = fd_combine(A, 55 * vs + e, G.al, Lal, gdt, ddt);
+  const double r0 = fd_combine(A, 56 * vs + e, G.bx, fma(0.75, G.bs0, G.ko_ab[1]), gdt, ddt);
+  const double r1 = fd_combine(A, 57 * vs + e, G.by, fma(0.75, G.bs1, G.ko_ab[2]), gdt, ddt);
+  const double r2 = fd_combine(A, 58 * vs + e, G.bz, fma(0.75, G.bs2, G.ko_ab[3]), gdt, ddt);
+  if (A.lam_out) lam_thread = fmax(lam_thread, PADD(P, ra, fmax(fmax(fabs(r0), fabs(r1)), fabs(r2))));
+}
+
+template <bool TMA>
+__device__ void fd_tile_gw59(const FdArgs& A, const FdWork& w, double* smem, uint64_t* bars, double& lam_thread) {
+  const dh_patch& pt = A.patches[w.patch];
+  const int p = pt.p;
+  const int t = threadIdx.x;
+  const int lx = t % FTX, ly = (t / FTX) % FTY, lz = t / (FTX * FTY);
+  const int64_t e = pt.offset + ((int64_t)(w.z0 + lz) * p + (w.y0 + ly)) * p + (w.x0 + lx);
   const double dx = pt.dx;
   const double r12 = 1.0 / (12.0 * dx);
   const double ko = A.sigma / (64.0 * dx);
   const double dt = *A.dt_dev;
   const double gdt = A.g * dt, ddt = A.d * dt;
-  constexpr int X = 1, Y = FBX, Z = FBX * FBY;
-
-  // lapse and shift: values, grad alpha, KO
-  fd_stage_vars(A, box, w, p, 55, 4);
-  __syncthreads();
-  const double al = box[c], bx = box[FBOX + c], by = box[2 * FBOX + c], bz = box[3 * FBOX + c];
-  const DevParams& P = A.P;
-  const double dal0 = fd_d1(P, box, c, X, r12), dal1 = fd_d1(P, box, c, Y, r12), dal2 = fd_d1(P, box, c, Z, r12);
-  double ko_ab[4];
-#pragma unroll
-  for (int v = 0; v < 4; ++v) ko_ab[v] = PMUL(P, ko, fd_ko3(P, box + v * FBOX, c));
-  // phi_b Pi_b at this voxel for the source coupling
-  double u[11];
-#pragma unroll
-  for (int bb = 0; bb < 11; ++bb) u[bb] = PMUL(P, __ldg(A.qs + (int64_t)(5 * bb) * vs + e), __ldg(A.qs + (int64_t)(5 * bb + 1) * vs + e));
-  double sumPi2 = 0.0, bs0 = 0.0, bs1 = 0.0, bs2 = 0.0;
-
+  Gw59State G;
+  if (TMA) {
+    // groups: 0 = lapse/shift (variables 55..59, 59 out of range reads as 0), 1..11 = fields 0..10
+    if (t == 0) tma_issue(A, w, p, smem, &bars[0], 55);
 #pragma unroll 1
-  for (int a = 0; a < 11; ++a) {
-    __syncthreads();  // previous group's box reads are done
-    fd_stage_vars(A, box, w, p, 5 * a, 5);
+    for (int gi = 0; gi < 12; ++gi) {
+      const int b = gi & 1;
+      if (gi + 1 < 12 && t == 0) tma_issue(A, w, p, smem + (b ^ 1) * TBUF, &bars[b ^ 1], 5 * gi);
+      if (!tma_wait_all(A, &bars[b], (gi >> 1) & 1)) {
+        // abandon the tile; the copy issued into the other buffer may still be in flight
+        if (gi + 1 < 12) mbar_wait(&bars[b ^ 1], ((gi + 1) >> 1) & 1);
+        return;
+      }
+      const TmaAcc S{smem + b * TBUF, lx, ly, lz};
+      if (gi == 0) gw59_lapse_shift(A, S, e, r12, ko, G);
+      else gw59_field(A, S, gi - 1, e, r12, ko, gdt, ddt, G);
+      __syncthreads();  // buffer b is free for the copy issued in the next iteration
+    }
+  } else {
+    const BoxAcc S{smem, fd_box(lx, ly, lz)};
+    fd_stage_vars(A, smem, w, p, 55, 4);
     __syncthreads();
-    const double* sphi = box;
-    const double* sPi = box + FBOX;
-    const double* spx = box + 2 * FBOX;
-    const double* spy = box + 3 * FBOX;
-    const double* spz = box + 4 * FBOX;
-    const double phi = sphi[c], Pi = sPi[c], px = spx[c], py = spy[c], pz = spz[c];
-    const double dPi0 = fd_d1(P, sPi, c, X, r12), dPi1 = fd_d1(P, sPi, c, Y, r12), dPi2 = fd_d1(P, sPi, c, Z, r12);
-    // coupling sum_b C_ab phi_b Pi_b
-    double cs = PMUL(P, A.P.C[11 * a], u[0]);
-#pragma unroll
-    for (int bb = 1; bb < 11; ++bb) cs = fma(A.P.C[11 * a + bb], u[bb], cs);
-    // phi: alpha Pi + beta . psi
-    const double Lphi = fma(al, Pi, fma(bx, px, fma(by, py, PMUL(P, bz, pz))));
-    // Pi: alpha div psi + beta . grad Pi + alpha cs
-    const double dpx0 = fd_d1(P, spx, c, X, r12), dpx1 = fd_d1(P, spx, c, Y, r12), dpx2 = fd_d1(P, spx, c, Z, r12);
-    const double dpy0 = fd_d1(P, spy, c, X, r12), dpy1 = fd_d1(P, spy, c, Y, r12), dpy2 = fd_d1(P, spy, c, Z, r12);
-    const double dpz0 = fd_d1(P, spz, c, X, r12), dpz1 = fd_d1(P, spz, c, Y, r12), dpz2 = fd_d1(P, spz, c, Z, r12);
-    const double LPi = fma(al, PADD(P, PADD(P, dpx0, dpy1), dpz2), fma(bx, dPi0, fma(by, dPi1, fma(bz, dPi2, PMUL(P, al, cs)))));
-    // psi_i: alpha d_i Pi + Pi d_i alpha + beta . grad psi_i
-    const double Lpx = fma(al, dPi0, fma(Pi, dal0, fma(bx, dpx0, fma(by, dpx1, PMUL(P, bz, dpx2)))));
-    const double Lpy = fma(al, dPi1, fma(Pi, dal1, fma(bx, dpy0, fma(by, dpy1, PMUL(P, bz, dpy2)))));
-    const double Lpz = fma(al, dPi2, fma(Pi, dal2, fma(bx, dpz0, fma(by, dpz1, PMUL(P, bz, dpz2)))));
-    sumPi2 = fma(Pi, Pi, sumPi2);
-    bs0 = fma(px, Pi, bs0);
-    bs1 = fma(py, Pi, bs1);
-    bs2 = fma(pz, Pi, bs2);
-    const int64_t eb = (int64_t)(5 * a) * vs + e;
-    fd_combine(A, eb, phi, fma(ko, fd_ko3(P, sphi, c), Lphi), gdt, ddt);
-    fd_combine(A, eb + vs, Pi, fma(ko, fd_ko3(P, sPi, c), LPi), gdt, ddt);
-    fd_combine(A, eb + 2 * vs, px, fma(ko, fd_ko3(P, spx, c), Lpx), gdt, ddt);
-    fd_combine(A, eb + 3 * vs, py, fma(ko, fd_ko3(P, spy, c), Lpy), gdt, ddt);
-    fd_combine(A, eb + 4 * vs, pz, fma(ko, fd_ko3(P, spz, c), Lpz), gdt, ddt);
+    gw59_lapse_shift(A, S, e, r12, ko, G);
+#pragma unroll 1
+    for (int a = 0; a < 11; ++a) {
+      __syncthreads();  // previous group's box reads are done
+      fd_stage_vars(A, smem, w, p, 5 * a, 5);
+      __syncthreads();
+      gw59_field(A, S, a, e, r12, ko, gdt, ddt, G);
+    }
   }
-  const double Lal = fma(PMUL(P, -A.P.kappa, PMUL(P, al, al)), sumPi2, ko_ab[0]);
-  const double ra = fd_combine(A, 55 * vs + e, al, Lal, gdt, ddt);
-  const double r0 = fd_combine(A, 56 * vs + e, bx, fma(0.75, bs0, ko_ab[1]), gdt, ddt);
-  const double r1 = fd_combine(A, 57 * vs + e, by, fma(0.75, bs1, ko_ab[2]), gdt, ddt);
-  const double r2 = fd_combine(A, 58 * vs + e, bz, fma(0.75, bs2, ko_ab[3]), gdt, ddt);
-  if (A.lam_out) lam_thread = fmax(lam_thread, PADD(P, ra, fmax(fmax(fabs(r0), fabs(r1)), fabs(r2))));
+  gw59_finish(A, e, gdt, ddt, G, lam_thread);
 }
 
 __device__ __forceinline__ double fd_warp_max(double v) {
@@ -290,22 +505,36 @@ __device__ void fd_publish_lambda(double lam, double* lam_out, unsigned long lon
   }
 }
 
-// Kernel variants (chosen per plan by the autotuner): VAR bit 1 caps the
-// registers at 128 so that two CTAs fit on an SM.
+// Kernel variants (chosen per plan by the autotuner):
+//   VAR bit 1: at most 128 registers so that two CTAs fit on an SM;
+//   VAR bit 2: TMA staging (double-buffered groups) instead of plain loads.
 template <class PDE, int VAR>
 __global__ void __launch_bounds__(FNT, (VAR & 2) ? 2 : 1) k_fd_stage(const __grid_constant__ FdArgs A) {
-  extern __shared__ __align__(16) double box[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[2];
+  constexpr bool TMA = (VAR & 4) != 0;
+  // TMA destinations start on a 128-byte boundary (the launch adds 128 bytes of slack)
+  double* smem = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~(uintptr_t)127);
+  if (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+  }
   const FdWork w = A.work[blockIdx.x];
   double lam = 0.0;
-  if constexpr (PDE::N == 59) fd_tile_gw59(A, w, box, lam);
-  else fd_tile_generic<PDE>(A, w, box, lam);
+  if constexpr (PDE::N == 59) fd_tile_gw59<TMA>(A, w, smem, bars, lam);
+  else fd_tile_generic<PDE, TMA>(A, w, smem, bars, lam);
   if (A.lam_out) fd_publish_lambda(lam, A.lam_out, A.red);
 }
 
 template <class PDE, int VAR>
 static dh_status fd_launch_var(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
+  constexpr bool TMA = (VAR & 4) != 0;
   constexpr int NB = PDE::N == 59 ? 5 : PDE::N;
-  const size_t smem = sizeof(double) * NB * FBOX;
+  const size_t smem = (TMA ? 2 * (size_t)TBYTES : sizeof(double) * NB * FBOX) + 128;
   static int configured_device = -1;
   if (configured_device != plan->device) {
     cudaError_t e = cudaFuncSetAttribute(k_fd_stage<PDE, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -318,21 +547,81 @@ static dh_status fd_launch_var(dh_plan* plan, const FdArgs& A, cudaStream_t stre
 
 template <class PDE>
 static dh_status fd_launch(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
-  return (plan->fd_var & 2) ? fd_launch_var<PDE, 2>(plan, A, stream) : fd_launch_var<PDE, 0>(plan, A, stream);
+  switch (plan->fd_var & 6) {
+    case 0: return fd_launch_var<PDE, 0>(plan, A, stream);
+    case 2: return fd_launch_var<PDE, 2>(plan, A, stream);
+    case 4: return fd_launch_var<PDE, 4>(plan, A, stream);
+    default: return fd_launch_var<PDE, 6>(plan, A, stream);
+  }
+}
+
+// ------------------------------------------------------------- tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 5-D maps over qs for every level: (x, y, z, patch, variable), four box shapes.
+static dh_status encode_maps(dh_plan* plan, const double* qs, FdArgs& A) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) { set_error("patch_update_fd_ko: cuTensorMapEncodeTiled is unavailable"); return DH_EUNSUPPORTED; }
+  static const cuuint32_t boxes[4][5] = {{8, 8, 4, 1, GV}, {4, 8, 4, 1, GV}, {8, 3, 4, 1, GV}, {8, 8, 3, 1, GV}};
+  for (int l = 0; l < plan->n_lvl; ++l) {
+    const uint64_t p = (uint64_t)plan->lvl_p[l];
+    const cuuint64_t dims[5] = {p, p, p, (cuuint64_t)plan->lvl_K[l], (cuuint64_t)plan->nq};
+    const cuuint64_t strides[4] = {p * 8, p * p * 8, p * p * p * 8, (cuuint64_t)plan->var_stride * 8};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    void* base = (void*)(qs + plan->lvl_off[l]);
+    for (int bt = 0; bt < 4; ++bt) {
+      CUtensorMap m;
+      CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 5, base, dims, strides, boxes[bt], estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        set_error("patch_update_fd_ko: cuTensorMapEncodeTiled failed (%d) for level %d", (int)r, l);
+        return DH_ECUDA;
+      }
+      static_assert(sizeof(TmaDesc) == sizeof(CUtensorMap), "tensor map size");
+      std::memcpy(&A.maps[l][bt], &m, sizeof(CUtensorMap));
+    }
+  }
+  return DH_OK;
 }
 
 dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
                           double sigma, double* lam_out, cudaStream_t stream) {
   FdArgs A;
+  std::memset(&A.maps, 0, sizeof(A.maps));
   A.patches = plan->d_patches;
   A.work = plan->d_fdwork;
+  A.lvl = plan->d_lvl;
   A.qs = qs; A.q0 = q0; A.out = out; A.acc = acc; A.mat = mat; A.dt_dev = dt_dev;
   A.a = a; A.b = b; A.g = g; A.d = d; A.sigma = sigma;
   A.lam_out = lam_out;
   A.red = plan->d_red;
+  A.err = reinterpret_cast<unsigned int*>(plan->d_red + 2);
+  A.debug_no_issue = plan->debug_flags & 1;
   A.vs = plan->var_stride;
   A.P = plan->params;
+  if (plan->fd_var & 4) {
+    if (!plan->tma_ok) { set_error("patch_update_fd_ko: the TMA variant needs contiguous levels (see dh_plan_create)"); return DH_EUNSUPPORTED; }
+    dh_status st = encode_maps(plan, qs, A);
+    if (st != DH_OK) return st;
+  }
   switch (plan->pde) {
     case DH_PDE_ADV_NCP: return fd_launch<PdeAdvNcp>(plan, A, stream);
     case DH_PDE_WAVE3D: return fd_launch<PdeWave>(plan, A, stream);

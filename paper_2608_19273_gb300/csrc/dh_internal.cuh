@@ -66,7 +66,16 @@ struct dh_plan {
   // FD tile list (8x8x4 tiles)
   dh::FdWork* d_fdwork = nullptr;
   int n_fdwork = 0;
-  // reduction scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter
+  // levels for the TMA staging of the FD stage: maximal runs of patches of equal p
+  // stored back to back (offset step p^3) whose face neighbours lie in the same run
+  bool tma_ok = false;
+  int n_lvl = 0;
+  int lvl_p[8] = {0}, lvl_K[8] = {0};
+  int64_t lvl_off[8] = {0};
+  int2* d_lvl = nullptr;  // per patch: (level, index within the level)
+  int debug_flags = 0;    // test hooks (bit 0: TMA barriers armed but no copy issued)
+  // scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter,
+  // [2] error flags (bit 0: a bounded TMA wait gave up), [3] unused
   unsigned long long* d_red = nullptr;
   int num_sms = 0;
   // con2prim settings used by dh_rk_step for SRHD3D

@@ -7,7 +7,7 @@
 //   FV stage: kernel variant (halo ring before / after the mid-plane barrier)
 //             x register cap (1 or 2 CTAs per SM)
 //             x work list (16x16 columns march whole patches / chunks of <= 16 planes)
-//   FD stage: register cap (1 or 2 CTAs per SM)
+//   FD stage: register cap (1 or 2 CTAs per SM) x staging (plain loads or TMA)
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -57,9 +57,13 @@ extern "C" {
 
 dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (fv_var < 0 || fv_var > 3 || fv_zs < 0 || fv_zs > 1 || (fd_var != 0 && fd_var != 2)) {
-    set_error("dh_plan_set_variant: fv_var in 0..3, fv_zs in 0..1, fd_var in {0, 2}");
+  if (fv_var < 0 || fv_var > 3 || fv_zs < 0 || fv_zs > 1 || fd_var < 0 || fd_var > 6 || (fd_var & 1)) {
+    set_error("dh_plan_set_variant: fv_var in 0..3, fv_zs in 0..1, fd_var in {0, 2, 4, 6}");
     return DH_EINVAL;
+  }
+  if ((fd_var & 4) && !plan->tma_ok) {
+    set_error("dh_plan_set_variant: TMA staging needs levels of back-to-back patches whose neighbours stay in the level");
+    return DH_EUNSUPPORTED;
   }
   plan->fv_var = fv_var;
   plan->fv_zs = fv_zs;
@@ -90,6 +94,10 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
   } else {
     cands[nc++] = {plan->fv_var, plan->fv_zs, 0};
     cands[nc++] = {plan->fv_var, plan->fv_zs, 2};
+    if (plan->tma_ok) {
+      cands[nc++] = {plan->fv_var, plan->fv_zs, 4};
+      cands[nc++] = {plan->fv_var, plan->fv_zs, 6};
+    }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

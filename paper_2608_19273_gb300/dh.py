@@ -25,7 +25,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
 
@@ -57,6 +57,8 @@ def lib():
         L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
         L.dh_autotune.argtypes = [vp, i32, vp, vp, vp, vp, i32, ctypes.c_char_p, vp, vp, vp]
         L.dh_plan_set_variant.argtypes = [vp, i32, i32, i32]
+        L.dh_plan_errors.argtypes = [vp, vp, i32]
+        L.dh_plan_set_debug.argtypes = [vp, i32]
         L.patch_update_fv_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp, vp, d, d, d, d,
                                               vp, vp]
         L.con2prim.argtypes = [vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp]
@@ -292,6 +294,16 @@ def dh_autotune(plan, scheme, qs, out, mat, dt_dev, reps=3, cache_path=None, str
 
 def dh_plan_set_variant(plan, fv_var, fv_zs, fd_var):
     _check(lib().dh_plan_set_variant(plan.handle, int(fv_var), int(fv_zs), int(fd_var)), "dh_plan_set_variant")
+
+
+def dh_plan_errors(plan, clear=True):
+    flags = ctypes.c_uint32()
+    _check(lib().dh_plan_errors(plan.handle, ctypes.byref(flags), int(bool(clear))), "dh_plan_errors")
+    return flags.value
+
+
+def dh_plan_set_debug(plan, flags):
+    _check(lib().dh_plan_set_debug(plan.handle, int(flags)), "dh_plan_set_debug")
 
 
 def dh_check_recip(x, y_nr, y_div, stream=None):

@@ -31,7 +31,7 @@ def test_fv_variants_match_oracle(orc, fv_var, fv_zs):
     assert_parity(got, ref, voxel_mask(mesh), what=f"variant {fv_var}/{fv_zs}")
 
 
-@pytest.mark.parametrize("fd_var", [0, 2])
+@pytest.mark.parametrize("fd_var", [0, 2, 4, 6])
 @pytest.mark.parametrize("pde", [synth.PDE_WAVE3D, synth.PDE_GW59])
 def test_fd_variants_match_oracle(orc, fd_var, pde):
     torch = require_cuda()
@@ -68,3 +68,43 @@ def test_autotune_picks_and_caches(orc, tmp_path):
     with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
         v2, z2, f2, cached2, _ = dh.dh_autotune(plan, 0, qs, out, None, d_dt, reps=2, cache_path=cache)
         assert cached2 and (v2, z2, f2) == (v, z, f)
+
+
+def test_fd_tma_on_single_self_periodic_patch(orc):
+    """TMA staging when every face neighbour is the patch itself (all slabs wrap around)."""
+    torch = require_cuda()
+    mesh = synth.make_mesh([synth.Level((1, 1, 1), 16, 1.0 / 16, 0)], dim=3)
+    q, mat = synth.wave_initial(mesh, 3)
+    ref = np.zeros_like(q)
+    orc.stage(1, synth.PDE_WAVE3D, 3, mesh.patches, 3, mesh.var_stride, q, out=ref, mat=mat, dt=1e-3, sigma=0.1,
+              params=[0.1])
+    with dh.Plan(synth.PDE_WAVE3D, 3, mesh.patches, 3, mesh.var_stride, [0.1]) as plan:
+        dh.dh_plan_set_variant(plan, 2, 0, 6)
+        out = torch.zeros(q.shape, dtype=torch.float64, device="cuda")
+        d_dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
+        dh.patch_update_fd_ko(plan, dev(torch, q), None, out, None, dev(torch, mat), d_dt, 0, 1, 1, 0, 0.1)
+        got = host(out)
+        assert dh.dh_plan_errors(plan) == 0
+    assert_parity(got, ref, voxel_mask(mesh), what="tma self-periodic")
+
+
+def test_fd_tma_bounded_wait_reports_timeout(orc):
+    """With the test hook that arms the TMA barriers but issues no copy, every wait runs out:
+    the kernel skips its tiles, raises the error flag and the context stays usable."""
+    torch = require_cuda()
+    mesh = synth.make_mesh([synth.Level((1, 1, 1), 16, 1.0 / 16, 0)], dim=3)
+    q, mat = synth.wave_initial(mesh, 4)
+    with dh.Plan(synth.PDE_WAVE3D, 3, mesh.patches, 3, mesh.var_stride, [0.1]) as plan:
+        dh.dh_plan_set_variant(plan, 2, 0, 6)
+        dh.dh_plan_set_debug(plan, 1)
+        out = torch.full(q.shape, float("nan"), dtype=torch.float64, device="cuda")
+        d_dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
+        dh.patch_update_fd_ko(plan, dev(torch, q), None, out, None, dev(torch, mat), d_dt, 0, 1, 1, 0, 0.1)
+        torch.cuda.synchronize()
+        assert dh.dh_plan_errors(plan) & 1
+        assert torch.isnan(out).all()          # every tile was skipped
+        dh.dh_plan_set_debug(plan, 0)
+        dh.patch_update_fd_ko(plan, dev(torch, q), None, out, None, dev(torch, mat), d_dt, 0, 1, 1, 0, 0.1)
+        torch.cuda.synchronize()
+        assert dh.dh_plan_errors(plan) == 0
+        assert torch.isfinite(out[:, :16 ** 3]).all()
