@@ -79,6 +79,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-con2prim", action="store_true", help="skip the con2prim seed comparison")
+    ap.add_argument("--no-aoas", action="store_true", help="skip the AoAoS gather/scatter measurement")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the patch counts per axis by this factor (small cases for profiling); 1 = full size")
     return ap.parse_args()
@@ -394,6 +395,44 @@ def con2prim_compare(torch, dh, stream):
     return res
 
 
+def measure_aoas(torch, dh, plan, mesh, nq, halo, stream, reps=5):
+    """Gather prologue / scatter epilogue (AoAoS <-> SoA arena) throughput on the workload's patches:
+    nq quantities per voxel, blocks of (p + 2 halo)^3 voxels as shuffled views of one buffer."""
+    lens = [(int(pt["p"]) + 2 * halo) ** mesh.dim * nq for pt in mesh.patches]
+    order = np.random.default_rng(synth.SEED_BASE).permutation(len(lens))
+    starts = np.zeros(len(lens), dtype=np.int64)
+    pos = 0
+    for k in order:
+        starts[k] = pos
+        pos += lens[k] + 1
+    buf = torch.empty(pos, dtype=torch.float64, device="cuda")
+    buf.normal_()
+    ptrs = torch.tensor([buf.data_ptr() + 8 * int(starts[k]) for k in range(len(lens))], dtype=torch.int64,
+                        device="cuda")
+    arena = torch.empty(nq * mesh.var_stride, dtype=torch.float64, device="cuda")
+    out = {}
+    for what in ("gather", "scatter"):
+        call = ((lambda: dh.dh_gather_aoas(plan, ptrs, nq, halo, arena, stream)) if what == "gather" else
+                (lambda: dh.dh_scatter_aoas(plan, arena, ptrs, nq, halo, stream)))
+        for _ in range(3):
+            call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            call()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[what + "_ms"] = ms
+        out[what + "_gbs"] = 16.0 * nq * mesh.nvox / (ms * 1e-3) / 1e9
+    del buf, arena, ptrs
+    torch.cuda.empty_cache()
+    out.update(nq=nq, aos_halo=halo, bytes_per_call=16 * nq * mesh.nvox,
+               note="algorithmic bytes: one read and one write of every interior element; "
+                    "every buffer is larger than L2")
+    return out
+
+
 def our_arm(args, rank, world, local_rank):
     import torch
     from paper_2608_19273_gb300 import dh
@@ -532,9 +571,14 @@ def our_arm(args, rank, world, local_rank):
         "clocks": clocks,
         "state_finite": finite,
     }
-    plan.close()
     del Q, U1, U2, ACC, Q_init, M_init, mat
     torch.cuda.empty_cache()
+    if rank == 0 and not args.no_aoas:
+        ao = measure_aoas(torch, dh, plan, mesh, plan.nq + plan.nm, w.halo, stream)
+        ao["gather_frac"] = ao["gather_gbs"] / hbm
+        ao["scatter_frac"] = ao["scatter_gbs"] / hbm
+        line["aoas"] = ao
+    plan.close()
     if rank == 0 and name in ("euler3d", "srhd3d") and not args.no_con2prim:
         line["con2prim"] = con2prim_compare(torch, dh, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

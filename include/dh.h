@@ -191,6 +191,29 @@ dh_status dh_mlp_train(float* w, float* m, float* v, const float* x, const float
                        int32_t steps, int32_t t0, float lr, float* partials, float* grad, float* loss_log,
                        void* stream);
 
+/* AoAoS <-> SoA arena: the gather prologue K~^(0) and scatter epilogue
+ * K~^(S+1) around the batched kernel (paper Sec. III-C Eq. 4; AoAoS layout
+ * Sec. II-B).  The caller's data are K separately allocated patch blocks,
+ * each an array of structs over the patch AND its halo of width aos_halo
+ * (p^ = p + 2 aos_halo voxels per dimension, Sec. II Eq. 2):
+ *     block_k[((z * p^ + y) * p^ + x) * nq + v]      (halo-inclusive x, y, z; z = 0 in 2D)
+ * aos_patches_dev : DEVICE array of K device pointers, block k for patch k of
+ *                   the plan; blocks are 8-byte aligned and do not overlap
+ *                   each other or the arena.  The caller owns all of them.
+ * arena           : nq-variable arena (nq * var_stride doubles, plan offsets).
+ * gather : arena[v*var_stride + off_k + (z*p + y)*p + x] = block_k[(((z+h)*p^ + y+h)*p^ + x+h)*nq + v]
+ * scatter: the reverse assignment.
+ * Only the p^d interior voxels are copied: halo entries of the blocks are
+ * neither read nor written, and arena elements outside the patches keep
+ * their values.  A combined state of N evolved and M material quantities per
+ * voxel gathers into one (N+M)-variable arena whose first N variables serve
+ * as qs and whose last M (at arena + N*var_stride) serve as mat.
+ * nq in [1, 256], aos_halo in [0, 8]; DH_EINVAL otherwise.  Bit-exact copies. */
+dh_status dh_gather_aoas(dh_plan* plan, const double* const* aos_patches_dev, int32_t nq, int32_t aos_halo,
+                         double* arena, void* stream);
+dh_status dh_scatter_aoas(dh_plan* plan, const double* arena, double* const* aos_patches_dev, int32_t nq,
+                          int32_t aos_halo, void* stream);
+
 /* dt_dev <- cfl * dx_min / (dim * lam_dev[0]) on the device (the CFL rule). */
 dh_status dh_cfl_dt(dh_plan* plan, const double* lam_dev, double cfl, double* dt_dev, void* stream);
 

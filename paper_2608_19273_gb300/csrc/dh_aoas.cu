@@ -1,0 +1,202 @@
+// AoAoS <-> SoA arena: the gather prologue K~^(0) and the scatter epilogue
+// K~^(S+1) that embed the batched kernel (paper Sec. III-C, Eq. 4).
+//
+// The paper's input is K separately allocated patches, each one array of
+// structs (Sec. II-B): voxel after voxel, the nq quantities of a voxel next to
+// each other, over the p^ = p + 2h voxels per dimension of the patch and its
+// halo (Sec. II, Eq. 2).  The kernels of this library work on the SoA arena
+// (one contiguous run per variable and patch), so these two kernels convert:
+//
+//   gather : arena[v*vs + off_k + (z*p + y)*p + x] = blk_k[(((z+h)*p^ + y+h)*p^ + x+h)*nq + v]
+//   scatter: the reverse assignment
+//
+// for the interior voxels only; halo entries of the blocks are never read or
+// written (halos come from the face neighbours inside the stage kernels).
+//
+// Design (an HBM-bound permutation, 16 bytes of traffic per element):
+//   * A CTA takes one unit of the plan's unit list: up to 64 interior rows
+//     (x-runs of p voxels) of one patch; units of long rows come first.
+//   * A warp takes one segment of <= SEG voxels of one row.  The segment is
+//     contiguous on both sides: SEG*nq doubles in the AoS block and SEG
+//     doubles per variable in the arena.  The warp loads it with coalesced
+//     reads into its own shared-memory slice (voxel-major, row pitch nq|1 so
+//     that the transposed reads are free of bank conflicts), then writes it
+//     out coalesced in the other order.  Only __syncwarp is needed.
+//   * Index splits j -> (voxel, quantity) use a float multiply by the
+//     reciprocal of the divisor: j < 2^14, so the quotient is exact.
+#include <algorithm>
+
+#include "dh_internal.cuh"
+
+namespace dh {
+namespace {
+
+constexpr int AO_WARPS = 8;
+constexpr int AO_MAX_NQ = 256;
+constexpr size_t AO_SMEM_TARGET = 96 * 1024;  // two CTAs per SM up to this size
+
+struct AoArgs {
+  const dh_patch* patches;
+  const int2* units;      // (patch, first row)
+  const double* const* src_blocks;
+  double* const* dst_blocks;
+  const double* src_arena;
+  double* dst_arena;
+  int64_t vs;
+  int nq, nqp, halo, dim, seg;
+  float inv_nq;
+};
+
+template <bool GATHER>
+__global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ AoArgs A) {
+  extern __shared__ double ao_smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nq = A.nq, nqp = A.nqp, seg = A.seg, h = A.halo;
+  double* s = ao_smem + (size_t)warp * seg * nqp;
+  const int2 u = A.units[blockIdx.x];
+  const int k = u.x;
+  const int p = A.patches[k].p;
+  const int64_t off = A.patches[k].offset;
+  const int ph = p + 2 * h;
+  const int rows = A.dim == 3 ? p * p : p;
+  const int nrows = min(AO_ROWS_PER_UNIT, rows - u.y);
+  const int nxs = (p + seg - 1) / seg;
+  const int nsegs = nrows * nxs;
+  const double* __restrict__ blk_in = GATHER ? A.src_blocks[k] : nullptr;
+  double* __restrict__ blk_out = GATHER ? nullptr : A.dst_blocks[k];
+  for (int sg = warp; sg < nsegs; sg += AO_WARPS) {
+    const int rl = sg / nxs;
+    const int row = u.y + rl;
+    const int xs = (sg - rl * nxs) * seg;
+    const int n = min(seg, p - xs);
+    int z = 0, y = row;
+    if (A.dim == 3) { z = row / p; y = row - z * p; }
+    const int64_t avox = A.dim == 3 ? ((int64_t)(z + h) * ph + (y + h)) * ph + (xs + h)
+                                    : (int64_t)(y + h) * ph + (xs + h);
+    const int64_t aoff = avox * nq;                     // first double of the segment in the block
+    const int64_t soff = off + (int64_t)row * p + xs;   // first voxel of the segment in the arena
+    const int tot = n * nq;
+    const float inv_n = 1.0f / (float)n;
+    if (GATHER) {
+#pragma unroll 4
+      for (int j = lane; j < tot; j += 32) {
+        const int lv = (int)(((float)j + 0.5f) * A.inv_nq);
+        s[lv * nqp + (j - lv * nq)] = __ldg(blk_in + aoff + j);
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int e = lane; e < tot; e += 32) {
+        const int v = (int)(((float)e + 0.5f) * inv_n);
+        const int lv = e - v * n;
+        A.dst_arena[v * A.vs + soff + lv] = s[lv * nqp + v];
+      }
+    } else {
+#pragma unroll 4
+      for (int e = lane; e < tot; e += 32) {
+        const int v = (int)(((float)e + 0.5f) * inv_n);
+        const int lv = e - v * n;
+        s[lv * nqp + v] = __ldg(A.src_arena + v * A.vs + soff + lv);
+      }
+      __syncwarp();
+#pragma unroll 4
+      for (int j = lane; j < tot; j += 32) {
+        const int lv = (int)(((float)j + 0.5f) * A.inv_nq);
+        blk_out[aoff + j] = s[lv * nqp + (j - lv * nq)];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Segment length: the longest of 64, 32, 16, 8 voxels whose per-CTA slices fit the target.
+int ao_seg(int nqp) {
+  int seg = 64;
+  while (seg > 8 && (size_t)AO_WARPS * seg * nqp * sizeof(double) > AO_SMEM_TARGET) seg >>= 1;
+  return seg;
+}
+
+template <bool GATHER>
+dh_status ao_launch(dh_plan* plan, const AoArgs& A, cudaStream_t s) {
+  const size_t smem = (size_t)AO_WARPS * A.seg * A.nqp * sizeof(double);
+  static int configured_device = -1;
+  if (configured_device != plan->device) {
+    const size_t mx = (size_t)AO_WARPS * ao_seg(AO_MAX_NQ | 1) * (AO_MAX_NQ | 1) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_aoas<GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_aoas)");
+    configured_device = plan->device;
+  }
+  k_aoas<GATHER><<<plan->n_aunits, AO_WARPS * 32, smem, s>>>(A);
+  return cuda_error(cudaGetLastError(), GATHER ? "dh_gather_aoas launch" : "dh_scatter_aoas launch");
+}
+
+dh_status ao_check(const dh_plan* plan, const void* blocks, const void* arena, int32_t nq, int32_t aos_halo,
+                   const char* who) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (!blocks || !arena) { set_error("%s: the block pointer array and the arena are required", who); return DH_EINVAL; }
+  if (nq < 1 || nq > AO_MAX_NQ) { set_error("%s: nq = %d outside [1, %d]", who, nq, AO_MAX_NQ); return DH_EINVAL; }
+  if (aos_halo < 0 || aos_halo > 8) { set_error("%s: aos_halo = %d outside [0, 8]", who, aos_halo); return DH_EINVAL; }
+  if (((uintptr_t)arena & 7) != 0 || ((uintptr_t)blocks & 7) != 0) {
+    set_error("%s: arena and block pointer array must be 8-byte aligned", who);
+    return DH_EINVAL;
+  }
+  if (plan->n_aunits <= 0 || !plan->d_aunits) { set_error("%s: plan has no unit list", who); return DH_EINVAL; }
+  return DH_OK;
+}
+
+AoArgs ao_args(const dh_plan* plan, int nq, int halo) {
+  AoArgs A{};
+  A.patches = plan->d_patches;
+  A.units = plan->d_aunits;
+  A.vs = plan->var_stride;
+  A.nq = nq;
+  A.nqp = nq | 1;
+  A.halo = halo;
+  A.dim = plan->dim;
+  A.seg = ao_seg(A.nqp);
+  A.inv_nq = 1.0f / (float)nq;
+  return A;
+}
+
+}  // namespace
+
+// Unit list of the plan: up to AO_ROWS_PER_UNIT rows of one patch per CTA,
+// units of the largest p first.
+std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim) {
+  std::vector<int> idx(K);
+  for (int k = 0; k < K; ++k) idx[k] = k;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return patches[a].p > patches[b].p; });
+  std::vector<int2> units;
+  for (int k : idx) {
+    const int p = patches[k].p, rows = dim == 3 ? p * p : p;
+    for (int r = 0; r < rows; r += AO_ROWS_PER_UNIT) units.push_back(make_int2(k, r));
+  }
+  return units;
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+dh_status dh_gather_aoas(dh_plan* plan, const double* const* aos_patches_dev, int32_t nq, int32_t aos_halo,
+                         double* arena, void* stream) {
+  dh_status st = ao_check(plan, aos_patches_dev, arena, nq, aos_halo, "dh_gather_aoas");
+  if (st != DH_OK) return st;
+  AoArgs A = ao_args(plan, nq, aos_halo);
+  A.src_blocks = aos_patches_dev;
+  A.dst_arena = arena;
+  return ao_launch<true>(plan, A, (cudaStream_t)stream);
+}
+
+dh_status dh_scatter_aoas(dh_plan* plan, const double* arena, double* const* aos_patches_dev, int32_t nq,
+                          int32_t aos_halo, void* stream) {
+  dh_status st = ao_check(plan, aos_patches_dev, arena, nq, aos_halo, "dh_scatter_aoas");
+  if (st != DH_OK) return st;
+  AoArgs A = ao_args(plan, nq, aos_halo);
+  A.dst_blocks = aos_patches_dev;
+  A.src_arena = arena;
+  return ao_launch<false>(plan, A, (cudaStream_t)stream);
+}
+
+}  // extern "C"

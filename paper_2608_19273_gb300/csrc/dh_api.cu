@@ -324,6 +324,11 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 4 * sizeof(unsigned long long));
+  const std::vector<int2> aunits = aoas_units(patches, K, dim);
+  plan->n_aunits = (int)aunits.size();
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_aunits, sizeof(int2) * aunits.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->d_aunits, aunits.data(), sizeof(int2) * aunits.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && plan->tma_ok) e = cudaMalloc(&plan->d_lvl, sizeof(int2) * K);
   if (e == cudaSuccess && plan->tma_ok) e = cudaMemcpy(plan->d_lvl, lvl.data(), sizeof(int2) * K, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -343,6 +348,7 @@ dh_status dh_plan_destroy(dh_plan* plan) {
   if (plan->d_red) cudaFree(plan->d_red);
   if (plan->d_fdwork) cudaFree(plan->d_fdwork);
   if (plan->d_lvl) cudaFree(plan->d_lvl);
+  if (plan->d_aunits) cudaFree(plan->d_aunits);
   if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
   for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);

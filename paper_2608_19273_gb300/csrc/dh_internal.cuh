@@ -36,6 +36,9 @@ struct Work {
   int16_t y0[4];
 };
 
+// Rows (x-runs of p voxels) per CTA of the AoAoS gather/scatter kernels.
+constexpr int AO_ROWS_PER_UNIT = 64;
+
 // One FD tile: an 8x8x4 block of one patch.
 struct FdWork {
   int32_t patch;
@@ -73,6 +76,9 @@ struct dh_plan {
   int lvl_p[8] = {0}, lvl_K[8] = {0};
   int64_t lvl_off[8] = {0};
   int2* d_lvl = nullptr;  // per patch: (level, index within the level)
+  // AoAoS gather/scatter units: (patch, first row), up to AO_ROWS_PER_UNIT rows each
+  int2* d_aunits = nullptr;
+  int n_aunits = 0;
   int debug_flags = 0;    // test hooks (bit 0: TMA barriers armed but no copy issued)
   // scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter,
   // [2] error flags (bit 0: a bounded TMA wait gave up), [3] unused
@@ -105,6 +111,8 @@ inline void finish_params(DevParams& P) {
   P.gm1 = P.gamma - 1.0;
   P.Gq = P.Gamma / (P.Gamma - 1.0);
 }
+
+std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim);
 
 dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,

@@ -24,7 +24,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
-           "dh_cfl_dt", "dh_prim2con", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
+           "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
            "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
@@ -53,6 +53,8 @@ def lib():
         L.max_wave_speed.argtypes = [vp, vp, vp, vp, vp]
         L.dh_cfl_dt.argtypes = [vp, vp, d, vp, vp]
         L.dh_prim2con.argtypes = [vp, vp, vp, vp]
+        L.dh_gather_aoas.argtypes = [vp, vp, i32, i32, vp, vp]
+        L.dh_scatter_aoas.argtypes = [vp, vp, vp, i32, i32, vp]
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
         L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
         L.dh_autotune.argtypes = [vp, i32, vp, vp, vp, vp, i32, ctypes.c_char_p, vp, vp, vp]
@@ -241,6 +243,28 @@ def dh_cfl_dt(plan, lam_dev, cfl, dt_dev, stream=None):
 
 def dh_prim2con(plan, prim, cons, stream=None):
     _check(lib().dh_prim2con(plan.handle, _ptr(prim, "prim"), _ptr(cons, "cons"), _stream(stream)), "dh_prim2con")
+
+
+def block_pointer_table(blocks):
+    """Device int64 tensor holding the data pointers of a list of CUDA tensors (one AoS block per patch)."""
+    import torch
+    for b in blocks:
+        _ptr(b, "AoS block")
+    return torch.tensor([b.data_ptr() for b in blocks], dtype=torch.int64).to(blocks[0].device)
+
+
+def dh_gather_aoas(plan, block_ptrs, nq, aos_halo, arena, stream=None):
+    """arena <- interior voxels of the K AoS patch blocks (paper Eq. 4 gather prologue).
+
+    ``block_ptrs``: device int64 tensor of K block addresses (block_pointer_table)."""
+    _check(lib().dh_gather_aoas(plan.handle, _ptr(block_ptrs, "block_ptrs"), int(nq), int(aos_halo),
+                                _ptr(arena, "arena"), _stream(stream)), "dh_gather_aoas")
+
+
+def dh_scatter_aoas(plan, arena, block_ptrs, nq, aos_halo, stream=None):
+    """Interior voxels of the K AoS patch blocks <- arena (paper Eq. 4 scatter epilogue)."""
+    _check(lib().dh_scatter_aoas(plan.handle, _ptr(arena, "arena"), _ptr(block_ptrs, "block_ptrs"), int(nq),
+                                 int(aos_halo), _stream(stream)), "dh_scatter_aoas")
 
 
 def dh_plan_set_con2prim(plan, mlp_w=None, tol=1e-12, max_iter=50, fail_count_dev=None):
