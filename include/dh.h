@@ -272,8 +272,9 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  *                  x register cap (1 or 2 CTAs per SM) x z-march in whole
  *                  patches or in chunks of <= 16 planes (8 candidates);
  *   FD (scheme 1): register cap x shared-memory staging by plain loads or by
- *                  TMA tensor copies (4 candidates; TMA only when every level
- *                  is a run of back-to-back patches, see dh_plan_set_variant).
+ *                  TMA tensor copies (2 candidates, or 6 with TMA -- 4 for
+ *                  GW59; TMA only when every level is a run of back-to-back
+ *                  patches, see dh_plan_set_variant).
  * `out` is overwritten.  If cache_path is not NULL the choice is first looked up
  * there (one JSON object per line, keyed by GPU name, PDE, scheme and patch-size
  * histogram) and, when timed, appended to it.  choice_out (optional, 4 ints):
@@ -286,7 +287,9 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
  * bit 1: two CTAs per SM), fv_zs 0..1 (z-chunks of <= 16 planes), fd_var
  * 0, 2, 4 or 6 (bit 1: two CTAs per SM; bit 2: TMA staging, which needs every
  * run of equal-size patches to be stored back to back with its face
- * neighbours inside the run; DH_EUNSUPPORTED otherwise). */
+ * neighbours inside the run; DH_EUNSUPPORTED otherwise), or, for systems of
+ * at most five variables (not GW59), 12 / 20: TMA staging with register caps
+ * for three / four CTAs per SM. */
 dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var);
 
 /* Error flags raised on the device by the plan's kernels (bit 0: a bounded

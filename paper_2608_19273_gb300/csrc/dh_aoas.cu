@@ -14,16 +14,20 @@
 // written (halos come from the face neighbours inside the stage kernels).
 //
 // Design (an HBM-bound permutation, 16 bytes of traffic per element):
-//   * A CTA takes one unit of the plan's unit list: up to 64 interior rows
-//     (x-runs of p voxels) of one patch; units of long rows come first.
-//   * A warp takes one segment of <= SEG voxels of one row.  The segment is
-//     contiguous on both sides: SEG*nq doubles in the AoS block and SEG
-//     doubles per variable in the arena.  The warp loads it with coalesced
-//     reads into its own shared-memory slice (voxel-major, row pitch nq|1 so
-//     that the transposed reads are free of bank conflicts), then writes it
-//     out coalesced in the other order.  Only __syncwarp is needed.
-//   * Index splits j -> (voxel, quantity) use a float multiply by the
-//     reciprocal of the divisor: j < 2^14, so the quotient is exact.
+//   * A CTA takes one unit of the plan's unit list: up to AO_UNIT_VOXELS
+//     consecutive interior voxels (arena order) of one patch; units of the
+//     largest patches come first.
+//   * A warp takes one segment of SEG consecutive interior voxels of the unit.
+//     In the arena a segment is one contiguous run per variable; in the AoS
+//     block it is SEG*nq doubles per row, rows separated by the halo.  The
+//     warp first tabulates the block position of each of its voxels, then
+//     reads the segment with coalesced loads (four in flight per lane) into
+//     its own shared-memory slice (voxel-major, pitch nq|1 so that the
+//     transposed reads are free of bank conflicts) and writes it out
+//     coalesced in the other order.  Only __syncwarp is needed.
+//   * Index splits j -> (voxel, quantity) and x -> (row, x) multiply by a
+//     float reciprocal of the divisor; every quotient involved is below 2^9
+//     and every dividend below 2^15, so the result is the exact quotient.
 #include <algorithm>
 
 #include "dh_internal.cuh"
@@ -33,11 +37,12 @@ namespace {
 
 constexpr int AO_WARPS = 8;
 constexpr int AO_MAX_NQ = 256;
+constexpr int AO_BATCH = 4;                   // loads in flight per lane
 constexpr size_t AO_SMEM_TARGET = 96 * 1024;  // two CTAs per SM up to this size
 
 struct AoArgs {
   const dh_patch* patches;
-  const int2* units;      // (patch, first row)
+  const int2* units;      // (patch, first voxel)
   const double* const* src_blocks;
   double* const* dst_blocks;
   const double* src_arena;
@@ -47,61 +52,104 @@ struct AoArgs {
   float inv_nq;
 };
 
+// Shared memory of one warp: SEG x nqp doubles, then SEG ints (block voxel index of each voxel).
+__host__ __device__ inline size_t ao_warp_bytes(int seg, int nqp) {
+  return (size_t)seg * nqp * sizeof(double) + (size_t)seg * sizeof(int);
+}
+
+__device__ __forceinline__ int fdiv_small(int a, float inv_b) { return (int)(((float)a + 0.5f) * inv_b); }
+
 template <bool GATHER>
 __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ AoArgs A) {
   extern __shared__ double ao_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nq = A.nq, nqp = A.nqp, seg = A.seg, h = A.halo;
-  double* s = ao_smem + (size_t)warp * seg * nqp;
+  unsigned char* wbase = reinterpret_cast<unsigned char*>(ao_smem) + (size_t)warp * ao_warp_bytes(seg, nqp);
+  double* s = reinterpret_cast<double*>(wbase);
+  int* tab = reinterpret_cast<int*>(wbase + (size_t)seg * nqp * sizeof(double));
   const int2 u = A.units[blockIdx.x];
   const int k = u.x;
   const int p = A.patches[k].p;
   const int64_t off = A.patches[k].offset;
   const int ph = p + 2 * h;
-  const int rows = A.dim == 3 ? p * p : p;
-  const int nrows = min(AO_ROWS_PER_UNIT, rows - u.y);
-  const int nxs = (p + seg - 1) / seg;
-  const int nsegs = nrows * nxs;
+  const int nvox = A.dim == 3 ? p * p * p : p * p;
+  const int uvox = min(AO_UNIT_VOXELS, nvox - u.y);
+  const int nsegs = (uvox + seg - 1) / seg;
+  const float inv_p = 1.0f / (float)p;
   const double* __restrict__ blk_in = GATHER ? A.src_blocks[k] : nullptr;
   double* __restrict__ blk_out = GATHER ? nullptr : A.dst_blocks[k];
   for (int sg = warp; sg < nsegs; sg += AO_WARPS) {
-    const int rl = sg / nxs;
-    const int row = u.y + rl;
-    const int xs = (sg - rl * nxs) * seg;
-    const int n = min(seg, p - xs);
-    int z = 0, y = row;
-    if (A.dim == 3) { z = row / p; y = row - z * p; }
-    const int64_t avox = A.dim == 3 ? ((int64_t)(z + h) * ph + (y + h)) * ph + (xs + h)
-                                    : (int64_t)(y + h) * ph + (xs + h);
-    const int64_t aoff = avox * nq;                     // first double of the segment in the block
-    const int64_t soff = off + (int64_t)row * p + xs;   // first voxel of the segment in the arena
+    const int i0 = u.y + sg * seg;               // first voxel of the segment (patch-local, arena order)
+    const int n = min(seg, u.y + uvox - i0);
+    // block voxel index of every voxel of the segment
+    const int row0 = i0 / p, x0 = i0 - row0 * p;
+    const int z0 = A.dim == 3 ? row0 / p : 0, y0 = row0 - z0 * p;
+    for (int lv = lane; lv < n; lv += 32) {
+      const int t = x0 + lv;
+      const int dr = fdiv_small(t, inv_p);       // rows advanced (t < p + seg)
+      const int x = t - dr * p;
+      int y = y0 + dr, z = z0;
+      if (A.dim == 3) {
+        const int dz = fdiv_small(y, inv_p);     // y < p + seg
+        y -= dz * p;
+        z += dz;
+      }
+      tab[lv] = A.dim == 3 ? ((z + h) * ph + (y + h)) * ph + (x + h) : (y + h) * ph + (x + h);
+    }
+    __syncwarp();
+    const int64_t soff = off + i0;
     const int tot = n * nq;
     const float inv_n = 1.0f / (float)n;
     if (GATHER) {
-#pragma unroll 4
-      for (int j = lane; j < tot; j += 32) {
-        const int lv = (int)(((float)j + 0.5f) * A.inv_nq);
-        s[lv * nqp + (j - lv * nq)] = __ldg(blk_in + aoff + j);
+      for (int jb = lane; jb < tot; jb += 32 * AO_BATCH) {
+        double r[AO_BATCH];
+#pragma unroll
+        for (int b = 0; b < AO_BATCH; ++b) {
+          const int j = jb + 32 * b;
+          if (j < tot) {
+            const int lv = fdiv_small(j, A.inv_nq);
+            r[b] = __ldg(blk_in + (int64_t)tab[lv] * nq + (j - lv * nq));
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < AO_BATCH; ++b) {
+          const int j = jb + 32 * b;
+          if (j < tot) {
+            const int lv = fdiv_small(j, A.inv_nq);
+            s[lv * nqp + (j - lv * nq)] = r[b];
+          }
+        }
       }
       __syncwarp();
-#pragma unroll 4
       for (int e = lane; e < tot; e += 32) {
-        const int v = (int)(((float)e + 0.5f) * inv_n);
+        const int v = fdiv_small(e, inv_n);
         const int lv = e - v * n;
         A.dst_arena[v * A.vs + soff + lv] = s[lv * nqp + v];
       }
     } else {
-#pragma unroll 4
-      for (int e = lane; e < tot; e += 32) {
-        const int v = (int)(((float)e + 0.5f) * inv_n);
-        const int lv = e - v * n;
-        s[lv * nqp + v] = __ldg(A.src_arena + v * A.vs + soff + lv);
+      for (int eb = lane; eb < tot; eb += 32 * AO_BATCH) {
+        double r[AO_BATCH];
+#pragma unroll
+        for (int b = 0; b < AO_BATCH; ++b) {
+          const int e = eb + 32 * b;
+          if (e < tot) {
+            const int v = fdiv_small(e, inv_n);
+            r[b] = __ldg(A.src_arena + v * A.vs + soff + (e - v * n));
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < AO_BATCH; ++b) {
+          const int e = eb + 32 * b;
+          if (e < tot) {
+            const int v = fdiv_small(e, inv_n);
+            s[(e - v * n) * nqp + v] = r[b];
+          }
+        }
       }
       __syncwarp();
-#pragma unroll 4
       for (int j = lane; j < tot; j += 32) {
-        const int lv = (int)(((float)j + 0.5f) * A.inv_nq);
-        blk_out[aoff + j] = s[lv * nqp + (j - lv * nq)];
+        const int lv = fdiv_small(j, A.inv_nq);
+        blk_out[(int64_t)tab[lv] * nq + (j - lv * nq)] = s[lv * nqp + (j - lv * nq)];
       }
     }
     __syncwarp();
@@ -111,16 +159,16 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
 // Segment length: the longest of 64, 32, 16, 8 voxels whose per-CTA slices fit the target.
 int ao_seg(int nqp) {
   int seg = 64;
-  while (seg > 8 && (size_t)AO_WARPS * seg * nqp * sizeof(double) > AO_SMEM_TARGET) seg >>= 1;
+  while (seg > 8 && AO_WARPS * ao_warp_bytes(seg, nqp) > AO_SMEM_TARGET) seg >>= 1;
   return seg;
 }
 
 template <bool GATHER>
 dh_status ao_launch(dh_plan* plan, const AoArgs& A, cudaStream_t s) {
-  const size_t smem = (size_t)AO_WARPS * A.seg * A.nqp * sizeof(double);
+  const size_t smem = AO_WARPS * ao_warp_bytes(A.seg, A.nqp);
   static int configured_device = -1;
   if (configured_device != plan->device) {
-    const size_t mx = (size_t)AO_WARPS * ao_seg(AO_MAX_NQ | 1) * (AO_MAX_NQ | 1) * sizeof(double);
+    const size_t mx = AO_WARPS * ao_warp_bytes(ao_seg(AO_MAX_NQ | 1), AO_MAX_NQ | 1);
     cudaError_t e = cudaFuncSetAttribute(k_aoas<GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_aoas)");
     configured_device = plan->device;
@@ -159,7 +207,7 @@ AoArgs ao_args(const dh_plan* plan, int nq, int halo) {
 
 }  // namespace
 
-// Unit list of the plan: up to AO_ROWS_PER_UNIT rows of one patch per CTA,
+// Unit list of the plan: up to AO_UNIT_VOXELS voxels of one patch per CTA,
 // units of the largest p first.
 std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim) {
   std::vector<int> idx(K);
@@ -167,8 +215,8 @@ std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim) {
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return patches[a].p > patches[b].p; });
   std::vector<int2> units;
   for (int k : idx) {
-    const int p = patches[k].p, rows = dim == 3 ? p * p : p;
-    for (int r = 0; r < rows; r += AO_ROWS_PER_UNIT) units.push_back(make_int2(k, r));
+    const int p = patches[k].p, nvox = dim == 3 ? p * p * p : p * p;
+    for (int i = 0; i < nvox; i += AO_UNIT_VOXELS) units.push_back(make_int2(k, i));
   }
   return units;
 }

@@ -507,9 +507,17 @@ __device__ void fd_publish_lambda(double lam, double* lam_out, unsigned long lon
 
 // Kernel variants (chosen per plan by the autotuner):
 //   VAR bit 1: at most 128 registers so that two CTAs fit on an SM;
-//   VAR bit 2: TMA staging (double-buffered groups) instead of plain loads.
+//   VAR bit 2: TMA staging (double-buffered groups) instead of plain loads;
+//   VAR bit 3 / bit 4: register caps for three / four CTAs per SM (80 / 64
+//              registers; with TMA staging the single group buffer of the
+//              generic path, 43.6 KB, lets that many CTAs share an SM).
+template <int VAR>
+constexpr int fd_min_blocks() {
+  return (VAR & 16) ? 4 : (VAR & 8) ? 3 : (VAR & 2) ? 2 : 1;
+}
+
 template <class PDE, int VAR>
-__global__ void __launch_bounds__(FNT, (VAR & 2) ? 2 : 1) k_fd_stage(const __grid_constant__ FdArgs A) {
+__global__ void __launch_bounds__(FNT, fd_min_blocks<VAR>()) k_fd_stage(const __grid_constant__ FdArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[2];
   constexpr bool TMA = (VAR & 4) != 0;
@@ -534,7 +542,8 @@ template <class PDE, int VAR>
 static dh_status fd_launch_var(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
   constexpr bool TMA = (VAR & 4) != 0;
   constexpr int NB = PDE::N == 59 ? 5 : PDE::N;
-  const size_t smem = (TMA ? 2 * (size_t)TBYTES : sizeof(double) * NB * FBOX) + 128;
+  // TMA: GW59 double-buffers its field groups, the generic path stages one group
+  const size_t smem = (TMA ? (PDE::N == 59 ? 2 : 1) * (size_t)TBYTES : sizeof(double) * NB * FBOX) + 128;
   static int configured_device = -1;
   if (configured_device != plan->device) {
     cudaError_t e = cudaFuncSetAttribute(k_fd_stage<PDE, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -547,6 +556,10 @@ static dh_status fd_launch_var(dh_plan* plan, const FdArgs& A, cudaStream_t stre
 
 template <class PDE>
 static dh_status fd_launch(dh_plan* plan, const FdArgs& A, cudaStream_t stream) {
+  if constexpr (PDE::N != 59) {
+    if (plan->fd_var == 12) return fd_launch_var<PDE, 12>(plan, A, stream);
+    if (plan->fd_var == 20) return fd_launch_var<PDE, 20>(plan, A, stream);
+  }
   switch (plan->fd_var & 6) {
     case 0: return fd_launch_var<PDE, 0>(plan, A, stream);
     case 2: return fd_launch_var<PDE, 2>(plan, A, stream);

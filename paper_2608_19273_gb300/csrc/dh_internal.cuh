@@ -36,8 +36,9 @@ struct Work {
   int16_t y0[4];
 };
 
-// Rows (x-runs of p voxels) per CTA of the AoAoS gather/scatter kernels.
-constexpr int AO_ROWS_PER_UNIT = 64;
+// Interior voxels per CTA of the AoAoS gather/scatter kernels (a multiple of
+// every segment length, 8..64).
+constexpr int AO_UNIT_VOXELS = 4096;
 
 // One FD tile: an 8x8x4 block of one patch.
 struct FdWork {
@@ -76,7 +77,7 @@ struct dh_plan {
   int lvl_p[8] = {0}, lvl_K[8] = {0};
   int64_t lvl_off[8] = {0};
   int2* d_lvl = nullptr;  // per patch: (level, index within the level)
-  // AoAoS gather/scatter units: (patch, first row), up to AO_ROWS_PER_UNIT rows each
+  // AoAoS gather/scatter units: (patch, first voxel), up to AO_UNIT_VOXELS voxels each
   int2* d_aunits = nullptr;
   int n_aunits = 0;
   int debug_flags = 0;    // test hooks (bit 0: TMA barriers armed but no copy issued)

@@ -7,7 +7,9 @@
 //   FV stage: kernel variant (halo ring before / after the mid-plane barrier)
 //             x register cap (1 or 2 CTAs per SM)
 //             x work list (16x16 columns march whole patches / chunks of <= 16 planes)
-//   FD stage: register cap (1 or 2 CTAs per SM) x staging (plain loads or TMA)
+//   FD stage: register cap (1 or 2 CTAs per SM) x staging (plain loads or TMA);
+//             with TMA staging of one group (systems of <= 5 variables) also
+//             caps for 3 and 4 CTAs per SM
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -57,8 +59,11 @@ extern "C" {
 
 dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (fv_var < 0 || fv_var > 3 || fv_zs < 0 || fv_zs > 1 || fd_var < 0 || fd_var > 6 || (fd_var & 1)) {
-    set_error("dh_plan_set_variant: fv_var in 0..3, fv_zs in 0..1, fd_var in {0, 2, 4, 6}");
+  const bool fd_ok = fd_var == 0 || fd_var == 2 || fd_var == 4 || fd_var == 6 ||
+                     ((fd_var == 12 || fd_var == 20) && plan->pde != DH_PDE_GW59);
+  if (fv_var < 0 || fv_var > 3 || fv_zs < 0 || fv_zs > 1 || !fd_ok) {
+    set_error("dh_plan_set_variant: fv_var in 0..3, fv_zs in 0..1, fd_var in {0, 2, 4, 6} "
+              "(and 12, 20 except for GW59)");
     return DH_EINVAL;
   }
   if ((fd_var & 4) && !plan->tma_ok) {
@@ -97,6 +102,10 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
     if (plan->tma_ok) {
       cands[nc++] = {plan->fv_var, plan->fv_zs, 4};
       cands[nc++] = {plan->fv_var, plan->fv_zs, 6};
+      if (plan->pde != DH_PDE_GW59) {
+        cands[nc++] = {plan->fv_var, plan->fv_zs, 12};
+        cands[nc++] = {plan->fv_var, plan->fv_zs, 20};
+      }
     }
   }
   cudaEvent_t e0, e1;

@@ -25,6 +25,8 @@ def mesh_for(case):
         return synth.make_mesh([synth.Level((2, 2, 2), 8, 1.0 / 16, 0)], dim=3)
     if case == "p24_cube":
         return synth.make_mesh([synth.Level((2, 2, 2), 24, 1.0 / 48, 0)], dim=3)
+    if case == "p256_2d":
+        return synth.make_mesh([synth.Level((2, 1, 1), 256, 1.0 / 512, 0)], dim=2)
     raise KeyError(case)
 
 
@@ -77,7 +79,7 @@ def run_case(torch, mesh, nq, halo, seed, separate=True):
 
 @pytest.mark.parametrize("case,nq,halo", [("euler3d_s4", 5, 0), ("euler3d_s4", 5, 1), ("gw59_s8", 59, 3),
                                           ("euler2d", 4, 1), ("p8_cube", 256, 2), ("p24_cube", 1, 0),
-                                          ("p24_cube", 10, 1), ("p8_cube", 23, 8)])
+                                          ("p24_cube", 10, 1), ("p8_cube", 23, 8), ("p256_2d", 3, 8)])
 def test_gather_scatter_bit_exact(case, nq, halo):
     torch = require_cuda()
     run_case(torch, mesh_for(case), nq, halo, seed=2608 + nq + 17 * halo)

@@ -31,10 +31,16 @@ def test_fv_variants_match_oracle(orc, fv_var, fv_zs):
     assert_parity(got, ref, voxel_mask(mesh), what=f"variant {fv_var}/{fv_zs}")
 
 
-@pytest.mark.parametrize("fd_var", [0, 2, 4, 6])
+@pytest.mark.parametrize("fd_var", [0, 2, 4, 6, 12, 20])
 @pytest.mark.parametrize("pde", [synth.PDE_WAVE3D, synth.PDE_GW59])
 def test_fd_variants_match_oracle(orc, fd_var, pde):
     torch = require_cuda()
+    if pde == synth.PDE_GW59 and fd_var in (12, 20):
+        with dh.Plan(pde, 3, synth.workload("gw59", scale=8).mesh.patches, 3,
+                     synth.workload("gw59", scale=8).mesh.var_stride, synth.workload("gw59", scale=8).params) as plan:
+            with pytest.raises(dh.DhError):
+                dh.dh_plan_set_variant(plan, 2, 0, fd_var)
+        return
     name = "wave3d" if pde == synth.PDE_WAVE3D else "gw59"
     w = synth.workload(name, scale=8)
     mesh = w.mesh
