@@ -104,7 +104,7 @@ struct FvTile {
                               int fidx, int fstride) {
     const double* F = d == 0 ? S.Fx : S.Fy;
     const double* L = d == 0 ? S.Lx : S.Ly;
-    const double s = fmax(L[Ls], L[Rs]);
+    const double s = max_nn(L[Ls], L[Rs]);
     double dq[N];
 #pragma unroll
     for (int v = 0; v < N; ++v) {
@@ -216,7 +216,7 @@ struct FvTile {
         load_q<PDE>(A, vox_index(A.patches, k, p, x, y, z0 - 1), Qm);
         PDE::prims(Qm, A.P, Wm);
         if (PDE::FLUX) PDE::flux(2, Qm, Wm, A.P, Fzm);
-        const double s = fmax(PDE::speed(2, Qm, Wm, A.P), Lzk);
+        const double s = max_nn(PDE::speed(2, Qm, Wm, A.P), Lzk);
         double dq[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
@@ -263,7 +263,7 @@ struct FvTile {
         PDE::prims(Qn, A.P, Wn);
         if (PDE::FLUX) PDE::flux(2, Qn, Wn, A.P, Fzn);
         Lzn = PDE::speed(2, Qn, Wn, A.P);
-        const double s = fmax(Lzk, Lzn);
+        const double s = max_nn(Lzk, Lzn);
         double dq[N];
 #pragma unroll
         for (int v = 0; v < N; ++v) {
@@ -320,9 +320,9 @@ struct FvTile {
           for (int v = N; v < NV; ++v) res[v] = Qk[v];
           double Wr[NW > 0 ? NW : 1];
           PDE::prims(res, A.P, Wr);
-          double l = fmax(PDE::speed(0, res, Wr, A.P), PDE::speed(1, res, Wr, A.P));
-          if (DIM == 3) l = fmax(l, PDE::speed(2, res, Wr, A.P));
-          lam_thread = fmax(lam_thread, l);
+          double l = max_nn(PDE::speed(0, res, Wr, A.P), PDE::speed(1, res, Wr, A.P));
+          if (DIM == 3) l = max_nn(l, PDE::speed(2, res, Wr, A.P));
+          lam_thread = max_nn(lam_thread, l);
         }
       }
       // ---- publish plane kz+1 (3D)

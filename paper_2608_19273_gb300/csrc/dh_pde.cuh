@@ -44,6 +44,14 @@ __device__ __forceinline__ double recip_nr(double a) {
   return fma(y, e, y);
 }
 
+// max(a, b) for a, b >= +0 (characteristic speeds): non-negative doubles order
+// like their bit patterns read as signed 64-bit integers, so the comparison
+// runs on the integer pipe instead of the FP64 pipe.
+__device__ __forceinline__ double max_nn(double a, double b) {
+  const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+  return __longlong_as_double(ia > ib ? ia : ib);
+}
+
 // ---------------------------------------------------------------- advection
 // dq/dt + div(a q) = 0 with material velocity a (M = 3).  F_d = a_d q, lambda_d = |a_d|.
 struct PdeAdvFlux {

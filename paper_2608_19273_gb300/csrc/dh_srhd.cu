@@ -17,19 +17,23 @@
 // Failures never trap: they are reported through status and the counter.
 #include "dh_internal.cuh"
 #include "dh_mlp.cuh"
+#include "dh_pde.cuh"
 
 namespace dh {
 
 // Returns iterations used (> 0) on convergence, -iterations on failure.
 // Adds and products are issued as FMAs with the run-time constants one/mone/zero
-// (GB300 runs DFMA faster than DADD/DMUL; results are bitwise the same).
+// (GB300 runs DFMA faster than DADD/DMUL; results are bitwise the same).  The
+// two reciprocals per iteration are Newton-Raphson refined hardware estimates
+// (recip_nr, <= 1 ulp from the IEEE quotient): the iteration converges to the
+// same root, and the stopping test still compares successive iterates.
 __device__ int srhd_newton_dev(double G, double D, double S2, double E, double p_lo, double p0, double tol,
                                int max_iter, double one, double mone, double zero, double* p_out) {
   const double gf = (G - 1.0) / G;
   double p = p0;
   for (int it = 1; it <= max_iter; ++it) {
     const double Ep = fma(E, one, p);
-    const double rEp = 1.0 / Ep;
+    const double rEp = recip_nr(Ep);
     const double t = fma(S2, rEp, zero);   // S^2/(E+p)
     const double s2e = fma(t, rEp, zero);  // S^2/(E+p)^2
     const double om = fma(s2e, mone, one);
@@ -37,7 +41,7 @@ __device__ int srhd_newton_dev(double G, double D, double S2, double E, double p
     const double rt = fma(om, rrt, zero);
     const double f = fma(gf, fma(-D, rt, fma(t, mone, Ep)), -p);
     const double fp = fma(gf, fma(-D, fma(fma(s2e, rEp, zero), rrt, zero), fma(s2e, one, one)), mone);
-    double pn = fma(-f, 1.0 / fp, p);
+    double pn = fma(-f, recip_nr(fp), p);
     if (!(pn == pn)) { *p_out = pn; return -it; }
     if (pn <= p_lo) {
       pn = fma(0.5, p, 0.5 * p_lo);
@@ -109,7 +113,7 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
     if (have2 && it2 > 0) st = 1;
     else { st = 2; p = have_prev ? A.p_prev[e] : cold; }
   }
-  const double rEp = 1.0 / (E + p);
+  const double rEp = recip_nr(E + p);
   const double vx = q[1] * rEp, vy = q[2] * rEp, vz = q[3] * rEp;
   const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
   // rho = D / W = D sqrt(1 - v^2)
