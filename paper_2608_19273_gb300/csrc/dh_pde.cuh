@@ -128,12 +128,13 @@ using PdeEuler3 = PdeEuler<3>;
 // ---------------------------------------------------------------- SRHD
 // Special-relativistic hydrodynamics, Q = (D, S_x, S_y, S_z, tau), ideal gas Gamma.
 // The material slots carry the primitives (rho, v_x, v_y, v_z, p) recovered by
-// con2prim.  W = (v_x, v_y, v_z, p, cs^2, v^2, 1/(1 - v^2 cs^2), cs).
+// con2prim.  W = (v_x, v_y, v_z, p, cs^2, v^2, 1/(1 - v^2 cs^2)).
 //   F_d = (D v_d, S v_d + p e_d, S_d - D v_d)
 //   lambda_pm = [v_d (1 - cs^2) +- cs sqrt((1 - v^2)(1 - v^2 cs^2 - v_d^2 (1 - cs^2)))] / (1 - v^2 cs^2)
-//   max(|lambda_+|, |lambda_-|) = (|v_d| (1 - cs^2) + cs sqrt(...)) / (1 - v^2 cs^2)
+//   max(|lambda_+|, |lambda_-|) = (|v_d| (1 - cs^2) + sqrt(cs^2 (1 - v^2)(...))) / (1 - v^2 cs^2)
+// (cs is folded under the square root: one square root per direction, none per voxel).
 struct PdeSRHD {
-  static constexpr int N = 5, M = 5, NW = 8, DIM = 3;
+  static constexpr int N = 5, M = 5, NW = 7, DIM = 3;
   static constexpr bool FLUX = true, NCP = false, SRC = false;
   __device__ static void prims(const double* q, const DevParams& P, double* w) {
     const double rho = q[5], vx = q[6], vy = q[7], vz = q[8], p = q[9];
@@ -142,7 +143,6 @@ struct PdeSRHD {
     const double cs2 = MUL(P, MUL(P, P.Gamma, p), recip_nr(rhoh));
     w[0] = vx; w[1] = vy; w[2] = vz; w[3] = p; w[4] = cs2; w[5] = v2;
     w[6] = recip_nr(fma(-v2, cs2, P.one));
-    w[7] = sqrt(cs2);
   }
   __device__ static void flux(int d, const double* q, const double* w, const DevParams& P, double* F) {
     const double v = sel3(d, w[0], w[1], w[2]), p = w[3];
@@ -155,8 +155,8 @@ struct PdeSRHD {
   __device__ static double speed(int d, const double*, const double* w, const DevParams& P) {
     const double v = sel3(d, w[0], w[1], w[2]), cs2 = w[4], v2 = w[5];
     const double omc = SUB(P, P.one, cs2);
-    const double disc = MUL(P, SUB(P, P.one, v2), fma(-MUL(P, v, v), omc, fma(-v2, cs2, P.one)));
-    return MUL(P, fma(fabs(v), omc, MUL(P, w[7], sqrt(disc))), w[6]);
+    const double disc = MUL(P, MUL(P, cs2, SUB(P, P.one, v2)), fma(-MUL(P, v, v), omc, fma(-v2, cs2, P.one)));
+    return MUL(P, fma(fabs(v), omc, sqrt(disc)), w[6]);
   }
   __device__ static void ncp(int, const double*, const double*, const DevParams&, double*) {}
   __device__ static void source(const double*, const double*, const DevParams&, double*) {}

@@ -42,10 +42,15 @@ __device__ int srhd_newton_dev(double G, double D, double S2, double E, double p
     const double f = fma(gf, fma(-D, rt, fma(t, mone, Ep)), -p);
     const double fp = fma(gf, fma(-D, fma(fma(s2e, rEp, zero), rrt, zero), fma(s2e, one, one)), mone);
     double pn = fma(-f, recip_nr(fp), p);
-    if (!(pn == pn)) { *p_out = pn; return -it; }
-    if (pn <= p_lo) {
+    // The three tests below compare bit patterns on the integer pipe: p_lo,
+    // |pn - p| and tol pn are non-negative, and a non-negative double orders
+    // like its bits read as a signed 64-bit integer (a negative pn reads as a
+    // negative integer, so it still compares below p_lo).
+    const long long ipn = __double_as_longlong(pn);
+    if ((ipn & 0x7fffffffffffffffll) > 0x7ff0000000000000ll) { *p_out = pn; return -it; }  // NaN
+    if (ipn <= __double_as_longlong(p_lo)) {
       pn = fma(0.5, p, 0.5 * p_lo);
-    } else if (fabs(fma(pn, one, -p)) <= fma(tol, pn, zero)) {
+    } else if (__double_as_longlong(fabs(fma(pn, one, -p))) <= __double_as_longlong(fma(tol, pn, zero))) {
       *p_out = pn;
       return it;
     }
@@ -79,7 +84,7 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   const double D = q[0], E = q[4] + q[0];
   const double S2 = fma(q[1], q[1], fma(q[2], q[2], q[3] * q[3]));
   const double S = sqrt(S2);
-  const double p_lo = fmax(0.0, S - E);
+  const double p_lo = S > E ? S - E : 0.0;  // max(0, S - E), and +0 (never -0) otherwise
   const double cold = fmax(fma(1.0 + 1e-8, p_lo, 1e-300), (G - 1.0) * q[4]);
   const bool have_prev = A.p_prev != nullptr;
   double s1, s2;
