@@ -80,6 +80,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-con2prim", action="store_true", help="skip the con2prim seed comparison")
     ap.add_argument("--no-aoas", action="store_true", help="skip the AoAoS gather/scatter measurement")
+    ap.add_argument("--no-offload", action="store_true", help="skip the offload-mode measurement")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the patch counts per axis by this factor (small cases for profiling); 1 = full size")
     return ap.parse_args()
@@ -433,6 +434,59 @@ def measure_aoas(torch, dh, plan, mesh, nq, halo, stream, reps=5):
     return out
 
 
+def measure_offload(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, stream, inner, compute_ms_per_step):
+    """Offload mode: the state lives in host page-locked AoAoS blocks (one per patch, halo included, shuffled
+    in one buffer); each call gathers it over NVLink-C2C, advances n steps on the GPU and scatters it back."""
+    nq, h = plan.nq + plan.nm, w.halo
+    lens = [(int(pt["p"]) + 2 * h) ** mesh.dim * nq for pt in mesh.patches]
+    order = np.random.default_rng(synth.SEED_BASE + 7).permutation(len(lens))
+    starts = np.zeros(len(lens), dtype=np.int64)
+    pos = 0
+    for k in order:
+        starts[k] = pos
+        pos += lens[k] + 1
+    hbuf = torch.zeros(pos, dtype=torch.float64).pin_memory()
+    addrs = [hbuf.data_ptr() + 8 * int(starts[k]) for k in range(len(lens))]
+    table = torch.tensor(addrs, dtype=torch.int64, device="cuda")
+    arena = arena_init.clone()
+    dh.dh_scatter_aoas(plan, arena, table, nq, h, stream)       # initial state into the host blocks
+    dh.dh_offload_bind(plan, addrs, nq, h)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+    nq_back = nq if spec["pde"] == synth.PDE_SRHD3D else plan.nq
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps):
+        fn()
+        stream.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            fn()
+        ev[1].record(stream)
+        ev[1].synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    g_ms = timed(lambda: dh.dh_gather_aoas(plan, table, nq, h, arena, stream), 3)
+    s_ms = timed(lambda: dh.dh_scatter_aoas(plan, arena, table, nq_back, h, stream), 3)
+    run = lambda n: dh.dh_offload_run(plan, spec["scheme"], spec["rk"], n, arena, U1, U2, ACC, dt, lam, spec["cfl"],
+                                      0.1, nq_back, stream)
+    one_ms = timed(lambda: run(1), 3)
+    many_ms = timed(lambda: run(inner), 1)
+    finite = bool(torch.isfinite(hbuf).all().item())
+    del hbuf, table, arena
+    torch.cuda.empty_cache()
+    nvox = mesh.nvox
+    return {"nq": nq, "nq_back": nq_back, "aos_halo": h, "blocks": "page-locked host memory, one block per patch",
+            "gather_ms": g_ms, "scatter_ms": s_ms,
+            "c2c_read_gbs": 8.0 * nq * nvox / (g_ms * 1e-3) / 1e9,
+            "c2c_write_gbs": 8.0 * nq_back * nvox / (s_ms * 1e-3) / 1e9,
+            "total_ms_1_step": one_ms, "total_ms_%d_steps" % inner: many_ms,
+            "compute_ms_per_step": compute_ms_per_step,
+            "total_over_compute_1_step": one_ms / compute_ms_per_step,
+            "total_over_compute_%d_steps" % inner: many_ms / (inner * compute_ms_per_step),
+            "host_blocks_finite": finite}
+
+
 def our_arm(args, rank, world, local_rank):
     import torch
     from paper_2608_19273_gb300 import dh
@@ -539,6 +593,12 @@ def our_arm(args, rank, world, local_rank):
         e2e_ms = f0.elapsed_time(f1)
         h2d = int(Q.numel() * 8 + (mat.numel() * 8 if mat is not None else 0))
 
+        offload = None
+        if rank == 0 and not args.no_offload and spec["pde"] != synth.PDE_GW59:
+            a0 = Q_init if M_init is None else torch.cat([Q_init, M_init])
+            offload = measure_offload(torch, dh, plan, mesh, spec, w, a0.contiguous(), U1, U2, ACC, stream, inner,
+                                      ms / args.steps / inner)
+
     nvox = mesh.nvox
     value = whole_job_rate(world, nvox, inner * args.steps, ms)
     flops_vs = json.load(open(FLOPS_FILE))[spec["flops"]]["flops_per_voxel"]
@@ -568,6 +628,7 @@ def our_arm(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(Q.numel() * 8)},
         "gpu_launches": int(n_kernels * args.steps),
         "autotune": tune,
+        "offload": offload,
         "clocks": clocks,
         "state_finite": finite,
     }

@@ -208,11 +208,38 @@ dh_status dh_mlp_train(float* w, float* m, float* v, const float* x, const float
  * their values.  A combined state of N evolved and M material quantities per
  * voxel gathers into one (N+M)-variable arena whose first N variables serve
  * as qs and whose last M (at arena + N*var_stride) serve as mat.
- * nq in [1, 256], aos_halo in [0, 8]; DH_EINVAL otherwise.  Bit-exact copies. */
+ * nq in [1, 256], aos_halo in [0, 8]; DH_EINVAL otherwise.  Bit-exact copies.
+ * The blocks may live in device memory or in page-locked host memory, which
+ * the GPU reads and writes in place over NVLink-C2C (see dh_offload_bind). */
 dh_status dh_gather_aoas(dh_plan* plan, const double* const* aos_patches_dev, int32_t nq, int32_t aos_halo,
                          double* arena, void* stream);
 dh_status dh_scatter_aoas(dh_plan* plan, const double* arena, double* const* aos_patches_dev, int32_t nq,
                           int32_t aos_halo, void* stream);
+
+/* Offload mode (paper Sec. III-C/D, Sec. IV): the caller's K patch blocks stay
+ * in host memory in the AoAoS layout above; each call gathers them into the
+ * device arena, advances n_steps time steps there and scatters the result
+ * back.  Page-locked host memory is read and written in place by the gather
+ * and scatter kernels (the host<->device transfer happens inside them).
+ * dh_offload_bind: blocks is a HOST array of K pointers (block k for patch k);
+ *   every block must be device memory, managed memory or page-locked host
+ *   memory (cudaHostAlloc, cudaHostRegister, pinned torch tensors), 8-byte
+ *   aligned, holding (p_k + 2 aos_halo)^d * nq doubles of one allocation;
+ *   pageable memory is rejected with DH_EINVAL.  nq >= N + M: quantities
+ *   0..N-1 are the evolved state, N..N+M-1 the material (SRHD: primitives).
+ *   The plan keeps a device copy of the table (allocated once, replaced by a
+ *   later bind).
+ * dh_offload_run: gather all nq quantities into `arena` (an nq-variable device
+ *   arena: qs = arena, mat = arena + N*var_stride); if cfl > 0 take the wave
+ *   speed of the gathered state; n_steps x dh_rk_step (same scheme, rk, cfl,
+ *   sigma and buffer rules; u1/u2/acc are N-variable device arenas); scatter
+ *   quantities 0..nq_back-1 of every interior voxel back into the blocks
+ *   (nq_back = N returns the evolved state; N + M also the material).
+ *   Asynchronous on `stream`; the blocks hold the result once it completes. */
+dh_status dh_offload_bind(dh_plan* plan, const double* const* blocks, int32_t nq, int32_t aos_halo);
+dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_steps, double* arena, double* u1,
+                         double* u2, double* acc, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
+                         int32_t nq_back, void* stream);
 
 /* dt_dev <- cfl * dx_min / (dim * lam_dev[0]) on the device (the CFL rule). */
 dh_status dh_cfl_dt(dh_plan* plan, const double* lam_dev, double cfl, double* dt_dev, void* stream);

@@ -48,13 +48,16 @@ struct AoArgs {
   const double* src_arena;
   double* dst_arena;
   int64_t vs;
-  int nq, nqp, halo, dim, seg;
-  float inv_nq;
+  int nq;        // quantities per voxel in a block (its struct size in doubles)
+  int v0, nv;    // quantities v0 .. v0+nv-1 of a voxel <-> arena variables 0 .. nv-1
+  int nvp;       // shared-memory pitch nv | 1
+  int halo, dim, seg;
+  float inv_nv;
 };
 
-// Shared memory of one warp: SEG x nqp doubles, then SEG ints (block voxel index of each voxel).
-__host__ __device__ inline size_t ao_warp_bytes(int seg, int nqp) {
-  return (size_t)seg * nqp * sizeof(double) + (size_t)seg * sizeof(int);
+// Shared memory of one warp: SEG x nvp doubles, then SEG ints (block voxel index of each voxel).
+__host__ __device__ inline size_t ao_warp_bytes(int seg, int nvp) {
+  return (size_t)seg * nvp * sizeof(double) + (size_t)seg * sizeof(int);
 }
 
 __device__ __forceinline__ int fdiv_small(int a, float inv_b) { return (int)(((float)a + 0.5f) * inv_b); }
@@ -63,10 +66,10 @@ template <bool GATHER>
 __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ AoArgs A) {
   extern __shared__ double ao_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nq = A.nq, nqp = A.nqp, seg = A.seg, h = A.halo;
-  unsigned char* wbase = reinterpret_cast<unsigned char*>(ao_smem) + (size_t)warp * ao_warp_bytes(seg, nqp);
+  const int nq = A.nq, nv = A.nv, nvp = A.nvp, seg = A.seg, h = A.halo;
+  unsigned char* wbase = reinterpret_cast<unsigned char*>(ao_smem) + (size_t)warp * ao_warp_bytes(seg, nvp);
   double* s = reinterpret_cast<double*>(wbase);
-  int* tab = reinterpret_cast<int*>(wbase + (size_t)seg * nqp * sizeof(double));
+  int* tab = reinterpret_cast<int*>(wbase + (size_t)seg * nvp * sizeof(double));
   const int2 u = A.units[blockIdx.x];
   const int k = u.x;
   const int p = A.patches[k].p;
@@ -76,8 +79,8 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
   const int uvox = min(AO_UNIT_VOXELS, nvox - u.y);
   const int nsegs = (uvox + seg - 1) / seg;
   const float inv_p = 1.0f / (float)p;
-  const double* __restrict__ blk_in = GATHER ? A.src_blocks[k] : nullptr;
-  double* __restrict__ blk_out = GATHER ? nullptr : A.dst_blocks[k];
+  const double* __restrict__ blk_in = GATHER ? A.src_blocks[k] + A.v0 : nullptr;
+  double* __restrict__ blk_out = GATHER ? nullptr : A.dst_blocks[k] + A.v0;
   for (int sg = warp; sg < nsegs; sg += AO_WARPS) {
     const int i0 = u.y + sg * seg;               // first voxel of the segment (patch-local, arena order)
     const int n = min(seg, u.y + uvox - i0);
@@ -98,7 +101,7 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
     }
     __syncwarp();
     const int64_t soff = off + i0;
-    const int tot = n * nq;
+    const int tot = n * nv;
     const float inv_n = 1.0f / (float)n;
     if (GATHER) {
       for (int jb = lane; jb < tot; jb += 32 * AO_BATCH) {
@@ -107,16 +110,16 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
         for (int b = 0; b < AO_BATCH; ++b) {
           const int j = jb + 32 * b;
           if (j < tot) {
-            const int lv = fdiv_small(j, A.inv_nq);
-            r[b] = __ldg(blk_in + (int64_t)tab[lv] * nq + (j - lv * nq));
+            const int lv = fdiv_small(j, A.inv_nv);
+            r[b] = __ldg(blk_in + (int64_t)tab[lv] * nq + (j - lv * nv));
           }
         }
 #pragma unroll
         for (int b = 0; b < AO_BATCH; ++b) {
           const int j = jb + 32 * b;
           if (j < tot) {
-            const int lv = fdiv_small(j, A.inv_nq);
-            s[lv * nqp + (j - lv * nq)] = r[b];
+            const int lv = fdiv_small(j, A.inv_nv);
+            s[lv * nvp + (j - lv * nv)] = r[b];
           }
         }
       }
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
       for (int e = lane; e < tot; e += 32) {
         const int v = fdiv_small(e, inv_n);
         const int lv = e - v * n;
-        A.dst_arena[v * A.vs + soff + lv] = s[lv * nqp + v];
+        A.dst_arena[v * A.vs + soff + lv] = s[lv * nvp + v];
       }
     } else {
       for (int eb = lane; eb < tot; eb += 32 * AO_BATCH) {
@@ -142,14 +145,14 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
           const int e = eb + 32 * b;
           if (e < tot) {
             const int v = fdiv_small(e, inv_n);
-            s[(e - v * n) * nqp + v] = r[b];
+            s[(e - v * n) * nvp + v] = r[b];
           }
         }
       }
       __syncwarp();
       for (int j = lane; j < tot; j += 32) {
-        const int lv = fdiv_small(j, A.inv_nq);
-        blk_out[(int64_t)tab[lv] * nq + (j - lv * nq)] = s[lv * nqp + (j - lv * nq)];
+        const int lv = fdiv_small(j, A.inv_nv);
+        blk_out[(int64_t)tab[lv] * nq + (j - lv * nv)] = s[lv * nvp + (j - lv * nv)];
       }
     }
     __syncwarp();
@@ -157,15 +160,15 @@ __global__ void __launch_bounds__(AO_WARPS * 32) k_aoas(const __grid_constant__ 
 }
 
 // Segment length: the longest of 64, 32, 16, 8 voxels whose per-CTA slices fit the target.
-int ao_seg(int nqp) {
+int ao_seg(int nvp) {
   int seg = 64;
-  while (seg > 8 && AO_WARPS * ao_warp_bytes(seg, nqp) > AO_SMEM_TARGET) seg >>= 1;
+  while (seg > 8 && AO_WARPS * ao_warp_bytes(seg, nvp) > AO_SMEM_TARGET) seg >>= 1;
   return seg;
 }
 
 template <bool GATHER>
 dh_status ao_launch(dh_plan* plan, const AoArgs& A, cudaStream_t s) {
-  const size_t smem = AO_WARPS * ao_warp_bytes(A.seg, A.nqp);
+  const size_t smem = AO_WARPS * ao_warp_bytes(A.seg, A.nvp);
   static int configured_device = -1;
   if (configured_device != plan->device) {
     const size_t mx = AO_WARPS * ao_warp_bytes(ao_seg(AO_MAX_NQ | 1), AO_MAX_NQ | 1);
@@ -191,21 +194,38 @@ dh_status ao_check(const dh_plan* plan, const void* blocks, const void* arena, i
   return DH_OK;
 }
 
-AoArgs ao_args(const dh_plan* plan, int nq, int halo) {
+AoArgs ao_args(const dh_plan* plan, int nq, int v0, int nv, int halo) {
   AoArgs A{};
   A.patches = plan->d_patches;
   A.units = plan->d_aunits;
   A.vs = plan->var_stride;
   A.nq = nq;
-  A.nqp = nq | 1;
+  A.v0 = v0;
+  A.nv = nv;
+  A.nvp = nv | 1;
   A.halo = halo;
   A.dim = plan->dim;
-  A.seg = ao_seg(A.nqp);
-  A.inv_nq = 1.0f / (float)nq;
+  A.seg = ao_seg(A.nvp);
+  A.inv_nv = 1.0f / (float)nv;
   return A;
 }
 
 }  // namespace
+
+// Quantities v0 .. v0+nv-1 of every interior voxel of the blocks <-> arena
+// variables 0 .. nv-1 (validated by the callers).
+dh_status aoas_move(dh_plan* plan, bool gather, const double* const* blocks, int nq, int v0, int nv, int halo,
+                    double* arena, cudaStream_t s) {
+  AoArgs A = ao_args(plan, nq, v0, nv, halo);
+  if (gather) {
+    A.src_blocks = blocks;
+    A.dst_arena = arena;
+    return ao_launch<true>(plan, A, s);
+  }
+  A.dst_blocks = const_cast<double* const*>(blocks);
+  A.src_arena = arena;
+  return ao_launch<false>(plan, A, s);
+}
 
 // Unit list of the plan: up to AO_UNIT_VOXELS voxels of one patch per CTA,
 // units of the largest p first.
@@ -231,20 +251,15 @@ dh_status dh_gather_aoas(dh_plan* plan, const double* const* aos_patches_dev, in
                          double* arena, void* stream) {
   dh_status st = ao_check(plan, aos_patches_dev, arena, nq, aos_halo, "dh_gather_aoas");
   if (st != DH_OK) return st;
-  AoArgs A = ao_args(plan, nq, aos_halo);
-  A.src_blocks = aos_patches_dev;
-  A.dst_arena = arena;
-  return ao_launch<true>(plan, A, (cudaStream_t)stream);
+  return aoas_move(plan, true, aos_patches_dev, nq, 0, nq, aos_halo, arena, (cudaStream_t)stream);
 }
 
 dh_status dh_scatter_aoas(dh_plan* plan, const double* arena, double* const* aos_patches_dev, int32_t nq,
                           int32_t aos_halo, void* stream) {
   dh_status st = ao_check(plan, aos_patches_dev, arena, nq, aos_halo, "dh_scatter_aoas");
   if (st != DH_OK) return st;
-  AoArgs A = ao_args(plan, nq, aos_halo);
-  A.dst_blocks = aos_patches_dev;
-  A.src_arena = arena;
-  return ao_launch<false>(plan, A, (cudaStream_t)stream);
+  return aoas_move(plan, false, aos_patches_dev, nq, 0, nq, aos_halo, const_cast<double*>(arena),
+                   (cudaStream_t)stream);
 }
 
 }  // extern "C"

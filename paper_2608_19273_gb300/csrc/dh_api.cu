@@ -349,6 +349,7 @@ dh_status dh_plan_destroy(dh_plan* plan) {
   if (plan->d_fdwork) cudaFree(plan->d_fdwork);
   if (plan->d_lvl) cudaFree(plan->d_lvl);
   if (plan->d_aunits) cudaFree(plan->d_aunits);
+  if (plan->d_offload) cudaFree(plan->d_offload);
   if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
   for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);

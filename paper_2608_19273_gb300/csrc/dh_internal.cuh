@@ -80,6 +80,9 @@ struct dh_plan {
   // AoAoS gather/scatter units: (patch, first voxel), up to AO_UNIT_VOXELS voxels each
   int2* d_aunits = nullptr;
   int n_aunits = 0;
+  // offload mode: device copy of the bound block pointer table (dh_offload_bind)
+  double** d_offload = nullptr;
+  int offload_nq = 0, offload_halo = 0;
   int debug_flags = 0;    // test hooks (bit 0: TMA barriers armed but no copy issued)
   // scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter,
   // [2] error flags (bit 0: a bounded TMA wait gave up), [3] unused
@@ -114,6 +117,8 @@ inline void finish_params(DevParams& P) {
 }
 
 std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim);
+dh_status aoas_move(dh_plan* plan, bool gather, const double* const* blocks, int nq, int v0, int nv, int halo,
+                    double* arena, cudaStream_t s);
 
 dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,

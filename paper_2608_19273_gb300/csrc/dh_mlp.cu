@@ -70,7 +70,7 @@ __global__ void k_mlp_stats_final(const double* __restrict__ part, int nb, int64
 // Forward pass on raw inputs (z-scored with the statistics in w).
 __global__ void k_mlp_forward(const float* __restrict__ wg, const float* __restrict__ x, int64_t n,
                               float* __restrict__ y) {
-  __shared__ float w[MLP_LEN];
+  __shared__ __align__(16) float w[MLP_LEN];
   for (int i = threadIdx.x; i < MLP_LEN; i += blockDim.x) w[i] = wg[i];
   __syncthreads();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -86,7 +86,7 @@ __global__ void k_mlp_forward(const float* __restrict__ wg, const float* __restr
 __global__ void __launch_bounds__(GB) k_mlp_grad(const float* __restrict__ wg, const float* __restrict__ x,
                                                  const float* __restrict__ t, int64_t off, int B,
                                                  float* __restrict__ part) {
-  __shared__ float w[MLP_LEN];
+  __shared__ __align__(16) float w[MLP_LEN];
   __shared__ float sh1[GB][33], sh2[GB][33], sg1[GB][33], sg2[GB][33];
   __shared__ float sx[GB][3], sgy[GB], sr2[GB];
   for (int i = threadIdx.x; i < MLP_LEN; i += blockDim.x) w[i] = wg[i];

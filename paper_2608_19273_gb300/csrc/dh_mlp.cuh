@@ -32,7 +32,19 @@ __device__ __forceinline__ void mlp_normalize(const float* w, const double* xd, 
   for (int j = 0; j < 3; ++j) x[j] = (float)((xd[j] - (double)w[MLP_MEAN + j]) / (double)w[MLP_STD + j]);
 }
 
-// Forward pass; h1/h2 receive the hidden activations.
+// z-scored FP32 network input formed in FP32 from D, E = tau + D and |S|
+// (the seed path of con2prim: the network is FP32, so its inputs need no FP64
+// divides or logarithm on the FP64 pipe).
+__device__ __forceinline__ void mlp_inputs_f32(const float* w, double D, double E, double S, float* x) {
+  const float rE = 1.0f / (float)E;
+  const float dE = (float)D * rE;
+  const float raw[3] = {(float)S * rE, dE, -logf(dE)};  // |S|/E, D/E, ln(E/D)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) x[j] = (raw[j] - w[MLP_MEAN + j]) / w[MLP_STD + j];
+}
+
+// Forward pass; h1/h2 receive the hidden activations.  w must be 16-byte
+// aligned: the rows of W2 are read as float4.
 __device__ __forceinline__ float mlp_forward(const float* w, const float* x, float* h1, float* h2) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
@@ -45,8 +57,15 @@ __device__ __forceinline__ float mlp_forward(const float* w, const float* x, flo
 #pragma unroll 4
   for (int i = 0; i < 32; ++i) {
     float s = w[MLP_B2 + i];
+    const float4* row = reinterpret_cast<const float4*>(w + MLP_W2 + 32 * i);
 #pragma unroll
-    for (int j = 0; j < 32; ++j) s = fmaf(w[MLP_W2 + 32 * i + j], h1[j], s);
+    for (int j = 0; j < 8; ++j) {
+      const float4 r = row[j];
+      s = fmaf(r.x, h1[4 * j], s);
+      s = fmaf(r.y, h1[4 * j + 1], s);
+      s = fmaf(r.z, h1[4 * j + 2], s);
+      s = fmaf(r.w, h1[4 * j + 3], s);
+    }
     h2[i] = tanhf(s);
     y = fmaf(w[MLP_W3 + i], h2[i], y);
   }

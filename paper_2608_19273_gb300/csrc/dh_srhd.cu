@@ -90,10 +90,8 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   double s1, s2;
   bool have2;
   if (w) {
-    double xd[3];
     float x[3], h1[32], h2[32];
-    srhd_invariants(q, xd);
-    mlp_normalize(w, xd, x);
+    mlp_inputs_f32(w, D, E, S, x);
     const float y = mlp_forward(w, x, h1, h2);
     const double ps = E * exp((double)y);
     const double lo = p_lo * (1.0 + 1e-12);
@@ -146,7 +144,7 @@ __device__ __forceinline__ void count_failures(int nfail, int32_t* fail_count) {
 // One CTA per patch.
 __global__ void __launch_bounds__(256) k_con2prim_patches(const dh_patch* __restrict__ patches, int dim,
                                                           const __grid_constant__ C2PArgs A) {
-  __shared__ float w[MLP_LEN];
+  __shared__ __align__(16) float w[MLP_LEN];
   if (A.mlp) load_mlp_smem(A.mlp, w);
   const dh_patch pt = patches[blockIdx.x];
   const int n = dim == 3 ? pt.p * pt.p * pt.p : pt.p * pt.p;
@@ -160,7 +158,7 @@ __global__ void __launch_bounds__(256) k_con2prim_patches(const dh_patch* __rest
 
 // Flat array of n voxels (element i of variable v at v * stride + i).
 __global__ void __launch_bounds__(256) k_con2prim_flat(int64_t n, const __grid_constant__ C2PArgs A) {
-  __shared__ float w[MLP_LEN];
+  __shared__ __align__(16) float w[MLP_LEN];
   if (A.mlp) load_mlp_smem(A.mlp, w);
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
