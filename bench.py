@@ -81,6 +81,8 @@ def parse_args():
     ap.add_argument("--no-con2prim", action="store_true", help="skip the con2prim seed comparison")
     ap.add_argument("--no-aoas", action="store_true", help="skip the AoAoS gather/scatter measurement")
     ap.add_argument("--no-offload", action="store_true", help="skip the offload-mode measurement")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (JSON lines): reuse a previous choice, else time and append")
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the patch counts per axis by this factor (small cases for profiling); 1 = full size")
     return ap.parse_args()
@@ -528,8 +530,9 @@ def our_arm(args, rank, world, local_rank):
         lam_init = lam.clone()
         # autotune the stage kernel variant on this workload (U1 is scratch here)
         dh.dh_cfl_dt(plan, lam, spec["cfl"], dt, stream)
-        tv, tz, tf, _, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3, stream=stream)
-        tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf,
+        tv, tz, tf, cached, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3,
+                                                    cache_path=args.tune_cache, stream=stream)
+        tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf, "from_cache": cached,
                 "candidate_ms": [round(t, 4) for t in ttimes if t > 0]}
         # eager warm-up step (sets kernel attributes outside of capture), then reset
         dh.dh_rk_step(plan, spec["scheme"], spec["rk"], Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1, stream)
