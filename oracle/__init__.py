@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FV, FD = 0, 1
+FV, FD, FV2 = 0, 1, 2
 
 
 def build(force: bool = False) -> str:

@@ -465,6 +465,112 @@ void fv_operator(int pde, const Params& P, Block<T>& B, double dxd, std::vector<
       }
 }
 
+// ---------------------------------------------------------------- FV operator, MUSCL
+// Second-order variant of the face step of Eq. 3: "reconstruct a Q from the
+// upper and lower voxel using a linear combination" (Sec. II-A) read as
+// piecewise-linear (MUSCL) reconstruction of the evolved quantities, one
+// component at a time, with the minmod slope limiter:
+//   sigma_i = minmod(Q_i - Q_{i-1}, Q_{i+1} - Q_i),
+//   minmod(a, b) = min(a, b) if a > 0 and b > 0, max(a, b) if a < 0 and b < 0, else 0,
+//   face f between voxels f-1 and f:  QL = Q_{f-1} + sigma_{f-1}/2,  QR = Q_f - sigma_f/2,
+// then the same Rusanov flux on (QL, QR):
+//   F^ = (F_d(QL) + F_d(QR))/2 - s/2 (QR - QL),  s = max(lambda_d(QL), lambda_d(QR)),
+//   L(Q)_i = -(1/dx) sum_d [F^_{i+1/2} - F^_{i-1/2}] + S(Q_i).
+// Material parameters of a face state are those of the voxel it was
+// reconstructed from.  Conservative systems only (B = 0); halo width 2.
+template <class T>
+T minmod(T a, T b) {
+  if (a > T(0.0) && b > T(0.0)) return a < b ? a : b;
+  if (a < T(0.0) && b < T(0.0)) return a > b ? a : b;
+  return T(0.0);
+}
+
+template <class T>
+void fv2_operator(int pde, const Params& P, Block<T>& B, double dxd, std::vector<T>& L) {
+  const PdeInfo I = pde_info(pde);
+  const int N = I.N, M = I.M, p = B.p, dim = B.dim;
+  const int pz = (dim == 3) ? p : 1;
+  const T dx = T(dxd);
+  const size_t nvox = (size_t)p * p * pz;
+  L.assign(nvox * N, T(0.0));
+  std::vector<T> sum(nvox * N, T(0.0));
+  std::vector<T> sig, Fh;
+  for (int d = 0; d < dim; ++d) {
+    const size_t lines = (size_t)p * pz;
+    auto coord = [&](size_t line, int i, int* c) {
+      int o[2] = {(int)(line % p), (int)(line / p)};
+      int j = 0;
+      for (int a = 0; a < 3; ++a) {
+        if (a == d) c[a] = i;
+        else if (a < dim) c[a] = o[j++];
+        else c[a] = 0;
+      }
+    };
+    // Step: limited slopes of voxels -1..p along each line.
+    const int ns = p + 2;
+    sig.assign(lines * ns * N, T(0.0));
+    for (size_t ln = 0; ln < lines; ++ln)
+      for (int i = -1; i <= p; ++i) {
+        int cm[3], c0[3], cp[3];
+        coord(ln, i - 1, cm); coord(ln, i, c0); coord(ln, i + 1, cp);
+        const T* qm = B.at(cm[0], cm[1], cm[2]);
+        const T* q0 = B.at(c0[0], c0[1], c0[2]);
+        const T* qp = B.at(cp[0], cp[1], cp[2]);
+        for (int v = 0; v < N; ++v) sig[(ln * ns + (i + 1)) * N + v] = minmod(q0[v] - qm[v], qp[v] - q0[v]);
+      }
+    // Step: face states, their fluxes and speeds, and the Rusanov flux of every face 0..p.
+    Fh.assign(lines * (p + 1) * N, T(0.0));
+    std::vector<T> QL(N + M), QR(N + M), WL(MAXW), WR(MAXW), FL(N), FR(N);
+    for (size_t ln = 0; ln < lines; ++ln)
+      for (int f = 0; f <= p; ++f) {
+        int cl[3], cr[3];
+        coord(ln, f - 1, cl); coord(ln, f, cr);
+        const T* ul = B.at(cl[0], cl[1], cl[2]);
+        const T* ur = B.at(cr[0], cr[1], cr[2]);
+        const T* sl = &sig[(ln * ns + f) * N];
+        const T* sr = &sig[(ln * ns + f + 1) * N];
+        for (int v = 0; v < N; ++v) {
+          QL[v] = ul[v] + T(0.5) * sl[v];
+          QR[v] = ur[v] - T(0.5) * sr[v];
+        }
+        for (int v = 0; v < M; ++v) { QL[N + v] = ul[N + v]; QR[N + v] = ur[N + v]; }
+        prims(pde, P, QL.data(), QL.data() + N, WL.data());
+        prims(pde, P, QR.data(), QR.data() + N, WR.data());
+        flux(pde, P, d, QL.data(), QL.data() + N, WL.data(), FL.data());
+        flux(pde, P, d, QR.data(), QR.data() + N, WR.data(), FR.data());
+        const T s = fmax(speed(pde, P, d, QL.data(), QL.data() + N, WL.data()),
+                         speed(pde, P, d, QR.data(), QR.data() + N, WR.data()));
+        const T hs = T(0.5) * s;
+        T* fh = &Fh[(ln * (p + 1) + f) * N];
+        for (int v = 0; v < N; ++v) fh[v] = T(0.5) * (FL[v] + FR[v]) - hs * (QR[v] - QL[v]);
+      }
+    // Step: accumulate the face differences of direction d into every voxel.
+    for (size_t ln = 0; ln < lines; ++ln)
+      for (int i = 0; i < p; ++i) {
+        int c[3]; coord(ln, i, c);
+        const size_t vox = ((size_t)c[2] * p + c[1]) * p + c[0];
+        const T* fm = &Fh[(ln * (p + 1) + i) * N];
+        const T* fp = &Fh[(ln * (p + 1) + i + 1) * N];
+        for (int v = 0; v < N; ++v) sum[vox * N + v] = sum[vox * N + v] + (fp[v] - fm[v]);
+      }
+  }
+  // Step: assemble L = -(1/dx) sum + S.
+  const T mrdx = -(T(1.0) / dx);
+  std::vector<T> S(N);
+  for (int z = 0; z < pz; ++z)
+    for (int y = 0; y < p; ++y)
+      for (int x = 0; x < p; ++x) {
+        const size_t vox = ((size_t)z * p + y) * p + x;
+        T* u = B.at(x, y, z);
+        if (I.source) source(pde, P, u, u + N, S.data());
+        for (int v = 0; v < N; ++v) {
+          T l = mrdx * sum[vox * N + v];
+          if (I.source) l = l + S[v];
+          L[vox * N + v] = l;
+        }
+      }
+}
+
 // ---------------------------------------------------------------- FD operator
 // L(Q) = -sum_d dF_d/dx_d - sum_d B_d(Q) dQ/dx_d + S(Q) + sigma/(64 dx) sum_d delta6_d Q
 //   dQ/dx  = [(Q_-2 - Q_+2) + 8 (Q_+1 - Q_-1)] / (12 dx)
@@ -579,6 +685,7 @@ void stage(int scheme, int pde, const Params& P, int dim, const Patch* patches, 
     gather_block(B, patches, k, dim, h, N, M, var_stride, qs, mat);
     std::vector<T> L;
     if (scheme == 0) fv_operator(pde, P, B, patches[k].dx, L);
+    else if (scheme == 2) fv2_operator(pde, P, B, patches[k].dx, L);
     else fd_operator(pde, P, B, patches[k].dx, sigma, L);
     const int p = patches[k].p, pz = (dim == 3) ? p : 1;
     const int64_t off = patches[k].offset;
@@ -716,7 +823,8 @@ int or_num_threads(int n) {
 int or_pde_nq(int pde) { return pde_info(pde).N; }
 int or_pde_nm(int pde) { return pde_info(pde).M; }
 
-// One FV stage (scheme 0) or FD4+KO stage (scheme 1) over all patches.
+// One FV stage (scheme 0), FD4+KO stage (scheme 1) or FV stage with MUSCL
+// minmod reconstruction (scheme 2, halo 2, conservative systems) over all patches.
 int or_stage(int scheme, int pde, int dim, const void* patches, int K, int halo, int64_t var_stride,
              const double* qs, const double* q0, double* out, double* acc, const double* mat,
              double dt, double a, double b, double g, double d, double sigma, const double* prm,

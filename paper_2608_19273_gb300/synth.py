@@ -27,7 +27,7 @@ PATCH_DTYPE = np.dtype([("p", "<i4"), ("level", "<i4"), ("dx", "<f8"), ("x0", "<
 assert PATCH_DTYPE.itemsize == 72
 
 PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE_GW59 = range(7)
-SCHEME_FV, SCHEME_FD = 0, 1
+SCHEME_FV, SCHEME_FD, SCHEME_FV2 = 0, 1, 2  # FV2: MUSCL-minmod reconstruction, halo 2
 PDE_NQ = {0: 1, 1: 1, 2: 4, 3: 5, 4: 5, 5: 5, 6: 59}
 PDE_NM = {0: 3, 1: 3, 2: 0, 3: 0, 4: 1, 5: 5, 6: 0}
 
