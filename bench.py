@@ -51,6 +51,10 @@ WORKLOADS = {
                     kernel="k_fv_stage<Euler3D>",
                     desc="3D Euler (5 vars, gamma 1.4), FV Rusanov, SSP-RK3; 4096x8^3 + 1024x16^3 + 128x32^3 "
                          "patches, halo 1"),
+    "euler3d_muscl": dict(pde=3, scheme=2, rk=3, inner=20, cfl=0.4, flops="fv2/euler3d/ssprk3_step", bytes=320,
+                          kernel="k_fv2_stage<Euler3D>",
+                          desc="3D Euler, second-order FV (MUSCL-minmod + Rusanov), SSP-RK3; 4096x8^3 + 1024x16^3 + "
+                               "128x32^3 patches, halo 2"),
     "euler2d": dict(pde=2, scheme=0, rk=1, inner=10, cfl=0.4, flops="fv/euler2d/fe_step", bytes=128,
                     kernel="k_fv_stage<Euler2D>",
                     desc="2D Euler (4 vars), FV Rusanov, forward Euler; 64 patches of 16^2, halo 1"),
@@ -120,7 +124,7 @@ def workload_config(name, w, mesh):
 def host_inputs(name, w):
     """(prim or cons on host, material on host or None, kind) of the workload."""
     mesh = w.mesh
-    if name in ("euler3d", "euler2d"):
+    if name in ("euler3d", "euler2d", "euler3d_muscl"):
         return synth.euler_prims(mesh, w.seed), None, "prim"
     if name == "wave3d":
         q, mat = synth.wave_initial(mesh, w.seed)
@@ -227,7 +231,7 @@ def oracle_sample(name, budget_s):
     else the same patch sizes with fewer patches per level (scaled box)."""
     import oracle
     cores = oracle.num_threads(0)
-    scale = {"euler3d": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
+    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)
@@ -257,7 +261,7 @@ def reference_arm(args, rank, world):
     name = args.workload
     import oracle
     cores = oracle.num_threads(0)
-    scale = {"euler3d": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
+    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)
@@ -530,10 +534,13 @@ def our_arm(args, rank, world, local_rank):
         lam_init = lam.clone()
         # autotune the stage kernel variant on this workload (U1 is scratch here)
         dh.dh_cfl_dt(plan, lam, spec["cfl"], dt, stream)
-        tv, tz, tf, cached, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3,
-                                                    cache_path=args.tune_cache, stream=stream)
-        tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf, "from_cache": cached,
-                "candidate_ms": [round(t, 4) for t in ttimes if t > 0]}
+        if spec["scheme"] == 2:
+            tune = {"note": "one kernel variant (no candidates)"}
+        else:
+            tv, tz, tf, cached, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3,
+                                                        cache_path=args.tune_cache, stream=stream)
+            tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf, "from_cache": cached,
+                    "candidate_ms": [round(t, 4) for t in ttimes if t > 0]}
         # eager warm-up step (sets kernel attributes outside of capture), then reset
         dh.dh_rk_step(plan, spec["scheme"], spec["rk"], Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1, stream)
         Q.copy_(Q_init)

@@ -132,6 +132,21 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
                              const double* mat, const double* dt_dev, double a, double b, double g,
                              double d, double sigma_ko, double* lam_out_dev, void* stream);
 
+/* Second-order FV stage: the face states of patch_update_fv's Rusanov flux
+ * come from MUSCL reconstruction with the minmod limiter (the paper's
+ * "reconstruct Q from the upper and lower voxel by a stencil" step of the
+ * face-flux operator, Sec. II-A Eq. 3):
+ *     sigma_i = minmod(Q_i - Q_{i-1}, Q_{i+1} - Q_i)   per component,
+ *     minmod(a, b) = 0 if a, b differ in sign, else the one of smaller magnitude,
+ *     QL = Q_{f-1} + sigma_{f-1}/2,  QR = Q_f - sigma_f/2  at face f,
+ *     F^ = (F_d(QL) + F_d(QR))/2 - s/2 (QR - QL),  s = max(lambda_d(QL), lambda_d(QR)).
+ * Conservative 3-D systems (ADV_FLUX, EULER3D; DH_EUNSUPPORTED otherwise);
+ * needs a plan with halo >= 2.  Same arguments and stage combination as
+ * patch_update_fv (lam_out_dev: speed of the cell-average result). */
+dh_status patch_update_fv_muscl(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                                const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                                double* lam_out_dev, void* stream);
+
 /* lam_out_dev <- max over voxels and directions of the characteristic speed of q
  * (the paper's scalar eigenvalue functions, Sec. II-B). */
 dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream);
@@ -256,7 +271,8 @@ dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* str
  *   rk = 3 SSP-RK3 (Shu-Osher): u1 = q + dt L(q); u2 = 3/4 q + 1/4 u1 + 1/4 dt L(u1);
  *          q <- 1/3 q + 2/3 u2 + 2/3 dt L(u2)
  *   rk = 4 classical RK4 with acc = q + dt/6 (k1 + 2 k2 + 2 k3 + k4), q <- acc
- * scheme 0 = FV stage (patch_update_fv), 1 = FD4+KO stage (patch_update_fd_ko).
+ * scheme 0 = FV stage (patch_update_fv), 1 = FD4+KO stage (patch_update_fd_ko),
+ * 2 = second-order FV stage (patch_update_fv_muscl).
  * If cfl > 0, dt_dev is first set on the device to cfl dx_min / (dim lam_dev[0])
  * and the last stage writes the new maximum wave speed into lam_dev, so
  * lam_dev must hold the speed of q on entry (max_wave_speed).  If cfl <= 0

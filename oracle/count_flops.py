@@ -60,6 +60,7 @@ def main():
     for key, args in {
         "fv/euler3d/ssprk3_step": (0, synth.PDE_EULER3D, 3, 1, 3, True),
         "fv/euler3d/stage_fe": (0, synth.PDE_EULER3D, 3, 1, 0, False),
+        "fv2/euler3d/ssprk3_step": (2, synth.PDE_EULER3D, 3, 2, 3, True),
         "fv/euler2d/fe_step": (0, synth.PDE_EULER2D, 2, 1, 1, True),
         "fd/wave3d/rk4_step": (1, synth.PDE_WAVE3D, 3, 3, 4, True),
         "fv/srhd3d/ssprk3_step": (0, synth.PDE_SRHD3D, 3, 1, 3, False),

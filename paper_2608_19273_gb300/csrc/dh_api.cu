@@ -391,6 +391,21 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
   return launch_fd_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, sigma_ko, lam_out_dev, (cudaStream_t)stream);
 }
 
+dh_status patch_update_fv_muscl(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                                const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                                double* lam_out_dev, void* stream) {
+  dh_status st = check_plan(plan);
+  if (st != DH_OK) return st;
+  if (!qs || !dt_dev) { set_error("patch_update_fv_muscl: qs and dt_dev are required"); return DH_EINVAL; }
+  if (!out && !acc) { set_error("patch_update_fv_muscl: nothing to write (out and acc are NULL)"); return DH_EINVAL; }
+  if (plan->nm > 0 && !mat) { set_error("patch_update_fv_muscl: PDE needs the material arena"); return DH_EINVAL; }
+  if (!q0 && a != 0.0) { set_error("patch_update_fv_muscl: q0 is NULL but a != 0"); return DH_EINVAL; }
+  if (out == qs || acc == qs || (out && out == acc)) { set_error("patch_update_fv_muscl: out/acc must not alias qs or each other"); return DH_EINVAL; }
+  if (plan->halo < 2) { set_error("patch_update_fv_muscl: the plan needs halo >= 2 (it has %d)", plan->halo); return DH_EINVAL; }
+  if (plan->dim != 3) { set_error("patch_update_fv_muscl: 3D only"); return DH_EUNSUPPORTED; }
+  return launch_fv2_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev, (cudaStream_t)stream);
+}
+
 dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream) {
   dh_status st = check_plan(plan);
   if (st != DH_OK) return st;

@@ -124,6 +124,10 @@ dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, dou
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
                           double sigma, double* lam_out, cudaStream_t stream);
 
+dh_status launch_fv2_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
+                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
+                           double* lam_out, cudaStream_t stream);
+
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
                           double* lam_out, cudaStream_t stream);

@@ -53,6 +53,7 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
   }
   DH_TRY(T.begin());
   if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
+  else if (scheme == 2) DH_TRY(patch_update_fv_muscl(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else DH_TRY(patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s));
   return T.end();
 }
@@ -95,7 +96,7 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
 static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
                           const double* mat, double* dt, double* lam, double cfl) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (scheme != 0 && scheme != 1) { set_error("scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
+  if (scheme < 0 || scheme > 2) { set_error("scheme must be 0 (FV), 1 (FD) or 2 (FV, MUSCL)"); return DH_EINVAL; }
   if (!q || !u1 || !dt || (rk == 3 && !u2) || (rk == 4 && (!u2 || !acc))) {
     set_error("dh_rk_step: missing state or stage buffer");
     return DH_EINVAL;

@@ -23,7 +23,8 @@ DH_OK, DH_EINVAL, DH_ECUDA, DH_EUNSUPPORTED, DH_ENOMEM, DH_ETIMEOUT = 0, -1, -2,
 PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE_GW59 = range(7)
 
 # Every symbol that include/dh.h declares (checked by the CPU tests).
-EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fd_ko", "max_wave_speed",
+EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fv_muscl", "patch_update_fd_ko",
+           "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_run", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
            "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
@@ -50,6 +51,7 @@ def lib():
         L.dh_plan_destroy.argtypes = [vp]
         L.patch_update_fv.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, d, vp, vp]
         L.patch_update_fd_ko.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, d, d, vp, vp]
+        L.patch_update_fv_muscl.argtypes = [vp, vp, vp, vp, vp, vp, vp, d, d, d, d, vp, vp]
         L.max_wave_speed.argtypes = [vp, vp, vp, vp, vp]
         L.dh_cfl_dt.argtypes = [vp, vp, d, vp, vp]
         L.dh_prim2con.argtypes = [vp, vp, vp, vp]
@@ -161,6 +163,13 @@ def patch_update_fv(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev
                                _ptr(mat, "mat"), _ptr(dt_dev, "dt_dev"), float(a), float(b), float(g), float(d),
                                _ptr(lam_out_dev, "lam_out_dev"), _stream(stream))
     _check(st, "patch_update_fv")
+
+
+def patch_update_fv_muscl(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev=None, stream=None):
+    st = lib().patch_update_fv_muscl(plan.handle, _ptr(qs, "qs"), _ptr(q0, "q0"), _ptr(out, "out"),
+                                     _ptr(acc, "acc"), _ptr(mat, "mat"), _ptr(dt_dev, "dt_dev"), float(a), float(b),
+                                     float(g), float(d), _ptr(lam_out_dev, "lam_out_dev"), _stream(stream))
+    _check(st, "patch_update_fv_muscl")
 
 
 def patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, sigma_ko=0.1, lam_out_dev=None,

@@ -212,11 +212,15 @@ def workload(name, scale=1):
     wave3d  : first-order wave system with c(x), FD4 + KO, RK4, 2048 patches of 16^3.
     srhd3d  : special-relativistic hydro, FV Rusanov + con2prim, SSP-RK3, 4096 patches of 16^3.
     gw59    : 59-unknown gravitational-wave stand-in, FD4 + KO, RK4, 3 levels of 24^3/16^3 patches.
+    euler3d_muscl : the euler3d mix and data with the second-order FV stage (MUSCL-minmod, halo 2).
     """
     if name == "euler2d":
         return Workload(name, PDE_EULER2D, SCHEME_FV, euler2d_mesh(), 1, 1, 10, 0.4, 0.0, SEED_BASE + 0)
     if name == "euler3d":
         return Workload(name, PDE_EULER3D, SCHEME_FV, euler3d_amr_mesh(scale), 1, 3, 100, 0.4, 0.0,
+                        SEED_BASE + 1)
+    if name == "euler3d_muscl":
+        return Workload(name, PDE_EULER3D, SCHEME_FV2, euler3d_amr_mesh(scale), 2, 3, 20, 0.4, 0.0,
                         SEED_BASE + 1)
     if name == "wave3d":
         s = scale
