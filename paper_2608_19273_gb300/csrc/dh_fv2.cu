@@ -20,10 +20,11 @@
 //     the limited slope of its voxel along d and its two face states (+ and -),
 //     each with derived quantities, flux F_d and speed; the first threads also
 //     compute the inward face state of each halo voxel next to the tile.  The
-//     states go to shared memory (F, lambda, Q of each).  Phase 2: each thread
-//     forms the Rusanov flux of its two faces along d from the stored states
-//     and accumulates their difference.  Face values hold twice the flux; the
-//     factor 1/2 is folded into -1/(2 dx).
+//     states go to shared memory (F, lambda, Q of each).  Phase 2: the
+//     threads form the Rusanov flux of every face along d once, from the
+//     stored states, in place of the left state's flux.  Phase 3: each thread
+//     accumulates the difference of its two faces.  Face values hold twice the
+//     flux; the factor 1/2 is folded into -1/(2 dx).
 //   * minmod and all speed maxima run on the integer pipe (sign bits and
 //     magnitude bits of the doubles).
 //   * lambda_max of the result: warp shuffles, one atomicMax per CTA on the
@@ -146,14 +147,14 @@ struct Fv2Tile {
     }
   }
 
-  // Twice the Rusanov flux of face f (states SP[f], SM[f]), added with sign w into sum.
-  __device__ static void face(const DevParams& P, const double* SP, const double* SM, int f, double w, double* sum) {
+  // Twice the Rusanov flux of face f from its states SP[f] and SM[f]; the result
+  // replaces the flux slots of SP[f] (no other face reads entry f).
+  __device__ static void face(const DevParams& P, double* SP, const double* SM, int f) {
     const double s = max_nn(SP[N * MFS + f], SM[N * MFS + f]);
 #pragma unroll
     for (int v = 0; v < N; ++v) {
       const double qL = SP[(N + 1 + v) * MFS + f], qR = SM[(N + 1 + v) * MFS + f];
-      const double h = fma(-s, SUB(P, qR, qL), ADD(P, SP[v * MFS + f], SM[v * MFS + f]));
-      sum[v] = fma(w, h, sum[v]);
+      SP[v * MFS + f] = fma(-s, SUB(P, qR, qL), ADD(P, SP[v * MFS + f], SM[v * MFS + f]));
     }
   }
 
@@ -206,9 +207,14 @@ struct Fv2Tile {
         else states(A, box, c, st, d, nullptr, 0, SM, T * area + oo);
       }
       __syncthreads();
-      // phase 2: the two faces of this voxel along d
-      face(P, SP, SM, a * area + o, -1.0, sum);
-      face(P, SP, SM, (a + 1) * area + o, 1.0, sum);
+      // phase 2: every face along d once ((T + 1) * area faces over the 256 threads)
+      const int nf = (T + 1) * area;
+      for (int f = t; f < nf; f += MNT) face(P, SP, SM, f);
+      __syncthreads();
+      // phase 3: difference of this voxel's two faces
+#pragma unroll
+      for (int v = 0; v < N; ++v)
+        sum[v] = ADD(P, sum[v], SUB(P, SP[v * MFS + (a + 1) * area + o], SP[v * MFS + a * area + o]));
       __syncthreads();
     }
     // update
