@@ -196,8 +196,10 @@ struct Fv2Tile {
       // at -1 (left state of face 0) and the - state of the voxel at T (right
       // state of face T).
       states(A, box, me, st, d, SP, (a + 1) * area + o, SM, a * area + o);
-      if (t < 2 * area) {
-        const int side = t / area, oo = t % area;
+      // (taken by the last warps: the first warps take the faces beyond 256 in phase 2)
+      const int ht = t - (MNT - 2 * area);
+      if (ht >= 0) {
+        const int side = ht / area, oo = ht % area;
         int hx, hy, hz;
         if (d == 0) { hx = side == 0 ? -1 : MX; hy = oo % MY; hz = oo / MY; }
         else if (d == 1) { hy = side == 0 ? -1 : MY; hx = oo % MX; hz = oo / MX; }
