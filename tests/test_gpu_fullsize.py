@@ -1,7 +1,7 @@
 """Parity at the full workload sizes, in the launch configuration the benchmark
 times (autotuned kernel variant, whole time steps through dh_rk_step).
 
-3D Euler (10.5M voxels), the wave system (8.4M) and SRHD (16.7M) are compared
+3D Euler (10.5M voxels, first and second order), the wave system (8.4M) and SRHD (16.7M) are compared
 with the oracle voxel by voxel after one full time step; GW59 (31M voxels x 59
 unknowns, 14.6 GB per state) is compared on a sample of patches from every
 level after one stage (the oracle updates only the sampled patches)."""
@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _gpu_step(torch, name, w, q, mat, steps=1):
-    spec = {"euler3d": (0, 3, 0.4), "wave3d": (1, 4, 0.25), "srhd3d": (0, 3, 0.4)}[name]
+    spec = {"euler3d": (0, 3, 0.4), "wave3d": (1, 4, 0.25), "srhd3d": (0, 3, 0.4), "euler3d_muscl": (2, 3, 0.4)}[name]
     scheme, rk, cfl = spec
     mesh = w.mesh
     with dh.Plan(w.pde, 3, mesh.patches, w.halo, mesh.var_stride, w.params) as plan:
@@ -32,7 +32,8 @@ def _gpu_step(torch, name, w, q, mat, steps=1):
             M.copy_(U2)
         dh.max_wave_speed(plan, Q, M, lam)
         dh.dh_cfl_dt(plan, lam, cfl, dt)
-        dh.dh_autotune(plan, scheme, Q, U1, M, dt, reps=1)
+        if scheme != 2:
+            dh.dh_autotune(plan, scheme, Q, U1, M, dt, reps=1)
         for _ in range(steps):
             dh.dh_rk_step(plan, scheme, rk, Q, U1, U2, ACC, M, dt, lam, cfl, 0.1)
         torch.cuda.synchronize()
@@ -49,6 +50,19 @@ def test_euler3d_full_size_step(orc):
     dts = orc.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=1, cfl=0.4)
     assert abs(dt - dts[0]) <= 1e-15 * dts[0]
     assert_parity(got, ref, voxel_mask(mesh), what="euler3d full size")
+
+
+def test_euler3d_muscl_full_size_step(orc):
+    """The second-order FV stage on the full AMR mix, one SSP-RK3 step with device dt."""
+    torch = require_cuda()
+    w = synth.workload("euler3d_muscl")
+    mesh = w.mesh
+    q = orc.prim2con(3, synth.euler_prims(mesh, w.seed), mesh.var_stride)
+    got, dt = _gpu_step(torch, "euler3d_muscl", w, q, None)
+    ref = q.copy()
+    dts = orc.rk_steps(2, 3, 3, mesh.patches, 2, mesh.var_stride, ref, rk=3, steps=1, cfl=0.4)
+    assert abs(dt - dts[0]) <= 1e-15 * dts[0]
+    assert_parity(got, ref, voxel_mask(mesh), what="euler3d MUSCL full size")
 
 
 def test_wave3d_full_size_step(orc):
