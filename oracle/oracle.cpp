@@ -19,7 +19,7 @@
 //     into an AoS block (the gather prologue of Eq. 4), updates it with plain
 //     loops, one temporary array per step, and scatters the interior back.
 //
-// Readings where the paper is silent (each listed in the design doc):
+// Readings where the paper is silent:
 //   * FV face flux: Rusanov, F^ = (F(QL)+F(QR))/2 - s/2 (QR-QL), with
 //     s = max(lambda_n(QL), lambda_n(QR)).
 //   * Non-conservative product: path-conservative, straight-line path,
