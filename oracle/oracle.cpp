@@ -312,6 +312,46 @@ void source(int pde, const Params& P, const T* q, const T* m, T* S) {
   }
 }
 
+// ---------------------------------------------------------------- coarse-fine coupling
+// Meshes of several refinement levels (the paper's meshes are Peano spacetrees,
+// Sec. IV; it defines no coupling).  Reading used: refinement ratio 2, every
+// patch of level l+1 covers one octant of a patch of level l (its parent),
+// same p, half the voxel spacing; a patch's face neighbour is either of its own
+// level or one level coarser.
+//   * Prolongation: a halo voxel taken from a coarser neighbour gets the value
+//     of the coarse voxel that contains it (piecewise constant).
+//   * Reflux: the first-order FV update of a coarse voxel next to the finer
+//     level uses, on that face, the mean of the 2^(d-1) fine face fluxes
+//     instead of its own coarse face flux (conservation across levels).
+//   * Restriction: after every stage each coarse voxel covered by the finer
+//     level becomes the mean of its 2^d fine voxels (out and acc).
+// Lattice index of a patch along axis a at its own level, and its octant bit.
+inline int lattice(const Patch& P, int a) { return (int)std::llround(P.x0[a] / (P.p * P.dx)); }
+inline int octant(const Patch& P, int a) { return lattice(P, a) & 1; }
+
+inline bool coupled_mesh(const Patch* patches, int K, int dim) {
+  for (int k = 0; k < K; ++k)
+    for (int f = 0; f < 2 * dim; ++f)
+      if (patches[patches[k].nbr[f]].level < patches[k].level) return true;
+  return false;
+}
+
+// Parent of every patch (-1 on the coarsest level): the patch one level coarser
+// whose lattice cell contains it.
+std::vector<int> parents(const Patch* patches, int K, int dim) {
+  std::vector<int> par(K, -1);
+  for (int k = 0; k < K; ++k) {
+    if (patches[k].level == 0) continue;
+    for (int c = 0; c < K; ++c) {
+      if (patches[c].level != patches[k].level - 1) continue;
+      bool in = true;
+      for (int a = 0; a < dim; ++a) in = in && lattice(patches[c], a) == lattice(patches[k], a) / 2;
+      if (in) { par[k] = c; break; }
+    }
+  }
+  return par;
+}
+
 // ---------------------------------------------------------------- patch gather
 // A patch with halo as the paper's AoS block: voxel (x,y,z), x,y,z in
 // [-h, p+h) (z only in 3D), all N+M quantities contiguous.  Halo voxels on a
@@ -347,8 +387,17 @@ void gather_block(Block<T>& B, const Patch* patches, int k, int dim, int h, int 
         int src = k;
         int s[3] = {x, y, z};
         if (outside == 1) {
-          if (c[dir] < 0) { src = pt.nbr[2 * dir]; s[dir] += p; }
-          else { src = pt.nbr[2 * dir + 1]; s[dir] -= p; }
+          src = c[dir] < 0 ? pt.nbr[2 * dir] : pt.nbr[2 * dir + 1];
+          if (patches[src].level < pt.level) {
+            // coarser neighbour: the coarse voxel containing this halo voxel
+            for (int a = 0; a < dim; ++a) {
+              const int fc = c[a];
+              if (a == dir) s[a] = fc < 0 ? p + (int)std::floor(fc / 2.0) : (int)std::floor((fc - p) / 2.0);
+              else s[a] = octant(pt, a) * (p / 2) + fc / 2;
+            }
+          } else {
+            s[dir] += c[dir] < 0 ? p : -p;
+          }
         }
         const Patch& ps = patches[src];
         int64_t e = ps.offset + ((int64_t)(dim == 3 ? s[2] : 0) * p + s[1]) * p + s[0];
@@ -662,6 +711,114 @@ void fd_operator(int pde, const Params& P, Block<T>& B, double dxd, double sigma
       }
 }
 
+// ---------------------------------------------------------------- coupling steps
+// Rusanov flux F^ = (F_d(QL) + F_d(QR))/2 - s/2 (QR - QL) of one face (qL, qR: N+M values).
+template <class T>
+void rusanov_face(int pde, const Params& P, int d, const T* qL, const T* qR, T* fh) {
+  const PdeInfo I = pde_info(pde);
+  const int N = I.N;
+  T WL[MAXW], WR[MAXW], FL[64], FR[64];
+  prims(pde, P, qL, qL + N, WL);
+  prims(pde, P, qR, qR + N, WR);
+  flux(pde, P, d, qL, qL + N, WL, FL);
+  flux(pde, P, d, qR, qR + N, WR, FR);
+  const T sp = fmax(speed(pde, P, d, qL, qL + N, WL), speed(pde, P, d, qR, qR + N, WR));
+  const T hs = T(0.5) * sp;
+  for (int v = 0; v < N; ++v) fh[v] = T(0.5) * (FL[v] + FR[v]) - hs * (qR[v] - qL[v]);
+}
+
+// Reflux and restriction after a first-order FV stage on a coupled mesh (see
+// "coarse-fine coupling" above).  qs: the stage input; out/acc as in stage().
+template <class T>
+void couple_levels(int pde, const Params& P, int dim, const Patch* patches, int K, int64_t vs,
+                   const double* qs, const double* mat, double* out, double* acc, double dt, double g,
+                   double dd) {
+  const PdeInfo I = pde_info(pde);
+  const int N = I.N, M = I.M;
+  const std::vector<int> par = parents(patches, K, dim);
+  auto load = [&](int k, int x, int y, int z, T* q) {
+    const int p = patches[k].p;
+    const int64_t e = patches[k].offset + ((int64_t)z * p + y) * p + x;
+    for (int v = 0; v < N; ++v) q[v] = T(qs[v * vs + e]);
+    for (int v = 0; v < M; ++v) q[N + v] = T(mat[v * vs + e]);
+    return e;
+  };
+  // Reflux: every face of a fine patch whose neighbour is coarser, one coarse voxel at a time.
+  std::vector<T> qC(N + M), qN(N + M), qF(N + M), fc(N), ff(N), fsum(N);
+  for (int k = 0; k < K; ++k) {
+    const Patch& F = patches[k];
+    const int p = F.p, h2 = p / 2;
+    for (int f = 0; f < 2 * dim; ++f) {
+      const int C = F.nbr[f];
+      if (patches[C].level >= F.level) continue;
+      const int a = f / 2, lo = (f % 2 == 0);  // lo: the coarse patch lies on the -a side of F
+      const int b0 = (a + 1) % dim, b1 = dim == 3 ? (a + 2) % dim : -1;
+      const int nj = h2, nk = dim == 3 ? h2 : 1;
+      for (int kk = 0; kk < nk; ++kk)
+        for (int jj = 0; jj < nj; ++jj) {
+          int cc[3] = {0, 0, 0}, cn[3] = {0, 0, 0};
+          cc[a] = lo ? p - 1 : 0;                         // coarse voxel next to the finer level
+          cn[a] = octant(F, a) * h2 + (lo ? 0 : h2 - 1);   // coarse voxel across the face (covered)
+          cc[b0] = cn[b0] = octant(F, b0) * h2 + jj;
+          if (b1 >= 0) cc[b1] = cn[b1] = octant(F, b1) * h2 + kk;
+          const int64_t eC = load(C, cc[0], cc[1], cc[2], qC.data());
+          load(par[k], cn[0], cn[1], cn[2], qN.data());
+          if (lo) rusanov_face(pde, P, a, qC.data(), qN.data(), fc.data());
+          else rusanov_face(pde, P, a, qN.data(), qC.data(), fc.data());
+          for (int v = 0; v < N; ++v) fsum[v] = T(0.0);
+          const int nfk = dim == 3 ? 2 : 1;
+          for (int sk = 0; sk < nfk; ++sk)
+            for (int sj = 0; sj < 2; ++sj) {
+              int cf[3] = {0, 0, 0};
+              cf[a] = lo ? 0 : p - 1;
+              cf[b0] = 2 * jj + sj;
+              if (b1 >= 0) cf[b1] = 2 * kk + sk;
+              load(k, cf[0], cf[1], cf[2], qF.data());
+              if (lo) rusanov_face(pde, P, a, qC.data(), qF.data(), ff.data());
+              else rusanov_face(pde, P, a, qF.data(), qC.data(), ff.data());
+              for (int v = 0; v < N; ++v) fsum[v] = fsum[v] + ff[v];
+            }
+          const T rn = T(1.0) / T(dim == 3 ? 4.0 : 2.0);
+          const T sgn = lo ? T(-1.0) : T(1.0);  // the face is the +a face of C (lo) or its -a face
+          for (int v = 0; v < N; ++v) {
+            const T dL = sgn * (fsum[v] * rn - fc[v]) / T(patches[C].dx);
+            const int64_t ev = v * vs + eC;
+            if (out) out[ev] = val(T(out[ev]) + T(g) * T(dt) * dL);
+            if (acc) acc[ev] = val(T(acc[ev]) + T(dd) * T(dt) * dL);
+          }
+        }
+    }
+  }
+  // Restriction: the coarse voxels under every fine patch.
+  for (int k = 0; k < K; ++k) {
+    if (par[k] < 0) continue;
+    const Patch& F = patches[k];
+    const Patch& Pp = patches[par[k]];
+    const int p = F.p, h2 = p / 2, hz = dim == 3 ? h2 : 1;
+    const int nsub = dim == 3 ? 8 : 4;
+    for (int z = 0; z < hz; ++z)
+      for (int y = 0; y < h2; ++y)
+        for (int x = 0; x < h2; ++x) {
+          const int cx = octant(F, 0) * h2 + x, cy = octant(F, 1) * h2 + y, cz = dim == 3 ? octant(F, 2) * h2 + z : 0;
+          const int64_t ec = Pp.offset + ((int64_t)cz * p + cy) * p + cx;
+          for (int w = 0; w < 2; ++w) {
+            double* arr = w == 0 ? out : acc;
+            if (!arr) continue;
+            for (int v = 0; v < N; ++v) {
+              T sum = T(0.0);
+              for (int sz = 0; sz < (dim == 3 ? 2 : 1); ++sz)
+                for (int sy = 0; sy < 2; ++sy)
+                  for (int sx = 0; sx < 2; ++sx) {
+                    const int64_t ef = F.offset + ((int64_t)(dim == 3 ? 2 * z + sz : 0) * p + 2 * y + sy) * p + 2 * x + sx;
+                    sum = sum + T(arr[v * vs + ef]);
+                  }
+              arr[v * vs + ec] = val(sum / T((double)nsub));
+            }
+          }
+        }
+  }
+}
+
 // ---------------------------------------------------------------- stage driver
 // One Runge-Kutta stage over all K patches (the batched kernel K~_{dt,K}):
 //   out = a Q0 + b Qs + g dt L(Qs)   (out may be NULL)
@@ -722,6 +879,8 @@ void stage(int scheme, int pde, const Params& P, int dim, const Patch* patches, 
           }
         }
   }
+  if (scheme == 0 && !only && coupled_mesh(patches, K, dim))
+    couple_levels<T>(pde, P, dim, patches, K, var_stride, qs, mat, out, acc, dt, g, dd);
   if (lam) *lam = lam_max;
 }
 
@@ -889,10 +1048,13 @@ int or_rk_steps(int scheme, int pde, int dim, const void* patches_v, int K, int 
   for (int k = 1; k < K; ++k) dxmin = std::min(dxmin, patches[k].dx);
   size_t nelem = (size_t)var_stride * I.N;
   double lam = or_max_wave_speed(pde, dim, patches_v, K, var_stride, q, mat, prm, nprm);
+  // on a coupled mesh the wave speed is taken from the state after the coupling
+  // steps (restriction, reflux) at the end of every step
+  const bool coupled = coupled_mesh(patches, K, dim);
   for (int s = 0; s < steps; ++s) {
     double dt = dt_fixed > 0 ? dt_fixed : or_cfl_dt(cfl, dxmin, dim, lam);
     if (dt_log) dt_log[s] = dt;
-    double* lp = (dt_fixed > 0) ? nullptr : &lam;
+    double* lp = (dt_fixed > 0 || coupled) ? nullptr : &lam;
     if (rk == 1) {
       stage<double>(scheme, pde, P, dim, patches, K, halo, var_stride, q, nullptr, u1, nullptr, mat,
                     dt, 0, 1, 1, 0, sigma, lp);
@@ -918,6 +1080,7 @@ int or_rk_steps(int scheme, int pde, int dim, const void* patches_v, int K, int 
     } else {
       return -1;
     }
+    if (coupled && dt_fixed <= 0) lam = or_max_wave_speed(pde, dim, patches_v, K, var_stride, q, mat, prm, nprm);
   }
   return 0;
 }
