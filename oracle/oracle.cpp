@@ -765,9 +765,11 @@ void couple_levels(int pde, const Params& P, int dim, const Patch* patches, int 
           load(par[k], cn[0], cn[1], cn[2], qN.data());
           if (lo) rusanov_face(pde, P, a, qC.data(), qN.data(), fc.data());
           else rusanov_face(pde, P, a, qN.data(), qC.data(), fc.data());
-          for (int v = 0; v < N; ++v) fsum[v] = T(0.0);
+          // fine face fluxes, summed as a balanced tree ((f00 + f10) + (f01 + f11)) so that equal
+          // fluxes sum exactly
           const int nfk = dim == 3 ? 2 : 1;
-          for (int sk = 0; sk < nfk; ++sk)
+          std::vector<T> pair(N);
+          for (int sk = 0; sk < nfk; ++sk) {
             for (int sj = 0; sj < 2; ++sj) {
               int cf[3] = {0, 0, 0};
               cf[a] = lo ? 0 : p - 1;
@@ -776,8 +778,10 @@ void couple_levels(int pde, const Params& P, int dim, const Patch* patches, int 
               load(k, cf[0], cf[1], cf[2], qF.data());
               if (lo) rusanov_face(pde, P, a, qC.data(), qF.data(), ff.data());
               else rusanov_face(pde, P, a, qF.data(), qC.data(), ff.data());
-              for (int v = 0; v < N; ++v) fsum[v] = fsum[v] + ff[v];
+              for (int v = 0; v < N; ++v) pair[v] = sj == 0 ? ff[v] : pair[v] + ff[v];
             }
+            for (int v = 0; v < N; ++v) fsum[v] = sk == 0 ? pair[v] : fsum[v] + pair[v];
+          }
           const T rn = T(1.0) / T(dim == 3 ? 4.0 : 2.0);
           const T sgn = lo ? T(-1.0) : T(1.0);  // the face is the +a face of C (lo) or its -a face
           for (int v = 0; v < N; ++v) {
@@ -805,13 +809,17 @@ void couple_levels(int pde, const Params& P, int dim, const Patch* patches, int 
             double* arr = w == 0 ? out : acc;
             if (!arr) continue;
             for (int v = 0; v < N; ++v) {
-              T sum = T(0.0);
-              for (int sz = 0; sz < (dim == 3 ? 2 : 1); ++sz)
-                for (int sy = 0; sy < 2; ++sy)
-                  for (int sx = 0; sx < 2; ++sx) {
-                    const int64_t ef = F.offset + ((int64_t)(dim == 3 ? 2 * z + sz : 0) * p + 2 * y + sy) * p + 2 * x + sx;
-                    sum = sum + T(arr[v * vs + ef]);
-                  }
+              // balanced tree: ((x pair) + (x pair)) per z layer, then the two layers
+              T layer[2] = {T(0.0), T(0.0)};
+              for (int sz = 0; sz < (dim == 3 ? 2 : 1); ++sz) {
+                T row[2];
+                for (int sy = 0; sy < 2; ++sy) {
+                  const int64_t ef = F.offset + ((int64_t)(dim == 3 ? 2 * z + sz : 0) * p + 2 * y + sy) * p + 2 * x;
+                  row[sy] = T(arr[v * vs + ef]) + T(arr[v * vs + ef + 1]);
+                }
+                layer[sz] = row[0] + row[1];
+              }
+              const T sum = dim == 3 ? layer[0] + layer[1] : layer[0];
               arr[v * vs + ec] = val(sum / T((double)nsub));
             }
           }

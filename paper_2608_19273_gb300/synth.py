@@ -87,6 +87,74 @@ def make_mesh(levels, dim, align=16):
     return Mesh(dim=dim, patches=patches, var_stride=_round_up(off, 32), levels=list(levels), level_ranges=ranges)
 
 
+def coupled_mesh(nc, p, dx_c, lo, m, dim=3, align=16):
+    """Two refinement levels with ratio 2: a periodic box of nc^dim coarse patches (level 0) and a
+    finer level (level 1) that covers the coarse patches with lattice indices [lo, lo + m)^dim by
+    (2m)^dim patches of the same p at dx_c / 2.  Fine patches on the border of the refined block
+    have the adjacent coarse patch (outside the block) as face neighbour; the coarse level keeps
+    its own periodic table (the coarse patches under the block stay in the list)."""
+    coarse = make_mesh([Level((nc,) * 3 if dim == 3 else (nc, nc, 1), p, dx_c, 0)], dim, align)
+    recs = [tuple(r) for r in coarse.patches.tolist()]
+    off = int(coarse.patches["offset"][-1]) + _round_up(p ** dim, align)
+    nf = 2 * m
+    first = len(recs)
+    nz = nf if dim == 3 else 1
+
+    def cid(i, j, k):
+        return ((k % nc) * nc + (j % nc)) * nc + (i % nc) if dim == 3 else (j % nc) * nc + (i % nc)
+
+    for k in range(nz):
+        for j in range(nf):
+            for i in range(nf):
+                def nb(di, dj, dk):
+                    ii, jj, kk = i + di, j + dj, k + dk
+                    if 0 <= ii < nf and 0 <= jj < nf and (dim == 2 or 0 <= kk < nf):
+                        return first + ((kk if dim == 3 else 0) * nf + jj) * nf + ii
+                    # coarse patch containing the neighbouring fine position
+                    gi, gj = 2 * lo + ii, 2 * lo + jj
+                    gk = 2 * lo + kk if dim == 3 else 0
+                    return cid(gi // 2, gj // 2, gk // 2)
+                nbr = [nb(-1, 0, 0), nb(1, 0, 0), nb(0, -1, 0), nb(0, 1, 0), -1, -1]
+                if dim == 3:
+                    nbr[4], nbr[5] = nb(0, 0, -1), nb(0, 0, 1)
+                dxf = dx_c / 2
+                x0 = ((2 * lo + i) * p * dxf, (2 * lo + j) * p * dxf, (2 * lo + k) * p * dxf if dim == 3 else 0.0)
+                recs.append((p, 1, dxf, x0, off, nbr))
+                off += _round_up(p ** dim, align)
+    patches = np.array(recs, dtype=PATCH_DTYPE)
+    levels = [Level((nc,) * 3 if dim == 3 else (nc, nc, 1), p, dx_c, 0),
+              Level((nf,) * 3 if dim == 3 else (nf, nf, 1), p, dx_c / 2, 1)]
+    return Mesh(dim=dim, patches=patches, var_stride=_round_up(off, 32), levels=levels,
+                level_ranges=[(0, first), (first, len(recs))])
+
+
+def coupled_fields(mesh, rng, specs):
+    """Fourier fields periodic on the coarse box, evaluated at every voxel centre of both levels."""
+    X = voxel_centres_any(mesh)
+    L = [mesh.levels[0].n[a] * mesh.levels[0].p * mesh.levels[0].dx for a in range(mesh.dim)]
+    out = np.zeros((len(specs), mesh.var_stride))
+    m = np.zeros(mesh.var_stride, dtype=bool)
+    for pt in mesh.patches:
+        m[int(pt["offset"]):int(pt["offset"]) + int(pt["p"]) ** mesh.dim] = True
+    for v, (mid, amp) in enumerate(specs):
+        out[v, m] = fourier_field(rng, X[:, m], L, mesh.dim, mid, amp)
+    return out
+
+
+def voxel_centres_any(mesh):
+    """Voxel-centre coordinates (3, var_stride) for any patch table (patch by patch)."""
+    X = np.zeros((3, mesh.var_stride))
+    for pt in mesh.patches:
+        p = int(pt["p"])
+        pz = p if mesh.dim == 3 else 1
+        z, y, x = np.meshgrid(np.arange(pz), np.arange(p), np.arange(p), indexing="ij")
+        loc = [x.ravel(), y.ravel(), z.ravel()]
+        o = int(pt["offset"])
+        for a in range(mesh.dim):
+            X[a, o:o + p * p * pz] = pt["x0"][a] + (loc[a] + 0.5) * pt["dx"]
+    return X
+
+
 def _level_block(mesh, li):
     """(first offset, patches, voxels per patch, contiguous?) of level li."""
     a, b = mesh.level_ranges[li]
