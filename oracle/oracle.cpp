@@ -711,6 +711,27 @@ void fd_operator(int pde, const Params& P, Block<T>& B, double dxd, double sigma
       }
 }
 
+// ---------------------------------------------------------------- wave speed
+// Maximum characteristic speed over all voxels and directions.
+double max_speed(const Patch* patches, int K, int pde, const Params& P, int dim, int64_t var_stride,
+                 const double* q, const double* mat) {
+  const PdeInfo I = pde_info(pde);
+  double lam = 0.0;
+#pragma omp parallel for reduction(max : lam) if (K > 1)
+  for (int k = 0; k < K; ++k) {
+    const int p = patches[k].p, pz = (dim == 3) ? p : 1;
+    double u[64], m[8], W[MAXW];
+    for (int vox = 0; vox < p * p * pz; ++vox) {
+      int64_t e = patches[k].offset + vox;
+      for (int v = 0; v < I.N; ++v) u[v] = q[v * var_stride + e];
+      for (int v = 0; v < I.M; ++v) m[v] = mat[v * var_stride + e];
+      prims(pde, P, u, m, W);
+      for (int d = 0; d < dim; ++d) lam = std::max(lam, speed(pde, P, d, u, m, W));
+    }
+  }
+  return lam;
+}
+
 // ---------------------------------------------------------------- coupling steps
 // Rusanov flux F^ = (F_d(QL) + F_d(QR))/2 - s/2 (QR - QL) of one face (qL, qR: N+M values).
 template <class T>
@@ -793,8 +814,11 @@ void couple_levels(int pde, const Params& P, int dim, const Patch* patches, int 
         }
     }
   }
-  // Restriction: the coarse voxels under every fine patch.
-  for (int k = 0; k < K; ++k) {
+  // Restriction: the coarse voxels under every fine patch, finest level first.
+  std::vector<int> order(K);
+  for (int k = 0; k < K; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return patches[a].level > patches[b].level; });
+  for (int k : order) {
     if (par[k] < 0) continue;
     const Patch& F = patches[k];
     const Patch& Pp = patches[par[k]];
@@ -887,8 +911,11 @@ void stage(int scheme, int pde, const Params& P, int dim, const Patch* patches, 
           }
         }
   }
-  if (scheme == 0 && !only && coupled_mesh(patches, K, dim))
+  if (scheme == 0 && !only && coupled_mesh(patches, K, dim)) {
     couple_levels<T>(pde, P, dim, patches, K, var_stride, qs, mat, out, acc, dt, g, dd);
+    // the wave speed of the coupled result (all voxels, covered coarse ones included)
+    if (lam) lam_max = max_speed(patches, K, pde, P, dim, var_stride, out ? out : acc, mat);
+  }
   if (lam) *lam = lam_max;
 }
 
@@ -1017,23 +1044,7 @@ int or_stage_subset(int scheme, int pde, int dim, const void* patches, int K, in
 // Maximum characteristic speed over all voxels and directions.
 double or_max_wave_speed(int pde, int dim, const void* patches_v, int K, int64_t var_stride,
                          const double* q, const double* mat, const double* prm, int nprm) {
-  const Patch* patches = (const Patch*)patches_v;
-  Params P = make_params(pde, prm, nprm);
-  const PdeInfo I = pde_info(pde);
-  double lam = 0.0;
-#pragma omp parallel for reduction(max : lam) if (K > 1)
-  for (int k = 0; k < K; ++k) {
-    const int p = patches[k].p, pz = (dim == 3) ? p : 1;
-    double u[64], m[8], W[MAXW];
-    for (int vox = 0; vox < p * p * pz; ++vox) {
-      int64_t e = patches[k].offset + vox;
-      for (int v = 0; v < I.N; ++v) u[v] = q[v * var_stride + e];
-      for (int v = 0; v < I.M; ++v) m[v] = mat[v * var_stride + e];
-      prims(pde, P, u, m, W);
-      for (int d = 0; d < dim; ++d) lam = std::max(lam, speed(pde, P, d, u, m, W));
-    }
-  }
-  return lam;
+  return max_speed((const Patch*)patches_v, K, pde, make_params(pde, prm, nprm), dim, var_stride, q, mat);
 }
 
 // dt = CFL dx / (dim lambda_max)

@@ -198,8 +198,11 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     for (int f = 0; f < 2 * dim; ++f) {
       const int nb = pt.nbr[f];
       if (nb < 0 || nb >= K) { set_error("patch %d: neighbour %d = %d out of range", k, f, nb); return DH_EINVAL; }
-      if (patches[nb].p != pt.p || patches[nb].dx != pt.dx) {
-        set_error("patch %d: neighbour %d (patch %d) has a different p or dx", k, f, nb);
+      const bool same = patches[nb].p == pt.p && patches[nb].dx == pt.dx && patches[nb].level == pt.level;
+      const bool coarser = patches[nb].p == pt.p && patches[nb].dx == 2.0 * pt.dx && patches[nb].level == pt.level - 1;
+      if (!same && !coarser) {
+        set_error("patch %d: neighbour %d (patch %d) must have the same p, dx and level, or be one level coarser "
+                  "with the same p and twice the dx", k, f, nb);
         return DH_EINVAL;
       }
     }
@@ -324,6 +327,10 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) {
+    dh_status ast = amr_build(plan, patches, K, dim);
+    if (ast != DH_OK) { dh_plan_destroy(plan); return ast; }
+  }
   const std::vector<int2> aunits = aoas_units(patches, K, dim);
   plan->n_aunits = (int)aunits.size();
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_aunits, sizeof(int2) * aunits.size());
@@ -350,6 +357,9 @@ dh_status dh_plan_destroy(dh_plan* plan) {
   if (plan->d_lvl) cudaFree(plan->d_lvl);
   if (plan->d_aunits) cudaFree(plan->d_aunits);
   if (plan->d_offload) cudaFree(plan->d_offload);
+  if (plan->d_amr_oct) cudaFree(plan->d_amr_oct);
+  if (plan->d_amr_reflux) cudaFree(plan->d_amr_reflux);
+  if (plan->d_amr_restrict) cudaFree(plan->d_amr_restrict);
   if (plan->graph_exec) cudaGraphExecDestroy(plan->graph_exec);
   for (cudaEvent_t e : plan->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : plan->ev_stop) cudaEventDestroy(e);
@@ -372,7 +382,19 @@ dh_status patch_update_fv(dh_plan* plan, const double* qs, const double* q0, dou
     set_error("patch_update_fv: PDE %d is evolved with patch_update_fd_ko", plan->pde);
     return DH_EUNSUPPORTED;
   }
-  return launch_fv_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev, (cudaStream_t)stream);
+  if (!plan->coupled)
+    return launch_fv_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev, (cudaStream_t)stream);
+  // coupled refinement levels: stage (prolongation inside), reflux, restriction, then the
+  // wave speed of the coupled result
+  if (plan->pde == DH_PDE_ADV_NCP) {
+    set_error("patch_update_fv: coupled refinement levels need a conservative system (no B(Q).grad Q)");
+    return DH_EUNSUPPORTED;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  st = launch_fv_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, nullptr, s);
+  if (st == DH_OK) st = amr_couple(plan, qs, mat, out, acc, dt_dev, g, d, s);
+  if (st == DH_OK && lam_out_dev) st = max_wave_speed(plan, out ? out : acc, mat, lam_out_dev, stream);
+  return st;
 }
 
 dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
@@ -386,6 +408,7 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
   if (!q0 && a != 0.0) { set_error("patch_update_fd_ko: q0 is NULL but a != 0"); return DH_EINVAL; }
   if (out == qs || acc == qs || (out && out == acc)) { set_error("patch_update_fd_ko: out/acc must not alias qs or each other"); return DH_EINVAL; }
   if (plan->halo < 3) { set_error("patch_update_fd_ko: the plan needs halo >= 3 (it has %d)", plan->halo); return DH_EINVAL; }
+  if (plan->coupled) { set_error("patch_update_fd_ko: coupled refinement levels are supported by patch_update_fv only"); return DH_EUNSUPPORTED; }
   if (plan->dim != 3) { set_error("patch_update_fd_ko: 3D only"); return DH_EUNSUPPORTED; }
   if (!(sigma_ko >= 0.0)) { set_error("patch_update_fd_ko: sigma must be >= 0"); return DH_EINVAL; }
   return launch_fd_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, sigma_ko, lam_out_dev, (cudaStream_t)stream);
@@ -402,6 +425,7 @@ dh_status patch_update_fv_muscl(dh_plan* plan, const double* qs, const double* q
   if (!q0 && a != 0.0) { set_error("patch_update_fv_muscl: q0 is NULL but a != 0"); return DH_EINVAL; }
   if (out == qs || acc == qs || (out && out == acc)) { set_error("patch_update_fv_muscl: out/acc must not alias qs or each other"); return DH_EINVAL; }
   if (plan->halo < 2) { set_error("patch_update_fv_muscl: the plan needs halo >= 2 (it has %d)", plan->halo); return DH_EINVAL; }
+  if (plan->coupled) { set_error("patch_update_fv_muscl: coupled refinement levels are supported by patch_update_fv only"); return DH_EUNSUPPORTED; }
   if (plan->dim != 3) { set_error("patch_update_fv_muscl: 3D only"); return DH_EUNSUPPORTED; }
   return launch_fv2_stage(plan, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev, (cudaStream_t)stream);
 }

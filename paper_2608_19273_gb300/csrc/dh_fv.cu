@@ -41,21 +41,46 @@ struct FvArgs {
   double a, b, g, d;
   double* lam_out;
   unsigned long long* red;
-  int64_t vs;  // var stride
+  const int* oct;  // octant bits per patch on coupled plans, else NULL
+  int64_t vs;      // var stride
   DevParams P;
 };
 
 // Arena index of voxel (x, y, z) of patch k; at most one coordinate may lie
 // outside [0, p): it is then taken from the face neighbour (periodic wrap is
-// encoded in the neighbour table).
-__device__ __forceinline__ int64_t vox_index(const dh_patch* __restrict__ P, int k, int p, int x, int y, int z) {
-  if (x < 0) { k = P[k].nbr[0]; x += p; }
-  else if (x >= p) { k = P[k].nbr[1]; x -= p; }
-  else if (y < 0) { k = P[k].nbr[2]; y += p; }
-  else if (y >= p) { k = P[k].nbr[3]; y -= p; }
-  else if (z < 0) { k = P[k].nbr[4]; z += p; }
-  else if (z >= p) { k = P[k].nbr[5]; z -= p; }
-  return P[k].offset + ((int64_t)z * p + y) * p + x;
+// encoded in the neighbour table).  On coupled plans (oct != NULL) a
+// neighbour one level coarser supplies the coarse voxel that contains the
+// position (piecewise-constant prolongation): along the face axis the coarse
+// index is p + floor(c/2) below the patch and floor((c - p)/2) above it,
+// across it the patch's octant half plus floor(c/2).
+__device__ __forceinline__ int64_t vox_index(const dh_patch* __restrict__ P, const int* __restrict__ oct, int k,
+                                             int p, int x, int y, int z) {
+  int f = -1;
+  if (x < 0) f = 0;
+  else if (x >= p) f = 1;
+  else if (y < 0) f = 2;
+  else if (y >= p) f = 3;
+  else if (z < 0) f = 4;
+  else if (z >= p) f = 5;
+  if (f < 0) return P[k].offset + ((int64_t)z * p + y) * p + x;
+  const int n = P[k].nbr[f];
+  if (oct && P[n].level < P[k].level) {
+    const int o = oct[k], h = p >> 1, a = f >> 1;
+    int c[3] = {x, y, z};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) c[b] = c[b] < 0 ? p + (c[b] >> 1) : (c[b] - p) >> 1;
+      else c[b] = ((o >> b) & 1) * h + (c[b] >> 1);
+    }
+    return P[n].offset + ((int64_t)c[2] * p + c[1]) * p + c[0];
+  }
+  if (f == 0) x += p;
+  else if (f == 1) x -= p;
+  else if (f == 2) y += p;
+  else if (f == 3) y -= p;
+  else if (f == 4) z += p;
+  else z -= p;
+  return P[n].offset + ((int64_t)z * p + y) * p + x;
 }
 
 template <class PDE>
@@ -137,7 +162,7 @@ struct FvTile {
     int x, y, d;
     if (j < TY) { d = 0; y = y0 + j; x = h == 0 ? x0 + TX : x0 - 1; }
     else { d = 1; x = x0 + (j - TY); y = h == 0 ? y0 + TY : y0 - 1; }
-    const int64_t e = vox_index(A.patches, k, p, x, y, z);
+    const int64_t e = vox_index(A.patches, A.oct, k, p, x, y, z);
     double q[NV], W[NW > 0 ? NW : 1], F[N];
     load_q<PDE>(A, e, q);
     PDE::prims(q, A.P, W);
@@ -213,7 +238,7 @@ struct FvTile {
         Lzk = PDE::speed(2, Qk, Wk, A.P);
         // plane -1 from the -z neighbour
         double Qm[NV], Wm[NW > 0 ? NW : 1], Fzm[N];
-        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, z0 - 1), Qm);
+        load_q<PDE>(A, vox_index(A.patches, A.oct, k, p, x, y, z0 - 1), Qm);
         PDE::prims(Qm, A.P, Wm);
         if (PDE::FLUX) PDE::flux(2, Qm, Wm, A.P, Fzm);
         const double s = max_nn(PDE::speed(2, Qm, Wm, A.P), Lzk);
@@ -259,7 +284,7 @@ struct FvTile {
 #pragma unroll
       for (int v = 0; v < N; ++v) { Hzhi[v] = 0.0; Dzhi[v] = 0.0; Fzn[v] = 0.0; }
       if (DIM == 3 && act) {
-        load_q<PDE>(A, vox_index(A.patches, k, p, x, y, zg + 1), Qn);
+        load_q<PDE>(A, vox_index(A.patches, A.oct, k, p, x, y, zg + 1), Qn);
         PDE::prims(Qn, A.P, Wn);
         if (PDE::FLUX) PDE::flux(2, Qn, Wn, A.P, Fzn);
         Lzn = PDE::speed(2, Qn, Wn, A.P);
@@ -439,6 +464,7 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
   A.a = a; A.b = b; A.g = g; A.d = d;
   A.lam_out = lam_out;
   A.red = plan->d_red;
+  A.oct = plan->coupled ? plan->d_amr_oct : nullptr;
   A.vs = plan->var_stride;
   A.P = plan->params;
   switch (plan->pde) {

@@ -40,6 +40,17 @@ struct Work {
 // every segment length, 8..64).
 constexpr int AO_UNIT_VOXELS = 4096;
 
+// Reflux entry of coupled refinement levels: coarse voxel eC of patch C next to
+// fine patch F across F's face (axis, lo: C on F's -axis side), the covered
+// coarse voxel eN of F's parent N across that face, and the first of the
+// 2^(d-1) fine voxels eF of F on the face (the others at +sb0, +sb1, +sb0+sb1).
+struct AmrReflux {
+  int C, N, F;
+  int eC, eN, eF;
+  int sb0, sb1;
+  int axis, lo;
+};
+
 // One FD tile: an 8x8x4 block of one patch.
 struct FdWork {
   int32_t patch;
@@ -80,6 +91,14 @@ struct dh_plan {
   // AoAoS gather/scatter units: (patch, first voxel), up to AO_UNIT_VOXELS voxels each
   int2* d_aunits = nullptr;
   int n_aunits = 0;
+  // coupled refinement levels (dh_amr.cu): octant bits per patch, reflux entries
+  // grouped by face direction, (fine patch, parent) pairs finest level first
+  bool coupled = false;
+  int* d_amr_oct = nullptr;
+  dh::AmrReflux* d_amr_reflux = nullptr;
+  int amr_reflux_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  int2* d_amr_restrict = nullptr;
+  std::vector<int> amr_restrict_off;
   // offload mode: device copy of the bound block pointer table (dh_offload_bind)
   double** d_offload = nullptr;
   int offload_nq = 0, offload_halo = 0;
@@ -117,6 +136,9 @@ inline void finish_params(DevParams& P) {
 }
 
 std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim);
+dh_status amr_build(dh_plan* plan, const dh_patch* patches, int K, int dim);
+dh_status amr_couple(dh_plan* plan, const double* qs, const double* mat, double* out, double* acc,
+                     const double* dt_dev, double g, double d, cudaStream_t s);
 dh_status aoas_move(dh_plan* plan, bool gather, const double* const* blocks, int nq, int v0, int nv, int halo,
                     double* arena, cudaStream_t s);
 

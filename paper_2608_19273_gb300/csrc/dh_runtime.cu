@@ -170,7 +170,16 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
   plan->graph_stages = timing ? stages : 0;
   const int nst = rk == 1 ? 1 : rk;
   const int srhd = plan->pde == DH_PDE_SRHD3D;
-  plan->graph_kernels = n_steps * (nst * (1 + srhd) + (cfl > 0 ? 1 + 2 * srhd : 0));
+  // coupled levels: per stage one reflux launch per face direction in use and one restriction
+  // launch per level; the last stage's wave speed is a separate launch
+  int cpl = 0;
+  if (plan->coupled && scheme == 0) {
+    for (int f = 0; f < 6; ++f) cpl += plan->amr_reflux_off[f + 1] > plan->amr_reflux_off[f];
+    for (size_t l = 0; l + 1 < plan->amr_restrict_off.size(); ++l)
+      cpl += plan->amr_restrict_off[l + 1] > plan->amr_restrict_off[l];
+  }
+  const int cpl_lam = plan->coupled && scheme == 0 && cfl > 0 && !srhd;
+  plan->graph_kernels = n_steps * (nst * (1 + srhd + cpl) + (cfl > 0 ? 1 + 2 * srhd + cpl_lam : 0));
   return DH_OK;
 }
 
