@@ -55,6 +55,11 @@ WORKLOADS = {
                           kernel="k_fv2_stage<Euler3D>",
                           desc="3D Euler, second-order FV (MUSCL-minmod + Rusanov), SSP-RK3; 4096x8^3 + 1024x16^3 + "
                                "128x32^3 patches, halo 2"),
+    "euler3d_amr2": dict(pde=3, scheme=0, rk=3, inner=20, cfl=0.4, flops="fv/euler3d/ssprk3_step", bytes=320,
+                         kernel="k_fv_stage<Euler3D> + k_reflux + k_restrict",
+                         desc="3D Euler on two coupled refinement levels (512 coarse 16^3 patches, dx 1/128, with the "
+                              "central 4^3 block refined into 512 patches of 16^3, dx 1/256): FV Rusanov with "
+                              "prolongation, reflux and restriction, SSP-RK3; halo 1"),
     "euler2d": dict(pde=2, scheme=0, rk=1, inner=10, cfl=0.4, flops="fv/euler2d/fe_step", bytes=128,
                     kernel="k_fv_stage<Euler2D>",
                     desc="2D Euler (4 vars), FV Rusanov, forward Euler; 64 patches of 16^2, halo 1"),
@@ -126,6 +131,8 @@ def host_inputs(name, w):
     mesh = w.mesh
     if name in ("euler3d", "euler2d", "euler3d_muscl"):
         return synth.euler_prims(mesh, w.seed), None, "prim"
+    if name == "euler3d_amr2":
+        return synth.euler_prims_coupled(mesh, w.seed), None, "prim"
     if name == "wave3d":
         q, mat = synth.wave_initial(mesh, w.seed)
         return q, mat, "cons"
@@ -231,7 +238,8 @@ def oracle_sample(name, budget_s):
     else the same patch sizes with fewer patches per level (scaled box)."""
     import oracle
     cores = oracle.num_threads(0)
-    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
+    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
+             "gw59": 4}[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)
@@ -261,7 +269,8 @@ def reference_arm(args, rank, world):
     name = args.workload
     import oracle
     cores = oracle.num_threads(0)
-    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler2d": 1, "wave3d": 2, "srhd3d": 2, "gw59": 4}[name]
+    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
+             "gw59": 4}[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)

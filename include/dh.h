@@ -93,9 +93,20 @@ typedef struct dh_plan dh_plan;
  *   params     : PDE parameters (host, may be NULL for defaults):
  *                EULER*: [gamma=1.4]  SRHD3D: [Gamma=5/3]  WAVE3D: [damping=0.1]
  *                GW59: [kappa=0.1, C_ab (121 values, row-major)]
- * Patch sizes: every p must be a multiple of 8.  Neighbours must have the
- * same p and dx.  Returns DH_EINVAL on a malformed table, DH_ENOMEM or
- * DH_ECUDA if the device tables cannot be created. */
+ * Patch sizes: every p must be a multiple of 8.  A face neighbour has the
+ * same p, dx and level, or -- coupled refinement levels -- is one level
+ * coarser with the same p and twice the dx; every patch above the coarsest
+ * level present must then cover one octant of a patch one level coarser (its
+ * parent, found from x0: lattice index round(x0 / (p dx)) halved), which stays
+ * in the list.  On such a plan patch_update_fv (first-order FV, conservative
+ * systems) adds, inside the same stage: piecewise-constant prolongation of the
+ * fine halos (a halo voxel takes the value of the coarse voxel containing it),
+ * reflux (a coarse voxel next to the finer level uses the mean of the fine
+ * face fluxes on that face) and restriction (covered coarse voxels become the
+ * mean of their 2^d fine voxels).  The paper's meshes are Peano spacetrees
+ * (Sec. IV); it defines no coupling, these are the readings used.
+ * Returns DH_EINVAL on a malformed table, DH_ENOMEM or DH_ECUDA if the device
+ * tables cannot be created. */
 dh_status dh_plan_create(dh_plan** plan, int32_t pde, int32_t dim, const dh_patch* patches, int32_t K,
                          int32_t halo, int64_t var_stride, const double* params, int32_t n_params);
 dh_status dh_plan_destroy(dh_plan* plan);

@@ -141,6 +141,13 @@ def coupled_fields(mesh, rng, specs):
     return out
 
 
+def euler_prims_coupled(mesh, seed):
+    """The euler_prims recipe on a coupled mesh: fields periodic on the coarse box at every voxel."""
+    rng = np.random.default_rng(seed)
+    specs = [(1.0, 0.5)] + [(0.0, 0.5)] * mesh.dim + [(1.0, 0.5)]
+    return coupled_fields(mesh, rng, specs)
+
+
 def voxel_centres_any(mesh):
     """Voxel-centre coordinates (3, var_stride) for any patch table (patch by patch)."""
     X = np.zeros((3, mesh.var_stride))
@@ -281,12 +288,19 @@ def workload(name, scale=1):
     srhd3d  : special-relativistic hydro, FV Rusanov + con2prim, SSP-RK3, 4096 patches of 16^3.
     gw59    : 59-unknown gravitational-wave stand-in, FD4 + KO, RK4, 3 levels of 24^3/16^3 patches.
     euler3d_muscl : the euler3d mix and data with the second-order FV stage (MUSCL-minmod, halo 2).
+    euler3d_amr2 : 3D Euler on two coupled refinement levels: 8^3 coarse patches of 16^3 (dx 1/128) and
+                   the block of coarse lattice [2, 6)^3 refined into 8^3 patches of 16^3 (dx 1/256);
+                   FV Rusanov with prolongation, reflux and restriction, SSP-RK3, CFL 0.4.
     """
     if name == "euler2d":
         return Workload(name, PDE_EULER2D, SCHEME_FV, euler2d_mesh(), 1, 1, 10, 0.4, 0.0, SEED_BASE + 0)
     if name == "euler3d":
         return Workload(name, PDE_EULER3D, SCHEME_FV, euler3d_amr_mesh(scale), 1, 3, 100, 0.4, 0.0,
                         SEED_BASE + 1)
+    if name == "euler3d_amr2":
+        s_ = scale
+        return Workload(name, PDE_EULER3D, SCHEME_FV, coupled_mesh(8 // s_, 16, 1.0 / 128, 2 // s_, 4 // s_), 1, 3,
+                        20, 0.4, 0.0, SEED_BASE + 6)
     if name == "euler3d_muscl":
         return Workload(name, PDE_EULER3D, SCHEME_FV2, euler3d_amr_mesh(scale), 2, 3, 20, 0.4, 0.0,
                         SEED_BASE + 1)
