@@ -17,7 +17,8 @@ pytestmark = pytest.mark.gpu
 
 
 def _gpu_step(torch, name, w, q, mat, steps=1):
-    spec = {"euler3d": (0, 3, 0.4), "wave3d": (1, 4, 0.25), "srhd3d": (0, 3, 0.4), "euler3d_muscl": (2, 3, 0.4)}[name]
+    spec = {"euler3d": (0, 3, 0.4), "wave3d": (1, 4, 0.25), "srhd3d": (0, 3, 0.4), "euler3d_muscl": (2, 3, 0.4),
+            "euler3d_amr2": (0, 3, 0.4)}[name]
     scheme, rk, cfl = spec
     mesh = w.mesh
     with dh.Plan(w.pde, 3, mesh.patches, w.halo, mesh.var_stride, w.params) as plan:
@@ -63,6 +64,19 @@ def test_euler3d_muscl_full_size_step(orc):
     dts = orc.rk_steps(2, 3, 3, mesh.patches, 2, mesh.var_stride, ref, rk=3, steps=1, cfl=0.4)
     assert abs(dt - dts[0]) <= 1e-15 * dts[0]
     assert_parity(got, ref, voxel_mask(mesh), what="euler3d MUSCL full size")
+
+
+def test_euler3d_coupled_levels_full_size_steps(orc):
+    """Two coupled refinement levels (4.2M voxels), two SSP-RK3 steps with device dt."""
+    torch = require_cuda()
+    w = synth.workload("euler3d_amr2")
+    mesh = w.mesh
+    q = orc.prim2con(3, synth.euler_prims_coupled(mesh, w.seed), mesh.var_stride)
+    got, dt = _gpu_step(torch, "euler3d_amr2", w, q, None, steps=2)
+    ref = q.copy()
+    dts = orc.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=2, cfl=0.4)
+    assert abs(dt - dts[-1]) <= 1e-14 * dts[-1]
+    assert_parity(got, ref, voxel_mask(mesh), what="coupled levels full size")
 
 
 def test_wave3d_full_size_step(orc):
