@@ -20,9 +20,11 @@
 //   * Restriction (k_restrict, last): every coarse voxel covered by the finer
 //     level becomes the mean of its 2^d fine voxels, finest level first.
 // The plan builds, once: the octant bits of every patch, one reflux entry
-// per (coarse voxel, face) grouped by face direction (a coarse voxel has at
-// most one entry per direction, so one launch per direction has no write
-// conflicts), and the list of (fine patch, parent) pairs by level.
+// per (coarse voxel, face) grouped by face direction, and the list of (fine
+// patch, parent) pairs by level.  A coarse voxel has at most one entry per
+// direction; when it also has at most one entry overall (a convex refined
+// region) all entries go in one launch, else one launch per direction, so no
+// two threads of a launch write the same voxel.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -58,40 +60,50 @@ __device__ __forceinline__ void c_load(const CplArgs& A, int64_t e, double* q) {
   for (int v = 0; v < PDE::M; ++v) q[PDE::N + v] = A.mat[v * A.vs + e];
 }
 
-// Rusanov flux (F_a(QL) + F_a(QR))/2 - s/2 (QR - QL), s = max(lambda_a(QL), lambda_a(QR)).
+// Flux F_a and speed lambda_a of one voxel state (N+M values).
 template <class PDE>
-__device__ __forceinline__ void c_rusanov(const DevParams& P, int a, const double* qL, const double* qR, double* fh) {
-  constexpr int N = PDE::N, NW = PDE::NW > 0 ? PDE::NW : 1;
-  double WL[NW], WR[NW], FL[N], FR[N];
-  PDE::prims(qL, P, WL);
-  PDE::prims(qR, P, WR);
-  PDE::flux(a, qL, WL, P, FL);
-  PDE::flux(a, qR, WR, P, FR);
-  const double hs = 0.5 * max_nn(PDE::speed(a, qL, WL, P), PDE::speed(a, qR, WR, P));
+__device__ __forceinline__ void c_flux(const DevParams& P, int a, const double* q, double* F, double& lam) {
+  double W[PDE::NW > 0 ? PDE::NW : 1];
+  PDE::prims(q, P, W);
+  PDE::flux(a, q, W, P, F);
+  lam = PDE::speed(a, q, W, P);
+}
+
+// Rusanov flux (F_L + F_R)/2 - max(lam_L, lam_R)/2 (Q_R - Q_L) from precomputed fluxes and speeds.
+template <int N>
+__device__ __forceinline__ void c_rusanov(const double* qL, const double* FL, double lL, const double* qR,
+                                          const double* FR, double lR, double* fh) {
+  const double hs = 0.5 * max_nn(lL, lR);
 #pragma unroll
   for (int v = 0; v < N; ++v) fh[v] = 0.5 * (FL[v] + FR[v]) - hs * (qR[v] - qL[v]);
 }
 
+// One thread per reflux entry; the derived quantities, flux and speed of every
+// voxel involved are computed once.
 template <class PDE>
-__global__ void __launch_bounds__(128) k_reflux(const __grid_constant__ CplArgs A) {
+__global__ void __launch_bounds__(64) k_reflux(const __grid_constant__ CplArgs A) {
   constexpr int N = PDE::N, NV = PDE::N + PDE::M;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.n) return;
   const AmrReflux R = A.reflux[i];
   const dh_patch& C = A.patches[R.C];
   const int64_t eC = C.offset + R.eC;
-  double qC[NV], qN[NV], qF[NV], fc[N], ff[N], pair[N], fsum[N];
+  const int a = R.axis;
+  double qC[NV], qN[NV], qF[NV], FC[N], FN[N], FF[N], fc[N], ff[N], pair[N], fsum[N], lC, lN, lF;
   c_load<PDE>(A, eC, qC);
   c_load<PDE>(A, A.patches[R.N].offset + R.eN, qN);
-  if (R.lo) c_rusanov<PDE>(A.P, R.axis, qC, qN, fc);
-  else c_rusanov<PDE>(A.P, R.axis, qN, qC, fc);
+  c_flux<PDE>(A.P, a, qC, FC, lC);
+  c_flux<PDE>(A.P, a, qN, FN, lN);
+  if (R.lo) c_rusanov<N>(qC, FC, lC, qN, FN, lN, fc);
+  else c_rusanov<N>(qN, FN, lN, qC, FC, lC, fc);
   const int64_t f0 = A.patches[R.F].offset + R.eF;
   const int nk = A.dim == 3 ? 2 : 1;
   for (int sk = 0; sk < nk; ++sk) {
     for (int sj = 0; sj < 2; ++sj) {
       c_load<PDE>(A, f0 + sj * R.sb0 + sk * R.sb1, qF);
-      if (R.lo) c_rusanov<PDE>(A.P, R.axis, qC, qF, ff);
-      else c_rusanov<PDE>(A.P, R.axis, qF, qC, ff);
+      c_flux<PDE>(A.P, a, qF, FF, lF);
+      if (R.lo) c_rusanov<N>(qC, FC, lC, qF, FF, lF, ff);
+      else c_rusanov<N>(qF, FF, lF, qC, FC, lC, ff);
 #pragma unroll
       for (int v = 0; v < N; ++v) pair[v] = sj == 0 ? ff[v] : pair[v] + ff[v];
     }
@@ -145,12 +157,16 @@ inline int lattice(const dh_patch& P, int a) { return (int)std::llround(P.x0[a] 
 
 template <class PDE>
 dh_status couple_pde(dh_plan* plan, CplArgs A, cudaStream_t s) {
-  for (int f = 0; f < 6; ++f) {
-    const int n = plan->amr_reflux_off[f + 1] - plan->amr_reflux_off[f];
+  // one launch for all entries when no coarse voxel has entries in two directions,
+  // else one launch per direction
+  const int groups = plan->amr_reflux_single ? 1 : 6;
+  for (int f = 0; f < groups; ++f) {
+    const int lo = plan->amr_reflux_off[f], hi = plan->amr_reflux_single ? plan->amr_reflux_off[6] : plan->amr_reflux_off[f + 1];
+    const int n = hi - lo;
     if (n == 0) continue;
-    A.reflux = plan->d_amr_reflux + plan->amr_reflux_off[f];
+    A.reflux = plan->d_amr_reflux + lo;
     A.n = n;
-    k_reflux<PDE><<<(n + 127) / 128, 128, 0, s>>>(A);
+    k_reflux<PDE><<<(n + 63) / 64, 64, 0, s>>>(A);
     dh_status st = cuda_error(cudaGetLastError(), "k_reflux launch");
     if (st != DH_OK) return st;
   }
@@ -258,6 +274,13 @@ dh_status amr_build(dh_plan* plan, const dh_patch* patches, int K, int dim) {
   for (int f = 0; f < 6; ++f) {
     all.insert(all.end(), ent[f].begin(), ent[f].end());
     plan->amr_reflux_off[f + 1] = (int)all.size();
+  }
+  {
+    std::vector<std::pair<int, int>> keys;
+    keys.reserve(all.size());
+    for (const AmrReflux& R : all) keys.push_back(std::make_pair(R.C, R.eC));
+    std::sort(keys.begin(), keys.end());
+    plan->amr_reflux_single = std::adjacent_find(keys.begin(), keys.end()) == keys.end();
   }
   cudaError_t e = cudaMalloc(&plan->d_amr_oct, sizeof(int) * K);
   if (e == cudaSuccess) e = cudaMemcpy(plan->d_amr_oct, oct.data(), sizeof(int) * K, cudaMemcpyHostToDevice);

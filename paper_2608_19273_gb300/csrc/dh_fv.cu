@@ -23,6 +23,7 @@
 //     shuffles, then one atomicMax per CTA on the bit pattern (valid for
 //     non-negative doubles), and the last CTA publishes it (no spin waits).
 #include <algorithm>
+#include <type_traits>
 
 #include "dh_internal.cuh"
 #include "dh_pde.cuh"
@@ -42,6 +43,8 @@ struct FvArgs {
   double* lam_out;
   unsigned long long* red;
   const int* oct;  // octant bits per patch on coupled plans, else NULL
+  const double* w_in;  // derived quantities W of qs (NW-variable arena) when the stage reads them
+  double* w_out;       // W of the result, written by a stage that computes it for lambda
   int64_t vs;      // var stride
   DevParams P;
 };
@@ -91,7 +94,20 @@ __device__ __forceinline__ void load_q(const FvArgs& A, int64_t e, double* q) {
   for (int v = 0; v < PDE::M; ++v) q[PDE::N + v] = __ldg(A.mat + v * A.vs + e);
 }
 
-template <class PDE, int TX, int TY, int G, bool EARLY>
+// Derived quantities W of the voxel at arena index e: read from the W arena the
+// previous step's last stage wrote (WM bit 0) or computed from q.  Both give
+// the same bits: the stored W was computed by PDE::prims from the same values.
+template <class PDE, int WM>
+__device__ __forceinline__ void derive(const FvArgs& A, int64_t e, const double* q, double* W) {
+  if (WM & 1) {
+#pragma unroll
+    for (int i = 0; i < PDE::NW; ++i) W[i] = __ldg(A.w_in + i * A.vs + e);
+  } else {
+    PDE::prims(q, A.P, W);
+  }
+}
+
+template <class PDE, int TX, int TY, int G, bool EARLY, int WM>
 struct FvTile {
   static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW, DIM = PDE::DIM;
   static constexpr int NT = TX * TY * G;
@@ -165,7 +181,7 @@ struct FvTile {
     const int64_t e = vox_index(A.patches, A.oct, k, p, x, y, z);
     double q[NV], W[NW > 0 ? NW : 1], F[N];
     load_q<PDE>(A, e, q);
-    PDE::prims(q, A.P, W);
+    derive<PDE, WM>(A, e, q, W);
     const int s = NT + buf * NR + r;
 #pragma unroll
     for (int v = 0; v < NV; ++v) S.Q[v * NS + s] = q[v];
@@ -220,7 +236,7 @@ struct FvTile {
     if (act) {
       double Wk[NW > 0 ? NW : 1], F[N];
       load_q<PDE>(A, off + ((int64_t)z0 * p + y) * p + x, Qk);
-      PDE::prims(Qk, A.P, Wk);
+      derive<PDE, WM>(A, off + ((int64_t)z0 * p + y) * p + x, Qk, Wk);
       if (PDE::FLUX) {
         PDE::flux(0, Qk, Wk, A.P, F);
 #pragma unroll
@@ -238,8 +254,9 @@ struct FvTile {
         Lzk = PDE::speed(2, Qk, Wk, A.P);
         // plane -1 from the -z neighbour
         double Qm[NV], Wm[NW > 0 ? NW : 1], Fzm[N];
-        load_q<PDE>(A, vox_index(A.patches, A.oct, k, p, x, y, z0 - 1), Qm);
-        PDE::prims(Qm, A.P, Wm);
+        const int64_t em = vox_index(A.patches, A.oct, k, p, x, y, z0 - 1);
+        load_q<PDE>(A, em, Qm);
+        derive<PDE, WM>(A, em, Qm, Wm);
         if (PDE::FLUX) PDE::flux(2, Qm, Wm, A.P, Fzm);
         const double s = max_nn(PDE::speed(2, Qm, Wm, A.P), Lzk);
         double dq[N];
@@ -284,8 +301,9 @@ struct FvTile {
 #pragma unroll
       for (int v = 0; v < N; ++v) { Hzhi[v] = 0.0; Dzhi[v] = 0.0; Fzn[v] = 0.0; }
       if (DIM == 3 && act) {
-        load_q<PDE>(A, vox_index(A.patches, A.oct, k, p, x, y, zg + 1), Qn);
-        PDE::prims(Qn, A.P, Wn);
+        const int64_t en = vox_index(A.patches, A.oct, k, p, x, y, zg + 1);
+        load_q<PDE>(A, en, Qn);
+        derive<PDE, WM>(A, en, Qn, Wn);
         if (PDE::FLUX) PDE::flux(2, Qn, Wn, A.P, Fzn);
         Lzn = PDE::speed(2, Qn, Wn, A.P);
         const double s = max_nn(Lzk, Lzn);
@@ -345,6 +363,10 @@ struct FvTile {
           for (int v = N; v < NV; ++v) res[v] = Qk[v];
           double Wr[NW > 0 ? NW : 1];
           PDE::prims(res, A.P, Wr);
+          if (WM & 2) {
+#pragma unroll
+            for (int i = 0; i < NW; ++i) A.w_out[i * A.vs + e] = Wr[i];
+          }
           double l = max_nn(PDE::speed(0, res, Wr, A.P), PDE::speed(1, res, Wr, A.P));
           if (DIM == 3) l = max_nn(l, PDE::speed(2, res, Wr, A.P));
           lam_thread = max_nn(lam_thread, l);
@@ -413,27 +435,32 @@ __device__ void publish_lambda(double lam, double* lam_out, unsigned long long* 
 // Kernel variants (chosen per plan by the autotuner, dh_autotune):
 //   VAR bit 0: EARLY -- the halo ring of the next plane is computed before the
 //              mid-plane barrier instead of after it;
-//   VAR bit 1: at most 128 registers so that two CTAs fit on an SM.
+//   VAR bit 1: at most 128 registers so that two CTAs fit on an SM;
+//   VAR bits 2-3: WM -- bit 2 reads W of qs from A.w_in instead of computing
+//              it, bit 3 writes W of the result to A.w_out (multi-step graphs:
+//              the last stage of a step hands W to the first stage of the next).
 template <class PDE, int VAR>
 __global__ void __launch_bounds__(256, (VAR & 2) ? 2 : 1) k_fv_stage(const __grid_constant__ FvArgs A) {
   extern __shared__ __align__(16) double smem[];
   constexpr bool EARLY = (VAR & 1) != 0;
+  constexpr int WM = (VAR >> 2) & 3;
   const Work w = A.work[blockIdx.x];
   double lam = 0.0;
-  if (w.cls == 0) FvTile<PDE, 16, 16, 1, EARLY>::run(A, w, smem, lam);
-  else FvTile<PDE, 8, 8, 4, EARLY>::run(A, w, smem, lam);
+  if (w.cls == 0) FvTile<PDE, 16, 16, 1, EARLY, WM>::run(A, w, smem, lam);
+  else FvTile<PDE, 8, 8, 4, EARLY, WM>::run(A, w, smem, lam);
   if (A.lam_out) publish_lambda(lam, A.lam_out, A.red);
 }
 
 template <class PDE, int VAR>
 static dh_status launch_var(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
   constexpr bool EARLY = (VAR & 1) != 0;
+  constexpr int WM = (VAR >> 2) & 3;
   const int zs = plan->fv_zs;
-  const size_t smem = std::max(plan->has_cls[0] ? FvTile<PDE, 16, 16, 1, EARLY>::SMEM : 0,
-                               plan->has_cls[1] ? FvTile<PDE, 8, 8, 4, EARLY>::SMEM : 0);
+  const size_t smem = std::max(plan->has_cls[0] ? FvTile<PDE, 16, 16, 1, EARLY, WM>::SMEM : 0,
+                               plan->has_cls[1] ? FvTile<PDE, 8, 8, 4, EARLY, WM>::SMEM : 0);
   static int configured_device = -1;  // attribute is per device function; set once per process and device
   if (configured_device != plan->device) {
-    const size_t mx = std::max(FvTile<PDE, 16, 16, 1, EARLY>::SMEM, FvTile<PDE, 8, 8, 4, EARLY>::SMEM);
+    const size_t mx = std::max(FvTile<PDE, 16, 16, 1, EARLY, WM>::SMEM, FvTile<PDE, 8, 8, 4, EARLY, WM>::SMEM);
     cudaError_t e = cudaFuncSetAttribute(k_fv_stage<PDE, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv_stage)");
     configured_device = plan->device;
@@ -444,19 +471,43 @@ static dh_status launch_var(dh_plan* plan, const FvArgs& A, cudaStream_t stream)
   return cuda_error(cudaGetLastError(), "k_fv_stage launch");
 }
 
-template <class PDE>
-static dh_status launch(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
+template <class PDE, int WM>
+static dh_status launch_wm(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
   switch (plan->fv_var & 3) {
-    case 0: return launch_var<PDE, 0>(plan, A, stream);
-    case 1: return launch_var<PDE, 1>(plan, A, stream);
-    case 2: return launch_var<PDE, 2>(plan, A, stream);
-    default: return launch_var<PDE, 3>(plan, A, stream);
+    case 0: return launch_var<PDE, 0 | (WM << 2)>(plan, A, stream);
+    case 1: return launch_var<PDE, 1 | (WM << 2)>(plan, A, stream);
+    case 2: return launch_var<PDE, 2 | (WM << 2)>(plan, A, stream);
+    default: return launch_var<PDE, 3 | (WM << 2)>(plan, A, stream);
   }
+}
+
+// W reuse is compiled for the Euler systems only (the systems whose derived
+// quantities cost a reciprocal and a square root per voxel).
+template <class PDE>
+static dh_status launch(dh_plan* plan, const FvArgs& A, int wmode, cudaStream_t stream) {
+  if constexpr (std::is_same<PDE, PdeEuler2>::value || std::is_same<PDE, PdeEuler3>::value) {
+    switch (wmode & 3) {
+      case 1: return launch_wm<PDE, 1>(plan, A, stream);
+      case 2: return launch_wm<PDE, 2>(plan, A, stream);
+      default: break;
+    }
+  }
+  return launch_wm<PDE, 0>(plan, A, stream);
 }
 
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
-                          double* lam_out, cudaStream_t stream) {
+                          double* lam_out, cudaStream_t stream, int wmode) {
+  // a stage either reads W (of its input) or writes it (of its result), never both:
+  // other CTAs would read halo W while it is overwritten
+  if (wmode == 3 || ((wmode & 2) && !lam_out)) {
+    set_error("launch_fv_stage: W is read or written (with lam_out), not both");
+    return DH_EINVAL;
+  }
+  if (wmode && !plan->d_w) {
+    set_error("launch_fv_stage: no W arena");
+    return DH_EINVAL;
+  }
   FvArgs A;
   A.patches = plan->d_patches;
   A.work = plan->d_work;
@@ -465,14 +516,16 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
   A.lam_out = lam_out;
   A.red = plan->d_red;
   A.oct = plan->coupled ? plan->d_amr_oct : nullptr;
+  A.w_in = plan->d_w;
+  A.w_out = plan->d_w;
   A.vs = plan->var_stride;
   A.P = plan->params;
   switch (plan->pde) {
-    case DH_PDE_ADV_FLUX: return launch<PdeAdvFlux>(plan, A, stream);
-    case DH_PDE_ADV_NCP: return launch<PdeAdvNcp>(plan, A, stream);
-    case DH_PDE_EULER2D: return launch<PdeEuler2>(plan, A, stream);
-    case DH_PDE_EULER3D: return launch<PdeEuler3>(plan, A, stream);
-    case DH_PDE_SRHD3D: return launch<PdeSRHD>(plan, A, stream);
+    case DH_PDE_ADV_FLUX: return launch<PdeAdvFlux>(plan, A, wmode, stream);
+    case DH_PDE_ADV_NCP: return launch<PdeAdvNcp>(plan, A, wmode, stream);
+    case DH_PDE_EULER2D: return launch<PdeEuler2>(plan, A, wmode, stream);
+    case DH_PDE_EULER3D: return launch<PdeEuler3>(plan, A, wmode, stream);
+    case DH_PDE_SRHD3D: return launch<PdeSRHD>(plan, A, wmode, stream);
     default:
       set_error("patch_update_fv: PDE %d not supported by the FV stage", plan->pde);
       return DH_EUNSUPPORTED;

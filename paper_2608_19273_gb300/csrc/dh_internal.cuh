@@ -97,8 +97,12 @@ struct dh_plan {
   int* d_amr_oct = nullptr;
   dh::AmrReflux* d_amr_reflux = nullptr;
   int amr_reflux_off[7] = {0, 0, 0, 0, 0, 0, 0};
+  bool amr_reflux_single = false;  // no coarse voxel has entries in two directions: one launch
   int2* d_amr_restrict = nullptr;
   std::vector<int> amr_restrict_off;
+  // derived quantities W (NW-variable arena) handed from the last stage of a time step to
+  // the first stage of the next inside a captured multi-step graph (Euler systems)
+  double* d_w = nullptr;
   // offload mode: device copy of the bound block pointer table (dh_offload_bind)
   double** d_offload = nullptr;
   int offload_nq = 0, offload_halo = 0;
@@ -150,8 +154,10 @@ dh_status launch_fv2_stage(dh_plan* plan, const double* qs, const double* q0, do
                            const double* mat, const double* dt_dev, double a, double b, double g, double d,
                            double* lam_out, cudaStream_t stream);
 
+// wmode: bit 0 reads the derived quantities W of qs from plan->d_w, bit 1 writes W
+// of the result there (needs lam_out); 0 outside multi-step graphs.
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
-                          double* lam_out, cudaStream_t stream);
+                          double* lam_out, cudaStream_t stream, int wmode = 0);
 
 }  // namespace dh

@@ -159,3 +159,35 @@ def test_newton_reciprocal_within_one_ulp():
     ulp = np.abs(a.view(np.int64) - b.view(np.int64))
     assert ulp.max() <= 1, ulp.max()
     assert np.array_equal(b, 1.0 / x)
+
+
+def test_graph_hands_derived_quantities_to_the_next_step(orc):
+    """Inside a multi-step SSP-RK3 graph the last stage of a step stores the derived quantities of
+    its result and the next step's first stage reads them: bitwise the same state and dt as eager
+    dh_rk_step calls (which recompute them)."""
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=4)
+    q = _euler_cons(orc, mesh, 37)
+    res = []
+    for graph in (False, True):
+        with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+            Q = dev(torch, q)
+            U1, U2 = torch.zeros_like(Q), torch.zeros_like(Q)
+            lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dh.max_wave_speed(plan, Q, None, lam)
+            torch.cuda.synchronize()
+            if graph:
+                s = torch.cuda.Stream()
+                dh.dh_rk_step(plan, FV, 3, Q.clone(), U1, U2, None, None, dt.clone(), lam.clone(), 0.4, 0.0, s)
+                s.synchronize()
+                dh.dh_graph_capture(plan, FV, 3, 4, Q, U1, U2, None, None, dt, lam, 0.4, 0.0, 0, s)
+                dh.dh_graph_launch(plan, s)
+                s.synchronize()
+            else:
+                for _ in range(4):
+                    dh.dh_rk_step(plan, FV, 3, Q, U1, U2, None, None, dt, lam, 0.4, 0.0)
+            res.append((host(Q), host(dt), host(lam)))
+    m = voxel_mask(mesh)
+    assert np.array_equal(res[0][0][:, m], res[1][0][:, m])
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
