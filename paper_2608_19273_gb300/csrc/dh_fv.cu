@@ -358,7 +358,7 @@ struct FvTile {
           }
           if (A.out) A.out[ev] = res[v];
         }
-        if (A.lam_out) {
+        if (A.lam_out || (WM & 2)) {
 #pragma unroll
           for (int v = N; v < NV; ++v) res[v] = Qk[v];
           double Wr[NW > 0 ? NW : 1];
@@ -367,9 +367,11 @@ struct FvTile {
 #pragma unroll
             for (int i = 0; i < NW; ++i) A.w_out[i * A.vs + e] = Wr[i];
           }
-          double l = max_nn(PDE::speed(0, res, Wr, A.P), PDE::speed(1, res, Wr, A.P));
-          if (DIM == 3) l = max_nn(l, PDE::speed(2, res, Wr, A.P));
-          lam_thread = max_nn(lam_thread, l);
+          if (A.lam_out) {
+            double l = max_nn(PDE::speed(0, res, Wr, A.P), PDE::speed(1, res, Wr, A.P));
+            if (DIM == 3) l = max_nn(l, PDE::speed(2, res, Wr, A.P));
+            lam_thread = max_nn(lam_thread, l);
+          }
         }
       }
       // ---- publish plane kz+1 (3D)
@@ -489,6 +491,7 @@ static dh_status launch(dh_plan* plan, const FvArgs& A, int wmode, cudaStream_t 
     switch (wmode & 3) {
       case 1: return launch_wm<PDE, 1>(plan, A, stream);
       case 2: return launch_wm<PDE, 2>(plan, A, stream);
+      case 3: return launch_wm<PDE, 3>(plan, A, stream);
       default: break;
     }
   }
@@ -497,15 +500,10 @@ static dh_status launch(dh_plan* plan, const FvArgs& A, int wmode, cudaStream_t 
 
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
-                          double* lam_out, cudaStream_t stream, int wmode) {
-  // a stage either reads W (of its input) or writes it (of its result), never both:
-  // other CTAs would read halo W while it is overwritten
-  if (wmode == 3 || ((wmode & 2) && !lam_out)) {
-    set_error("launch_fv_stage: W is read or written (with lam_out), not both");
-    return DH_EINVAL;
-  }
-  if (wmode && !plan->d_w) {
-    set_error("launch_fv_stage: no W arena");
+                          double* lam_out, cudaStream_t stream, int wmode, const double* w_in, double* w_out) {
+  // a stage that reads and writes W needs two arenas: other CTAs read halo W of the input
+  if (((wmode & 1) && !w_in) || ((wmode & 2) && !w_out) || (wmode == 3 && w_in == w_out)) {
+    set_error("launch_fv_stage: W arenas missing or aliased");
     return DH_EINVAL;
   }
   FvArgs A;
@@ -516,8 +514,8 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
   A.lam_out = lam_out;
   A.red = plan->d_red;
   A.oct = plan->coupled ? plan->d_amr_oct : nullptr;
-  A.w_in = plan->d_w;
-  A.w_out = plan->d_w;
+  A.w_in = w_in;
+  A.w_out = w_out;
   A.vs = plan->var_stride;
   A.P = plan->params;
   switch (plan->pde) {

@@ -102,7 +102,7 @@ struct dh_plan {
   std::vector<int> amr_restrict_off;
   // derived quantities W (NW-variable arena) handed from the last stage of a time step to
   // the first stage of the next inside a captured multi-step graph (Euler systems)
-  double* d_w = nullptr;
+  double* d_w = nullptr;  // two NW-variable arenas back to back (stage results alternate)
   // offload mode: device copy of the bound block pointer table (dh_offload_bind)
   double** d_offload = nullptr;
   int offload_nq = 0, offload_halo = 0;
@@ -154,10 +154,11 @@ dh_status launch_fv2_stage(dh_plan* plan, const double* qs, const double* q0, do
                            const double* mat, const double* dt_dev, double a, double b, double g, double d,
                            double* lam_out, cudaStream_t stream);
 
-// wmode: bit 0 reads the derived quantities W of qs from plan->d_w, bit 1 writes W
-// of the result there (needs lam_out); 0 outside multi-step graphs.
+// wmode: bit 0 reads the derived quantities W of qs from w_in, bit 1 writes W of the
+// result to w_out (a different arena when both are set); 0 outside multi-step graphs.
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
-                          double* lam_out, cudaStream_t stream, int wmode = 0);
+                          double* lam_out, cudaStream_t stream, int wmode = 0, const double* w_in = nullptr,
+                          double* w_out = nullptr);
 
 }  // namespace dh

@@ -16,9 +16,17 @@
 namespace dh {
 
 struct Timer;
+// Hand-over of the derived quantities W from stage to stage inside a multi-step graph:
+// stage j of the graph writes W of its result into buf[j % 2] and stage j + 1 (whose input
+// that result is) reads it from there.
+struct WChain {
+  bool on = false;
+  int next = 0, total = 0;
+  double* buf[2] = {nullptr, nullptr};
+};
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
-                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, int wmode = 0);
+                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc = nullptr);
 
 struct Timer {
   dh_plan* plan;
@@ -43,7 +51,7 @@ struct Timer {
 // One stage launch, timed (when timing is on) around the stage kernel only.
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
-                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, int wmode) {
+                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc) {
   if (plan->pde == DH_PDE_SRHD3D) {
     // primitives of the stage input, seeded by the previous primitives (in place)
     double* prim = const_cast<double*>(mat);
@@ -52,20 +60,21 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
     lam = nullptr;
   }
   DH_TRY(T.begin());
-  if (scheme == 0 && wmode) DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, wmode));
-  else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
+  if (scheme == 0 && wc && wc->on) {
+    const int j = wc->next++;
+    const int wmode = (j > 0 ? 1 : 0) | (j + 1 < wc->total ? 2 : 0);
+    DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, wmode, wc->buf[(j + 1) & 1],
+                           wc->buf[j & 1]));
+  } else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else if (scheme == 2) DH_TRY(patch_update_fv_muscl(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else DH_TRY(patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s));
   return T.end();
 }
 
 // One time step.  bufs: q (state, in/out), u1, u2 (stage buffers), acc (RK4).
-// wflags (SSP-RK3 FV stages of Euler systems inside a multi-step graph): bit 0 -- the
-// first stage reads the derived quantities W of q that the previous step's last stage
-// wrote; bit 1 -- the last stage writes W of its result.
 static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
                          const double* mat, double* dt, double* lam, double cfl, double sigma, Timer& T,
-                         cudaStream_t s, int wflags = 0) {
+                         cudaStream_t s, WChain* wc = nullptr) {
   const size_t bytes = sizeof(double) * (size_t)plan->nq * (size_t)plan->var_stride;
   double* lam_last = cfl > 0 ? lam : nullptr;
   if (cfl > 0 && plan->pde == DH_PDE_SRHD3D) {
@@ -80,10 +89,10 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s));
     DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
   } else if (rk == 3) {
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wflags & 1));
-    DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc));
+    DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, T, s, wc));
     DH_TRY(stage_call(plan, scheme, u2, q, q, nullptr, mat, dt, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, sigma, lam_last,
-                      T, s, lam_last ? (wflags & 2) : 0));
+                      T, s, wc));
   } else if (rk == 4) {
     DH_TRY(cuda_error(cudaMemcpyAsync(acc, q, bytes, cudaMemcpyDeviceToDevice, s), "copy q -> acc"));
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 0.5, 1.0 / 6.0, sigma, nullptr, T, s));
@@ -163,17 +172,19 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
   // hand the derived quantities of the state from one step to the next (SSP-RK3 FV, Euler)
   const bool reuse = scheme == 0 && rk == 3 && cfl > 0 && n_steps > 1 && !plan->coupled &&
                      (plan->pde == DH_PDE_EULER2D || plan->pde == DH_PDE_EULER3D);
-  if (reuse && !plan->d_w) {
-    const size_t nw = (size_t)(plan->dim + 3) * (size_t)plan->var_stride;
-    DH_TRY(cuda_error(cudaMalloc(&plan->d_w, sizeof(double) * nw), "dh_graph_capture: W arena"));
-  }
+  const size_t nw = (size_t)(plan->dim + 3) * (size_t)plan->var_stride;
+  if (reuse && !plan->d_w)
+    DH_TRY(cuda_error(cudaMalloc(&plan->d_w, 2 * sizeof(double) * nw), "dh_graph_capture: W arenas"));
+  WChain wc;
+  wc.on = reuse;
+  wc.total = 3 * n_steps;
+  wc.buf[0] = plan->d_w;
+  wc.buf[1] = plan->d_w ? plan->d_w + nw : nullptr;
   DH_TRY(cuda_error(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"));
   Timer T{plan, timing != 0, s};
   dh_status st = DH_OK;
-  for (int i = 0; i < n_steps && st == DH_OK; ++i) {
-    const int wflags = reuse ? ((i > 0 ? 1 : 0) | (i + 1 < n_steps ? 2 : 0)) : 0;
-    st = rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s, wflags);
-  }
+  for (int i = 0; i < n_steps && st == DH_OK; ++i)
+    st = rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s, &wc);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &graph);
   if (st != DH_OK) { if (graph) cudaGraphDestroy(graph); return st; }
