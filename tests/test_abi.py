@@ -75,3 +75,18 @@ def test_binding_refuses_cpu_tensors(libdh):
 def test_null_plan_rejected(libdh):
     L = dh.lib()
     assert L.patch_update_fv(None, None, None, None, None, None, None, 0.0, 1.0, 1.0, 0.0, None, None) == dh.DH_EINVAL
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda P, f: P["dx"].__setitem__(f, P["dx"][f] * 2.0),       # fine patch with the coarse spacing
+    lambda P, f: P["level"].__setitem__(f, 2),                   # neighbour two levels coarser
+    lambda P, f: P["p"].__setitem__(f, 16),                      # different p across levels
+])
+def test_coupled_plan_validation_rejects(libdh, mutate):
+    """Coupled refinement levels: a coarser face neighbour must be exactly one level coarser, with
+    the same p and twice the dx (checked on the host before any device allocation)."""
+    mesh = synth.coupled_mesh(4, 8, 1.0 / 32, 1, 2, dim=3)
+    P = mesh.patches.copy()
+    mutate(P, mesh.level_ranges[1][0])
+    assert _create(P, vs=mesh.var_stride) == dh.DH_EINVAL
+    assert len(dh.lib().dh_last_error()) > 0
