@@ -3,10 +3,12 @@
 // with KO dissipation; KO normalisation sigma/(64 dx) is the r = 3 form):
 //   L(Q) = -sum_d B_d(Q) dQ/dx_d + S(Q) + sigma/(64 dx) sum_d delta6_d Q
 //   dQ/dx  = [(Q_-2 - Q_+2) + 8 (Q_+1 - Q_-1)] / (12 dx)
-//   delta6 = (Q_-3 + Q_+3 - 2Q_0) - 6 (Q_-2 + Q_+2 - 2Q_0) + 15 (Q_-1 + Q_+1 - 2Q_0)
+//   delta6 = Q_-3 - 6 Q_-2 + 15 Q_-1 - 20 Q_0 + 15 Q_+1 - 6 Q_+2 + Q_+3
 //   out = a q0 + b qs + g dt L ; acc += d dt L
-// (the bracketed delta6 form is exactly zero on constant data, so constant
-// states stay bitwise constant).
+// The three directional sixth differences are summed grouped by distance r
+// (T_r = sum_d (Q_-r + Q_+r) - 6 Q_0, with 6 Q_0 formed by the same additions),
+// which is exactly zero on constant data, so constant states stay bitwise
+// constant.
 //
 // Kernel design: a CTA owns an 8x8x4 tile of one patch (one voxel per
 // thread).  The variables are staged in groups of at most five into shared
@@ -132,16 +134,6 @@ __device__ __forceinline__ int fd_box(int x, int y, int z) { return ((z + FH) * 
 __device__ __forceinline__ double st_d1(const DevParams& P, double m2, double m1, double p1, double p2, double r12) {
   return PMUL(P, fma(8.0, PSUB(P, p1, m1), PSUB(P, m2, p2)), r12);
 }
-// Bracketed sixth difference (exactly 0 on constants).
-__device__ __forceinline__ double st_d6(const DevParams& P, double m3, double m2, double m1, double c, double p1,
-                                        double p2, double p3) {
-  const double two = PMUL(P, 2.0, c);
-  const double t3 = PSUB(P, PADD(P, m3, p3), two);
-  const double t2 = PSUB(P, PADD(P, m2, p2), two);
-  const double t1 = PSUB(P, PADD(P, m1, p1), two);
-  return fma(15.0, t1, fma(-6.0, t2, t3));
-}
-
 // Read access to one staged group: the padded box ...
 struct BoxAcc {
   const double* box;
@@ -184,16 +176,26 @@ template <int D, class Acc>
 __device__ __forceinline__ double acc_d1(const DevParams& P, const Acc& S, int v, double r12) {
   return st_d1(P, S.template nb<D>(v, -2), S.template nb<D>(v, -1), S.template nb<D>(v, 1), S.template nb<D>(v, 2), r12);
 }
+// Sum over the three directions of the sixth differences, grouped by distance:
+//   sum_d delta6_d = T3 - 6 T2 + 15 T1,   T_r = S_r - 6c,
+//   S_r = ((Q_-r + Q_+r)_x + (Q_-r + Q_+r)_y) + (Q_-r + Q_+r)_z,
+// with 6c formed as ((2c + 2c) + 2c) -- the very additions S_r performs on
+// constant data -- so every T_r is exactly 0 on constants (23 FP64 operations
+// per variable instead of 27 for three bracketed directional differences).
 template <class Acc>
 __device__ __forceinline__ double acc_ko3(const DevParams& P, const Acc& S, int v) {
   const double c = S.val(v);
-  const double dx = st_d6(P, S.template nb<0>(v, -3), S.template nb<0>(v, -2), S.template nb<0>(v, -1), c,
-                          S.template nb<0>(v, 1), S.template nb<0>(v, 2), S.template nb<0>(v, 3));
-  const double dy = st_d6(P, S.template nb<1>(v, -3), S.template nb<1>(v, -2), S.template nb<1>(v, -1), c,
-                          S.template nb<1>(v, 1), S.template nb<1>(v, 2), S.template nb<1>(v, 3));
-  const double dz = st_d6(P, S.template nb<2>(v, -3), S.template nb<2>(v, -2), S.template nb<2>(v, -1), c,
-                          S.template nb<2>(v, 1), S.template nb<2>(v, 2), S.template nb<2>(v, 3));
-  return PADD(P, PADD(P, dx, dy), dz);
+  const double two = PMUL(P, 2.0, c);
+  const double six = PADD(P, PADD(P, two, two), two);
+  double T[3];
+#pragma unroll
+  for (int r = 1; r <= 3; ++r) {
+    const double sx = PADD(P, S.template nb<0>(v, -r), S.template nb<0>(v, r));
+    const double sy = PADD(P, S.template nb<1>(v, -r), S.template nb<1>(v, r));
+    const double sz = PADD(P, S.template nb<2>(v, -r), S.template nb<2>(v, r));
+    T[r - 1] = PSUB(P, PADD(P, PADD(P, sx, sy), sz), six);
+  }
+  return fma(15.0, T[0], fma(-6.0, T[1], T[2]));
 }
 
 // ------------------------------------------------------------- staging
