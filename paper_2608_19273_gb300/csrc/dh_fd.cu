@@ -28,6 +28,7 @@
 #include <cuda.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "dh_internal.cuh"
 #include "dh_pde.cuh"
@@ -344,6 +345,38 @@ __device__ void fd_voxel_generic(const FdArgs& A, const Acc& S, int64_t e, doubl
   }
 }
 
+// The wave system written out (same operator as the generic path with
+// PdeWave's B and S): the 1/(12 dx) of the derivatives is folded into the
+// FMAs that consume them.
+//   L_phi   = Pi + KO,   L_Pi = c^2 r12 (Dx psi_x + Dy psi_y + Dz psi_z) - damp Pi + KO,
+//   L_psi_d = r12 Dd Pi + KO,   Dd q = (q_-2 - q_+2) + 8 (q_+1 - q_-1) along d.
+template <int D, class Acc>
+__device__ __forceinline__ double acc_raw(const DevParams& P, const Acc& S, int v) {
+  return fma(8.0, PSUB(P, S.template nb<D>(v, 1), S.template nb<D>(v, -1)),
+             PSUB(P, S.template nb<D>(v, -2), S.template nb<D>(v, 2)));
+}
+
+template <class Acc>
+__device__ void fd_voxel_wave(const FdArgs& A, const Acc& S, int64_t e, double dx, double& lam_thread) {
+  const DevParams& P = A.P;
+  const double r12 = 1.0 / (12.0 * dx);
+  const double ko = A.sigma / (64.0 * dx);
+  const double dt = *A.dt_dev;
+  const double gdt = A.g * dt, ddt = A.d * dt;
+  const double q[5] = {S.val(0), S.val(1), S.val(2), S.val(3), S.val(4)};
+  const double c = __ldg(A.mat + e);
+  const double div = PADD(P, PADD(P, acc_raw<0>(P, S, 2), acc_raw<1>(P, S, 3)), acc_raw<2>(P, S, 4));
+  double L[5];
+  L[0] = fma(ko, acc_ko3(P, S, 0), q[1]);
+  L[1] = fma(ko, acc_ko3(P, S, 1), fma(PMUL(P, PMUL(P, c, c), r12), div, PMUL(P, -P.damp, q[1])));
+  L[2] = fma(ko, acc_ko3(P, S, 2), PMUL(P, r12, acc_raw<0>(P, S, 1)));
+  L[3] = fma(ko, acc_ko3(P, S, 3), PMUL(P, r12, acc_raw<1>(P, S, 1)));
+  L[4] = fma(ko, acc_ko3(P, S, 4), PMUL(P, r12, acc_raw<2>(P, S, 1)));
+#pragma unroll
+  for (int v = 0; v < 5; ++v) fd_combine(A, (int64_t)v * A.vs + e, q[v], L[v], gdt, ddt);
+  if (A.lam_out) lam_thread = fmax(lam_thread, c);
+}
+
 template <class PDE, bool TMA>
 __device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* smem, uint64_t* bars, double& lam_thread) {
   static_assert(PDE::N <= GV, "generic FD path stages one group of at most five variables");
@@ -355,11 +388,13 @@ __device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* smem, 
   if (TMA) {
     if (t == 0) tma_issue(A, w, p, smem, &bars[0], 0);
     if (!tma_wait_all(A, &bars[0], 0)) return;
-    fd_voxel_generic<PDE>(A, TmaAcc{smem, lx, ly, lz}, e, pt.dx, lam_thread);
+    if constexpr (std::is_same<PDE, PdeWave>::value) fd_voxel_wave(A, TmaAcc{smem, lx, ly, lz}, e, pt.dx, lam_thread);
+    else fd_voxel_generic<PDE>(A, TmaAcc{smem, lx, ly, lz}, e, pt.dx, lam_thread);
   } else {
     fd_stage_vars(A, smem, w, p, 0, PDE::N);
     __syncthreads();
-    fd_voxel_generic<PDE>(A, BoxAcc{smem, fd_box(lx, ly, lz)}, e, pt.dx, lam_thread);
+    if constexpr (std::is_same<PDE, PdeWave>::value) fd_voxel_wave(A, BoxAcc{smem, fd_box(lx, ly, lz)}, e, pt.dx, lam_thread);
+    else fd_voxel_generic<PDE>(A, BoxAcc{smem, fd_box(lx, ly, lz)}, e, pt.dx, lam_thread);
   }
 }
 
