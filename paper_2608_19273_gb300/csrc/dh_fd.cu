@@ -401,6 +401,7 @@ __device__ void fd_tile_generic(const FdArgs& A, const FdWork& w, double* smem, 
 // ------------------------------------------------------------- GW59
 struct Gw59State {
   double al, bx, by, bz, dal0, dal1, dal2, ko_ab[4], u[11], sumPi2, bs0, bs1, bs2;
+  double alr, bxr, byr, bzr;  // alpha and beta times 1/(12 dx): the field derivatives stay unscaled
 };
 
 template <class Acc>
@@ -408,6 +409,7 @@ __device__ __forceinline__ void gw59_lapse_shift(const FdArgs& A, const Acc& S, 
                                                  Gw59State& G) {
   const DevParams& P = A.P;
   G.al = S.val(0); G.bx = S.val(1); G.by = S.val(2); G.bz = S.val(3);
+  G.alr = PMUL(P, G.al, r12); G.bxr = PMUL(P, G.bx, r12); G.byr = PMUL(P, G.by, r12); G.bzr = PMUL(P, G.bz, r12);
   G.dal0 = acc_d1<0>(P, S, 0, r12);
   G.dal1 = acc_d1<1>(P, S, 0, r12);
   G.dal2 = acc_d1<2>(P, S, 0, r12);
@@ -427,7 +429,8 @@ __device__ __forceinline__ void gw59_field(const FdArgs& A, const Acc& S, int a,
   const int64_t vs = A.vs;
   const double al = G.al, bx = G.bx, by = G.by, bz = G.bz;
   const double phi = S.val(0), Pi = S.val(1), px = S.val(2), py = S.val(3), pz = S.val(4);
-  const double dPi0 = acc_d1<0>(P, S, 1, r12), dPi1 = acc_d1<1>(P, S, 1, r12), dPi2 = acc_d1<2>(P, S, 1, r12);
+  // unscaled derivatives (the 1/(12 dx) sits in alr, bxr, byr, bzr)
+  const double dPi0 = acc_raw<0>(P, S, 1), dPi1 = acc_raw<1>(P, S, 1), dPi2 = acc_raw<2>(P, S, 1);
   // coupling sum_b C_ab phi_b Pi_b
   double cs = PMUL(P, P.C[11 * a], G.u[0]);
 #pragma unroll
@@ -435,14 +438,15 @@ __device__ __forceinline__ void gw59_field(const FdArgs& A, const Acc& S, int a,
   // phi: alpha Pi + beta . psi
   const double Lphi = fma(al, Pi, fma(bx, px, fma(by, py, PMUL(P, bz, pz))));
   // Pi: alpha div psi + beta . grad Pi + alpha cs
-  const double dpx0 = acc_d1<0>(P, S, 2, r12), dpx1 = acc_d1<1>(P, S, 2, r12), dpx2 = acc_d1<2>(P, S, 2, r12);
-  const double dpy0 = acc_d1<0>(P, S, 3, r12), dpy1 = acc_d1<1>(P, S, 3, r12), dpy2 = acc_d1<2>(P, S, 3, r12);
-  const double dpz0 = acc_d1<0>(P, S, 4, r12), dpz1 = acc_d1<1>(P, S, 4, r12), dpz2 = acc_d1<2>(P, S, 4, r12);
-  const double LPi = fma(al, PADD(P, PADD(P, dpx0, dpy1), dpz2), fma(bx, dPi0, fma(by, dPi1, fma(bz, dPi2, PMUL(P, al, cs)))));
+  const double dpx0 = acc_raw<0>(P, S, 2), dpx1 = acc_raw<1>(P, S, 2), dpx2 = acc_raw<2>(P, S, 2);
+  const double dpy0 = acc_raw<0>(P, S, 3), dpy1 = acc_raw<1>(P, S, 3), dpy2 = acc_raw<2>(P, S, 3);
+  const double dpz0 = acc_raw<0>(P, S, 4), dpz1 = acc_raw<1>(P, S, 4), dpz2 = acc_raw<2>(P, S, 4);
+  const double alr = G.alr, bxr = G.bxr, byr = G.byr, bzr = G.bzr;
+  const double LPi = fma(alr, PADD(P, PADD(P, dpx0, dpy1), dpz2), fma(bxr, dPi0, fma(byr, dPi1, fma(bzr, dPi2, PMUL(P, al, cs)))));
   // psi_i: alpha d_i Pi + Pi d_i alpha + beta . grad psi_i
-  const double Lpx = fma(al, dPi0, fma(Pi, G.dal0, fma(bx, dpx0, fma(by, dpx1, PMUL(P, bz, dpx2)))));
-  const double Lpy = fma(al, dPi1, fma(Pi, G.dal1, fma(bx, dpy0, fma(by, dpy1, PMUL(P, bz, dpy2)))));
-  const double Lpz = fma(al, dPi2, fma(Pi, G.dal2, fma(bx, dpz0, fma(by, dpz1, PMUL(P, bz, dpz2)))));
+  const double Lpx = fma(alr, dPi0, fma(Pi, G.dal0, fma(bxr, dpx0, fma(byr, dpx1, PMUL(P, bzr, dpx2)))));
+  const double Lpy = fma(alr, dPi1, fma(Pi, G.dal1, fma(bxr, dpy0, fma(byr, dpy1, PMUL(P, bzr, dpy2)))));
+  const double Lpz = fma(alr, dPi2, fma(Pi, G.dal2, fma(bxr, dpz0, fma(byr, dpz1, PMUL(P, bzr, dpz2)))));
   G.sumPi2 = fma(Pi, Pi, G.sumPi2);
   G.bs0 = fma(px, Pi, G.bs0);
   G.bs1 = fma(py, Pi, G.bs1);
