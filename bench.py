@@ -377,8 +377,9 @@ def con2prim_compare(torch, dh, stream):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
+        hist = torch.bincount(it.long().clamp(0, 101)).cpu().tolist()
         return prim, {"ns_per_voxel": ms * 1e6 / mesh.nvox, "iters_mean": float(it.double().mean().item()),
-                      "fails": int(fails.item()) // reps}
+                      "iters_hist": [[k, c] for k, c in enumerate(hist) if c], "fails": int(fails.item()) // reps}
 
     with torch.cuda.stream(stream):
         # cold: i.i.d. primitives (rho, p log-uniform on [0.1, 10], W uniform on [1, 10])

@@ -329,7 +329,9 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  *                  TMA tensor copies (2 candidates, or 6 with TMA -- 4 for
  *                  GW59; TMA only when every level is a run of back-to-back
  *                  patches, see dh_plan_set_variant).
- * `out` is overwritten.  If cache_path is not NULL the choice is first looked up
+ * `out` is overwritten.  If cache_path is NULL the environment variable
+ * DH_TUNE_CACHE names the cache file (no cache when it is unset).  With a cache
+ * file the choice is first looked up
  * there (one JSON object per line, keyed by GPU name, PDE, scheme and patch-size
  * histogram) and, when timed, appended to it.  choice_out (optional, 4 ints):
  * fv_var, fv_zs, fd_var, 1 if taken from the cache.  times_out (optional, 8

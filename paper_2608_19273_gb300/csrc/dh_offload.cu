@@ -16,6 +16,8 @@
 //   dh_offload_run : gather (all nq quantities of every interior voxel) ->
 //     n_steps Runge-Kutta steps on the device arena -> scatter of the first
 //     nq_back quantities, all asynchronous on one stream.
+#include <nvtx3/nvToolsExt.h>
+
 #include "dh_internal.cuh"
 
 using namespace dh;
@@ -67,7 +69,9 @@ dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_st
   cudaStream_t s = (cudaStream_t)stream;
   const int nq = plan->offload_nq, h = plan->offload_halo;
   double* mat = plan->nm > 0 ? arena + (int64_t)plan->nq * plan->var_stride : nullptr;
+  nvtxRangePushA("dh offload gather");
   dh_status st = aoas_move(plan, true, plan->d_offload, nq, 0, nq, h, arena, s);
+  nvtxRangePop();
   if (st != DH_OK) return st;
   if (n_steps > 0 && cfl > 0 && plan->pde != DH_PDE_SRHD3D) {
     // the first step's dt needs the wave speed of the gathered state
@@ -78,7 +82,9 @@ dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_st
     st = dh_rk_step(plan, scheme, rk, arena, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, stream);
     if (st != DH_OK) return st;
   }
+  nvtxRangePushA("dh offload scatter");
   if (nq_back > 0) st = aoas_move(plan, false, plan->d_offload, nq, 0, nq_back, h, arena, s);
+  nvtxRangePop();
   return st;
 }
 

@@ -11,6 +11,8 @@
 // without any host round trip.
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dh_internal.cuh"
 
 namespace dh {
@@ -59,6 +61,11 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
                     nullptr, nullptr, plan->c2p_fail, s));
     lam = nullptr;
   }
+  // NVTX range per stage (host-side marker for profilers; a no-op without one attached)
+  struct Range {
+    explicit Range(const char* n) { nvtxRangePushA(n); }
+    ~Range() { nvtxRangePop(); }
+  } range(scheme == 0 ? "dh FV stage" : (scheme == 2 ? "dh FV2 stage" : "dh FD stage"));
   DH_TRY(T.begin());
   if (scheme == 0 && wc && wc->on) {
     const int j = wc->next++;

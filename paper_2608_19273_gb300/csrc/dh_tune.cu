@@ -11,6 +11,7 @@
 //             with TMA staging of one group (systems of <= 5 variables) also
 //             caps for 3 and 4 CTAs per SM
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -83,6 +84,7 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
   if (scheme != 0 && scheme != 1) { set_error("dh_autotune: scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
   if (!qs || !out || !dt_dev || reps < 1 || reps > 1000) { set_error("dh_autotune: bad arguments"); return DH_EINVAL; }
   const std::string key = tune_key(plan, scheme);
+  if (!cache_path) cache_path = std::getenv("DH_TUNE_CACHE");  // NULL and unset: no cache
   int v = 0, z = 0, f = 0;
   if (cache_path && cache_lookup(cache_path, key, &v, &z, &f)) {
     dh_status st = dh_plan_set_variant(plan, v, z, f);
