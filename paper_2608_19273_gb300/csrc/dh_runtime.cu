@@ -28,7 +28,8 @@ struct WChain {
 };
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
-                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc = nullptr);
+                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc = nullptr,
+                            bool prims_current = false);
 
 struct Timer {
   dh_plan* plan;
@@ -53,12 +54,15 @@ struct Timer {
 // One stage launch, timed (when timing is on) around the stage kernel only.
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
-                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc) {
+                            double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc,
+                            bool prims_current) {
   if (plan->pde == DH_PDE_SRHD3D) {
-    // primitives of the stage input, seeded by the previous primitives (in place)
+    // primitives of the stage input, seeded by the previous primitives (in place), unless
+    // they were just recovered from this very input (the step start's wave speed)
     double* prim = const_cast<double*>(mat);
-    DH_TRY(con2prim(plan, qs, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol, plan->c2p_max_iter,
-                    nullptr, nullptr, plan->c2p_fail, s));
+    if (!prims_current)
+      DH_TRY(con2prim(plan, qs, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol, plan->c2p_max_iter,
+                      nullptr, nullptr, plan->c2p_fail, s));
     lam = nullptr;
   }
   // NVTX range per stage (host-side marker for profilers; a no-op without one attached)
@@ -84,6 +88,9 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
                          cudaStream_t s, WChain* wc = nullptr) {
   const size_t bytes = sizeof(double) * (size_t)plan->nq * (size_t)plan->var_stride;
   double* lam_last = cfl > 0 ? lam : nullptr;
+  // SRHD: with a CFL step the primitives of q are recovered here for the wave speed and
+  // then serve the first stage as well
+  const bool srhd_cur = cfl > 0 && plan->pde == DH_PDE_SRHD3D;
   if (cfl > 0 && plan->pde == DH_PDE_SRHD3D) {
     // the wave speed needs the primitives of q: recover them, then take the maximum
     double* prim = const_cast<double*>(mat);
@@ -93,16 +100,18 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
   }
   if (cfl > 0) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
   if (rk == 1) {
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s));
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s, nullptr,
+                      srhd_cur));
     DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
   } else if (rk == 3) {
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc));
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc, srhd_cur));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, T, s, wc));
     DH_TRY(stage_call(plan, scheme, u2, q, q, nullptr, mat, dt, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, sigma, lam_last,
                       T, s, wc));
   } else if (rk == 4) {
     DH_TRY(cuda_error(cudaMemcpyAsync(acc, q, bytes, cudaMemcpyDeviceToDevice, s), "copy q -> acc"));
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 0.5, 1.0 / 6.0, sigma, nullptr, T, s));
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 0.5, 1.0 / 6.0, sigma, nullptr, T, s, nullptr,
+                      srhd_cur));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 1, 0, 0.5, 1.0 / 3.0, sigma, nullptr, T, s));
     DH_TRY(stage_call(plan, scheme, u2, q, u1, acc, mat, dt, 1, 0, 1.0, 1.0 / 3.0, sigma, nullptr, T, s));
     DH_TRY(stage_call(plan, scheme, u1, nullptr, nullptr, acc, mat, dt, 0, 0, 0, 1.0 / 6.0, sigma, lam_last, T, s));
@@ -213,7 +222,7 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
       cpl += plan->amr_restrict_off[l + 1] > plan->amr_restrict_off[l];
   }
   const int cpl_lam = plan->coupled && scheme == 0 && cfl > 0 && !srhd;
-  plan->graph_kernels = n_steps * (nst * (1 + srhd + cpl) + (cfl > 0 ? 1 + 2 * srhd + cpl_lam : 0));
+  plan->graph_kernels = n_steps * (nst * (1 + srhd + cpl) + (cfl > 0 ? 1 + srhd + cpl_lam : 0));
   return DH_OK;
 }
 
