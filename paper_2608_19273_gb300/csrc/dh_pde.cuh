@@ -44,6 +44,16 @@ __device__ __forceinline__ double recip_nr(double a) {
   return fma(y, e, y);
 }
 
+// sqrt(x) as x * rsqrt(x) for finite x > 0 (CUDA's rsqrt, within about an ulp;
+// the product adds one rounding: a couple of ulps against the correctly
+// rounded sqrt, which the stage kernels' 1e-12 tolerance absorbs); zero,
+// negative, infinite and NaN arguments take sqrt itself.  The bit tests run on
+// the integer pipe.
+__device__ __forceinline__ double sqrt_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  return (b > 0 && b < 0x7ff0000000000000ll) ? x * rsqrt(x) : sqrt(x);
+}
+
 // max(a, b) for a, b >= +0 (characteristic speeds): non-negative doubles order
 // like their bit patterns read as signed 64-bit integers, so the comparison
 // runs on the integer pipe instead of the FP64 pipe.
@@ -103,7 +113,7 @@ struct PdeEuler {
     }
     const double p = MUL(P, P.gm1, fma(-0.5, kin, q[DIM + 1]));
     w[DIM] = p;
-    w[DIM + 1] = sqrt(MUL(P, MUL(P, P.gamma, p), r));
+    w[DIM + 1] = sqrt_pos(MUL(P, MUL(P, P.gamma, p), r));
     w[DIM + 2] = ADD(P, q[DIM + 1], p);
   }
   __device__ static void flux(int d, const double* q, const double* w, const DevParams& P, double* F) {
@@ -156,7 +166,7 @@ struct PdeSRHD {
     const double v = sel3(d, w[0], w[1], w[2]), cs2 = w[4], v2 = w[5];
     const double omc = SUB(P, P.one, cs2);
     const double disc = MUL(P, MUL(P, cs2, SUB(P, P.one, v2)), fma(-MUL(P, v, v), omc, fma(-v2, cs2, P.one)));
-    return MUL(P, fma(fabs(v), omc, sqrt(disc)), w[6]);
+    return MUL(P, fma(fabs(v), omc, sqrt_pos(disc)), w[6]);
   }
   __device__ static void ncp(int, const double*, const double*, const DevParams&, double*) {}
   __device__ static void source(const double*, const double*, const DevParams&, double*) {}
