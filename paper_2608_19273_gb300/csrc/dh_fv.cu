@@ -107,6 +107,25 @@ __device__ __forceinline__ void derive(const FvArgs& A, int64_t e, const double*
   }
 }
 
+// F_x and F_y of one voxel (F_z already formed in 3D): systems with a symmetric
+// flux share its off-diagonal products between directions.
+template <class PDE>
+__device__ __forceinline__ void flux_xy(const double* q, const double* W, const double* Fz, const DevParams& P,
+                                        double* Fx, double* Fy) {
+  if constexpr (PDE::SYM) {
+    PDE::flux_xy(q, W, Fz, P, Fx, Fy);
+  } else {
+    PDE::flux(0, q, W, P, Fx);
+    PDE::flux(1, q, W, P, Fy);
+  }
+}
+
+// Systems whose derived quantities are many (SRHD: eight) form all three
+// speeds of a voxel where its z flux is formed, so that only the two in-plane
+// speeds, not the speed factors, stay live across the plane's barrier.
+template <class PDE>
+constexpr bool speeds_with_z() { return PDE::NW >= 8; }
+
 template <class PDE, int TX, int TY, int G, bool EARLY, int WM>
 struct FvTile {
   static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW, DIM = PDE::DIM;
@@ -118,6 +137,10 @@ struct FvTile {
   static constexpr int FXG = (TX + 1) * TY, FYG = TX * (TY + 1);
   static constexpr int FX = G * FXG, FY = G * FYG;
   static constexpr int NF = PDE::NCP ? 2 : 1;
+  // first thread of the +x/+y boundary faces: with one column per CTA the halo
+  // ring occupies warps 0 and 1, so the faces go to warp 2 (another SM
+  // sub-partition: the extra FP64 work of a plane is spread over three of them)
+  static constexpr int FT0 = (NR <= 64 && NT >= 96) ? 64 : 0;
   static constexpr size_t SMEM = sizeof(double) * ((size_t)NV * NS + 2 * (size_t)N * NS + 2 * NS +
                                                    (size_t)NF * N * (FX + FY));
   static_assert(NT == 256, "tile classes use 256 threads");
@@ -237,20 +260,18 @@ struct FvTile {
       double Wk[NW > 0 ? NW : 1], F[N];
       load_q<PDE>(A, off + ((int64_t)z0 * p + y) * p + x, Qk);
       derive<PDE, WM>(A, off + ((int64_t)z0 * p + y) * p + x, Qk, Wk);
+      if (DIM == 3 && PDE::FLUX) PDE::flux(2, Qk, Wk, A.P, Fzk);
       if (PDE::FLUX) {
-        PDE::flux(0, Qk, Wk, A.P, F);
+        double F2[N];
+        flux_xy<PDE>(Qk, Wk, Fzk, A.P, F, F2);
 #pragma unroll
-        for (int v = 0; v < N; ++v) S.Fx[v * NS + me] = F[v];
-        PDE::flux(1, Qk, Wk, A.P, F);
-#pragma unroll
-        for (int v = 0; v < N; ++v) S.Fy[v * NS + me] = F[v];
+        for (int v = 0; v < N; ++v) { S.Fx[v * NS + me] = F[v]; S.Fy[v * NS + me] = F2[v]; }
       }
       S.Lx[me] = PDE::speed(0, Qk, Wk, A.P);
       S.Ly[me] = PDE::speed(1, Qk, Wk, A.P);
 #pragma unroll
       for (int v = 0; v < NV; ++v) S.Q[v * NS + me] = Qk[v];
       if (DIM == 3) {
-        if (PDE::FLUX) PDE::flux(2, Qk, Wk, A.P, Fzk);
         Lzk = PDE::speed(2, Qk, Wk, A.P);
         // plane -1 from the -z neighbour
         double Qm[NV], Wm[NW > 0 ? NW : 1], Fzm[N];
@@ -284,20 +305,20 @@ struct FvTile {
         face(S, A.P, 0, buf ? xm1 : xm0, me, S.Hx, S.Dx, fxl, FX);
         face(S, A.P, 1, buf ? ym1 : ym0, me, S.Hy, S.Dy, fyl, FY);
       }
-      if (tid < HALF) {
+      if (tid >= FT0 && tid < FT0 + HALF) {
         // +x and +y boundary faces of the column: one call with a run-time
         // direction so that a warp holding both kinds does not diverge
-        const int gg = tid / RG, j = tid % RG;
+        const int ft = tid - FT0, gg = ft / RG, j = ft % RG;
         if (w.patch[gg] >= 0) {
           const bool isx = j < TY;
           const int Ls = isx ? gg * TX * TY + j * TX + (TX - 1) : gg * TX * TY + (TY - 1) * TX + (j - TY);
           const int fidx = isx ? gg * FXG + j * (TX + 1) + TX : gg * FYG + TY * TX + (j - TY);
-          face(S, A.P, isx ? 0 : 1, Ls, NT + buf * NR + tid, isx ? S.Hx : S.Hy, isx ? S.Dx : S.Dy, fidx,
+          face(S, A.P, isx ? 0 : 1, Ls, NT + buf * NR + ft, isx ? S.Hx : S.Hy, isx ? S.Dx : S.Dy, fidx,
                isx ? FX : FY);
         }
       }
       // ---- next plane's own voxel (3D): derived quantities, z flux, z face
-      double Qn[NV], Wn[NW > 0 ? NW : 1], Fzn[N], Lzn = 0.0, Hzhi[N], Dzhi[N];
+      double Qn[NV], Wn[NW > 0 ? NW : 1], Fzn[N], Lzn = 0.0, Lxn = 0.0, Lyn = 0.0, Hzhi[N], Dzhi[N];
 #pragma unroll
       for (int v = 0; v < N; ++v) { Hzhi[v] = 0.0; Dzhi[v] = 0.0; Fzn[v] = 0.0; }
       if (DIM == 3 && act) {
@@ -306,6 +327,10 @@ struct FvTile {
         derive<PDE, WM>(A, en, Qn, Wn);
         if (PDE::FLUX) PDE::flux(2, Qn, Wn, A.P, Fzn);
         Lzn = PDE::speed(2, Qn, Wn, A.P);
+        if (speeds_with_z<PDE>()) {
+          Lxn = PDE::speed(0, Qn, Wn, A.P);
+          Lyn = PDE::speed(1, Qn, Wn, A.P);
+        }
         const double s = max_nn(Lzk, Lzn);
         double dq[N];
 #pragma unroll
@@ -377,17 +402,14 @@ struct FvTile {
       // ---- publish plane kz+1 (3D)
       if (DIM == 3 && kz + 1 < pz) {
         if (act) {
-          double F[N];
           if (PDE::FLUX) {
-            PDE::flux(0, Qn, Wn, A.P, F);
+            double F[N], F2[N];
+            flux_xy<PDE>(Qn, Wn, Fzn, A.P, F, F2);
 #pragma unroll
-            for (int v = 0; v < N; ++v) S.Fx[v * NS + me] = F[v];
-            PDE::flux(1, Qn, Wn, A.P, F);
-#pragma unroll
-            for (int v = 0; v < N; ++v) S.Fy[v * NS + me] = F[v];
+            for (int v = 0; v < N; ++v) { S.Fx[v * NS + me] = F[v]; S.Fy[v * NS + me] = F2[v]; }
           }
-          S.Lx[me] = PDE::speed(0, Qn, Wn, A.P);
-          S.Ly[me] = PDE::speed(1, Qn, Wn, A.P);
+          S.Lx[me] = speeds_with_z<PDE>() ? Lxn : PDE::speed(0, Qn, Wn, A.P);
+          S.Ly[me] = speeds_with_z<PDE>() ? Lyn : PDE::speed(1, Qn, Wn, A.P);
 #pragma unroll
           for (int v = 0; v < NV; ++v) { S.Q[v * NS + me] = Qn[v]; Qk[v] = Qn[v]; }
 #pragma unroll

@@ -29,19 +29,19 @@ __device__ __forceinline__ double SUB(const DevParams& P, double a, double b) { 
 __device__ __forceinline__ double MUL(const DevParams& P, double a, double b) { return fma(a, b, P.zero); }
 
 // 1/a for a normal, finite, positive or negative a: the hardware reciprocal
-// estimate (PTX rcp.approx.ftz.f64) refined by two Newton-Raphson steps for
-// f(y) = 1/y - a, y <- y + y (1 - a y), each of which squares the relative
-// error (quadratic convergence; Newton's method as used for floating-point
-// reciprocals by Markstein, IBM J. Res. Dev. 34, 1990).  Four FMAs instead of
-// a full IEEE division; the result is within one unit in the last place of
-// the correctly rounded reciprocal (checked against 1.0/a by the GPU tests).
+// estimate y (PTX rcp.approx.ftz.f64, relative error below 2^-19.9 over 2^28
+// sampled mantissas and exponents on GB300) refined by one step of the
+// third-order (Householder, order 2) iteration for f(y) = 1/y - a:
+// with e = 1 - a y, 1/a = y / (1 - e) = y (1 + e + e^2 + e^3 + ...), and
+// y (1 + e + e^2) leaves a relative error of e^3 < 2^-59.  Three FMAs instead of
+// a full IEEE division (about 5.7 FMA times); the result is within one unit
+// in the last place of the correctly rounded reciprocal (checked against 1.0/a
+// by the GPU tests).
 __device__ __forceinline__ double recip_nr(double a) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(a));
-  double e = fma(-a, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-a, y, 1.0);
-  return fma(y, e, y);
+  const double e = fma(-a, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // sqrt(x) as x * rsqrt(x) for finite x > 0 (CUDA's rsqrt, within about an ulp;
@@ -66,7 +66,7 @@ __device__ __forceinline__ double max_nn(double a, double b) {
 // dq/dt + div(a q) = 0 with material velocity a (M = 3).  F_d = a_d q, lambda_d = |a_d|.
 struct PdeAdvFlux {
   static constexpr int N = 1, M = 3, NW = 1, DIM = 3;
-  static constexpr bool FLUX = true, NCP = false, SRC = false;
+  static constexpr bool FLUX = true, NCP = false, SRC = false, SYM = false;
   __device__ static void prims(const double*, const DevParams&, double*) {}
   __device__ static void flux(int d, const double* q, const double*, const DevParams& P, double* F) {
     F[0] = MUL(P, sel3(d, q[1], q[2], q[3]), q[0]);
@@ -81,7 +81,7 @@ struct PdeAdvFlux {
 // dq/dt + a . grad q = 0 (non-conservative form, F = 0): B_d = a_d.
 struct PdeAdvNcp {
   static constexpr int N = 1, M = 3, NW = 1, DIM = 3;
-  static constexpr bool FLUX = false, NCP = true, SRC = false;
+  static constexpr bool FLUX = false, NCP = true, SRC = false, SYM = false;
   __device__ static constexpr bool needs_grad(int, int v) { return v == 0; }
   __device__ static void prims(const double*, const DevParams&, double*) {}
   __device__ static void flux(int, const double*, const double*, const DevParams&, double*) {}
@@ -101,7 +101,7 @@ struct PdeAdvNcp {
 template <int D_>
 struct PdeEuler {
   static constexpr int DIM = D_, N = D_ + 2, M = 0, NW = D_ + 3;
-  static constexpr bool FLUX = true, NCP = false, SRC = false;
+  static constexpr bool FLUX = true, NCP = false, SRC = false, SYM = true;
   __device__ static void prims(const double* q, const DevParams& P, double* w) {
     const double r = recip_nr(q[0]);
     w[0] = MUL(P, q[1], r);
@@ -116,13 +116,35 @@ struct PdeEuler {
     w[DIM + 1] = sqrt_pos(MUL(P, MUL(P, P.gamma, p), r));
     w[DIM + 2] = ADD(P, q[DIM + 1], p);
   }
+  // The momentum flux rho u_k u_d is symmetric in (k, d); every direction forms
+  // it as m_min(k,d) u_max(k,d), so the x, y and z fluxes of one voxel share
+  // their off-diagonal products bit for bit (flux_xy).
   __device__ static void flux(int d, const double* q, const double* w, const DevParams& P, double* F) {
     const double u = (DIM == 3) ? sel3(d, w[0], w[1], w[DIM == 3 ? 2 : 0]) : (d == 0 ? w[0] : w[1]);
     const double p = w[DIM];
     F[0] = (DIM == 3) ? sel3(d, q[1], q[2], q[DIM == 3 ? 3 : 1]) : (d == 0 ? q[1] : q[2]);
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) F[1 + k] = fma(q[1 + k], u, d == k ? p : P.zero);
+    for (int k = 0; k < DIM; ++k)
+      F[1 + k] = fma(k < d ? q[1 + k] : F[0], k < d ? u : w[k], d == k ? p : P.zero);
     F[DIM + 1] = MUL(P, w[DIM + 2], u);
+  }
+  // F_x and F_y of a voxel whose F_z (3D) is already formed: the same values as
+  // flux(0) and flux(1), with the products m_x u_y, m_x u_z, m_y u_z formed once.
+  __device__ static void flux_xy(const double* q, const double* w, const double* Fz, const DevParams& P, double* Fx,
+                                 double* Fy) {
+    const double p = w[DIM], cxy = MUL(P, q[1], w[1]);
+    Fx[0] = q[1];
+    Fx[1] = fma(q[1], w[0], p);
+    Fx[2] = cxy;
+    Fy[0] = q[2];
+    Fy[1] = cxy;
+    Fy[2] = fma(q[2], w[1], p);
+    if (DIM == 3) {
+      Fx[DIM == 3 ? 3 : 0] = Fz[1];
+      Fy[DIM == 3 ? 3 : 0] = Fz[2];
+    }
+    Fx[DIM + 1] = MUL(P, w[DIM + 2], w[0]);
+    Fy[DIM + 1] = MUL(P, w[DIM + 2], w[1]);
   }
   __device__ static double speed(int d, const double*, const double* w, const DevParams& P) {
     const double u = (DIM == 3) ? sel3(d, w[0], w[1], w[DIM == 3 ? 2 : 0]) : (d == 0 ? w[0] : w[1]);
@@ -138,35 +160,54 @@ using PdeEuler3 = PdeEuler<3>;
 // ---------------------------------------------------------------- SRHD
 // Special-relativistic hydrodynamics, Q = (D, S_x, S_y, S_z, tau), ideal gas Gamma.
 // The material slots carry the primitives (rho, v_x, v_y, v_z, p) recovered by
-// con2prim.  W = (v_x, v_y, v_z, p, cs^2, v^2, 1/(1 - v^2 cs^2)).
+// con2prim.  W = (v_x, v_y, v_z, p, 1 - cs^2, cs^2 (1 - v^2), 1 - v^2 cs^2,
+// 1/(1 - v^2 cs^2)): the direction-independent factors of the speeds.
 //   F_d = (D v_d, S v_d + p e_d, S_d - D v_d)
 //   lambda_pm = [v_d (1 - cs^2) +- cs sqrt((1 - v^2)(1 - v^2 cs^2 - v_d^2 (1 - cs^2)))] / (1 - v^2 cs^2)
 //   max(|lambda_+|, |lambda_-|) = (|v_d| (1 - cs^2) + sqrt(cs^2 (1 - v^2)(...))) / (1 - v^2 cs^2)
 // (cs is folded under the square root: one square root per direction, none per voxel).
 struct PdeSRHD {
-  static constexpr int N = 5, M = 5, NW = 7, DIM = 3;
-  static constexpr bool FLUX = true, NCP = false, SRC = false;
+  static constexpr int N = 5, M = 5, NW = 8, DIM = 3;
+  static constexpr bool FLUX = true, NCP = false, SRC = false, SYM = true;
   __device__ static void prims(const double* q, const DevParams& P, double* w) {
     const double rho = q[5], vx = q[6], vy = q[7], vz = q[8], p = q[9];
     const double v2 = fma(vx, vx, fma(vy, vy, MUL(P, vz, vz)));
     const double rhoh = fma(P.Gq, p, rho);
     const double cs2 = MUL(P, MUL(P, P.Gamma, p), recip_nr(rhoh));
-    w[0] = vx; w[1] = vy; w[2] = vz; w[3] = p; w[4] = cs2; w[5] = v2;
-    w[6] = recip_nr(fma(-v2, cs2, P.one));
+    const double c0 = fma(-v2, cs2, P.one);
+    w[0] = vx; w[1] = vy; w[2] = vz; w[3] = p;
+    w[4] = SUB(P, P.one, cs2);
+    w[5] = MUL(P, cs2, SUB(P, P.one, v2));
+    w[6] = c0;
+    w[7] = recip_nr(c0);
   }
+  // S_k v_d = rho h W^2 v_k v_d is symmetric in (k, d); every direction forms
+  // it as S_min(k,d) v_max(k,d) (shared products, flux_xy).
   __device__ static void flux(int d, const double* q, const double* w, const DevParams& P, double* F) {
-    const double v = sel3(d, w[0], w[1], w[2]), p = w[3];
+    const double v = sel3(d, w[0], w[1], w[2]), p = w[3], Sd = sel3(d, q[1], q[2], q[3]);
     F[0] = MUL(P, q[0], v);
-    F[1] = fma(q[1], v, d == 0 ? p : P.zero);
-    F[2] = fma(q[2], v, d == 1 ? p : P.zero);
-    F[3] = fma(q[3], v, d == 2 ? p : P.zero);
-    F[4] = fma(-q[0], v, sel3(d, q[1], q[2], q[3]));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F[1 + k] = fma(k < d ? q[1 + k] : Sd, k < d ? v : w[k], d == k ? p : P.zero);
+    F[4] = fma(-q[0], v, Sd);
+  }
+  __device__ static void flux_xy(const double* q, const double* w, const double* Fz, const DevParams& P, double* Fx,
+                                 double* Fy) {
+    const double p = w[3], cxy = MUL(P, q[1], w[1]);
+    Fx[0] = MUL(P, q[0], w[0]);
+    Fx[1] = fma(q[1], w[0], p);
+    Fx[2] = cxy;
+    Fx[3] = Fz[1];
+    Fx[4] = fma(-q[0], w[0], q[1]);
+    Fy[0] = MUL(P, q[0], w[1]);
+    Fy[1] = cxy;
+    Fy[2] = fma(q[2], w[1], p);
+    Fy[3] = Fz[2];
+    Fy[4] = fma(-q[0], w[1], q[2]);
   }
   __device__ static double speed(int d, const double*, const double* w, const DevParams& P) {
-    const double v = sel3(d, w[0], w[1], w[2]), cs2 = w[4], v2 = w[5];
-    const double omc = SUB(P, P.one, cs2);
-    const double disc = MUL(P, MUL(P, cs2, SUB(P, P.one, v2)), fma(-MUL(P, v, v), omc, fma(-v2, cs2, P.one)));
-    return MUL(P, fma(fabs(v), omc, sqrt_pos(disc)), w[6]);
+    const double v = sel3(d, w[0], w[1], w[2]), omc = w[4];
+    const double disc = MUL(P, w[5], fma(-MUL(P, v, v), omc, w[6]));
+    return MUL(P, fma(fabs(v), omc, sqrt_pos(disc)), w[7]);
   }
   __device__ static void ncp(int, const double*, const double*, const DevParams&, double*) {}
   __device__ static void source(const double*, const double*, const DevParams&, double*) {}
@@ -179,7 +220,7 @@ struct PdeSRHD {
 // S = (Pi, -gamma Pi, 0, 0, 0).  Material: c (M = 1).  lambda_d = c.
 struct PdeWave {
   static constexpr int N = 5, M = 1, NW = 1, DIM = 3;
-  static constexpr bool FLUX = false, NCP = true, SRC = true;
+  static constexpr bool FLUX = false, NCP = true, SRC = true, SYM = false;
   __device__ static constexpr bool needs_grad(int d, int v) { return v == 1 || v == 2 + d; }
   __device__ static void prims(const double*, const DevParams&, double*) {}
   __device__ static void flux(int, const double*, const double*, const DevParams&, double*) {}
@@ -211,7 +252,7 @@ struct PdeWave {
 // alpha at 55, beta at 56..58.  lambda_d = alpha + |beta^d|.
 struct PdeGW59 {
   static constexpr int N = 59, M = 0, NW = 1, DIM = 3;
-  static constexpr bool FLUX = false, NCP = true, SRC = true;
+  static constexpr bool FLUX = false, NCP = true, SRC = true, SYM = false;
   __device__ static void prims(const double*, const DevParams&, double*) {}
   __device__ static double speed(int d, const double* q, const double*, const DevParams&) {
     return q[55] + fabs(sel3(d, q[56], q[57], q[58]));

@@ -24,8 +24,8 @@ namespace dh {
 // Returns iterations used (> 0) on convergence, -iterations on failure.
 // Adds and products are issued as FMAs with the run-time constants one/mone/zero
 // (GB300 runs DFMA faster than DADD/DMUL; results are bitwise the same).  The
-// two reciprocals per iteration are Newton-Raphson refined hardware estimates
-// (recip_nr, <= 1 ulp from the IEEE quotient): the iteration converges to the
+// two reciprocals per iteration are refined hardware estimates (recip_nr, one
+// third-order step, <= 1 ulp from the IEEE quotient): the iteration converges to the
 // same root, and the stopping test still compares successive iterates.
 __device__ int srhd_newton_dev(double G, double D, double S2, double E, double p_lo, double p0, double tol,
                                int max_iter, double one, double mone, double zero, double* p_out) {

@@ -147,7 +147,7 @@ def test_single_self_periodic_patch(orc, p):
 
 
 def test_newton_reciprocal_within_one_ulp():
-    """The kernels' reciprocal (hardware estimate + two Newton-Raphson steps) against IEEE 1.0/x."""
+    """The kernels' reciprocal (hardware estimate + one third-order refinement step) against IEEE 1.0/x."""
     torch = require_cuda()
     rng = np.random.default_rng(17)
     x = np.concatenate([np.exp(rng.uniform(-30, 30, 400000)), -np.exp(rng.uniform(-30, 30, 100000)),
