@@ -535,7 +535,8 @@ def our_arm(args, rank, world, local_rank):
             del d_h
         U1 = torch.empty_like(Q)
         U2 = torch.empty_like(Q) if spec["rk"] >= 3 else None
-        ACC = torch.empty_like(Q) if spec["rk"] == 4 else None
+        # RK4 accumulator; for SSP-RK3 FV steps the raw face-flux sums of the stage-sum form
+        ACC = torch.empty_like(Q) if spec["rk"] == 4 or (spec["rk"] == 3 and spec["scheme"] == 0) else None
         lam = torch.zeros(1, dtype=torch.float64, device="cuda")
         dt = torch.zeros(1, dtype=torch.float64, device="cuda")
         Q_init = Q.clone()

@@ -4,6 +4,15 @@
 // product as the readings of the unspecified face flux):
 //   L(Q)_i = -(1/dx) sum_d [F^_{i+1/2} - F^_{i-1/2} + (D_{i+1/2} + D_{i-1/2})/2] + S(Q_i)
 //   out = a q0 + b qs + g dt L ; acc += d dt L
+// or, for the three stages of SSP-RK3 (Shu-Osher) written in its Butcher form
+// u1 = u0 + dt L0, u2 = u0 + dt/4 (L0 + L1), u3 = u0 + dt/6 (L0 + L1) + 2 dt/3 L2
+// (the same scheme; "stage-sum form"), with acc holding the raw face-flux sum R
+// of the earlier stages (R = s0, then s0 + s1; L = -s/(2 dx) for the systems
+// without a source term):
+//   stage 1: out = qs + g dt L,             R  = s
+//   stage 2: out = q0 + g dt (-(R + s)/(2 dx)), R = R + s      (g = 1/4)
+//   stage 3: out = q0 + d dt (-R/(2 dx)) + g dt L              (d = 1/6, g = 2/3)
+// i.e. one or two FP64 operations per quantity and stage instead of up to three.
 //
 // Kernel design (GB300: the FP64 pipe, ~2 FMA/clk/SM, is the bottleneck, so
 // every FP64 operation is done once and only by full warps):
@@ -45,6 +54,7 @@ struct FvArgs {
   const int* oct;  // octant bits per patch on coupled plans, else NULL
   const double* w_in;  // derived quantities W of qs (NW-variable arena) when the stage reads them
   double* w_out;       // W of the result, written by a stage that computes it for lambda
+  int form;        // 0: the general stage above; 1-3: SSP-RK3 stage 1-3 in stage-sum form (acc = R)
   int64_t vs;      // var stride
   DevParams P;
 };
@@ -371,6 +381,22 @@ struct FvTile {
             sum = ADD(P, sum, dsum);
           }
           const int64_t ev = v * A.vs + e;
+          if (!PDE::SRC && A.form != 0) {
+            double o;
+            if (A.form == 1) {
+              o = fma(cS, sum, Qk[v]);
+              A.acc[ev] = sum;
+            } else if (A.form == 2) {
+              const double t = ADD(P, A.acc[ev], sum);
+              o = fma(cS, t, __ldg(A.q0 + ev));
+              A.acc[ev] = t;
+            } else {
+              o = fma(cS, sum, fma(cA, A.acc[ev], __ldg(A.q0 + ev)));
+            }
+            res[v] = o;
+            A.out[ev] = o;
+            continue;
+          }
           if (A.out) {
             double base = b1 ? Qk[v] : MUL(P, A.b, Qk[v]);
             if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
@@ -522,10 +548,15 @@ static dh_status launch(dh_plan* plan, const FvArgs& A, int wmode, cudaStream_t 
 
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
-                          double* lam_out, cudaStream_t stream, int wmode, const double* w_in, double* w_out) {
+                          double* lam_out, cudaStream_t stream, int wmode, const double* w_in, double* w_out,
+                          int form) {
   // a stage that reads and writes W needs two arenas: other CTAs read halo W of the input
   if (((wmode & 1) && !w_in) || ((wmode & 2) && !w_out) || (wmode == 3 && w_in == w_out)) {
     set_error("launch_fv_stage: W arenas missing or aliased");
+    return DH_EINVAL;
+  }
+  if (form < 0 || form > 3 || (form && (!acc || !out || plan->coupled || (form > 1 && !q0)))) {
+    set_error("launch_fv_stage: stage-sum form %d needs acc, out (and q0), uncoupled levels", form);
     return DH_EINVAL;
   }
   FvArgs A;
@@ -538,6 +569,7 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
   A.oct = plan->coupled ? plan->d_amr_oct : nullptr;
   A.w_in = w_in;
   A.w_out = w_out;
+  A.form = form;
   A.vs = plan->var_stride;
   A.P = plan->params;
   switch (plan->pde) {

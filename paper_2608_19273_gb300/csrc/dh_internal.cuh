@@ -156,9 +156,11 @@ dh_status launch_fv2_stage(dh_plan* plan, const double* qs, const double* q0, do
 
 // wmode: bit 0 reads the derived quantities W of qs from w_in, bit 1 writes W of the
 // result to w_out (a different arena when both are set); 0 outside multi-step graphs.
+// form: 0 for the general stage; 1-3 for stage 1-3 of SSP-RK3 in stage-sum form, acc
+// holding the raw face-flux sum of the earlier stages (uncoupled plans).
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
                           double* lam_out, cudaStream_t stream, int wmode = 0, const double* w_in = nullptr,
-                          double* w_out = nullptr);
+                          double* w_out = nullptr, int form = 0);
 
 }  // namespace dh

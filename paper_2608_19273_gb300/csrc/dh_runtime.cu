@@ -29,7 +29,7 @@ struct WChain {
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
                             double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc = nullptr,
-                            bool prims_current = false);
+                            bool prims_current = false, int form = 0);
 
 struct Timer {
   dh_plan* plan;
@@ -55,7 +55,7 @@ struct Timer {
 static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const double* q0, double* out,
                             double* acc, const double* mat, const double* dt, double a, double b, double g,
                             double d, double sigma, double* lam, Timer& T, cudaStream_t s, WChain* wc,
-                            bool prims_current) {
+                            bool prims_current, int form) {
   if (plan->pde == DH_PDE_SRHD3D) {
     // primitives of the stage input, seeded by the previous primitives (in place), unless
     // they were just recovered from this very input (the step start's wave speed)
@@ -75,8 +75,10 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
     const int j = wc->next++;
     const int wmode = (j > 0 ? 1 : 0) | (j + 1 < wc->total ? 2 : 0);
     DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, wmode, wc->buf[(j + 1) & 1],
-                           wc->buf[j & 1]));
-  } else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
+                           wc->buf[j & 1], form));
+  } else if (scheme == 0 && form) DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, 0,
+                                                         nullptr, nullptr, form));
+  else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else if (scheme == 2) DH_TRY(patch_update_fv_muscl(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else DH_TRY(patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s));
   return T.end();
@@ -103,6 +105,12 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s, nullptr,
                       srhd_cur));
     DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
+  } else if (rk == 3 && scheme == 0 && acc && !plan->coupled) {
+    // the stage-sum form of the same scheme: acc carries the raw face-flux sum of the earlier stages
+    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc, srhd_cur, 1));
+    DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 0, 0, 0.25, 0, sigma, nullptr, T, s, wc, false, 2));
+    DH_TRY(stage_call(plan, scheme, u2, q, q, acc, mat, dt, 0, 0, 2.0 / 3.0, 1.0 / 6.0, sigma, lam_last, T, s, wc,
+                      false, 3));
   } else if (rk == 3) {
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc, srhd_cur));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, T, s, wc));
@@ -132,6 +140,7 @@ static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* 
     return DH_EINVAL;
   }
   if (cfl > 0 && !lam) { set_error("dh_rk_step: cfl > 0 needs lam_dev"); return DH_EINVAL; }
+  if (acc && (acc == q || acc == u1 || acc == u2)) { set_error("dh_rk_step: acc aliases a state buffer"); return DH_EINVAL; }
   if (plan->pde == DH_PDE_SRHD3D && !mat) { set_error("dh_rk_step: SRHD3D needs the primitive arena as mat"); return DH_EINVAL; }
   if (rk != 1 && rk != 3 && rk != 4) { set_error("dh_rk_step: rk must be 1, 3 or 4"); return DH_EINVAL; }
   return DH_OK;

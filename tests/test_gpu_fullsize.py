@@ -25,7 +25,8 @@ def _gpu_step(torch, name, w, q, mat, steps=1):
         Q = dev(torch, q)
         M = dev(torch, mat) if mat is not None else None
         U1, U2 = torch.empty_like(Q), torch.empty_like(Q)
-        ACC = torch.empty_like(Q) if rk == 4 else None
+        # as the benchmark: RK4 accumulator, or the raw stage sums of SSP-RK3 FV steps (stage-sum form)
+        ACC = torch.empty_like(Q) if rk == 4 or (rk == 3 and scheme == 0) else None
         lam = torch.zeros(1, dtype=torch.float64, device="cuda")
         dt = torch.zeros(1, dtype=torch.float64, device="cuda")
         if name == "srhd3d":

@@ -191,3 +191,74 @@ def test_graph_hands_derived_quantities_to_the_next_step(orc):
     m = voxel_mask(mesh)
     assert np.array_equal(res[0][0][:, m], res[1][0][:, m])
     assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_ssprk3_stage_sum_form(orc, dim):
+    """SSP-RK3 steps through dh_rk_step with acc (the stage-sum form u2 = q + dt/4 (L0 + L1),
+    q <- q + dt/6 (L0 + L1) + 2 dt/3 L2) against the oracle's Shu-Osher steps, and the same steps
+    replayed from a captured graph (derived-quantity hand-over on): bitwise equal to the eager steps."""
+    torch = require_cuda()
+    if dim == 3:
+        mesh, pde = synth.euler3d_amr_mesh(scale=4), synth.PDE_EULER3D
+    else:
+        mesh, pde = synth.workload("euler2d").mesh, synth.PDE_EULER2D
+    q = _euler_cons(orc, mesh, 41, pde)
+    ref = q.copy()
+    dts = orc.rk_steps(FV, pde, dim, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=3, cfl=0.4)
+    res = []
+    for graph in (False, True):
+        with dh.Plan(pde, dim, mesh.patches, 1, mesh.var_stride) as plan:
+            Q = dev(torch, q)
+            U1, U2, R = torch.zeros_like(Q), torch.zeros_like(Q), torch.zeros_like(Q)
+            lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dh.max_wave_speed(plan, Q, None, lam)
+            torch.cuda.synchronize()
+            if graph:
+                s = torch.cuda.Stream()
+                dh.dh_rk_step(plan, FV, 3, Q.clone(), U1, U2, R, None, dt.clone(), lam.clone(), 0.4, 0.0, s)
+                s.synchronize()
+                dh.dh_graph_capture(plan, FV, 3, 3, Q, U1, U2, R, None, dt, lam, 0.4, 0.0, 0, s)
+                dh.dh_graph_launch(plan, s)
+                s.synchronize()
+            else:
+                for _ in range(3):
+                    dh.dh_rk_step(plan, FV, 3, Q, U1, U2, R, None, dt, lam, 0.4, 0.0)
+            res.append((host(Q), float(host(dt)[0])))
+    m = voxel_mask(mesh)
+    assert_parity(res[0][0], ref, m, what=f"euler{dim}d SSP-RK3 stage-sum form")
+    assert abs(res[0][1] - dts[-1]) <= 1e-14 * dts[-1]
+    assert np.array_equal(res[0][0][:, m], res[1][0][:, m]) and res[0][1] == res[1][1]
+
+
+def test_ssprk3_stage_sum_form_free_stream_bitwise():
+    """A constant state stays bitwise constant through SSP-RK3 steps in the stage-sum form (every
+    stage adds a multiple of an exactly zero face-flux sum to q)."""
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=4)
+    q = arena(mesh, 5)
+    for v, c in enumerate([1.3, 0.37, -0.21, 0.11, 2.9]):
+        q[v] = c
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        Q = dev(torch, q)
+        U1, U2, R = torch.zeros_like(Q), torch.zeros_like(Q), torch.zeros_like(Q)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, Q, None, lam)
+        for _ in range(2):
+            dh.dh_rk_step(plan, FV, 3, Q, U1, U2, R, None, dt, lam, 0.4, 0.0)
+        got = host(Q)
+    m = voxel_mask(mesh)
+    assert np.array_equal(got[:, m], q[:, m])
+
+
+def test_stage_sum_form_rejects_aliased_acc():
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=8)
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        Q = torch.ones((5, mesh.var_stride), dtype=torch.float64, device="cuda")
+        U1, U2 = torch.zeros_like(Q), torch.zeros_like(Q)
+        dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
+        with pytest.raises(dh.DhError):
+            dh.dh_rk_step(plan, FV, 3, Q, U1, U2, U1, None, dt, None, 0.0, 0.0)
