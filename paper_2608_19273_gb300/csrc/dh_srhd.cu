@@ -22,26 +22,31 @@
 namespace dh {
 
 // Returns iterations used (> 0) on convergence, -iterations on failure.
-// Adds and products are issued as FMAs with the run-time constants one/mone/zero
-// (GB300 runs DFMA faster than DADD/DMUL; results are bitwise the same).  The
-// two reciprocals per iteration are refined hardware estimates (recip_nr, one
-// third-order step, <= 1 ulp from the IEEE quotient): the iteration converges to the
-// same root, and the stopping test still compares successive iterates.
-__device__ int srhd_newton_dev(double G, double D, double S2, double E, double p_lo, double p0, double tol,
+// The Newton step is evaluated in an equivalent algebraic form that needs one
+// reciprocal and one reciprocal square root per iteration.  With y = E + p and
+// q = sqrt(y^2 - S^2) = y sqrt(1 - S^2/y^2) (the square-root term of f is D q / y):
+//   y f  = gf q (q - D) - p y          (gf = (G-1)/G)
+//   y^2 f' = gf S^2 (q - D)/q + (gf - 1) y^2
+//   p_new = p - (y^2 f) / (y^2 f') = p - y (gf q (q - D) - p y) / (gf S^2 (q - D)/q + (gf - 1) y^2)
+// The root and the iterates agree with the textbook form to rounding (the
+// stopping test still compares successive iterates).  Adds and products are
+// issued as FMAs with the run-time constants one/mone/zero (GB300 runs DFMA
+// faster than DADD/DMUL; results are bitwise the same); the reciprocal is a
+// refined hardware estimate (recip_nr, one third-order step, <= 1 ulp from the
+// IEEE quotient).  A state whose y^2 - S^2 is not positive gives NaN (failure).
+__device__ int srhd_newton_dev(double gf, double D, double S2, double E, double p_lo, double p0, double tol,
                                int max_iter, double one, double mone, double zero, double* p_out) {
-  const double gf = (G - 1.0) / G;
+  const double gfS2 = fma(gf, S2, zero), gm1 = fma(gf, one, mone);
   double p = p0;
   for (int it = 1; it <= max_iter; ++it) {
-    const double Ep = fma(E, one, p);
-    const double rEp = recip_nr(Ep);
-    const double t = fma(S2, rEp, zero);   // S^2/(E+p)
-    const double s2e = fma(t, rEp, zero);  // S^2/(E+p)^2
-    const double om = fma(s2e, mone, one);
-    const double rrt = rsqrt(om);          // 1/sqrt(1 - S^2/(E+p)^2)
-    const double rt = fma(om, rrt, zero);
-    const double f = fma(gf, fma(-D, rt, fma(t, mone, Ep)), -p);
-    const double fp = fma(gf, fma(-D, fma(fma(s2e, rEp, zero), rrt, zero), fma(s2e, one, one)), mone);
-    double pn = fma(-f, recip_nr(fp), p);
+    const double y = fma(E, one, p);
+    const double d = fma(y, y, -S2);                      // q^2
+    const double iq = rsqrt(d);                           // 1/q
+    const double q = fma(d, iq, zero);
+    const double qmD = fma(D, mone, q);                   // q - D
+    const double num = fma(fma(-p, y, fma(fma(gf, q, zero), qmD, zero)), y, zero);   // y^2 f
+    const double den = fma(fma(gm1, y, zero), y, fma(fma(gfS2, qmD, zero), iq, zero)); // y^2 f'
+    double pn = fma(-num, recip_nr(den), p);
     // The three tests below compare bit patterns on the integer pipe: p_lo,
     // |pn - p| and tol pn are non-negative, and a non-negative double orders
     // like its bits read as a signed 64-bit integer (a negative pn reads as a
@@ -72,6 +77,7 @@ struct C2PArgs {
   int32_t* fail_count;
   int64_t vs;
   double G;
+  double gf;               // (G - 1)/G
   double one, mone, zero;  // 1, -1, 0 for the FMA forms of adds and products
 };
 
@@ -104,13 +110,13 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
     have2 = have_prev;
   }
   double p;
-  int it1 = srhd_newton_dev(G, D, S2, E, p_lo, s1, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
+  int it1 = srhd_newton_dev(A.gf, D, S2, E, p_lo, s1, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
   int total = it1 > 0 ? it1 : -it1;
   uint8_t st = 0;
   if (it1 <= 0) {
     int it2 = 0;
     if (have2) {
-      it2 = srhd_newton_dev(G, D, S2, E, p_lo, s2, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
+      it2 = srhd_newton_dev(A.gf, D, S2, E, p_lo, s2, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
       total += it2 > 0 ? it2 : -it2;
     }
     if (have2 && it2 > 0) st = 1;
@@ -120,7 +126,7 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   const double vx = q[1] * rEp, vy = q[2] * rEp, vz = q[3] * rEp;
   const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
   // rho = D / W = D sqrt(1 - v^2)
-  A.prim[e] = D * sqrt(1.0 - v2);
+  A.prim[e] = D * sqrt_pos(1.0 - v2);
   A.prim[vs + e] = vx;
   A.prim[2 * vs + e] = vy;
   A.prim[3 * vs + e] = vz;
@@ -187,8 +193,9 @@ dh_status con2prim(dh_plan* plan, const double* cons, double* prim, const double
   if (plan->pde != DH_PDE_SRHD3D) { set_error("con2prim: the plan's PDE is not SRHD3D"); return DH_EUNSUPPORTED; }
   dh_status st = c2p_check(cons, prim, tol, max_iter);
   if (st != DH_OK) return st;
-  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, plan->var_stride, plan->params.Gamma,
-            1.0, -1.0, 0.0};
+  const double G = plan->params.Gamma;
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, plan->var_stride, G,
+            (G - 1.0) / G, 1.0, -1.0, 0.0};
   k_con2prim_patches<<<plan->K, 256, 0, (cudaStream_t)stream>>>(plan->d_patches, plan->dim, A);
   return cuda_error(cudaGetLastError(), "con2prim launch");
 }
@@ -200,7 +207,8 @@ dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t str
   if (st != DH_OK) return st;
   if (n <= 0 || stride < n) { set_error("con2prim_flat: need 0 < n <= stride"); return DH_EINVAL; }
   if (!(Gamma > 1.0)) { set_error("con2prim_flat: Gamma must exceed 1"); return DH_EINVAL; }
-  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, stride, Gamma, 1.0, -1.0, 0.0};
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, stride, Gamma,
+            (Gamma - 1.0) / Gamma, 1.0, -1.0, 0.0};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
