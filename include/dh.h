@@ -289,7 +289,7 @@ dh_status dh_prim2con(dh_plan* plan, const double* prim, double* cons, void* str
  * lam_dev must hold the speed of q on entry (max_wave_speed).  If cfl <= 0
  * the caller's dt_dev is used unchanged.  All buffers are N-variable arenas
  * owned by the caller; u2 is needed for rk >= 3 and acc for rk = 4.
- * rk = 3 with scheme 0 on an uncoupled plan and acc != NULL: the same scheme
+ * rk = 3 with scheme 0 and acc != NULL: the same scheme
  * in its Butcher (stage-sum) form, u1 = q + dt L0, u2 = q + dt/4 (L0 + L1),
  * q <- q + dt/6 (L0 + L1) + 2 dt/3 L2, with acc (N variables, not aliasing the
  * other buffers) holding the raw face-flux sums of the earlier stages: fewer

@@ -11,7 +11,9 @@
 //   * Reflux (k_reflux, after the stage kernel): a coarse voxel next to the
 //     finer level uses, on that face, the mean of the 2^(d-1) fine face
 //     fluxes instead of its own coarse face flux:
-//         out += g dt sgn (mean(F^_fine) - F^_coarse) / dx_coarse   (acc with d dt),
+//         out += g dt sgn (mean(F^_fine) - F^_coarse) / dx_coarse   (acc with d dt;
+//         in the SSP-RK3 stage-sum form acc holds raw face-flux sums and takes
+//         -2 sgn (mean(F^_fine) - F^_coarse) in stages 1 and 2),
 //     sgn = -1 for the coarse voxel's +a face, +1 for its -a face.  Fine face
 //     fluxes use the coarse voxel as the halo value, exactly as the fine
 //     patch's own update did, so mass, momentum and energy are conserved
@@ -47,6 +49,7 @@ struct CplArgs {
   double* acc;
   const double* dt_dev;
   double g, d;
+  int form;  // 0: general stage (acc += d dt L); 1-3: SSP-RK3 stage-sum form (acc = raw face-flux sums)
   int64_t vs;
   int n, dim;
   DevParams P;
@@ -119,7 +122,9 @@ __global__ void __launch_bounds__(64) k_reflux(const __grid_constant__ CplArgs A
     const double dL = sgn * (fsum[v] * rn - fc[v]) / C.dx;
     const int64_t ev = v * A.vs + eC;
     if (A.out) A.out[ev] = A.out[ev] + gdt * dL;
-    if (A.acc) A.acc[ev] = A.acc[ev] + ddt * dL;
+    if (A.acc && A.form == 0) A.acc[ev] = A.acc[ev] + ddt * dL;
+    // stage-sum form: the raw sum (twice the face fluxes, L = -sum/(2 dx)) of stages 1 and 2
+    if (A.acc && (A.form == 1 || A.form == 2)) A.acc[ev] = A.acc[ev] - 2.0 * sgn * (fsum[v] * rn - fc[v]);
   }
 }
 
@@ -174,6 +179,8 @@ dh_status couple_pde(dh_plan* plan, CplArgs A, cudaStream_t s) {
     const int n = plan->amr_restrict_off[l + 1] - plan->amr_restrict_off[l];
     if (n == 0) continue;
     A.restrict_list = plan->d_amr_restrict + plan->amr_restrict_off[l];
+    // the raw sums of the stage-sum form are never read for covered coarse voxels
+    if (A.form != 0) A.acc = nullptr;
     k_restrict<<<n, 256, 0, s>>>(A, plan->nq);
     dh_status st = cuda_error(cudaGetLastError(), "k_restrict launch");
     if (st != DH_OK) return st;
@@ -295,12 +302,13 @@ dh_status amr_build(dh_plan* plan, const dh_patch* patches, int K, int dim) {
 
 // Reflux and restriction after a first-order FV stage on a coupled plan.
 dh_status amr_couple(dh_plan* plan, const double* qs, const double* mat, double* out, double* acc,
-                     const double* dt_dev, double g, double d, cudaStream_t s) {
+                     const double* dt_dev, double g, double d, cudaStream_t s, int form) {
   CplArgs A{};
   A.patches = plan->d_patches;
   A.oct = plan->d_amr_oct;
   A.qs = qs; A.mat = mat; A.out = out; A.acc = acc; A.dt_dev = dt_dev;
   A.g = g; A.d = d;
+  A.form = form;
   A.vs = plan->var_stride;
   A.dim = plan->dim;
   A.P = plan->params;

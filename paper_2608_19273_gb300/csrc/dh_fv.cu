@@ -555,8 +555,8 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
     set_error("launch_fv_stage: W arenas missing or aliased");
     return DH_EINVAL;
   }
-  if (form < 0 || form > 3 || (form && (!acc || !out || plan->coupled || (form > 1 && !q0)))) {
-    set_error("launch_fv_stage: stage-sum form %d needs acc, out (and q0), uncoupled levels", form);
+  if (form < 0 || form > 3 || (form && (!acc || !out || (form > 1 && !q0)))) {
+    set_error("launch_fv_stage: stage-sum form %d needs acc, out (and q0)", form);
     return DH_EINVAL;
   }
   FvArgs A;

@@ -141,8 +141,9 @@ inline void finish_params(DevParams& P) {
 
 std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim);
 dh_status amr_build(dh_plan* plan, const dh_patch* patches, int K, int dim);
+// form: as launch_fv_stage (0: acc += d dt L; 1-3: SSP-RK3 stage-sum form, acc = raw sums)
 dh_status amr_couple(dh_plan* plan, const double* qs, const double* mat, double* out, double* acc,
-                     const double* dt_dev, double g, double d, cudaStream_t s);
+                     const double* dt_dev, double g, double d, cudaStream_t s, int form = 0);
 dh_status aoas_move(dh_plan* plan, bool gather, const double* const* blocks, int nq, int v0, int nv, int halo,
                     double* arena, cudaStream_t s);
 
@@ -157,7 +158,8 @@ dh_status launch_fv2_stage(dh_plan* plan, const double* qs, const double* q0, do
 // wmode: bit 0 reads the derived quantities W of qs from w_in, bit 1 writes W of the
 // result to w_out (a different arena when both are set); 0 outside multi-step graphs.
 // form: 0 for the general stage; 1-3 for stage 1-3 of SSP-RK3 in stage-sum form, acc
-// holding the raw face-flux sum of the earlier stages (uncoupled plans).
+// holding the raw face-flux sum of the earlier stages (coupled plans: amr_couple with the
+// same form follows).
 dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
                           double* lam_out, cudaStream_t stream, int wmode = 0, const double* w_in = nullptr,

@@ -76,9 +76,15 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
     const int wmode = (j > 0 ? 1 : 0) | (j + 1 < wc->total ? 2 : 0);
     DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, wmode, wc->buf[(j + 1) & 1],
                            wc->buf[j & 1], form));
-  } else if (scheme == 0 && form) DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, 0,
-                                                         nullptr, nullptr, form));
-  else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
+  } else if (scheme == 0 && form) {
+    DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, plan->coupled ? nullptr : lam, s, 0,
+                           nullptr, nullptr, form));
+    if (plan->coupled) {
+      // reflux and restriction, then the wave speed of the coupled result
+      DH_TRY(amr_couple(plan, qs, mat, out, acc, dt, g, d, s, form));
+      if (lam) DH_TRY(max_wave_speed(plan, out, mat, lam, s));
+    }
+  } else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else if (scheme == 2) DH_TRY(patch_update_fv_muscl(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else DH_TRY(patch_update_fd_ko(plan, qs, q0, out, acc, mat, dt, a, b, g, d, sigma, lam, s));
   return T.end();
@@ -105,7 +111,7 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s, nullptr,
                       srhd_cur));
     DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
-  } else if (rk == 3 && scheme == 0 && acc && !plan->coupled) {
+  } else if (rk == 3 && scheme == 0 && acc) {
     // the stage-sum form of the same scheme: acc carries the raw face-flux sum of the earlier stages
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc, srhd_cur, 1));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 0, 0, 0.25, 0, sigma, nullptr, T, s, wc, false, 2));

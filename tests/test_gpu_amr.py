@@ -160,3 +160,59 @@ def test_coupled_plan_rejections():
     bad["dx"][first_fine] *= 2.0     # a fine patch whose coarse neighbour is not exactly twice as coarse
     with pytest.raises(dh.DhError):
         dh.Plan(3, 3, bad, 1, mesh.var_stride)
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_coupled_ssprk3_stage_sum_form(orc, dim):
+    """SSP-RK3 steps in the stage-sum form (acc given: raw face-flux sums, reflux corrections added
+    to them) on coupled levels against the oracle's Shu-Osher steps, eager and from a graph."""
+    torch = require_cuda()
+    mesh = _mesh(dim)
+    pde, q = _cons(orc, mesh, 110 + dim)
+    ref = q.copy()
+    dts = orc.rk_steps(FV, pde, dim, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=3, cfl=0.4)
+    outs = []
+    for use_graph in (False, True):
+        with dh.Plan(pde, dim, mesh.patches, 1, mesh.var_stride) as plan:
+            Q = dev(torch, q)
+            U1, U2, R = torch.zeros_like(Q), torch.zeros_like(Q), torch.zeros_like(Q)
+            lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dh.max_wave_speed(plan, Q, None, lam)
+            if use_graph:
+                torch.cuda.synchronize()
+                s = torch.cuda.Stream()
+                dh.dh_rk_step(plan, FV, 3, Q.clone(), U1, U2, R, None, dt.clone(), lam.clone(), 0.4, 0.0, s)
+                s.synchronize()
+                dh.dh_graph_capture(plan, FV, 3, 3, Q, U1, U2, R, None, dt, lam, 0.4, 0.0, 0, s)
+                dh.dh_graph_launch(plan, s)
+                s.synchronize()
+            else:
+                for _ in range(3):
+                    dh.dh_rk_step(plan, FV, 3, Q, U1, U2, R, None, dt, lam, 0.4, 0.0)
+            outs.append((host(Q), float(host(dt)[0])))
+    m = _mask(mesh)
+    assert_parity(outs[0][0], ref, m, what=f"coupled {dim}D SSP-RK3 stage-sum form")
+    assert abs(outs[0][1] - dts[-1]) <= 1e-14 * dts[-1]
+    assert np.array_equal(outs[0][0][:, m], outs[1][0][:, m])
+
+
+def test_coupled_ssprk3_stage_sum_form_free_stream_bitwise():
+    """With the stage-sum form, SSP-RK3 steps keep a constant state bitwise constant on coupled
+    levels (each stage adds multiples of exactly zero sums and corrections to q)."""
+    torch = require_cuda()
+    mesh = _mesh(3)
+    q = np.zeros((5, mesh.var_stride))
+    for v, c in enumerate([1.3, 0.37, -0.21, 0.11, 2.9]):
+        q[v, :] = c
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        Q = dev(torch, q)
+        U1, U2, R = torch.zeros_like(Q), torch.zeros_like(Q), torch.zeros_like(Q)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, Q, None, lam)
+        for _ in range(2):
+            dh.dh_rk_step(plan, FV, 3, Q, U1, U2, R, None, dt, lam, 0.4, 0.0)
+        got = host(Q)
+    m = _mask(mesh)
+    assert np.array_equal(got[:, m], q[:, m])
