@@ -120,6 +120,9 @@ def workload_config(name, w, mesh):
     spec = WORKLOADS[name]
     return {"workload": name, "description": spec["desc"], "voxels": mesh.nvox, "patches": int(mesh.K),
             "time_steps_per_step": spec["inner"], "cfl": spec["cfl"], "cuda_graph": True,
+            "time_integrator": {1: "forward Euler", 4: "classical RK4"}.get(
+                spec["rk"], "SSP-RK3, stage-sum (Butcher) form: acc holds the raw face-flux sums"
+                if spec["scheme"] == 0 else "SSP-RK3, Shu-Osher form"),
             "l2": "no flush: every state array is larger than L2 (129 MB)" if mesh.nvox * 40 > 129e6
             else "state fits in L2 (small workload)",
             "seed": int(w.seed)}
