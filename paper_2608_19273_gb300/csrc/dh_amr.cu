@@ -50,6 +50,7 @@ struct CplArgs {
   const double* dt_dev;
   double g, d;
   int form;  // 0: general stage (acc += d dt L); 1-3: SSP-RK3 stage-sum form (acc = raw face-flux sums)
+  double* w_out;  // derived quantities W of the result (NW-variable arena) to refresh, or NULL
   int64_t vs;
   int n, dim;
   DevParams P;
@@ -117,14 +118,72 @@ __global__ void __launch_bounds__(64) k_reflux(const __grid_constant__ CplArgs A
   const double sgn = R.lo ? -1.0 : 1.0;
   const double dt = *A.dt_dev;
   const double gdt = A.g * dt, ddt = A.d * dt;
+  double qn[NV];
 #pragma unroll
   for (int v = 0; v < N; ++v) {
     const double dL = sgn * (fsum[v] * rn - fc[v]) / C.dx;
     const int64_t ev = v * A.vs + eC;
-    if (A.out) A.out[ev] = A.out[ev] + gdt * dL;
+    if (A.out) {
+      qn[v] = A.out[ev] + gdt * dL;
+      A.out[ev] = qn[v];
+    }
     if (A.acc && A.form == 0) A.acc[ev] = A.acc[ev] + ddt * dL;
     // stage-sum form: the raw sum (twice the face fluxes, L = -sum/(2 dx)) of stages 1 and 2
     if (A.acc && (A.form == 1 || A.form == 2)) A.acc[ev] = A.acc[ev] - 2.0 * sgn * (fsum[v] * rn - fc[v]);
+  }
+  // the derived quantities of the corrected voxel, for the next stage (multi-step graphs)
+  if (A.w_out && A.out) {
+#pragma unroll
+    for (int v = N; v < NV; ++v) qn[v] = A.mat[(v - N) * A.vs + eC];
+    double W[PDE::NW > 0 ? PDE::NW : 1];
+    PDE::prims(qn, A.P, W);
+#pragma unroll
+    for (int i = 0; i < PDE::NW; ++i) A.w_out[i * A.vs + eC] = W[i];
+  }
+}
+
+// Mean of the 2^d fine voxels under coarse voxel (x, y, z) of the covered block:
+// pairs along x, then rows, then layers (balanced tree).
+__device__ __forceinline__ double fine_mean(const double* a, int p, int dim, int x, int y, int z) {
+  double layer[2];
+  for (int sz = 0; sz < (dim == 3 ? 2 : 1); ++sz) {
+    const int64_t r0 = ((int64_t)(dim == 3 ? 2 * z + sz : 0) * p + 2 * y) * p + 2 * x;
+    const double row0 = a[r0] + a[r0 + 1];
+    const double row1 = a[r0 + p] + a[r0 + p + 1];
+    layer[sz] = row0 + row1;
+  }
+  const double sum = dim == 3 ? layer[0] + layer[1] : layer[0];
+  return sum * (dim == 3 ? 0.125 : 0.25);
+}
+
+// As k_restrict, one thread per covered coarse voxel (all N variables), which
+// then refreshes that voxel's derived quantities W in A.w_out.
+template <class PDE>
+__global__ void __launch_bounds__(256) k_restrict_w(const __grid_constant__ CplArgs A) {
+  constexpr int N = PDE::N, NV = PDE::N + PDE::M;
+  const int2 fp = A.restrict_list[blockIdx.x];
+  const dh_patch& F = A.patches[fp.x];
+  const dh_patch& Pp = A.patches[fp.y];
+  const int p = F.p, h = p >> 1, o = A.oct[fp.x];
+  const int hz = A.dim == 3 ? h : 1;
+  const int nvox = h * h * hz;
+  for (int r = threadIdx.x; r < nvox; r += blockDim.x) {
+    const int x = r % h, y = (r / h) % h, z = r / (h * h);
+    const int cx = (o & 1) * h + x, cy = ((o >> 1) & 1) * h + y, cz = A.dim == 3 ? ((o >> 2) & 1) * h + z : 0;
+    const int64_t ec = Pp.offset + ((int64_t)cz * p + cy) * p + cx;
+    double qn[NV];
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      qn[v] = fine_mean(A.out + (int64_t)v * A.vs + F.offset, p, A.dim, x, y, z);
+      A.out[(int64_t)v * A.vs + ec] = qn[v];
+      if (A.acc) A.acc[(int64_t)v * A.vs + ec] = fine_mean(A.acc + (int64_t)v * A.vs + F.offset, p, A.dim, x, y, z);
+    }
+#pragma unroll
+    for (int v = N; v < NV; ++v) qn[v] = A.mat[(v - N) * A.vs + ec];
+    double W[PDE::NW > 0 ? PDE::NW : 1];
+    PDE::prims(qn, A.P, W);
+#pragma unroll
+    for (int i = 0; i < PDE::NW; ++i) A.w_out[i * A.vs + ec] = W[i];
   }
 }
 
@@ -144,16 +203,7 @@ __global__ void __launch_bounds__(256) k_restrict(const __grid_constant__ CplArg
     for (int w = 0; w < 2; ++w) {
       double* arr = w == 0 ? A.out : A.acc;
       if (!arr) continue;
-      const double* a = arr + (int64_t)v * A.vs + F.offset;
-      double layer[2];
-      for (int sz = 0; sz < (A.dim == 3 ? 2 : 1); ++sz) {
-        const int64_t r0 = ((int64_t)(A.dim == 3 ? 2 * z + sz : 0) * p + 2 * y) * p + 2 * x;
-        const double row0 = a[r0] + a[r0 + 1];
-        const double row1 = a[r0 + p] + a[r0 + p + 1];
-        layer[sz] = row0 + row1;
-      }
-      const double sum = A.dim == 3 ? layer[0] + layer[1] : layer[0];
-      arr[(int64_t)v * A.vs + ec] = sum * (A.dim == 3 ? 0.125 : 0.25);
+      arr[(int64_t)v * A.vs + ec] = fine_mean(arr + (int64_t)v * A.vs + F.offset, p, A.dim, x, y, z);
     }
   }
 }
@@ -181,7 +231,8 @@ dh_status couple_pde(dh_plan* plan, CplArgs A, cudaStream_t s) {
     A.restrict_list = plan->d_amr_restrict + plan->amr_restrict_off[l];
     // the raw sums of the stage-sum form are never read for covered coarse voxels
     if (A.form != 0) A.acc = nullptr;
-    k_restrict<<<n, 256, 0, s>>>(A, plan->nq);
+    if (A.w_out && A.out) k_restrict_w<PDE><<<n, 256, 0, s>>>(A);
+    else k_restrict<<<n, 256, 0, s>>>(A, plan->nq);
     dh_status st = cuda_error(cudaGetLastError(), "k_restrict launch");
     if (st != DH_OK) return st;
   }
@@ -302,8 +353,9 @@ dh_status amr_build(dh_plan* plan, const dh_patch* patches, int K, int dim) {
 
 // Reflux and restriction after a first-order FV stage on a coupled plan.
 dh_status amr_couple(dh_plan* plan, const double* qs, const double* mat, double* out, double* acc,
-                     const double* dt_dev, double g, double d, cudaStream_t s, int form) {
+                     const double* dt_dev, double g, double d, cudaStream_t s, int form, double* w_out) {
   CplArgs A{};
+  A.w_out = w_out;
   A.patches = plan->d_patches;
   A.oct = plan->d_amr_oct;
   A.qs = qs; A.mat = mat; A.out = out; A.acc = acc; A.dt_dev = dt_dev;

@@ -87,6 +87,58 @@ __global__ void __launch_bounds__(256) k_max_speed(const dh_patch* __restrict__ 
   }
 }
 
+// The same maximum from the derived quantities W of the state (systems whose
+// speeds depend on W alone: Euler), e.g. those a stage kernel just wrote.
+template <class PDE>
+__global__ void __launch_bounds__(256) k_max_speed_w(const dh_patch* __restrict__ patches, int dim, int64_t vs,
+                                                     const double* __restrict__ w, DevParams P, double* lam_out,
+                                                     unsigned long long* red) {
+  __shared__ double wmax[8];
+  __shared__ bool last;
+  const dh_patch pt = patches[blockIdx.x];
+  const int n = dim == 3 ? pt.p * pt.p * pt.p : pt.p * pt.p;
+  double lam = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double W[PDE::NW];
+    const int64_t e = pt.offset + i;
+#pragma unroll
+    for (int v = 0; v < PDE::NW; ++v) W[v] = w[v * vs + e];
+    double l = fmax(PDE::speed(0, nullptr, W, P), PDE::speed(1, nullptr, W, P));
+    if (dim == 3) l = fmax(l, PDE::speed(2, nullptr, W, P));
+    lam = fmax(lam, l);
+  }
+  lam = warp_max_d(lam);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lam;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, wmax[i]);
+    atomicMax(red, (unsigned long long)__double_as_longlong(m));
+    __threadfence();
+    last = atomicAdd(red + 1, 1ull) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    *lam_out = __longlong_as_double((long long)atomicAdd(red, 0ull));
+    red[0] = 0ull;
+    red[1] = 0ull;
+    __threadfence();
+  }
+}
+
+dh_status max_wave_speed_w(dh_plan* plan, const double* w, double* lam_out_dev, cudaStream_t s) {
+  const dh_patch* P = plan->d_patches;
+  switch (plan->pde) {
+    case DH_PDE_EULER2D: k_max_speed_w<PdeEuler2><<<plan->K, 256, 0, s>>>(P, 2, plan->var_stride, w, plan->params, lam_out_dev, plan->d_red); break;
+    case DH_PDE_EULER3D: k_max_speed_w<PdeEuler3><<<plan->K, 256, 0, s>>>(P, 3, plan->var_stride, w, plan->params, lam_out_dev, plan->d_red); break;
+    default:
+      set_error("max_wave_speed_w: PDE %d keeps no derived quantities", plan->pde);
+      return DH_EUNSUPPORTED;
+  }
+  return cuda_error(cudaGetLastError(), "max_wave_speed_w launch");
+}
+
 __global__ void k_cfl_dt(const double* lam, double cfl, double dx_dim, double* dt) {
   // dt = cfl * dx / (dim * lambda); dx_dim = dx / dim
   *dt = cfl * dx_dim / lam[0];

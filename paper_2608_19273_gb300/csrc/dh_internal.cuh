@@ -141,9 +141,14 @@ inline void finish_params(DevParams& P) {
 
 std::vector<int2> aoas_units(const dh_patch* patches, int K, int dim);
 dh_status amr_build(dh_plan* plan, const dh_patch* patches, int K, int dim);
-// form: as launch_fv_stage (0: acc += d dt L; 1-3: SSP-RK3 stage-sum form, acc = raw sums)
+// Maximum characteristic speed from the derived quantities W of a state (Euler systems).
+dh_status max_wave_speed_w(dh_plan* plan, const double* w, double* lam_out_dev, cudaStream_t s);
+// form: as launch_fv_stage (0: acc += d dt L; 1-3: SSP-RK3 stage-sum form, acc = raw sums);
+// w_out: the derived quantities of out written by the stage, refreshed for the voxels the
+// coupling changes (NULL: none kept)
 dh_status amr_couple(dh_plan* plan, const double* qs, const double* mat, double* out, double* acc,
-                     const double* dt_dev, double g, double d, cudaStream_t s, int form = 0);
+                     const double* dt_dev, double g, double d, cudaStream_t s, int form = 0,
+                     double* w_out = nullptr);
 dh_status aoas_move(dh_plan* plan, bool gather, const double* const* blocks, int nq, int v0, int nv, int halo,
                     double* arena, cudaStream_t s);
 

@@ -71,18 +71,24 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
     ~Range() { nvtxRangePop(); }
   } range(scheme == 0 ? "dh FV stage" : (scheme == 2 ? "dh FV2 stage" : "dh FD stage"));
   DH_TRY(T.begin());
-  if (scheme == 0 && wc && wc->on) {
-    const int j = wc->next++;
-    const int wmode = (j > 0 ? 1 : 0) | (j + 1 < wc->total ? 2 : 0);
-    DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s, wmode, wc->buf[(j + 1) & 1],
-                           wc->buf[j & 1], form));
-  } else if (scheme == 0 && form) {
-    DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, plan->coupled ? nullptr : lam, s, 0,
-                           nullptr, nullptr, form));
+  if (scheme == 0 && (form || (wc && wc->on))) {
+    int wmode = 0;
+    const double* w_in = nullptr;
+    double* w_out = nullptr;
+    if (wc && wc->on) {
+      const int j = wc->next++;
+      wmode = (j > 0 ? 1 : 0) | (j + 1 < wc->total ? 2 : 0);
+      w_in = wc->buf[(j + 1) & 1];
+      w_out = wc->buf[j & 1];
+    }
+    DH_TRY(launch_fv_stage(plan, qs, q0, out, acc, mat, dt, a, b, g, d, plan->coupled ? nullptr : lam, s, wmode,
+                           w_in, w_out, form));
     if (plan->coupled) {
-      // reflux and restriction, then the wave speed of the coupled result
-      DH_TRY(amr_couple(plan, qs, mat, out, acc, dt, g, d, s, form));
-      if (lam) DH_TRY(max_wave_speed(plan, out, mat, lam, s));
+      // reflux and restriction (refreshing W of the voxels they change), then the wave
+      // speed of the coupled result
+      DH_TRY(amr_couple(plan, qs, mat, out, acc, dt, g, d, s, form, (wmode & 2) ? w_out : nullptr));
+      if (lam && (wmode & 2)) DH_TRY(max_wave_speed_w(plan, w_out, lam, s));
+      else if (lam) DH_TRY(max_wave_speed(plan, out, mat, lam, s));
     }
   } else if (scheme == 0) DH_TRY(patch_update_fv(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
   else if (scheme == 2) DH_TRY(patch_update_fv_muscl(plan, qs, q0, out, acc, mat, dt, a, b, g, d, lam, s));
@@ -201,7 +207,7 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
     }
   }
   // hand the derived quantities of the state from one step to the next (SSP-RK3 FV, Euler)
-  const bool reuse = scheme == 0 && rk == 3 && cfl > 0 && n_steps > 1 && !plan->coupled &&
+  const bool reuse = scheme == 0 && rk == 3 && cfl > 0 && n_steps > 1 &&
                      (plan->pde == DH_PDE_EULER2D || plan->pde == DH_PDE_EULER3D);
   const size_t nw = (size_t)(plan->dim + 3) * (size_t)plan->var_stride;
   if (reuse && !plan->d_w)
