@@ -42,6 +42,9 @@ from paper_2608_19273_gb300 import synth  # noqa: E402
 METRIC = "FP64 cell-updates/s + % of roofline; learned-seed vs plain con2prim at 1e-12"
 UNIT = "cell-updates/s"
 FLOPS_FILE = os.path.join(ROOT, "oracle", "flop_counts.json")
+# DRAM bytes per voxel and launch of each workload's dominant kernel, read from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the hash of the kernel sources profiled
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
 
 # name: pde, scheme (0 FV, 1 FD), rk, time steps per graph replay, CFL, flop-count key,
 # algorithmic bytes per voxel-step (state reads and writes of all stages, materials,
@@ -95,6 +98,35 @@ def parse_args():
     ap.add_argument("--scale", type=int, default=1,
                     help="divide the patch counts per axis by this factor (small cases for profiling); 1 = full size")
     return ap.parse_args()
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources and the C header (names and bytes): identifies the kernels a
+    stored ncu capture describes."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2608_19273_gb300", "csrc", "*.cu*")) +
+                   glob.glob(os.path.join(ROOT, "include", "*.h")))
+    for f in files:
+        h.update(os.path.relpath(f, ROOT).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(name, nvox):
+    """DRAM bytes per launch of the workload's dominant kernel from the stored ncu capture, scaled to
+    this workload's voxel count; None when no capture exists or the kernels changed since."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = t.get("workloads", {}).get(name)
+    if not e or t.get("source_hash") != kernel_source_hash():
+        return None
+    return float(e["bytes_per_voxel_launch"]) * nvox
 
 
 def max_over_ranks(value, dist=None, device=None):
@@ -640,7 +672,7 @@ def our_arm(args, rank, world, local_rank):
         "config": dict(workload_config(name, w, mesh), parallelism="replicas" if world > 1 else "single-gpu",
                        scale=args.scale),
         "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                     "frac": ach / peak, "traffic": None,
+                     "frac": ach / peak, "traffic": measured_traffic(name, nvox),
                      "peak_source": "FP64 FMA peak measured live on this GPU (dh_probe_dfma, 2 FLOP per FMA)",
                      "flops_per_voxel_step": flops_vs,
                      "timed_launches": int(n_timed), "stage_ms_mean": float(stage_ms.mean()),
