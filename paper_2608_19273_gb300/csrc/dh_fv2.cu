@@ -196,9 +196,11 @@ struct Fv2Tile {
       // at -1 (left state of face 0) and the - state of the voxel at T (right
       // state of face T).
       states(A, box, me, st, d, SP, (a + 1) * area + o, SM, a * area + o);
-      // (taken by the last warps: the first warps take the faces beyond 256 in phase 2)
-      const int ht = t - (MNT - 2 * area);
-      if (ht >= 0) {
+      // (taken by the last warps along x and z and by warps 4 and 5 along y, so that the
+      // extra work of x and y falls on different SM sub-partitions; the faces beyond 256
+      // in phase 2 go to warp 0, or to warp 2 along y)
+      const int ht = t - (d == 1 ? 4 * 32 : MNT - 2 * area);
+      if (ht >= 0 && ht < 2 * area) {
         const int side = ht / area, oo = ht % area;
         int hx, hy, hz;
         if (d == 0) { hx = side == 0 ? -1 : MX; hy = oo % MY; hz = oo / MY; }
@@ -211,7 +213,11 @@ struct Fv2Tile {
       __syncthreads();
       // phase 2: every face along d once ((T + 1) * area faces over the 256 threads)
       const int nf = (T + 1) * area;
-      for (int f = t; f < nf; f += MNT) face(P, SP, SM, f);
+      face(P, SP, SM, t);
+      {
+        const int fx = MNT + t - (d == 1 ? 2 * 32 : 0);
+        if (fx >= MNT && fx < nf) face(P, SP, SM, fx);
+      }
       __syncthreads();
       // phase 3: difference of this voxel's two faces
 #pragma unroll

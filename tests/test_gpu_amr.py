@@ -216,3 +216,28 @@ def test_coupled_ssprk3_stage_sum_form_free_stream_bitwise():
         got = host(Q)
     m = _mask(mesh)
     assert np.array_equal(got[:, m], q[:, m])
+
+
+@pytest.mark.parametrize("coef", [(0.0, 1.0, 1.0), (0.75, 0.25, 0.25)])
+def test_coupled_srhd_stage(orc, coef):
+    """SRHD (primitives in the material slots) on coupled levels: the fine halos take the coarse
+    voxel's conserved state and primitives, reflux uses both sides' primitives."""
+    torch = require_cuda()
+    mesh = _mesh(3)
+    rng = np.random.default_rng(121)
+    specs = [(1.0, 0.5), (0.0, 0.3), (0.0, 0.3), (0.0, 0.3), (1.0, 0.5)]
+    prim = synth.coupled_fields(mesh, rng, specs)
+    cons = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
+    q0 = orc.prim2con(synth.PDE_SRHD3D, synth.coupled_fields(mesh, rng, specs), mesh.var_stride)
+    a, b, g = coef
+    dt = 1e-3
+    ref = np.zeros_like(cons)
+    orc.stage(FV, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, cons, q0=q0 if a else None, out=ref,
+              mat=prim, dt=dt, a=a, b=b, g=g)
+    with dh.Plan(synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        out = torch.zeros(cons.shape, dtype=torch.float64, device="cuda")
+        d_dt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        dh.patch_update_fv(plan, dev(torch, cons), dev(torch, q0) if a else None, out, None, dev(torch, prim), d_dt,
+                           a, b, g, 0)
+        got = host(out)
+    assert_parity(got, ref, _mask(mesh), what=f"coupled SRHD stage {coef}")
