@@ -100,14 +100,22 @@ def parse_args():
     return ap.parse_args()
 
 
-def kernel_source_hash():
-    """Hash of the CUDA sources and the C header (names and bytes): identifies the kernels a
-    stored ncu capture describes."""
-    import glob
+# sources of each workload's dominant kernel (besides the shared headers)
+KERNEL_SOURCES = {
+    "euler3d": ["dh_fv.cu"], "euler2d": ["dh_fv.cu"], "euler3d_amr2": ["dh_fv.cu", "dh_amr.cu"],
+    "euler3d_muscl": ["dh_fv2.cu"], "srhd3d": ["dh_fv.cu", "dh_srhd.cu", "dh_mlp.cuh"],
+    "wave3d": ["dh_fd.cu"], "gw59": ["dh_fd.cu"],
+}
+
+
+def kernel_source_hash(name):
+    """Hash (names and bytes) of the sources of a workload's dominant kernel: its .cu files, the
+    shared device headers and the C header; identifies the kernel a stored ncu capture describes."""
     import hashlib
+    csrc = os.path.join(ROOT, "paper_2608_19273_gb300", "csrc")
+    files = [os.path.join(csrc, f) for f in sorted(KERNEL_SOURCES[name] + ["dh_internal.cuh", "dh_pde.cuh"])]
+    files.append(os.path.join(ROOT, "include", "dh.h"))
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(ROOT, "paper_2608_19273_gb300", "csrc", "*.cu*")) +
-                   glob.glob(os.path.join(ROOT, "include", "*.h")))
     for f in files:
         h.update(os.path.relpath(f, ROOT).encode())
         with open(f, "rb") as fh:
@@ -117,14 +125,14 @@ def kernel_source_hash():
 
 def measured_traffic(name, nvox):
     """DRAM bytes per launch of the workload's dominant kernel from the stored ncu capture, scaled to
-    this workload's voxel count; None when no capture exists or the kernels changed since."""
+    this workload's voxel count; None when no capture exists or that kernel's sources changed since."""
     try:
         with open(TRAFFIC_FILE) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
     e = t.get("workloads", {}).get(name)
-    if not e or t.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(name):
         return None
     return float(e["bytes_per_voxel_launch"]) * nvox
 
