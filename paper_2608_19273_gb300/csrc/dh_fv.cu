@@ -96,6 +96,8 @@ __device__ __forceinline__ int64_t vox_index(const dh_patch* __restrict__ P, con
   return P[n].offset + ((int64_t)z * p + y) * p + x;
 }
 
+__device__ __forceinline__ void prefetch_l2(const double* a) { asm volatile("prefetch.global.L2 [%0];" ::"l"(a)); }
+
 template <class PDE>
 __device__ __forceinline__ void load_q(const FvArgs& A, int64_t e, double* q) {
 #pragma unroll
@@ -310,6 +312,16 @@ struct FvTile {
     for (int kz = 0; kz < pz; ++kz) {
       const int buf = kz & 1;
       const int zg = z0 + kz;  // plane index within the patch
+      // the update of the next plane reads its q0 (and, in the stage-sum form, its
+      // raw sums R) straight from memory: bring those lines into L2 a plane ahead
+      if (act && kz + 1 < pz && (A.q0 || A.form >= 2)) {
+        const int64_t e1 = off + ((int64_t)(zg + 1) * p + y) * p + x;
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          if (A.q0) prefetch_l2(A.q0 + v * A.vs + e1);
+          if (A.form >= 2) prefetch_l2(A.acc + v * A.vs + e1);
+        }
+      }
       // ---- faces of plane kz inside the plane
       if (act) {
         face(S, A.P, 0, buf ? xm1 : xm0, me, S.Hx, S.Dx, fxl, FX);
