@@ -322,6 +322,19 @@ struct FvTile {
           if (A.form >= 2) prefetch_l2(A.acc + v * A.vs + e1);
         }
       }
+      // the state (and stored derived quantities) of the plane after next, which the
+      // next iteration loads for its own voxel
+      if (DIM == 3 && act && kz + 1 < pz) {
+        const int64_t e2 = vox_index(A.patches, A.oct, k, p, x, y, zg + 2);
+#pragma unroll
+        for (int v = 0; v < N; ++v) prefetch_l2(A.qs + v * A.vs + e2);
+#pragma unroll
+        for (int v = 0; v < PDE::M; ++v) prefetch_l2(A.mat + v * A.vs + e2);
+        if (WM & 1) {
+#pragma unroll
+          for (int i = 0; i < NW; ++i) prefetch_l2(A.w_in + i * A.vs + e2);
+        }
+      }
       // ---- faces of plane kz inside the plane
       if (act) {
         face(S, A.P, 0, buf ? xm1 : xm0, me, S.Hx, S.Dx, fxl, FX);
