@@ -323,7 +323,8 @@ struct FvTile {
         }
       }
       // the state (and stored derived quantities) of the plane after next, which the
-      // next iteration loads for its own voxel
+      // next iteration loads for its own voxel (z <= p: at most the +z neighbour's
+      // first plane)
       if (DIM == 3 && act && kz + 1 < pz) {
         const int64_t e2 = vox_index(A.patches, A.oct, k, p, x, y, zg + 2);
 #pragma unroll
