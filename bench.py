@@ -108,8 +108,16 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/C++ source without comments and blank lines (string literals here hold no comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_hash(name):
-    """Hash (names and bytes) of the sources of a workload's dominant kernel: its .cu files, the
+    """Hash of the code (comments excluded) of a workload's dominant kernel: its .cu files, the
     shared device headers and the C header; identifies the kernel a stored ncu capture describes."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2608_19273_gb300", "csrc")
@@ -118,8 +126,8 @@ def kernel_source_hash(name):
     h = hashlib.sha256()
     for f in files:
         h.update(os.path.relpath(f, ROOT).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -59,7 +59,9 @@ typedef enum {
  *   WAVE3D    N=5 M=1  (phi, Pi, psi_x, psi_y, psi_z), material c(x)
  *   SRHD3D    N=5 M=5  (D, S_x, S_y, S_z, tau); the material arena carries
  *                      the primitives (rho, v_x, v_y, v_z, p) from con2prim
- *   GW59      N=59 M=0 59-unknown gravitational-wave stand-in (see DESIGN) */
+ *   GW59      N=59 M=0 59-unknown gravitational-wave stand-in: 11 coupled
+ *                      scalar waves, lapse and shift, F = 0, B(Q).grad Q and a
+ *                      nonlinear source (a defined substitute for CCZ4) */
 typedef enum {
   DH_PDE_ADV_FLUX = 0,
   DH_PDE_ADV_NCP = 1,

@@ -24,3 +24,10 @@ def test_source_hashes():
         assert len(bench.kernel_source_hash(name)) == 16
     assert bench.kernel_source_hash("wave3d") == bench.kernel_source_hash("gw59")
     assert bench.kernel_source_hash("euler3d") != bench.kernel_source_hash("wave3d")
+
+
+def test_hash_ignores_comments():
+    a = "int f(int x) {  // the answer\n  return x; /* done */\n}\n"
+    b = "int f(int x) {\n\n  return x;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(b.replace("x;", "x + 1;"))

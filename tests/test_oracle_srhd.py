@@ -1,7 +1,7 @@
 """Pins of the SRHD oracle: prim2con / con2prim (Newton on p) and the MLP seed maths (CPU only).
 
 Special-relativistic hydro is not in the paper; the system, the Newton
-iteration and the learned seed follow textbook definitions (see DESIGN)."""
+iteration and the learned seed follow textbook definitions."""
 import math
 
 import numpy as np
