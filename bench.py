@@ -539,11 +539,27 @@ def measure_offload(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, str
                                       0.1, nq_back, stream)
     one_ms = timed(lambda: run(1), 3)
     many_ms = timed(lambda: run(inner), 1)
+    small = 8.0 * nq * mesh.nvox <= 4e9
+    two = two_st = None
+    if small:
+        two = measure_two_offload_problems(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, stream, starts, pos,
+                                           nq, h, nq_back, run, timed, compute_ms_per_step, False)
+    # staged: the blocks' host span moved by the copy engine (one cudaMemcpyAsync each way)
+    dh.dh_offload_bind_staged(plan, addrs, nq, h)
+    one_st = timed(lambda: run(1), 3)
+    many_st = timed(lambda: run(inner), 1)
+    if small:
+        two_st = measure_two_offload_problems(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, stream, starts,
+                                              pos, nq, h, nq_back, run, timed, compute_ms_per_step, True)
     finite = bool(torch.isfinite(hbuf).all().item())
     del hbuf, table, arena
     torch.cuda.empty_cache()
     nvox = mesh.nvox
-    return {"nq": nq, "nq_back": nq_back, "aos_halo": h, "blocks": "page-locked host memory, one block per patch",
+    return {"two_problems_two_streams": two,
+            "staged": {"total_ms_1_step": one_st, "total_ms_%d_steps" % inner: many_st,
+                       "total_over_compute_1_step": one_st / compute_ms_per_step,
+                       "total_over_compute_%d_steps" % inner: many_st / (inner * compute_ms_per_step),
+                       "two_problems_two_streams": two_st},"nq": nq, "nq_back": nq_back, "aos_halo": h, "blocks": "page-locked host memory, one block per patch",
             "gather_ms": g_ms, "scatter_ms": s_ms,
             "c2c_read_gbs": 8.0 * nq * nvox / (g_ms * 1e-3) / 1e9,
             "c2c_write_gbs": 8.0 * nq_back * nvox / (s_ms * 1e-3) / 1e9,
@@ -552,6 +568,44 @@ def measure_offload(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, str
             "total_over_compute_1_step": one_ms / compute_ms_per_step,
             "total_over_compute_%d_steps" % inner: many_ms / (inner * compute_ms_per_step),
             "host_blocks_finite": finite}
+
+
+def measure_two_offload_problems(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, stream, starts, pos, nq, h,
+                                 nq_back, run_a, timed, compute_ms_per_step, staged):
+    """A second, independent problem (own plan, host blocks and device buffers), one time step per call:
+    the two calls on one stream one after the other, then on two streams at once, so that each
+    problem's host transfers can overlap the other's compute."""
+    plan_b = dh.Plan(spec["pde"], mesh.dim, mesh.patches, w.halo, mesh.var_stride, w.params)
+    hbuf_b = torch.zeros(pos, dtype=torch.float64).pin_memory()
+    addrs_b = [hbuf_b.data_ptr() + 8 * int(starts[k]) for k in range(len(starts))]
+    table_b = torch.tensor(addrs_b, dtype=torch.int64, device="cuda")
+    arena_b = arena_init.clone()
+    dh.dh_scatter_aoas(plan_b, arena_b, table_b, nq, h, stream)
+    (dh.dh_offload_bind_staged if staged else dh.dh_offload_bind)(plan_b, addrs_b, nq, h)
+    like = lambda t: torch.empty_like(t) if t is not None else None
+    u1b, u2b, accb = like(U1), like(U2), like(ACC)
+    dt_b = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam_b = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream_b = torch.cuda.Stream()
+    run_b = lambda s: dh.dh_offload_run(plan_b, spec["scheme"], spec["rk"], 1, arena_b, u1b, u2b, accb, dt_b, lam_b,
+                                        spec["cfl"], 0.1, nq_back, s)
+    seq_ms = timed(lambda: (run_a(1), run_b(stream)), 3)
+    fork, join = torch.cuda.Event(), torch.cuda.Event()
+
+    def both():
+        fork.record(stream)
+        stream_b.wait_event(fork)
+        run_a(1)
+        run_b(stream_b)
+        join.record(stream_b)
+        stream.wait_event(join)
+    par_ms = timed(both, 3)
+    stream.synchronize()
+    stream_b.synchronize()
+    plan_b.close()
+    del hbuf_b, table_b, arena_b, u1b, u2b, accb
+    return {"sequential_ms": seq_ms, "concurrent_ms": par_ms, "overlap_gain": seq_ms / par_ms,
+            "total_over_compute_1_step_concurrent": par_ms / (2 * compute_ms_per_step)}
 
 
 def our_arm(args, rank, world, local_rank):

@@ -265,6 +265,19 @@ dh_status dh_scatter_aoas(dh_plan* plan, const double* arena, double* const* aos
  *   (nq_back = N returns the evolved state; N + M also the material).
  *   Asynchronous on `stream`; the blocks hold the result once it completes. */
 dh_status dh_offload_bind(dh_plan* plan, const double* const* blocks, int32_t nq, int32_t aos_halo);
+/* dh_offload_bind_staged: as dh_offload_bind for page-locked HOST blocks, but each
+ *   run moves them with the copy engine instead of SM loads over NVLink-C2C: the
+ *   span from the lowest block to the end of the highest is copied into a device
+ *   staging buffer with one cudaMemcpyAsync, gathered from there, and after the
+ *   scatter the whole span is copied back with one cudaMemcpyAsync.  So the
+ *   span should be one page-locked allocation, and nothing outside the blocks
+ *   within it may change while a run is in flight (it is written back as it
+ *   was read).  The copies use no SM time, so the kernels of a second problem
+ *   on another stream run while they are in flight.  The plan allocates the
+ *   staging buffer (span bytes) once, and again only for a larger span.
+ *   DH_EINVAL if a block is not page-locked host memory or the span exceeds
+ *   4x the blocks' bytes. */
+dh_status dh_offload_bind_staged(dh_plan* plan, const double* const* blocks, int32_t nq, int32_t aos_halo);
 dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_steps, double* arena, double* u1,
                          double* u2, double* acc, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
                          int32_t nq_back, void* stream);

@@ -409,6 +409,7 @@ dh_status dh_plan_destroy(dh_plan* plan) {
   if (plan->d_lvl) cudaFree(plan->d_lvl);
   if (plan->d_aunits) cudaFree(plan->d_aunits);
   if (plan->d_offload) cudaFree(plan->d_offload);
+  if (plan->d_stage) cudaFree(plan->d_stage);
   if (plan->d_amr_oct) cudaFree(plan->d_amr_oct);
   if (plan->d_w) cudaFree(plan->d_w);
   if (plan->d_amr_reflux) cudaFree(plan->d_amr_reflux);

@@ -106,6 +106,12 @@ struct dh_plan {
   // offload mode: device copy of the bound block pointer table (dh_offload_bind)
   double** d_offload = nullptr;
   int offload_nq = 0, offload_halo = 0;
+  // staged offload (dh_offload_bind_staged): the host span of the blocks is copied
+  // to / from a device staging buffer by the copy engine; the table points into it
+  bool offload_staged = false;
+  char* d_stage = nullptr;
+  size_t stage_cap = 0, stage_bytes = 0;
+  char* stage_host = nullptr;
   int debug_flags = 0;    // test hooks (bit 0: TMA barriers armed but no copy issued)
   // scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter,
   // [2] error flags (bit 0: a bounded TMA wait gave up), [3] unused

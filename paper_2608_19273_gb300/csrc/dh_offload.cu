@@ -13,10 +13,18 @@
 //   dh_offload_bind: validates that each of the K block pointers is device
 //     accessible (device, managed, or page-locked host memory) and keeps a
 //     device copy of the pointer table in the plan.
+//   dh_offload_bind_staged: for page-locked host blocks that lie in one span of
+//     host memory: the run copies that span to a device staging buffer with
+//     one cudaMemcpyAsync (the copy engine, no SM time, so a second problem's
+//     kernels can run meanwhile), gathers from the staged copy at HBM speed,
+//     scatters into it and copies the span back with one cudaMemcpyAsync.
 //   dh_offload_run : gather (all nq quantities of every interior voxel) ->
 //     n_steps Runge-Kutta steps on the device arena -> scatter of the first
 //     nq_back quantities, all asynchronous on one stream.
 #include <nvtx3/nvToolsExt.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "dh_internal.cuh"
 
@@ -54,6 +62,50 @@ dh_status dh_offload_bind(dh_plan* plan, const double* const* blocks, int32_t nq
   if (e != cudaSuccess) return cuda_error(e, "dh_offload_bind: table upload");
   plan->offload_nq = nq;
   plan->offload_halo = aos_halo;
+  plan->offload_staged = false;
+  return DH_OK;
+}
+
+dh_status dh_offload_bind_staged(dh_plan* plan, const double* const* blocks, int32_t nq, int32_t aos_halo) {
+  dh_status st = dh_offload_bind(plan, blocks, nq, aos_halo);  // validation and the in-place table
+  if (st != DH_OK) return st;
+  uintptr_t lo = UINTPTR_MAX, hi = 0;
+  size_t total = 0;
+  std::vector<double*> staged(plan->K);
+  for (int k = 0; k < plan->K; ++k) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, blocks[k]) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();
+      set_error("dh_offload_bind_staged: block %d is not page-locked host memory", k);
+      return DH_EINVAL;
+    }
+    const int p = plan->h_patches[k].p, n = p + 2 * aos_halo;
+    const size_t bytes = sizeof(double) * (size_t)nq * (size_t)n * (size_t)n * (size_t)(plan->dim == 3 ? n : 1);
+    lo = std::min(lo, (uintptr_t)blocks[k]);
+    hi = std::max(hi, (uintptr_t)blocks[k] + bytes);
+    total += bytes;
+  }
+  const size_t span = hi - lo;
+  if (span > 4 * total) {
+    set_error("dh_offload_bind_staged: the blocks span %zu bytes for %zu bytes of blocks (more than 4x); "
+              "use dh_offload_bind", span, total);
+    return DH_EINVAL;
+  }
+  if (plan->stage_cap < span) {
+    if (plan->d_stage) cudaFree(plan->d_stage);
+    plan->d_stage = nullptr;
+    plan->stage_cap = 0;
+    cudaError_t e = cudaMalloc(&plan->d_stage, span);
+    if (e != cudaSuccess) { plan->d_stage = nullptr; return cuda_error(e, "dh_offload_bind_staged: staging buffer"); }
+    plan->stage_cap = span;
+  }
+  for (int k = 0; k < plan->K; ++k)
+    staged[k] = reinterpret_cast<double*>(plan->d_stage + ((uintptr_t)blocks[k] - lo));
+  cudaError_t e = cudaMemcpy(plan->d_offload, staged.data(), sizeof(double*) * plan->K, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "dh_offload_bind_staged: table upload");
+  plan->stage_host = reinterpret_cast<char*>(lo);
+  plan->stage_bytes = span;
+  plan->offload_staged = true;
   return DH_OK;
 }
 
@@ -70,6 +122,10 @@ dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_st
   const int nq = plan->offload_nq, h = plan->offload_halo;
   double* mat = plan->nm > 0 ? arena + (int64_t)plan->nq * plan->var_stride : nullptr;
   nvtxRangePushA("dh offload gather");
+  if (plan->offload_staged) {
+    cudaError_t e = cudaMemcpyAsync(plan->d_stage, plan->stage_host, plan->stage_bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { nvtxRangePop(); return cuda_error(e, "dh_offload_run: staging copy in"); }
+  }
   dh_status st = aoas_move(plan, true, plan->d_offload, nq, 0, nq, h, arena, s);
   nvtxRangePop();
   if (st != DH_OK) return st;
@@ -84,6 +140,9 @@ dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_st
   }
   nvtxRangePushA("dh offload scatter");
   if (nq_back > 0) st = aoas_move(plan, false, plan->d_offload, nq, 0, nq_back, h, arena, s);
+  if (st == DH_OK && plan->offload_staged && nq_back > 0)
+    st = cuda_error(cudaMemcpyAsync(plan->stage_host, plan->d_stage, plan->stage_bytes, cudaMemcpyDeviceToHost, s),
+                    "dh_offload_run: staging copy out");
   nvtxRangePop();
   return st;
 }

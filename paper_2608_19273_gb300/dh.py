@@ -25,7 +25,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 # Every symbol that include/dh.h declares (checked by the CPU tests).
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fv_muscl", "patch_update_fd_ko",
            "max_wave_speed",
-           "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_run", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
+           "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_bind_staged", "dh_offload_run", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
            "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
@@ -58,6 +58,7 @@ def lib():
         L.dh_gather_aoas.argtypes = [vp, vp, i32, i32, vp, vp]
         L.dh_scatter_aoas.argtypes = [vp, vp, vp, i32, i32, vp]
         L.dh_offload_bind.argtypes = [vp, vp, i32, i32]
+        L.dh_offload_bind_staged.argtypes = [vp, vp, i32, i32]
         L.dh_offload_run.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, d, d, i32, vp]
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
         L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
@@ -284,6 +285,14 @@ def dh_offload_bind(plan, block_addrs, nq, aos_halo):
     table = (ctypes.c_void_p * len(addrs))(*addrs)
     _check(lib().dh_offload_bind(plan.handle, ctypes.cast(table, ctypes.c_void_p), int(nq), int(aos_halo)),
            "dh_offload_bind")
+
+
+def dh_offload_bind_staged(plan, block_addrs, nq, aos_halo):
+    """Bind page-locked host blocks for runs that move their span with the copy engine."""
+    addrs = [b if isinstance(b, int) else b.data_ptr() for b in block_addrs]
+    table = (ctypes.c_void_p * len(addrs))(*addrs)
+    _check(lib().dh_offload_bind_staged(plan.handle, ctypes.cast(table, ctypes.c_void_p), int(nq), int(aos_halo)),
+           "dh_offload_bind_staged")
 
 
 def dh_offload_run(plan, scheme, rk, n_steps, arena, u1, u2, acc, dt_dev, lam_dev, cfl, sigma_ko, nq_back,

@@ -41,8 +41,8 @@ def blocks_from_arena(mesh, arena_rows, nq, halo, seed):
     return blocks
 
 
-def run_offload(torch, plan, mesh, views, nq, halo, n_q, scheme, rk, steps, cfl, nq_back):
-    dh.dh_offload_bind(plan, views, nq, halo)
+def run_offload(torch, plan, mesh, views, nq, halo, n_q, scheme, rk, steps, cfl, nq_back, staged=False):
+    (dh.dh_offload_bind_staged if staged else dh.dh_offload_bind)(plan, views, nq, halo)
     arena = torch.zeros(nq * mesh.var_stride, dtype=torch.float64, device="cuda")
     u1 = torch.zeros(n_q * mesh.var_stride, dtype=torch.float64, device="cuda")
     u2 = torch.zeros_like(u1) if rk >= 3 else None
@@ -54,7 +54,8 @@ def run_offload(torch, plan, mesh, views, nq, halo, n_q, scheme, rk, steps, cfl,
     return float(dt.item())
 
 
-def test_offload_euler3d_ssprk3(orc):
+@pytest.mark.parametrize("staged", [False, True])
+def test_offload_euler3d_ssprk3(orc, staged):
     torch = require_cuda()
     mesh = synth.euler3d_amr_mesh(scale=4)
     q = orc.prim2con(3, synth.euler_prims(mesh, 41), mesh.var_stride)
@@ -66,7 +67,7 @@ def test_offload_euler3d_ssprk3(orc):
     aoas.scatter_aoas(mesh.patches, ref_q.ravel(), ref_blocks, 5, halo, mesh.var_stride, 3)
     with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
         buf, views = pinned_blocks(torch, mesh, 5, halo, blocks, 3)
-        dt = run_offload(torch, plan, mesh, views, 5, halo, 5, FV, 3, 3, 0.4, 5)
+        dt = run_offload(torch, plan, mesh, views, 5, halo, 5, FV, 3, 3, 0.4, 5, staged)
     # compare through the oracle gather (interior) and bitwise on the halo entries
     got_arena = aoas.gather_aoas(mesh.patches, [v.numpy() for v in views], 5, halo, mesh.var_stride, 3)
     assert_parity(got_arena.reshape(5, -1), ref_q, voxel_mask(mesh), what="offload euler3d")
@@ -122,3 +123,62 @@ def test_offload_bind_rejects_pageable_memory():
         arena = torch.zeros(5 * mesh.var_stride, dtype=torch.float64, device="cuda")
         with pytest.raises(dh.DhError):   # nothing bound
             dh.dh_offload_run(plan, FV, 3, 1, arena, None, None, None, None, None, 0.0, 0.1, 5)
+
+
+@pytest.mark.parametrize("staged", [False, True])
+def test_two_offload_problems_on_two_streams(orc, staged):
+    """Two independent problems (own plans, host blocks and device buffers) enqueued on two streams,
+    so that one's host transfers can overlap the other's compute: each ends bitwise equal to the
+    same problem advanced alone, and agrees with the oracle."""
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=4)
+    qs = [orc.prim2con(3, synth.euler_prims(mesh, 51 + i), mesh.var_stride) for i in range(2)]
+    halo, steps = 1, 2
+    res = {}
+    for mode in ("alone", "together"):
+        plans = [dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) for _ in range(2)]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+        bufs, views, dev = [], [], []
+        for i in range(2):
+            b, v = pinned_blocks(torch, mesh, 5, halo, blocks_from_arena(mesh, qs[i], 5, halo, 60 + i), 70 + i)
+            bufs.append(b)
+            views.append(v)
+            (dh.dh_offload_bind_staged if staged else dh.dh_offload_bind)(plans[i], v, 5, halo)
+            z = lambda: torch.zeros(5 * mesh.var_stride, dtype=torch.float64, device="cuda")
+            dev.append((z(), z(), z(), z(), torch.zeros(1, dtype=torch.float64, device="cuda"),
+                        torch.zeros(1, dtype=torch.float64, device="cuda")))
+        torch.cuda.synchronize()
+        for i in range(2):
+            arena, u1, u2, acc, dt, lam = dev[i]
+            s = streams[0] if mode == "alone" else streams[i]
+            dh.dh_offload_run(plans[i], FV, 3, steps, arena, u1, u2, acc, dt, lam, 0.4, 0.1, 5, s)
+            if mode == "alone":
+                s.synchronize()
+        torch.cuda.synchronize()
+        res[mode] = (bufs, views)
+        for p in plans:
+            p.close()
+    for i in range(2):
+        assert torch.equal(res["alone"][0][i], res["together"][0][i]), f"problem {i} differs when overlapped"
+    ref = qs[0].copy()
+    orc.rk_steps(FV, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=steps, cfl=0.4)
+    got = aoas.gather_aoas(mesh.patches, [v.numpy() for v in res["together"][1][0]], 5, halo, mesh.var_stride, 3)
+    assert_parity(got.reshape(5, -1), ref, voxel_mask(mesh), what="overlapped offload problem 0")
+
+
+def test_staged_bind_rejections():
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=8)
+    lens = [aoas.block_len(int(pt["p"]), 3, 5, 1) for pt in mesh.patches]
+    with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
+        dev_blocks = [torch.zeros(n, dtype=torch.float64, device="cuda") for n in lens]
+        with pytest.raises(dh.DhError):          # device memory, not host blocks
+            dh.dh_offload_bind_staged(plan, dev_blocks, 5, 1)
+        # page-locked blocks 9x the largest block apart: the span is more than 4x the blocks
+        gap = 9 * max(lens)
+        buf = torch.zeros(gap * len(lens), dtype=torch.float64).pin_memory()
+        views = [buf[k * gap:k * gap + n] for k, n in enumerate(lens)]
+        with pytest.raises(dh.DhError):
+            dh.dh_offload_bind_staged(plan, views, 5, 1)
+        dense = [buf[int(a):int(a) + n] for a, n in zip(np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)]
+        dh.dh_offload_bind_staged(plan, dense, 5, 1)   # back to back: accepted
