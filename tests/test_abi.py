@@ -59,6 +59,12 @@ def test_plan_validation_rejects(libdh, mutate, code):
     assert len(dh.lib().dh_last_error()) > 0
 
 
+def test_empty_patch_list_rejected(libdh):
+    mesh = synth.euler3d_amr_mesh(scale=8)
+    assert _create(mesh.patches[:0].copy(), vs=mesh.var_stride) == dh.DH_EINVAL
+    assert b"empty" in dh.lib().dh_last_error()
+
+
 def test_plan_validation_dim_and_pde(libdh):
     mesh = synth.euler3d_amr_mesh(scale=8)
     assert _create(mesh.patches.copy(), pde=2, dim=3, vs=mesh.var_stride) == dh.DH_EINVAL

@@ -79,8 +79,10 @@ def test_offload_euler3d_ssprk3(orc, staged):
     assert abs(dt - dts[-1]) <= 1e-14 * dts[-1]
 
 
-def test_offload_wave_rk4_with_material(orc):
-    """Wave system: 6 quantities per voxel (5 evolved + c); only the 5 evolved ones are written back."""
+@pytest.mark.parametrize("staged", [False, True])
+def test_offload_wave_rk4_with_material(orc, staged):
+    """Wave system: 6 quantities per voxel (5 evolved + c); only the 5 evolved ones are written back
+    (staged: the whole span goes back, the material and halos as they were read)."""
     torch = require_cuda()
     w = synth.workload("wave3d", scale=8)
     mesh = w.mesh
@@ -93,20 +95,21 @@ def test_offload_wave_rk4_with_material(orc):
                  cfl=w.cfl, sigma=0.1, params=w.params)
     with dh.Plan(synth.PDE_WAVE3D, 3, mesh.patches, 3, mesh.var_stride, w.params) as plan:
         buf, views = pinned_blocks(torch, mesh, 6, halo, blocks, 4)
-        run_offload(torch, plan, mesh, views, 6, halo, 5, FD, 4, 2, w.cfl, 5)
+        run_offload(torch, plan, mesh, views, 6, halo, 5, FD, 4, 2, w.cfl, 5, staged)
     got = aoas.gather_aoas(mesh.patches, [v.numpy() for v in views], 6, halo, mesh.var_stride, 3).reshape(6, -1)
     assert_parity(got[:5], ref_q, voxel_mask(mesh), what="offload wave")
     assert np.array_equal(got[5][voxel_mask(mesh)], mat[0][voxel_mask(mesh)]), "material must come back unchanged"
 
 
-def test_offload_zero_steps_round_trip():
+@pytest.mark.parametrize("staged", [False, True])
+def test_offload_zero_steps_round_trip(staged):
     torch = require_cuda()
     mesh = synth.make_mesh([synth.Level((2, 2, 2), 8, 1.0 / 16, 0)], dim=3)
     rng = np.random.default_rng(5)
     blocks = [rng.standard_normal(aoas.block_len(8, 3, 5, 2)) for _ in mesh.patches]
     with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
         buf, views = pinned_blocks(torch, mesh, 5, 2, blocks, 6)
-        run_offload(torch, plan, mesh, views, 5, 2, 5, FV, 3, 0, 0.0, 5)
+        run_offload(torch, plan, mesh, views, 5, 2, 5, FV, 3, 0, 0.0, 5, staged)
         for k, v in enumerate(views):
             assert np.array_equal(v.numpy(), blocks[k])
 
