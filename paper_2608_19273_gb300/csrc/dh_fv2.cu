@@ -130,7 +130,9 @@ struct Fv2Tile {
       double* S = sgn == 0 ? sp : sm;
       if (!S) continue;
       const int idx = sgn == 0 ? ip : im;
-      const double h = sgn == 0 ? 0.5 : -0.5;
+      // +-1/2 from the kernel parameters: with a literal the compiler splits the FMA into
+      // a product and a plain add
+      const double h = sgn == 0 ? P.half : -P.half;
       double u[NV], W[NW > 0 ? NW : 1], F[N];
 #pragma unroll
       for (int v = 0; v < N; ++v) u[v] = fma(h, sig[v], q[v]);
@@ -167,6 +169,9 @@ struct Fv2Tile {
     const int p = pt.p;
     const int t = threadIdx.x;
     const int tx = t % MX, ty = (t / MX) % MY, tz = t / (MX * MY);
+    // -1/(2 dx): one IEEE division per CTA, shared (one voxel per thread would pay it per voxel)
+    __shared__ double s_cL;
+    if (t == 0) s_cL = -0.5 / pt.dx;
     // stage the tile and its two-voxel face halos
     for (int s = t; s < MSLOT; s += MNT) {
       int x, y, z;
@@ -227,7 +232,7 @@ struct Fv2Tile {
     }
     // update
     const double dt = *A.dt_dev;
-    const double cL = -0.5 / pt.dx;
+    const double cL = s_cL;
     const double gdt = A.g * dt, ddt = A.d * dt;
     const bool b1 = A.b == 1.0;
     const int64_t e = pt.offset + ((int64_t)(w.z0 + tz) * p + (w.y0 + ty)) * p + (w.x0 + tx);

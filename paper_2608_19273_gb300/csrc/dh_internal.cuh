@@ -16,6 +16,7 @@ namespace dh {
 // adds and multiplies are issued as DFMA (see dh_pde.cuh).
 struct DevParams {
   double one, mone, zero;
+  double half;    // 0.5 as a run-time value (an FMA with it stays one FMA)
   double gamma;   // Euler ratio of specific heats
   double gm1;     // gamma - 1
   double Gamma;   // SRHD adiabatic index
@@ -141,6 +142,7 @@ inline void finish_params(DevParams& P) {
   P.one = 1.0;
   P.mone = -1.0;
   P.zero = 0.0;
+  P.half = 0.5;
   P.gm1 = P.gamma - 1.0;
   P.Gq = P.Gamma / (P.Gamma - 1.0);
 }
