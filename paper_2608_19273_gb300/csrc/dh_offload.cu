@@ -34,6 +34,7 @@ extern "C" {
 
 dh_status dh_offload_bind(dh_plan* plan, const double* const* blocks, int32_t nq, int32_t aos_halo) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  plan->offload_nq = 0;  // a failed bind leaves the plan unbound
   if (!blocks) { set_error("dh_offload_bind: blocks is NULL"); return DH_EINVAL; }
   if (nq < 1 || nq > 256) { set_error("dh_offload_bind: nq = %d outside [1, 256]", nq); return DH_EINVAL; }
   if (nq < plan->nq + plan->nm) {
@@ -69,6 +70,7 @@ dh_status dh_offload_bind(dh_plan* plan, const double* const* blocks, int32_t nq
 dh_status dh_offload_bind_staged(dh_plan* plan, const double* const* blocks, int32_t nq, int32_t aos_halo) {
   dh_status st = dh_offload_bind(plan, blocks, nq, aos_halo);  // validation and the in-place table
   if (st != DH_OK) return st;
+  plan->offload_nq = 0;  // unbound until the staged table is in place (a failed bind leaves no binding)
   uintptr_t lo = UINTPTR_MAX, hi = 0;
   size_t total = 0;
   std::vector<double*> staged(plan->K);
@@ -106,6 +108,7 @@ dh_status dh_offload_bind_staged(dh_plan* plan, const double* const* blocks, int
   plan->stage_host = reinterpret_cast<char*>(lo);
   plan->stage_bytes = span;
   plan->offload_staged = true;
+  plan->offload_nq = nq;
   return DH_OK;
 }
 
@@ -113,7 +116,10 @@ dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_st
                          double* u2, double* acc, double* dt_dev, double* lam_dev, double cfl, double sigma_ko,
                          int32_t nq_back, void* stream) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (!plan->d_offload) { set_error("dh_offload_run: no blocks bound (dh_offload_bind)"); return DH_EINVAL; }
+  if (!plan->d_offload || plan->offload_nq <= 0) {
+    set_error("dh_offload_run: no blocks bound (dh_offload_bind or a successful dh_offload_bind_staged)");
+    return DH_EINVAL;
+  }
   if (!arena || ((uintptr_t)arena & 7) != 0) { set_error("dh_offload_run: arena is NULL or misaligned"); return DH_EINVAL; }
   if (n_steps < 0 || n_steps > 1000000) { set_error("dh_offload_run: n_steps out of range"); return DH_EINVAL; }
   if (nq_back < 0 || nq_back > plan->offload_nq) { set_error("dh_offload_run: nq_back outside [0, nq]"); return DH_EINVAL; }

@@ -183,5 +183,10 @@ def test_staged_bind_rejections():
         views = [buf[k * gap:k * gap + n] for k, n in enumerate(lens)]
         with pytest.raises(dh.DhError):
             dh.dh_offload_bind_staged(plan, views, 5, 1)
+        # a failed bind leaves the plan unbound: a run is refused
+        z = lambda: torch.zeros(5 * mesh.var_stride, dtype=torch.float64, device="cuda")
+        one = lambda: torch.zeros(1, dtype=torch.float64, device="cuda")
+        with pytest.raises(dh.DhError):
+            dh.dh_offload_run(plan, FV, 3, 1, z(), z(), z(), None, one(), one(), 0.0, 0.1, 5)
         dense = [buf[int(a):int(a) + n] for a, n in zip(np.concatenate([[0], np.cumsum(lens)[:-1]]), lens)]
         dh.dh_offload_bind_staged(plan, dense, 5, 1)   # back to back: accepted
