@@ -89,11 +89,19 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   const double G = A.G;
   const double D = q[0], E = q[4] + q[0];
   const double S2 = fma(q[1], q[1], fma(q[2], q[2], q[3] * q[3]));
-  const double S = sqrt(S2);
-  const double p_lo = S > E ? S - E : 0.0;  // max(0, S - E), and +0 (never -0) otherwise
-  const double cold = fmax(fma(1.0 + 1e-8, p_lo, 1e-300), (G - 1.0) * q[4]);
+  // p_lo = max(0, |S| - E) (+0, never -0).  For E > 0 and |S|^2 < E^2 (1 - 2^-50) the
+  // correctly rounded |S| lies below E whatever the roundings of that bound, so p_lo = 0
+  // without the square root (the usual case: physical states have |S| < E); the learned
+  // seed needs |S| itself.
+  double S = 0.0, p_lo = 0.0;
+  if (w || !(E > 0.0 && S2 < E * E * (1.0 - 0x1p-50))) {
+    S = sqrt(S2);
+    p_lo = S > E ? S - E : 0.0;
+  }
+  // the cold seed is formed only where it is used
+  auto cold = [&]() { return fmax(fma(1.0 + 1e-8, p_lo, 1e-300), (G - 1.0) * q[4]); };
   const bool have_prev = A.p_prev != nullptr;
-  double s1, s2;
+  double s1;
   bool have2;
   if (w) {
     float x[3], h1[32], h2[32];
@@ -101,12 +109,10 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
     const float y = mlp_forward(w, x, h1, h2);
     const double ps = E * exp((double)y);
     const double lo = p_lo * (1.0 + 1e-12);
-    s1 = ps > lo ? ps : cold;
-    s2 = have_prev ? A.p_prev[e] : cold;
+    s1 = ps > lo ? ps : cold();
     have2 = true;
   } else {
-    s1 = have_prev ? A.p_prev[e] : cold;
-    s2 = cold;
+    s1 = have_prev ? A.p_prev[e] : cold();
     have2 = have_prev;
   }
   double p;
@@ -116,11 +122,13 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   if (it1 <= 0) {
     int it2 = 0;
     if (have2) {
+      // second seed: the previous pressure after the learned one, else the cold seed
+      const double s2 = (w && have_prev) ? A.p_prev[e] : cold();
       it2 = srhd_newton_dev(A.gf, D, S2, E, p_lo, s2, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
       total += it2 > 0 ? it2 : -it2;
     }
     if (have2 && it2 > 0) st = 1;
-    else { st = 2; p = have_prev ? A.p_prev[e] : cold; }
+    else { st = 2; p = have_prev ? A.p_prev[e] : cold(); }
   }
   const double rEp = recip_nr(E + p);
   const double vx = q[1] * rEp, vy = q[2] * rEp, vz = q[3] * rEp;
