@@ -390,6 +390,10 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     e = cudaMemcpy(plan->d_aunits, aunits.data(), sizeof(int2) * aunits.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && plan->tma_ok) e = cudaMalloc(&plan->d_lvl, sizeof(int2) * K);
   if (e == cudaSuccess && plan->tma_ok) e = cudaMemcpy(plan->d_lvl, lvl.data(), sizeof(int2) * K, cudaMemcpyHostToDevice);
+  // cudaMemset, and cudaMemcpy from pageable host memory, can return before the device
+  // holds the data (they run on the legacy default stream); the first launch may come on
+  // a non-blocking stream, so wait for them here
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
     dh_status st = cuda_error(e, "dh_plan_create");
     dh_plan_destroy(plan);
@@ -540,6 +544,7 @@ dh_status dh_plan_errors(dh_plan* plan, uint32_t* flags, int32_t clear) {
   *flags = (uint32_t)v;
   if (clear) {
     e = cudaMemset(plan->d_red + 2, 0, sizeof(v));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);  // cleared before any later launch on any stream
     if (e != cudaSuccess) return cuda_error(e, "dh_plan_errors");
   }
   return DH_OK;

@@ -60,6 +60,9 @@ dh_status dh_offload_bind(dh_plan* plan, const double* const* blocks, int32_t nq
     if (e != cudaSuccess) { plan->d_offload = nullptr; return cuda_error(e, "dh_offload_bind: cudaMalloc"); }
   }
   cudaError_t e = cudaMemcpy(plan->d_offload, blocks, sizeof(double*) * plan->K, cudaMemcpyHostToDevice);
+  // (a copy from pageable memory may return before the device holds it: wait, a run may
+  // follow on a non-blocking stream)
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) return cuda_error(e, "dh_offload_bind: table upload");
   plan->offload_nq = nq;
   plan->offload_halo = aos_halo;
@@ -104,6 +107,7 @@ dh_status dh_offload_bind_staged(dh_plan* plan, const double* const* blocks, int
   for (int k = 0; k < plan->K; ++k)
     staged[k] = reinterpret_cast<double*>(plan->d_stage + ((uintptr_t)blocks[k] - lo));
   cudaError_t e = cudaMemcpy(plan->d_offload, staged.data(), sizeof(double*) * plan->K, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) return cuda_error(e, "dh_offload_bind_staged: table upload");
   plan->stage_host = reinterpret_cast<char*>(lo);
   plan->stage_bytes = span;
