@@ -118,10 +118,12 @@ def _code_only(text):
 
 def kernel_source_hash(name):
     """Hash of the code (comments excluded) of a workload's dominant kernel: its .cu files, the
-    shared device headers and the C header; identifies the kernel a stored ncu capture describes."""
+    shared device headers, the plan code that builds its work lists and the C header; identifies
+    the kernel a stored ncu capture describes."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2608_19273_gb300", "csrc")
-    files = [os.path.join(csrc, f) for f in sorted(KERNEL_SOURCES[name] + ["dh_internal.cuh", "dh_pde.cuh"])]
+    # dh_api.cu builds the tile work lists the launches run
+    files = [os.path.join(csrc, f) for f in sorted(KERNEL_SOURCES[name] + ["dh_internal.cuh", "dh_pde.cuh", "dh_api.cu"])]
     files.append(os.path.join(ROOT, "include", "dh.h"))
     h = hashlib.sha256()
     for f in files:

@@ -281,7 +281,16 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   finish_params(P);
   // Tile work lists: 16x16 columns for p % 16 == 0, groups of four 8x8 columns
   // (same p) otherwise; largest work first.  List 1 also splits the z-march of
-  // the 16x16 columns into chunks of at most 16 planes (more, shorter CTAs).
+  // the 16x16 columns into chunks of at most 16 planes (more, shorter CTAs), and
+  // fills a thin last wave (two CTAs resident per SM) by splitting the cheapest
+  // full columns into two half-height chunks, which then come last.
+  int n_sm = 152;
+  {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+      n_sm = 152;
+    cudaGetLastError();
+  }
   std::vector<Work> lists[2];
   for (int zs = 0; zs < 2; ++zs) {
     std::vector<Work>& work = lists[zs];
@@ -322,6 +331,23 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
       return (long long)(w.cls == 0 ? 256 : 64 * ng) * w.pz;
     };
     std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
+    if (zs == 1 && dim == 3) {
+      const long long R = 2LL * n_sm;
+      long long m = (R - (long long)work.size() % R) % R;
+      std::vector<Work> halves;
+      for (int i = (int)work.size() - 1; i >= 0 && m > 0; --i) {
+        Work& w = work[i];
+        if (w.cls != 0 || w.pz < 16) continue;
+        Work upper = w;
+        w.pz = w.pz / 2;
+        upper.pz = upper.pz - w.pz;
+        upper.z0 = w.z0 + w.pz;
+        halves.push_back(upper);
+        --m;
+      }
+      work.insert(work.end(), halves.begin(), halves.end());
+      std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
+    }
     for (const Work& w : work) plan->has_cls[w.cls] = true;
     plan->n_work_z[zs] = (int)work.size();
   }
