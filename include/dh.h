@@ -361,7 +361,8 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
                       const double* dt_dev, int32_t reps, const char* cache_path, int32_t* choice_out,
                       float* times_out, void* stream);
 /* Select a variant directly: fv_var 0..3 (bit 0: ring before the barrier,
- * bit 1: two CTAs per SM), fv_zs 0..1 (z-chunks of <= 16 planes), fd_var
+ * bit 1: two CTAs per SM), fv_zs 0..1 (tile list 1: z-chunks of <= 16 planes, and a
+ * thin last wave filled with half-height chunks of the cheapest columns), fd_var
  * 0, 2, 4 or 6 (bit 1: two CTAs per SM; bit 2: TMA staging, which needs every
  * run of equal-size patches to be stored back to back with its face
  * neighbours inside the run; DH_EUNSUPPORTED otherwise), or, for systems of
