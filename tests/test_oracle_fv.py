@@ -184,3 +184,29 @@ def test_euler2d_runs_and_conserves(orc):
     dts = orc.rk_steps(FV, 2, 2, mesh.patches, 1, mesh.var_stride, q, rk=1, steps=10, cfl=0.4)
     assert np.all(dts > 0) and np.all(np.isfinite(q))
     assert np.max(np.abs(q.sum(axis=1) - s0) / np.abs(q).sum(axis=1)) < 1e-13
+
+
+def test_ssprk3_stage_sum_form_is_the_shu_osher_step(orc):
+    """The SSP-RK3 step in the Butcher ("stage-sum") form the GPU path evaluates when given acc,
+    u1 = q + k0, u2 = q + (k0 + k1)/4, q' = q + (k0 + k1)/6 + 2 k2/3 with k_i = dt L(u_i), built here
+    from the oracle's own L, equals the oracle's Shu-Osher step to rounding."""
+    mesh = single_level((2, 2, 2), 8, 1.0 / 16)
+    q = _euler_state(orc, mesh, 23)
+    dt = 2e-3
+    ref = q.copy()
+    orc.rk_steps(FV, synth.PDE_EULER3D, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=1, dt_fixed=dt)
+
+    def k(u):  # dt L(u): a stage with a = b = 0, g = 1
+        out = np.zeros_like(u)
+        orc.stage(FV, synth.PDE_EULER3D, 3, mesh.patches, 1, mesh.var_stride, u, out=out, dt=dt, a=0, b=0, g=1)
+        return out
+    k0 = k(q)
+    u1 = q + k0
+    k1 = k(u1)
+    u2 = q + (k0 + k1) / 4
+    k2 = k(u2)
+    got = q + (k0 + k1) / 6 + 2 * k2 / 3
+    m = voxel_mask(mesh)
+    scale = np.abs(ref[:, m]).max(axis=1, keepdims=True)
+    assert np.max(np.abs(got[:, m] - ref[:, m]) / scale) < 1e-14
+    assert not np.allclose(ref[:, m], q[:, m])   # the step changed the state

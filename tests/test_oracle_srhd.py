@@ -140,3 +140,36 @@ def test_adam_first_step_closed_form(orc):
     m, v = np.zeros(4), np.zeros(4)
     orc.adam(w, m, v, g, 1, lr=1e-3)
     assert np.max(np.abs(w + 1e-3 * g / (np.abs(g) + 1e-8))) < 1e-18
+
+
+def test_newton_step_forms_agree(orc):
+    """The con2prim Newton step in the form the GPU evaluates (y f and y^2 f' with y = E + p and
+    q = sqrt(y^2 - S^2), one reciprocal) equals the textbook step f / f' to rounding, on i.i.d.
+    states and pressures around the solution; and the oracle's converged pressure is a root of it."""
+    w = iid_prims(4000, 9)
+    n = w.shape[1]
+    cons = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    G = 5.0 / 3.0
+    gf = (G - 1) / G
+    D, E = cons[0], cons[4] + cons[0]
+    S2 = cons[1] ** 2 + cons[2] ** 2 + cons[3] ** 2
+    rng = np.random.default_rng(10)
+    for rel in (1e-3, 3e-2, 0.3):
+        p = w[4] * (1 + rel * rng.uniform(-1, 1, n))
+        y = E + p
+        a = S2 / y ** 2
+        f = gf * (y - S2 / y - D * np.sqrt(1 - a)) - p
+        fp = gf * (1 + a - D * S2 / (y ** 3 * np.sqrt(1 - a))) - 1
+        q = np.sqrt(y * y - S2)
+        num = y * (gf * q * (q - D) - p * y)
+        den = gf * S2 * (q - D) / q + (gf - 1) * y * y
+        step_text, step_gpu = f / fp, num / den
+        # both forms cancel digits for ultra-relativistic states (S^2/y^2 near 1); the steps agree
+        # far below the stopping tolerance 1e-12 p
+        assert np.all(np.abs(step_gpu - step_text) <= 1e-9 * np.abs(step_text) + 1e-12 * p)
+    prim, st, _, _ = orc.con2prim(cons, n)
+    assert np.all(st == 0)
+    ps = prim[4]
+    y = E + ps
+    q = np.sqrt(y * y - S2)
+    assert np.all(np.abs(gf * q * (q - D) - ps * y) <= 1e-11 * y * ps)
