@@ -1,0 +1,157 @@
+"""Pins of the FV oracle against hand-worked examples (CPU only).
+
+Each fixture under ``golden/`` is a two-state Riemann problem on a periodic
+row of 16 voxels, worked out by hand in exact rational arithmetic: the
+physical fluxes, the Rusanov face fluxes (Sec. II-A, Eq. 3 with the Rusanov
+reading) and the four voxels next to the two faces after one forward-Euler
+stage.  The oracle runs the same stage along every axis of a 2D or 3D
+patch row and must reproduce those values to rounding, while every other
+voxel stays bitwise unchanged.  A dropped flux term (the p u of the energy
+flux, the p of the normal momentum flux), a wrong dissipation speed, a wrong
+sign or a transposed velocity component moves at least one listed value."""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from helpers import arena, from_grid, single_level, to_grid
+
+FV = 0
+EULER2D, EULER3D, SRHD3D = 2, 3, 5
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def load(name):
+    """Fixture -> {section: {key: [Fraction, ...]}}; section "" holds the global keys."""
+    out, sec = {"": {}}, ""
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            if line.startswith("[") and line.endswith("]"):
+                sec = line[1:-1]
+                out[sec] = {}
+                continue
+            key, val = (t.strip() for t in line.split("=", 1))
+            out[sec][key] = [Fraction(t) for t in val.split()]
+    return out
+
+
+def _rusanov_lines_agree(g):
+    """The fixture's Rusanov lines follow from its F, Q and s lines (exact)."""
+    s = g["speed_max"][0]
+    for a, b, ql, qr, lr, rl in zip(g["F_L"], g["F_R"], g["Q_L"], g["Q_R"], g["Fstar_LR"], g["Fstar_RL"]):
+        assert (a + b) / 2 - s / 2 * (qr - ql) == lr
+        assert (a + b) / 2 - s / 2 * (ql - qr) == rl
+
+
+def _update_lines_agree(g, r):
+    QL, QR, FL, FR, LR, RL = (g[k] for k in ("Q_L", "Q_R", "F_L", "F_R", "Fstar_LR", "Fstar_RL"))
+    for v in range(len(QL)):
+        assert g["voxel_7"][v] == QL[v] - r * (LR[v] - FL[v])
+        assert g["voxel_8"][v] == QR[v] - r * (FR[v] - LR[v])
+        assert g["voxel_15"][v] == QR[v] - r * (RL[v] - FR[v])
+        assert g["voxel_0"][v] == QL[v] - r * (FL[v] - RL[v])
+
+
+def _to_axes(vec_nt, axis, dim):
+    """(normal, t1[, t2]) components -> physical axes (tangential axes in increasing order)."""
+    out = [None] * dim
+    out[axis] = vec_nt[0]
+    others = [a for a in range(dim) if a != axis]
+    for j, a in enumerate(others):
+        out[a] = vec_nt[1 + j]
+    return out
+
+
+def _row_case(orc, pde, dim, axis, g, r, nq, nm, prim_to_mat=None):
+    """Run one FE stage on a periodic row of 2 patches of 8 voxels along `axis`; return the
+    oracle's 16 voxels of the row (per quantity, normal/tangential order) and the grids."""
+    p = 8
+    n = [1, 1, 1]
+    n[axis] = 2
+    dx = Fraction(1, 16)
+    mesh = single_level(tuple(n), p, float(dx), dim=dim)
+    shape = (16 if axis == 2 else p, 16 if axis == 1 else p, 16 if axis == 0 else p)[3 - dim:]
+    grid_axis = dim - 1 - axis
+    idx = np.arange(16)
+    left = idx < 8
+
+    def fill(vals_L, vals_R, rows):
+        a = arena(mesh, rows)
+        for v in range(rows):
+            G = np.empty(shape)
+            line = np.where(left, float(vals_L[v]), float(vals_R[v]))
+            G[...] = np.expand_dims(line, tuple(k for k in range(dim) if k != grid_axis))
+            from_grid(mesh, G, a[v])
+        return a
+
+    def phys(Q):  # conserved (scalar, vector n/t..., [scalar]) -> physical component order
+        vec = _to_axes(Q[1:1 + dim], axis, dim)
+        return [Q[0]] + vec + list(Q[1 + dim:])
+
+    q = fill(phys(g["Q_L"]), phys(g["Q_R"]), nq)
+    mat = None
+    if nm:
+        mL, mR = prim_to_mat(g["prim_L"]), prim_to_mat(g["prim_R"])
+        mat = fill(mL, mR, nm)
+    out = np.zeros_like(q)
+    dt = float(r * dx)
+    orc.stage(FV, pde, dim, mesh.patches, 1, mesh.var_stride, q, out=out, mat=mat, dt=dt, a=0, b=1, g=1)
+    Gq = [to_grid(mesh, q[v]) for v in range(nq)]
+    Go = [to_grid(mesh, out[v]) for v in range(nq)]
+    return Gq, Go, phys, grid_axis
+
+
+def _check_row(Gq, Go, phys, grid_axis, g, nq, tol=1e-14):
+    for i in range(16):
+        key = f"voxel_{i}"
+        for v in range(nq):
+            got = np.take(Go[v], i, axis=grid_axis)
+            if key in g:
+                exp = float(phys(g[key])[v])
+                assert np.all(np.abs(got - exp) <= tol * max(1.0, abs(exp))), (key, v, got.ravel()[:3], exp)
+            else:  # no face of voxel i carries a jump: bitwise unchanged
+                assert np.array_equal(got, np.take(Gq[v], i, axis=grid_axis)), (key, v)
+
+
+@pytest.mark.parametrize("dim,axis", [(2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
+def test_euler_rusanov_riemann_worked_example(orc, dim, axis):
+    fx = load("euler_rusanov_riemann.txt")
+    r = fx[""]["dt_over_dx"][0]
+    g = fx[f"{dim}d"]
+    _rusanov_lines_agree(g)
+    _update_lines_agree(g, r)
+    pde = EULER2D if dim == 2 else EULER3D
+    nq = dim + 2
+    Gq, Go, phys, ga = _row_case(orc, pde, dim, axis, g, r, nq, 0)
+    _check_row(Gq, Go, phys, ga, g, nq)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_srhd_rusanov_riemann_worked_example(orc, axis):
+    fx = load("srhd_rusanov_riemann.txt")
+    r = fx[""]["dt_over_dx"][0]
+    g = fx["3d"]
+    _rusanov_lines_agree(g)
+    _update_lines_agree(g, r)
+
+    def prim_to_mat(prim):  # (rho, v_n, v_t1, v_t2, p) -> (rho, vx, vy, vz, p)
+        return [prim[0]] + _to_axes(prim[1:4], axis, 3) + [prim[4]]
+
+    Gq, Go, phys, ga = _row_case(orc, SRHD3D, 3, axis, g, r, 5, 5, prim_to_mat)
+    _check_row(Gq, Go, phys, ga, g, 5)
+
+
+def test_srhd_speed_along_the_flow_is_the_relativistic_sum():
+    """The fixture's s = 17/19 is |(v - cs)/(1 - v cs)| for v = -4/5, cs = 1/3 (state R)."""
+    g = load("srhd_rusanov_riemann.txt")["3d"]
+    rho, v, p = g["prim_R"][0], g["prim_R"][1], g["prim_R"][4]
+    Gm = Fraction(5, 3)
+    h = 1 + Gm / (Gm - 1) * p / rho
+    cs2 = Gm * p / (rho * h)
+    assert cs2 == Fraction(1, 9)
+    cs = Fraction(1, 3)
+    assert max(abs((v + cs) / (1 + v * cs)), abs((v - cs) / (1 - v * cs))) == g["speed_max"][0]
