@@ -173,3 +173,33 @@ def test_newton_step_forms_agree(orc):
     y = E + ps
     q = np.sqrt(y * y - S2)
     assert np.all(np.abs(gf * q * (q - D) - ps * y) <= 1e-11 * y * ps)
+
+
+def test_mlp_forward_layout_closed_form(orc):
+    """With two isolated paths through the network (input 2 -> hidden-1 unit 5 -> hidden-2 unit 11,
+    input 0 -> unit 20 -> unit 3) the forward pass is a closed form in tanh; this fixes the weight
+    layout W1[32][3], b1, W2[32][32] (row = output unit), b2, W3, b3 that the GPU kernels share."""
+    w = np.zeros(1217)
+    W1, b1, W2, b2, W3, b3 = 0, 96, 128, 1152, 1184, 1216
+    w[W1 + 3 * 5 + 2], w[b1 + 5], w[W2 + 32 * 11 + 5], w[b2 + 11], w[W3 + 11] = 0.7, 0.1, -1.3, 0.2, 0.9
+    w[W1 + 3 * 20 + 0], w[W2 + 32 * 3 + 20], w[W3 + 3] = -0.45, 0.8, 1.7
+    w[b3] = -0.4
+    x = np.array([[0.3, -2.0, 0.5], [-1.1, 0.4, -0.25], [0.0, 0.0, 0.0]])
+    y = orc.mlp_forward(w, x)
+    for k in range(len(x)):
+        a = 0.9 * math.tanh(-1.3 * math.tanh(0.7 * x[k, 2] + 0.1) + 0.2)
+        b = 1.7 * math.tanh(0.8 * math.tanh(-0.45 * x[k, 0]))
+        assert abs(y[k] - (a + b - 0.4)) <= 1e-15, (k, y[k], a + b - 0.4)
+
+
+def test_invariants_closed_form(orc):
+    """(|S|/E, D/E, ln(E/D)) with E = tau + D, on a state at rest and on a moving state whose
+    conserved variables are exact: rho = 1, |v| = 3/5 (W = 5/4), p = 6/25 gives D = 5/4,
+    S = 5/2 v, |S| = 3/2, tau = 101/100."""
+    cons = np.zeros((5, 2))
+    cons[:, 0] = [2.0, 0.0, 0.0, 0.0, 0.3 / (G - 1.0)]
+    cons[:, 1] = [1.25, 0.9, 0.96, 0.72, 1.01]
+    x = orc.srhd_invariants(cons, 2)
+    E0, E1 = 2.0 + 0.45, 2.26
+    assert np.allclose(x[0], [0.0, 2.0 / E0, math.log(E0 / 2.0)], rtol=1e-15, atol=1e-16)
+    assert np.allclose(x[1], [1.5 / E1, 1.25 / E1, math.log(E1 / 1.25)], rtol=1e-15, atol=1e-16)
