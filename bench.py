@@ -371,7 +371,6 @@ def train_seed(torch, dh, stream, n=1 << 20, steps=6000, seed=synth.SEED_BASE + 
     """Train the con2prim seed MLP on n (conserved, pressure) pairs with the library's kernels.
     The pairs come from the library's prim2con kernel on i.i.d. primitives (the tests pin that
     kernel, and the training itself, to the oracle's prim2con)."""
-    from paper_2608_19273_gb300 import dh as _dh  # noqa: F401
     mesh = synth.make_mesh([synth.Level((8, 8, 4), 16, 1.0 / 256, 0)], dim=3)
     prim = synth.srhd_iid_prims(mesh.var_stride, seed)
     plan = dh.Plan(5, 3, mesh.patches, 1, mesh.var_stride)

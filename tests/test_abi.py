@@ -4,7 +4,6 @@ import ctypes
 import os
 import re
 
-import numpy as np
 import pytest
 
 from paper_2608_19273_gb300 import build as dhbuild

@@ -5,7 +5,6 @@ iteration and the learned seed follow textbook definitions."""
 import math
 
 import numpy as np
-import pytest
 
 from helpers import arena, single_level, voxel_mask
 from paper_2608_19273_gb300 import synth

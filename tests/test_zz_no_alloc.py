@@ -9,7 +9,6 @@ fresh process."""
 import numpy as np
 import pytest
 
-import oracle
 from gpu_util import assert_parity, dev, host, require_cuda
 from helpers import voxel_mask
 from paper_2608_19273_gb300 import dh, synth
