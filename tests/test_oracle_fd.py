@@ -178,3 +178,56 @@ def test_mirror_symmetry_x(orc, pde):
     for v in range(nq):
         G = to_grid(mesh, L[v])[:, :, ::-1]
         assert np.array_equal(to_grid(mesh, Lm[v]), -G if v in odd else G), v
+
+
+def _interior(mesh, h=3):
+    """Voxels of a single self-periodic patch whose h-wide stencils do not wrap around."""
+    p = int(mesh.patches[0]["p"])
+    z, y, x = np.meshgrid(np.arange(p), np.arange(p), np.arange(p), indexing="ij")
+    return ((x >= h) & (x < p - h) & (y >= h) & (y < p - h) & (z >= h) & (z < p - h)).ravel()
+
+
+def test_fd4_exact_on_quartics(orc):
+    """The centred 4th-order derivative is exact on polynomials of degree <= 4 and the 6th
+    difference of the KO term vanishes on them, so on quartic data (away from the periodic
+    seam) the wave operator equals its continuous value to rounding: L(phi) = Pi,
+    L(Pi) = c^2 div psi - gamma Pi, L(psi_d) = d_d Pi."""
+    mesh = single_level((1, 1, 1), 16, 1.0 / 16)
+    X = synth.voxel_centres(mesh)
+    x, y, z = X[0], X[1], X[2]
+    q = arena(mesh, 5)
+    q[0] = 0.3 * x ** 4 - 0.2 * x * y ** 3 + 0.5 * z * z * x - 0.1
+    q[1] = 0.7 * y ** 4 + 0.4 * x * z - 0.3 * x * x * y + 0.25 * z ** 4
+    q[2] = 0.2 * z ** 4 - x ** 3 * y + 0.6 * x ** 4
+    q[3] = -0.5 * y ** 3 * z + 0.8 * y ** 4
+    q[4] = 0.9 * x * y * z * z - 0.4 * z ** 4
+    c, gam = 1.3, 0.1
+    mat = arena(mesh, 1)
+    mat[0] = c
+    L = _operator(orc, WAVE, mesh, q, mat, sigma=0.1, params=[gam])
+    dPi = [0.4 * z - 0.6 * x * y, 2.8 * y ** 3 - 0.3 * x * x, 0.4 * x + z ** 3]
+    div_psi = (-3 * x * x * y + 2.4 * x ** 3) + (-1.5 * y * y * z + 3.2 * y ** 3) + (1.8 * x * y * z - 1.6 * z ** 3)
+    exact = np.stack([q[1], c * c * div_psi - gam * q[1], dPi[0], dPi[1], dPi[2]])
+    m = _interior(mesh)
+    n = 16 ** 3
+    err = np.abs(L[:, :n][:, m] - exact[:, :n][:, m])
+    assert np.max(err) <= 1e-12 * np.max(np.abs(exact[:, :n][:, m])), np.max(err)
+
+
+def test_ko_stencil_on_monomials(orc):
+    """KO alone (zero-velocity advection: B = 0): sigma/(64 dx) delta^6 vanishes on x^k for
+    k <= 5 and gives sigma/(64 dx) 720 dx^6 on x^6 (the 6th difference of x^6 is 6! dx^6);
+    together with the checkerboard this fixes all seven stencil weights."""
+    dx, sigma = 1.0 / 16, 0.1
+    mesh = single_level((1, 1, 1), 16, dx)
+    X = synth.voxel_centres(mesh)
+    mat = arena(mesh, 3)
+    m = _interior(mesh)
+    n = 16 ** 3
+    for k in range(7):
+        for axis in range(3):
+            q = arena(mesh, 1)
+            q[0] = (X[axis] - 0.5) ** k
+            L = _operator(orc, synth.PDE_ADV_NCP, mesh, q, mat, sigma=sigma)[0, :n][m]
+            expect = sigma / (64 * dx) * 720 * dx ** 6 if k == 6 else 0.0
+            assert np.max(np.abs(L - expect)) <= 1e-13, (k, axis, np.max(np.abs(L - expect)))
