@@ -155,3 +155,34 @@ def test_srhd_speed_along_the_flow_is_the_relativistic_sum():
     assert cs2 == Fraction(1, 9)
     cs = Fraction(1, 3)
     assert max(abs((v + cs) / (1 + v * cs)), abs((v - cs) / (1 - v * cs))) == g["speed_max"][0]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_ncp_advection_midpoint_worked_example(orc, axis):
+    """Path-conservative midpoint fluctuation with Rusanov dissipation on a material jump:
+    bitwise, since every value of the worked example is dyadic."""
+    g = load("ncp_advection_midpoint.txt")[""]
+    p, ADV_NCP = 8, 1
+    n = [1, 1, 1]
+    n[axis] = 2
+    dx = Fraction(1, 16)
+    mesh = single_level(tuple(n), p, float(dx), dim=3)
+    shape = (16 if axis == 2 else p, 16 if axis == 1 else p, 16 if axis == 0 else p)
+    ga = 2 - axis
+    left = np.expand_dims(np.arange(16) < 8, tuple(k for k in range(3) if k != ga))
+    q = arena(mesh, 1)
+    from_grid(mesh, np.broadcast_to(np.where(left, float(g["Q_left"][0]), float(g["Q_right"][0])), shape).copy(),
+              q[0])
+    mat = arena(mesh, 3)
+    from_grid(mesh, np.broadcast_to(np.where(left, float(g["a_left"][0]), float(g["a_right"][0])), shape).copy(),
+              mat[axis])
+    out = np.zeros_like(q)
+    orc.stage(FV, ADV_NCP, 3, mesh.patches, 1, mesh.var_stride, q, out=out, mat=mat,
+              dt=float(g["dt_over_dx"][0] * dx), a=0, b=1, g=1)
+    got, before = to_grid(mesh, out[0]), to_grid(mesh, q[0])
+    for i in range(16):
+        row = np.take(got, i, axis=ga)
+        if f"voxel_{i}" in g:
+            assert np.all(row == float(g[f"voxel_{i}"][0])), (i, row.ravel()[:2])
+        else:
+            assert np.array_equal(row, np.take(before, i, axis=ga))
