@@ -186,3 +186,16 @@ def test_ncp_advection_midpoint_worked_example(orc, axis):
             assert np.all(row == float(g[f"voxel_{i}"][0])), (i, row.ravel()[:2])
         else:
             assert np.array_equal(row, np.take(before, i, axis=ga))
+
+
+def test_srhd_conversions_on_the_worked_example_states(orc):
+    """prim2con of the example's exact primitive states gives its exact conserved states, and
+    con2prim (Newton on p, cold seed) recovers the primitives from them."""
+    g = load("srhd_rusanov_riemann.txt")["3d"]
+    prim = np.array([[float(x) for x in g["prim_L"]], [float(x) for x in g["prim_R"]]]).T.copy()
+    cons = np.array([[float(x) for x in g["Q_L"]], [float(x) for x in g["Q_R"]]]).T.copy()
+    got = orc.prim2con(SRHD3D, prim, 2)
+    assert np.allclose(got, cons, rtol=4e-16, atol=4e-16), got - cons
+    rec, status, iters, fails = orc.con2prim(cons, 2)
+    assert fails == 0 and np.all(status == 0)
+    assert np.allclose(rec, prim, rtol=1e-12, atol=1e-14), rec - prim
