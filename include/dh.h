@@ -146,9 +146,8 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
                              double d, double sigma_ko, double* lam_out_dev, void* stream);
 
 /* Second-order FV stage: the face states of patch_update_fv's Rusanov flux
- * come from MUSCL reconstruction with the minmod limiter (the paper's
- * "reconstruct Q from the upper and lower voxel by a stencil" step of the
- * face-flux operator, Sec. II-A Eq. 3):
+ * come from MUSCL reconstruction with the minmod limiter (the face-state
+ * stencil of the face-flux operator, Sec. II-A Eq. 3):
  *     sigma_i = minmod(Q_i - Q_{i-1}, Q_{i+1} - Q_i)   per component,
  *     minmod(a, b) = 0 if a, b differ in sign, else the one of smaller magnitude,
  *     QL = Q_{f-1} + sigma_{f-1}/2,  QR = Q_f - sigma_f/2  at face f,

@@ -515,8 +515,8 @@ void fv_operator(int pde, const Params& P, Block<T>& B, double dxd, std::vector<
 }
 
 // ---------------------------------------------------------------- FV operator, MUSCL
-// Second-order variant of the face step of Eq. 3: "reconstruct a Q from the
-// upper and lower voxel using a linear combination" (Sec. II-A) read as
+// Second-order variant of the face step of Eq. 3 (Sec. II-A builds each face
+// state from the voxels beside the face with a linear stencil), read as
 // piecewise-linear (MUSCL) reconstruction of the evolved quantities, one
 // component at a time, with the minmod slope limiter:
 //   sigma_i = minmod(Q_i - Q_{i-1}, Q_{i+1} - Q_i),

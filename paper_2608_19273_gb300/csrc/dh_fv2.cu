@@ -1,7 +1,8 @@
 // Second-order finite-volume Runge-Kutta stage over all patches in one launch:
 // MUSCL reconstruction with the minmod limiter feeding the Rusanov flux (the
-// "reconstruct Q from the upper and lower voxel by a stencil" step of the
-// face-flux operator, Sec. II-A Eq. 3), for conservative systems (B = 0):
+// face-state step of the face-flux operator, Sec. II-A Eq. 3, where a state on
+// each side of a face comes from a linear stencil over neighbouring voxels),
+// for conservative systems (B = 0):
 //   sigma_i = minmod(Q_i - Q_{i-1}, Q_{i+1} - Q_i)            (per component)
 //   minmod(a, b) = 0 if a, b differ in sign, else the one of smaller magnitude
 //   QL = Q_{f-1} + sigma_{f-1}/2,  QR = Q_f - sigma_f/2         (face f)

@@ -1,6 +1,6 @@
 """Pins of the oracle's second-order FV stage (MUSCL reconstruction with the
-minmod limiter feeding the Rusanov flux; the reading of the "reconstruct Q
-from the upper and lower voxel by a stencil" step of Sec. II-A Eq. 3) against
+minmod limiter feeding the Rusanov flux; the reading of the face-state
+stencil of Sec. II-A Eq. 3) against
 facts fixed by the mathematics.  CPU only."""
 import numpy as np
 import pytest
