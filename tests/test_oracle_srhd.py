@@ -202,3 +202,21 @@ def test_invariants_closed_form(orc):
     E0, E1 = 2.0 + 0.45, 2.26
     assert np.allclose(x[0], [0.0, 2.0 / E0, math.log(E0 / 2.0)], rtol=1e-15, atol=1e-16)
     assert np.allclose(x[1], [1.5 / E1, 1.25 / E1, math.log(E1 / 1.25)], rtol=1e-15, atol=1e-16)
+
+
+def test_learned_seed_converges_to_the_same_pressure(orc):
+    """Whatever network seeds Newton (here an untrained one with random weights), the seeded solve
+    converges to the same root as the cold-seeded one within the con2prim tolerance."""
+    w = iid_prims(3000, 17, wmax=10.0)
+    n = w.shape[1]
+    cons = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    rng = np.random.default_rng(4)
+    mlp = np.zeros(1217 + 6, dtype=np.float32)
+    mlp[:1217] = rng.normal(scale=0.3, size=1217)
+    mlp[1217:1220] = 0.0  # z-score mean
+    mlp[1220:1223] = 1.0  # z-score std
+    plain, st0, it0, f0 = orc.con2prim(cons, n)
+    seeded, st1, it1, f1 = orc.con2prim(cons, n, mlp=mlp)
+    assert f0 == 0 and f1 == 0
+    assert np.max(np.abs(seeded[4] - plain[4]) / plain[4]) <= 1e-10
+    assert np.max(np.abs(seeded[4] - w[4]) / w[4]) <= 1e-10
