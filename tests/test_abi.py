@@ -95,3 +95,30 @@ def test_coupled_plan_validation_rejects(libdh, mutate):
     mutate(P, mesh.level_ranges[1][0])
     assert _create(P, vs=mesh.var_stride) == dh.DH_EINVAL
     assert len(dh.lib().dh_last_error()) > 0
+
+
+@pytest.mark.parametrize("case", ["p_too_large", "halo_zero", "halo_too_wide", "stride_too_small", "dx_nan",
+                                  "bad_params"])
+def test_plan_limits_rejected(libdh, case):
+    """The documented limits of dh_plan_create: p a multiple of 8 in [8, 256], halo in [1, 8],
+    every block inside var_stride, a positive dx, a parameter array when n_params > 0."""
+    mesh = synth.euler3d_amr_mesh(scale=8)
+    P = mesh.patches.copy()
+    halo, vs, nprm = 1, mesh.var_stride, 0
+    if case == "p_too_large":
+        P["p"][0] = 264
+    elif case == "halo_zero":
+        halo = 0
+    elif case == "halo_too_wide":
+        halo = 9
+    elif case == "stride_too_small":
+        vs = int(P["offset"].max())  # the last block ends beyond it (a multiple of 32 below the end)
+        vs -= vs % 32
+    elif case == "dx_nan":
+        P["dx"][3] = float("nan")
+    elif case == "bad_params":
+        nprm = 2  # but no array
+    h = ctypes.c_void_p()
+    st = dh.lib().dh_plan_create(ctypes.byref(h), 3, 3, P.ctypes.data, len(P), halo, vs, None, nprm)
+    assert st == dh.DH_EINVAL and not h.value
+    assert len(dh.lib().dh_last_error()) > 0
