@@ -122,3 +122,34 @@ def test_plan_limits_rejected(libdh, case):
     st = dh.lib().dh_plan_create(ctypes.byref(h), 3, 3, P.ctypes.data, len(P), halo, vs, None, nprm)
     assert st == dh.DH_EINVAL and not h.value
     assert len(dh.lib().dh_last_error()) > 0
+
+
+ENTRY_POINTS = ["patch_update_fv", "patch_update_fd_ko", "patch_update_fv_muscl", "max_wave_speed", "dh_cfl_dt",
+                "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_bind_staged",
+                "dh_offload_run", "dh_autotune", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug",
+                "con2prim", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch",
+                "dh_graph_info", "dh_graph_stage_times", "con2prim_flat", "dh_mlp_features", "dh_mlp_standardize",
+                "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train", "dh_check_recip", "dh_probe_dfma",
+                "patch_update_fv_noalloc"]
+
+
+@pytest.mark.parametrize("name", ENTRY_POINTS)
+def test_null_arguments_rejected(libdh, name):
+    """Every entry point called with a NULL plan / NULL buffers and zero sizes returns DH_EINVAL
+    with a message, before touching the device."""
+    f = getattr(dh.lib(), name)
+    args = [0.0 if t in (ctypes.c_double, ctypes.c_float) else 0 if t in (ctypes.c_int32, ctypes.c_int64)
+            else None for t in f.argtypes]
+    assert f(*args) == dh.DH_EINVAL
+    assert len(dh.lib().dh_last_error()) > 0
+
+
+def test_destroy_null_plan_is_a_no_op(libdh):
+    assert dh.lib().dh_plan_destroy(None) == dh.DH_OK
+
+
+def test_null_argument_list_covers_the_header():
+    """Every entry point of dh.h is in the NULL-argument test, apart from plan creation and
+    destruction (tested above) and the two string getters."""
+    assert set(_declared()) == set(ENTRY_POINTS) | {"dh_plan_create", "dh_plan_destroy", "dh_last_error",
+                                                    "dh_version"}
