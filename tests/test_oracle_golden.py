@@ -199,3 +199,28 @@ def test_srhd_conversions_on_the_worked_example_states(orc):
     rec, status, iters, fails = orc.con2prim(cons, 2)
     assert fails == 0 and np.all(status == 0)
     assert np.allclose(rec, prim, rtol=1e-12, atol=1e-14), rec - prim
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_muscl_advection_kink_worked_example(orc, axis):
+    """Second-order stage (MUSCL-minmod into Rusanov) on a ramp between plateaus: bitwise."""
+    g = load("muscl_advection_kink.txt")[""]
+    p, ADV_FLUX, FV2 = 8, 0, 2
+    n = [1, 1, 1]
+    n[axis] = 2
+    dx = Fraction(1, 16)
+    mesh = single_level(tuple(n), p, float(dx), dim=3)
+    shape = (16 if axis == 2 else p, 16 if axis == 1 else p, 16 if axis == 0 else p)
+    ga = 2 - axis
+    other = tuple(k for k in range(3) if k != ga)
+    line = np.array([float(x) for x in g["Q"]])
+    q = arena(mesh, 1)
+    from_grid(mesh, np.broadcast_to(np.expand_dims(line, other), shape).copy(), q[0])
+    mat = arena(mesh, 3)
+    mat[axis] = float(g["a"][0])
+    out = np.zeros_like(q)
+    orc.stage(FV2, ADV_FLUX, 3, mesh.patches, 2, mesh.var_stride, q, out=out, mat=mat,
+              dt=float(g["dt_over_dx"][0] * dx), a=0, b=1, g=1)
+    got = to_grid(mesh, out[0])
+    expect = np.broadcast_to(np.expand_dims(np.array([float(x) for x in g["out"]]), other), shape)
+    assert np.array_equal(got, expect), np.take(got, 0, axis=other[0]).ravel()[:16]
