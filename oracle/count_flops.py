@@ -55,7 +55,8 @@ def per_voxel(scheme, pde, dim, halo, rk, with_lam, sizes=(8, 16, 24)):
     return A, B, C, c
 
 
-def main():
+def compute():
+    """The table: per time-step kind, exact FP64 operations per voxel, per face layer and per stage."""
     res = {}
     for key, args in {
         "fv/euler3d/ssprk3_step": (0, synth.PDE_EULER3D, 3, 1, 3, True),
@@ -71,6 +72,11 @@ def main():
         assert abs(A - A2) < 1e-6 and abs(A - round(A)) < 1e-6, (key, A, A2)
         res[key] = {"flops_per_voxel": int(round(A)), "halo_term": round(B, 6), "constant": round(C, 6),
                     "raw_counts": c}
+    return res
+
+
+def main():
+    res = compute()
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1, sort_keys=True)
     print(json.dumps(res, indent=1, sort_keys=True))

@@ -79,3 +79,14 @@ def test_stored_counts_are_the_hand_counts(key):
     assert table[key]["flops_per_voxel"] == A
     assert table[key]["halo_term"] == B
     assert table[key]["constant"] == C
+
+
+def test_stored_table_is_what_the_oracle_counts_now():
+    """The stored table (the benchmark's algorithmic FLOPs) equals a fresh count of the oracle."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("count_flops", os.path.join(ROOT, "oracle", "count_flops.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    fresh = json.loads(json.dumps(mod.compute(), sort_keys=True))
+    with open(os.path.join(ROOT, "oracle", "flop_counts.json")) as f:
+        assert json.load(f) == fresh
