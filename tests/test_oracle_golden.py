@@ -8,7 +8,12 @@ stage.  The oracle runs the same stage along every axis of a 2D or 3D
 patch row and must reproduce those values to rounding, while every other
 voxel stays bitwise unchanged.  A dropped flux term (the p u of the energy
 flux, the p of the normal momentum flux), a wrong dissipation speed, a wrong
-sign or a transposed velocity component moves at least one listed value."""
+sign or a transposed velocity component moves at least one listed value.
+
+Every stored number traces back to the primitive states: the tests first check,
+in exact rational arithmetic, that each fixture line follows from the lines
+before it (conserved states and fluxes from the primitives, face fluxes from
+those, voxel values from the update rule)."""
 import os
 from fractions import Fraction
 
@@ -45,6 +50,39 @@ def _rusanov_lines_agree(g):
     for a, b, ql, qr, lr, rl in zip(g["F_L"], g["F_R"], g["Q_L"], g["Q_R"], g["Fstar_LR"], g["Fstar_RL"]):
         assert (a + b) / 2 - s / 2 * (qr - ql) == lr
         assert (a + b) / 2 - s / 2 * (ql - qr) == rl
+
+
+def _euler_lines_agree(g, gamma, dim):
+    """The fixture's conserved and flux lines follow from its primitive lines (exact):
+    E = p/(gamma-1) + rho |u|^2/2, F_n = (rho u_n, rho u u_n + p e_n, (E + p) u_n)."""
+    for side in ("L", "R"):
+        rho, u, p = g[f"prim_{side}"][0], g[f"prim_{side}"][1:1 + dim], g[f"prim_{side}"][1 + dim]
+        E = p / (gamma - 1) + rho * sum(x * x for x in u) / 2
+        assert g[f"Q_{side}"] == [rho] + [rho * x for x in u] + [E]
+        F = [rho * u[0]] + [rho * x * u[0] for x in u] + [(E + p) * u[0]]
+        F[1] += p
+        assert g[f"F_{side}"] == F
+
+
+def _exact_sqrt(x):
+    import math
+    a, b = math.isqrt(x.numerator), math.isqrt(x.denominator)
+    assert a * a == x.numerator and b * b == x.denominator, x
+    return Fraction(a, b)
+
+
+def _srhd_lines_agree(g, Gamma):
+    """The same for SRHD: W = 1/sqrt(1 - v^2), h = 1 + Gamma p/((Gamma - 1) rho), D = rho W,
+    S = rho h W^2 v, tau = rho h W^2 - p - D, F_n = (D v_n, S v_n + p e_n, S_n - D v_n)."""
+    for side in ("L", "R"):
+        rho, v, p = g[f"prim_{side}"][0], g[f"prim_{side}"][1:4], g[f"prim_{side}"][4]
+        W = 1 / _exact_sqrt(1 - sum(x * x for x in v))
+        h = 1 + Gamma * p / ((Gamma - 1) * rho)
+        D, S = rho * W, [rho * h * W * W * x for x in v]
+        assert g[f"Q_{side}"] == [D] + S + [rho * h * W * W - p - D]
+        F = [D * v[0]] + [x * v[0] for x in S] + [S[0] - D * v[0]]
+        F[1] += p
+        assert g[f"F_{side}"] == F
 
 
 def _update_lines_agree(g, r):
@@ -122,6 +160,7 @@ def test_euler_rusanov_riemann_worked_example(orc, dim, axis):
     fx = load("euler_rusanov_riemann.txt")
     r = fx[""]["dt_over_dx"][0]
     g = fx[f"{dim}d"]
+    _euler_lines_agree(g, fx[""]["gamma"][0], dim)
     _rusanov_lines_agree(g)
     _update_lines_agree(g, r)
     pde = EULER2D if dim == 2 else EULER3D
@@ -135,6 +174,7 @@ def test_srhd_rusanov_riemann_worked_example(orc, axis):
     fx = load("srhd_rusanov_riemann.txt")
     r = fx[""]["dt_over_dx"][0]
     g = fx["3d"]
+    _srhd_lines_agree(g, fx[""]["Gamma"][0])
     _rusanov_lines_agree(g)
     _update_lines_agree(g, r)
 
