@@ -231,3 +231,46 @@ def test_ko_stencil_on_monomials(orc):
             L = _operator(orc, synth.PDE_ADV_NCP, mesh, q, mat, sigma=sigma)[0, :n][m]
             expect = sigma / (64 * dx) * 720 * dx ** 6 if k == 6 else 0.0
             assert np.max(np.abs(L - expect)) <= 1e-13, (k, axis, np.max(np.abs(L - expect)))
+
+
+def test_gw59_operator_on_quadratic_fields(orc):
+    """Every GW59 field a quadratic polynomial in x, y, z (lapse near 1): the FD4 derivatives are
+    exact and the KO term vanishes, so away from the periodic seam the discrete operator equals the
+    system's right-hand side evaluated with the exact gradients, nonlinear products included:
+      dphi_a = alpha Pi_a + beta^k psi_ak,
+      dPi_a = alpha d_k psi_ak + beta^k d_k Pi_a + alpha sum_b C_ab phi_b Pi_b,
+      dpsi_ai = alpha d_i Pi_a + Pi_a d_i alpha + beta^k d_k psi_ai,
+      dalpha = -kappa alpha^2 sum_a Pi_a^2,  dbeta^i = 3/4 sum_a psi_ai Pi_a."""
+    mesh = single_level((1, 1, 1), 16, 1.0 / 16)
+    X = synth.voxel_centres(mesh)[:, :16 ** 3] - 0.5
+    rng = np.random.default_rng(59)
+    # f = c0 + c . x + x^T A x (A symmetric), gradient c + 2 A x
+    c0 = rng.uniform(-0.2, 0.2, 59)
+    c1 = rng.uniform(-0.3, 0.3, (59, 3))
+    A = rng.uniform(-0.3, 0.3, (59, 3, 3))
+    A = 0.5 * (A + A.transpose(0, 2, 1))
+    c0[55] = 1.0
+    val = c0[:, None] + c1 @ X + np.einsum("vij,in,jn->vn", A, X, X)
+    grad = c1[:, :, None] + 2.0 * np.einsum("vij,jn->vin", A, X)  # (59, 3, n)
+    q = arena(mesh, 59)
+    q[:, :16 ** 3] = val
+    params = synth.workload("gw59", scale=8).params
+    kappa, C = params[0], params[1:].reshape(11, 11)
+    L = _operator(orc, GW, mesh, q, sigma=0.1, params=params)[:, :16 ** 3]
+    al, be = val[55], val[56:59]
+    phi, Pi, psi = val[0:55:5], val[1:55:5], np.stack([val[2 + i:55:5] for i in range(3)], 1)  # psi (11, 3, n)
+    dPi = np.stack([grad[1 + 5 * a] for a in range(11)])                                    # (11, 3, n)
+    dpsi = np.stack([np.stack([grad[2 + i + 5 * a] for i in range(3)]) for a in range(11)])  # (11, i, k, n)
+    ref = np.zeros_like(val)
+    for a in range(11):
+        o = 5 * a
+        ref[o] = al * Pi[a] + (be * psi[a]).sum(0)
+        ref[o + 1] = (al * np.einsum("kkn->n", dpsi[a]) + (be * dPi[a]).sum(0)
+                      + al * (C[a][:, None] * phi * Pi).sum(0))
+        for i in range(3):
+            ref[o + 2 + i] = al * dPi[a][i] + Pi[a] * grad[55][i] + (be * dpsi[a][i]).sum(0)
+    ref[55] = -kappa * al * al * (Pi * Pi).sum(0)
+    ref[56:59] = 0.75 * (psi * Pi[:, None, :]).sum(0)
+    m = _interior(mesh)
+    err = np.abs(L[:, m] - ref[:, m]).max()
+    assert err <= 1e-12 * np.abs(ref[:, m]).max(), err
