@@ -326,7 +326,9 @@ def reference_arm(args, rank, world):
         return 0
     name = args.workload
     import oracle
-    cores = oracle.num_threads(0)
+    # under torchrun every rank starts with one OpenMP thread; rank 0 runs alone here, so it takes
+    # the host's cores
+    cores = oracle.num_threads(len(os.sched_getaffinity(0)) if world > 1 else 0)
     scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
              "gw59": 4}[name]
     w = synth.workload(name, scale=scale)
