@@ -23,6 +23,13 @@
  *   - Data errors found on the device never trap: they are reported through
  *     status arrays and counters (con2prim).
  *   - dh_last_error() returns a thread-local message for the last failure.
+ *   - One plan's calls must not overlap on the GPU: issue them on one stream,
+ *     or order the streams with events.  A plan owns one pair of reduction
+ *     slots that every call writing a wave speed (lam_out_dev, max_wave_speed,
+ *     dh_rk_step with cfl > 0) accumulates into and resets, and one set of
+ *     graph, derived-quantity and offload buffers; two calls of one plan that
+ *     run at the same time race on them.  Different plans share nothing and
+ *     may run concurrently on different streams.
  *
  * State layout ("SoA arena").  A state with V variables is one device array
  * of V * var_stride doubles.  Variable v of voxel (x, y, z) of patch k is at
@@ -398,13 +405,17 @@ dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void*
  * patch_update_fv.  It takes the plan-creation arguments (host patch table,
  * K, var_stride, params) together with the stage arguments of
  * patch_update_fv, and keeps the patch table, the work list and the two
- * reduction slots in one file-scope device array of 1,376,512 bytes that
+ * reduction slots in one file-scope device array of 1,310,976 bytes that
  * every GPU loading the library holds until exit.  Limits: K <= 8192 patches
  * and at most 16384 tile work items (a 16x16 column of a patch, or four 8x8
  * columns); larger inputs return DH_EINVAL.  PDEs: ADV_FLUX, ADV_NCP,
- * EULER2D, EULER3D; halo 1.  Each call uploads the tables with
- * cudaMemcpyAsync from host memory (staged before the call returns), clears
- * the reduction slots, then launches the stage on `stream`; it calls no
+ * EULER2D, EULER3D; halo 1; every face neighbour on the same level (coupled
+ * refinement levels, which dh_plan_create accepts, return DH_EINVAL here).
+ * Each call copies the patch table and the work list it builds into static
+ * host buffers of the library and uploads them from there with
+ * cudaMemcpyAsync (staged before the call returns, so `patches` may be freed
+ * or reused as soon as the call returns, page-locked or not), clears the
+ * reduction slots, then launches the stage on `stream`; it calls no
  * cudaMalloc, cudaFree or other allocating routine.  All calls share the one
  * array and overwrite the previous call's contents, so calls that overlap on
  * the GPU race.  The first call on a device looks up the array's address

@@ -11,9 +11,11 @@
 // What it does instead: the tables and the reduction slots live in one
 // file-scope __device__ array (NA_SCRATCH_BYTES, below), which every GPU that
 // loads this library holds until the process exits.  Each call validates the
-// patch list exactly like dh_plan_create, builds the tile work list in a
-// static host buffer, copies both into the device array with cudaMemcpyAsync
-// from host memory (staged by the driver before the call returns), clears the
+// patch list like dh_plan_create (same-level neighbours only: coupled
+// refinement levels are not supported here), copies it and the tile work list
+// it builds into static host buffers, uploads both into the device array with
+// cudaMemcpyAsync from those pageable buffers (staged by the driver before the
+// call returns, so the caller's table is free again on return), clears the
 // two reduction slots with cudaMemsetAsync, and launches the same stage
 // kernel as patch_update_fv.  It calls no cudaMalloc, cudaFree or other
 // allocating routine.
@@ -36,12 +38,19 @@ constexpr int NA_MAX_WORK = 16384;
 constexpr size_t NA_RED_BYTES = 256;
 constexpr size_t NA_PATCH_BYTES = sizeof(dh_patch) * NA_MAX_PATCHES;
 constexpr size_t NA_WORK_BYTES = sizeof(Work) * NA_MAX_WORK;
-constexpr size_t NA_SCRATCH_BYTES = NA_RED_BYTES + NA_PATCH_BYTES + NA_WORK_BYTES;  // 1,376,512 bytes
+constexpr size_t NA_SCRATCH_BYTES = NA_RED_BYTES + NA_PATCH_BYTES + NA_WORK_BYTES;
+// the size the header states (72-byte patch records, 44-byte work items)
+static_assert(sizeof(dh_patch) == 72 && sizeof(Work) == 44, "record sizes changed: update the stated size");
+static_assert(NA_SCRATCH_BYTES == 1310976, "scratch size changed: update the header");
 
 static __device__ __align__(256) unsigned char g_na_scratch[NA_SCRATCH_BYTES];
 
 static std::mutex g_na_mutex;
-static Work g_na_work[NA_MAX_WORK];  // host staging of the work list (static, not heap)
+// host staging of the patch table and the work list (static, not heap): every upload reads
+// the library's own pageable copy, so the caller's array is free again when the call returns,
+// even when it is page-locked (a copy from page-locked memory would still be in flight)
+static dh_patch g_na_patches[NA_MAX_PATCHES];
+static Work g_na_work[NA_MAX_WORK];
 constexpr int NA_MAX_DEVICES = 64;
 static unsigned char* g_na_addr[NA_MAX_DEVICES] = {nullptr};
 
@@ -129,6 +138,10 @@ extern "C" dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_
   if (out == qs || acc == qs || (out && out == acc)) { set_error("patch_update_fv_noalloc: out/acc alias"); return DH_EINVAL; }
 
   std::lock_guard<std::mutex> lock(g_na_mutex);
+  // the whole table is validated and the work list built on the host before any CUDA call
+  bool has_cls[2];
+  const int nw = na_build_work(dim, patches, K, 1, var_stride, has_cls);
+  if (nw < 0) return (dh_status)nw;
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -139,16 +152,14 @@ extern "C" dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(scratch)");
     g_na_addr[device] = static_cast<unsigned char*>(ptr);
   }
-  bool has_cls[2];
-  const int nw = na_build_work(dim, patches, K, 1, var_stride, has_cls);
-  if (nw < 0) return (dh_status)nw;
 
   unsigned char* base = g_na_addr[device];
   unsigned long long* red = reinterpret_cast<unsigned long long*>(base);
   dh_patch* d_patches = reinterpret_cast<dh_patch*>(base + NA_RED_BYTES);
   Work* d_work = reinterpret_cast<Work*>(base + NA_RED_BYTES + NA_PATCH_BYTES);
   cudaStream_t s = (cudaStream_t)stream;
-  e = cudaMemcpyAsync(d_patches, patches, sizeof(dh_patch) * K, cudaMemcpyHostToDevice, s);
+  std::memcpy(g_na_patches, patches, sizeof(dh_patch) * K);
+  e = cudaMemcpyAsync(d_patches, g_na_patches, sizeof(dh_patch) * K, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_work, g_na_work, sizeof(Work) * nw, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_error(e, "patch_update_fv_noalloc: table upload");

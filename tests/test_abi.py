@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2608_19273_gb300 import build as dhbuild
@@ -153,3 +154,28 @@ def test_null_argument_list_covers_the_header():
     destruction (tested above) and the two string getters."""
     assert set(_declared()) == set(ENTRY_POINTS) | {"dh_plan_create", "dh_plan_destroy", "dh_last_error",
                                                     "dh_version"}
+
+
+def _noalloc(P, vs, pde=3, dim=3):
+    """patch_update_fv_noalloc with dummy (never dereferenced) device pointers."""
+    return dh.lib().patch_update_fv_noalloc(pde, dim, P.ctypes.data, len(P), vs, None, 0, 8, None, 16, None, None,
+                                            24, 0.0, 1.0, 1.0, 0.0, None, None)
+
+
+def test_noalloc_rejects_too_many_work_items(libdh):
+    """65 2D patches of 256^2 need 65 x 256 = 16,640 tile work items, above the static limit of
+    16,384: rejected on the host, before any CUDA call."""
+    mesh = synth.make_mesh([synth.Level((1, 1, 1), 256, 1.0 / 256, 0)], dim=2)
+    P = np.repeat(mesh.patches, 65)
+    P["nbr"][:, :4] = 0
+    P["offset"] = 0
+    assert _noalloc(P, mesh.var_stride, pde=2, dim=2) == dh.DH_EINVAL
+    assert b"work items" in dh.lib().dh_last_error()
+
+
+def test_noalloc_rejects_coupled_levels(libdh):
+    """A table with coarser face neighbours (coupled refinement levels, accepted by
+    dh_plan_create) is rejected by the allocation-free entry point."""
+    mesh = synth.coupled_mesh(4, 8, 1.0 / 32, 1, 2, dim=3)
+    assert _noalloc(mesh.patches.copy(), mesh.var_stride) == dh.DH_EINVAL
+    assert b"neighbour" in dh.lib().dh_last_error()

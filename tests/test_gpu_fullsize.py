@@ -112,7 +112,9 @@ def test_srhd3d_full_size_step(orc):
             pr[:], st, _, _ = orc.con2prim(qs, vs, p_prev=np.ascontiguousarray(pr[4]))
         assert np.all(st == 0)
         orc.stage(0, 5, 3, mesh.patches, 1, vs, qs, q0=q0, out=out, mat=pr, dt=dt, a=a, b=b, g=g, params=w.params)
-    assert_parity(got, q, voxel_mask(mesh), tol=1e-10, what="srhd3d full size")
+    # the evolved state is held to the 1e-12 rule (the 1e-10 of con2prim applies to primitives only)
+    worst = assert_parity(got, q, voxel_mask(mesh), tol=1e-12, what="srhd3d full size")
+    print(f"srhd3d full size, one SSP-RK3 step: max relative error {worst:.3e}")
 
 
 def test_gw59_full_size_sampled_stage(orc):

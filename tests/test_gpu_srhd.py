@@ -9,7 +9,7 @@ import pytest
 from gpu_util import assert_parity, dev, host, require_cuda
 from helpers import arena, single_level, voxel_mask
 from paper_2608_19273_gb300 import dh, synth
-from test_oracle_srhd import iid_prims
+from test_oracle_srhd import constant_seed_mlp, fallback_states, iid_prims
 
 pytestmark = pytest.mark.gpu
 G = 5.0 / 3.0
@@ -227,4 +227,46 @@ def test_srhd_fv_stage_and_rk3(orc):
             dh.patch_update_fv(plan, qs, q0, o, None, PR, d_dt, a, b, g, 0)
         got = host(Q)
         assert int(host(fails)[0]) == 0
-    assert_parity(got, q_o, m, tol=1e-10, what="srhd SSP-RK3 step")
+    # the evolved state is held to the 1e-12 rule; only the primitives con2prim returns have 1e-10
+    worst = assert_parity(got, q_o, m, tol=1e-12, what="srhd SSP-RK3 step")
+    print(f"srhd SSP-RK3 step (rough data, W <= 3): max relative error {worst:.3e}")
+    worst_p = assert_parity(host(PR), pr_o, m, tol=1e-10, what="srhd primitives of the last stage")
+    print(f"srhd primitives of the last stage input: max relative error {worst_p:.3e}")
+
+
+def test_seeded_solve_fallback_matches_oracle(orc):
+    """The seeded-solve fallback: a network whose seed (E e^30) cannot converge within max_iter = 3
+    steps, and a previous pressure 1e-7 off from which Newton converges in 2.  Every voxel takes
+    the fallback (status 1) on both sides; status and iteration arrays equal the oracle's
+    exactly and the primitives match within 1e-10.  Then both seeds fail (status 2): the
+    pressure is the previous pressure and every voxel is counted."""
+    torch = require_cuda()
+    w, cons = fallback_states(20000, 43)
+    n = w.shape[1]
+    mlp = constant_seed_mlp(30.0)
+    p_prev = np.ascontiguousarray(w[4] * (1 + 1e-7))
+    ref, st_ref, it_ref, f_ref = orc.con2prim(cons, n, p_prev=p_prev, mlp=mlp, max_iter=3)
+    assert np.all(st_ref == 1) and f_ref == 0
+
+    def run(pp):
+        d_cons = dev(torch, cons)
+        prim = torch.zeros_like(d_cons)
+        status = torch.zeros(n, dtype=torch.uint8, device="cuda")
+        iters = torch.zeros(n, dtype=torch.int32, device="cuda")
+        fails = torch.zeros(1, dtype=torch.int32, device="cuda")
+        dh.con2prim_flat(d_cons, prim, n, n, dev(torch, pp), dev(torch, mlp), G, 1e-12, 3, status, iters, fails)
+        torch.cuda.synchronize()
+        return host(prim), host(status), host(iters), int(host(fails)[0])
+
+    got, st, it, f = run(p_prev)
+    assert np.array_equal(st, st_ref) and np.array_equal(it, it_ref) and f == 0
+    worst = assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what="fallback con2prim")
+    assert_parity(got, w, np.ones(n, dtype=bool), tol=1e-10, what="fallback round trip")
+    print(f"seeded-solve fallback on {n} voxels: status 1 everywhere, max relative error {worst:.3e}")
+    bad = np.ascontiguousarray((cons[4] + cons[0]) * math.exp(30.0))
+    ref2, st_ref2, it_ref2, f_ref2 = orc.con2prim(cons, n, p_prev=bad, mlp=mlp, max_iter=3)
+    got2, st2, it2, f2 = run(bad)
+    assert np.all(st_ref2 == 2) and f_ref2 == n
+    assert np.array_equal(st2, st_ref2) and np.array_equal(it2, it_ref2) and f2 == n
+    assert np.array_equal(got2[4], bad)
+    assert_parity(got2, ref2, np.ones(n, dtype=bool), tol=1e-12, what="both seeds failed")

@@ -241,3 +241,58 @@ def test_oracle_training_reduces_the_seed_loss(orc):
         orc.adam(wt, m, v, g, step, lr=3e-3)
     loss1 = orc.mlp_loss_grad(wt, x, t)[0]
     assert loss1 < 0.5 * loss0, (loss0, loss1)
+
+
+def constant_seed_mlp(ln_p_over_E):
+    """A network whose output is the constant ln(p/E) = c for every input (all weights zero,
+    output bias c; unit z-score scales): its seed is p = E exp(c)."""
+    w = np.zeros(1224, dtype=np.float32)
+    w[1216] = ln_p_over_E
+    w[1220:1223] = 1.0
+    return w
+
+
+def fallback_states(n, seed, min_iters=6):
+    """i.i.d. states from which a seed at E e^30 needs at least `min_iters` Newton steps (so that a
+    cap of 3 steps misses tolerance by a wide margin), with their exact primitives."""
+    import oracle
+    w = iid_prims(n, seed)
+    cons = oracle.prim2con(synth.PDE_SRHD3D, w, n)
+    _, st, it, _ = oracle.con2prim(cons, n, mlp=constant_seed_mlp(30.0), max_iter=50)
+    # and from which Newton from the previous pressure (1e-7 off) stops after 2 steps even at a
+    # tolerance 100x tighter, so the second step's decision has a wide margin too
+    _, st2, it2, _ = oracle.con2prim(cons, n, p_prev=w[4] * (1 + 1e-7), tol=1e-14, max_iter=50)
+    keep = (st == 0) & (it >= min_iters) & (st2 == 0) & (it2 == 2)
+    w = np.ascontiguousarray(w[:, keep])
+    return w, np.ascontiguousarray(cons[:, keep])
+
+
+def test_seeded_solve_falls_back_to_the_previous_pressure(orc):
+    """The learned seed misses tolerance within max_iter = 3 steps; Newton from the previous
+    pressure (1e-7 off) then converges in 2: status 1 on every voxel, 3 + 2 iterations, and the
+    recovered primitives are the ones the states were made from."""
+    w, cons = fallback_states(20000, 41)
+    n = w.shape[1]
+    assert n > 5000
+    prim, st, it, fails = orc.con2prim(cons, n, p_prev=w[4] * (1 + 1e-7), mlp=constant_seed_mlp(30.0),
+                                       max_iter=3)
+    assert fails == 0 and np.all(st == 1)
+    assert np.all(it == 5)
+    assert np.max(np.abs(prim[4] - w[4]) / w[4]) < 1e-10
+    assert np.max(np.abs(prim[0] - w[0]) / w[0]) < 1e-10
+    assert np.max(np.abs(prim[1:4] - w[1:4])) < 1e-10
+
+
+def test_both_seeds_failing_keeps_the_previous_pressure(orc):
+    """When the fallback seed misses tolerance too, status is 2, the pressure is the previous
+    pressure itself, the voxel is counted, and v, rho follow from that pressure."""
+    w, cons = fallback_states(4000, 42)
+    n = w.shape[1]
+    E = cons[4] + cons[0]
+    p_prev = E * math.exp(30.0)
+    prim, st, it, fails = orc.con2prim(cons, n, p_prev=p_prev, mlp=constant_seed_mlp(30.0), max_iter=3)
+    assert fails == n and np.all(st == 2) and np.all(it == 6)
+    assert np.array_equal(prim[4], p_prev)
+    v = cons[1:4] / (E + p_prev)
+    assert np.allclose(prim[1:4], v, rtol=1e-15, atol=0)
+    assert np.allclose(prim[0], cons[0] * np.sqrt(1 - np.sum(v * v, axis=0)), rtol=1e-15, atol=0)

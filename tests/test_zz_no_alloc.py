@@ -47,3 +47,26 @@ def test_noalloc_rejects_oversize(orc):
     with pytest.raises(dh.DhError) as ei:
         dh.patch_update_fv_noalloc(3, 3, big, mesh.var_stride, None, 1, None, 1, None, None, 1, 0, 1, 1, 0)
     assert ei.value.status == dh.DH_EINVAL
+
+
+def test_noalloc_euler2d_gamma_matches_plan_path(orc):
+    """2D Euler with a non-default ratio of specific heats (gamma = 5/3, passed in params) on two
+    calls in a row, against the plan path with the same parameter."""
+    torch = require_cuda()
+    w = synth.workload("euler2d")
+    mesh = w.mesh
+    m = voxel_mask(mesh)
+    params = np.array([5.0 / 3.0])
+    d_dt = torch.tensor([2.1e-3], dtype=torch.float64, device="cuda")
+    with dh.Plan(2, 2, mesh.patches, 1, mesh.var_stride, params) as plan:
+        for call, seed in enumerate((81, 82)):
+            qs = dev(torch, orc.prim2con(2, synth.euler_prims(mesh, seed), mesh.var_stride, params=params))
+            ref, got = torch.zeros_like(qs), torch.full_like(qs, np.nan)
+            lam_ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+            lam_got = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+            dh.patch_update_fv(plan, qs, None, ref, None, None, d_dt, 0.0, 1.0, 1.0, 0.0, lam_ref)
+            dh.patch_update_fv_noalloc(2, 2, mesh.patches, mesh.var_stride, params, qs, None, got, None, None, d_dt,
+                                       0.0, 1.0, 1.0, 0.0, lam_got)
+            torch.cuda.synchronize()
+            assert_parity(host(got), host(ref), m, what=f"noalloc euler2d call {call}")
+            assert abs(float(host(lam_got)[0]) - float(host(lam_ref)[0])) <= 1e-14 * float(host(lam_ref)[0])
