@@ -71,6 +71,10 @@ def lib():
             L.or_adam.restype = None
             L.or_count_flops.argtypes = [i, i, i, i, i, i, i, vp, vp, vp, i]
             L.or_count_flops.restype = ctypes.c_longlong
+            L.or_count_con2prim.argtypes = [vp, i64, i64, vp, d, i, d, vp]
+            L.or_count_con2prim.restype = ctypes.c_longlong
+            L.or_count_max_speed.argtypes = [i, i, vp, vp, i64, i64, vp, i]
+            L.or_count_max_speed.restype = ctypes.c_longlong
             _lib = L
     return _lib
 
@@ -198,3 +202,20 @@ def count_flops(scheme, pde, dim, p, halo, qs, mat=None, rk=0, with_lam=False, p
     prm = _f64(params)
     return lib().or_count_flops(scheme, pde, dim, p, halo, rk, int(with_lam), _p(_f64(qs)), _p(_f64(mat)),
                                 _p(prm), 0 if prm is None else len(prm))
+
+
+def count_con2prim(cons, n, p_prev=None, tol=1e-12, max_iter=50, Gamma=5.0 / 3.0):
+    """(FP64 operations, Newton iterations) of the plain-seeded recovery of the first n voxels of a
+    flat conserved array (variable v of voxel i at v * stride + i, stride = cons.shape[1])."""
+    cons = _f64(cons)
+    it = ctypes.c_longlong(0)
+    fl = lib().or_count_con2prim(_p(cons), int(n), cons.shape[1], _p(_f64(p_prev)), tol, max_iter, Gamma,
+                                 ctypes.byref(it))
+    return int(fl), int(it.value)
+
+
+def count_max_speed(pde, dim, q, mat, n, params=None):
+    """FP64 operations of the maximum characteristic speed (all directions) of n voxels of flat arrays."""
+    q, mat, prm = _f64(q), _f64(mat), _f64(params)
+    return int(lib().or_count_max_speed(pde, dim, _p(q), _p(mat), int(n), q.shape[1], _p(prm),
+                                        0 if prm is None else len(prm)))

@@ -75,8 +75,35 @@ def compute():
     return res
 
 
+def con2prim_counts(n=20000, seed=5):
+    """Exact split of the plain-seeded SRHD recovery into a per-voxel part (E, |S|^2, |S|, the
+    bracket, the cold seed, the recovery of v and rho) and a per-Newton-iteration part:
+    count = A n + B iterations, solved from two seeds of different quality on the same states and
+    checked on a third (warm seeds: no safeguard step is taken)."""
+    prim = synth.srhd_iid_prims(n, seed)
+    cons = oracle.prim2con(synth.PDE_SRHD3D, prim, n)
+    rows, rhs = [], []
+    for rel in (1e-3, 1e-9, 1e-6):
+        fl, it = oracle.count_con2prim(cons, n, p_prev=prim[4] * (1 + rel))
+        rows.append([n, it])
+        rhs.append(fl)
+    A, B = np.linalg.solve(np.array(rows[:2], dtype=float), np.array(rhs[:2], dtype=float))
+    assert abs(A - round(A)) < 1e-6 and abs(B - round(B)) < 1e-6, (A, B)
+    assert round(A) * rows[2][0] + round(B) * rows[2][1] == rhs[2]
+    speed = oracle.count_max_speed(synth.PDE_SRHD3D, 3, cons, prim, n)
+    assert speed % n == 0
+    return {"c2p/srhd3d/voxel": {"flops_per_voxel": int(round(A)),
+                                 "note": "setup and recovery of one voxel, plain seed, without the Newton iterations"},
+            "c2p/srhd3d/newton_iteration": {"flops_per_voxel": int(round(B)),
+                                            "note": "one Newton iteration on the pressure (no safeguard step)"},
+            "speed/srhd3d/voxel": {"flops_per_voxel": speed // n,
+                                   "note": "derived quantities and the speeds of all three directions, from the "
+                                           "primitives"}}
+
+
 def main():
     res = compute()
+    res.update(con2prim_counts())
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1, sort_keys=True)
     print(json.dumps(res, indent=1, sort_keys=True))

@@ -943,21 +943,21 @@ void srhd_prim2con(double Gamma, const T* w, T* q) {
 // p_lo (safeguard: plain Newton from a cold seed overshoots below zero for
 // fast flows).  Fails on NaN or when max_iter iterations did not converge.
 // Returns iterations used (>0) on success, -iterations on failure.
-int srhd_newton(double G, double D, double S2, double E, double p_lo, double p0, double tol,
-                int max_iter, double* p_out) {
-  double p = p0;
-  const double gf = (G - 1.0) / G;
+template <class T>
+int srhd_newton(double G, T D, T S2, T E, T p_lo, T p0, double tol, int max_iter, T* p_out) {
+  T p = p0;
+  const T gf = T((G - 1.0) / G), one = T(1.0);
   for (int it = 1; it <= max_iter; ++it) {
-    double Ep = E + p;
-    double s2e = S2 / (Ep * Ep);
-    double rt = std::sqrt(1.0 - s2e);
-    double f = gf * (Ep - S2 / Ep - D * rt) - p;
-    double fp = gf * (1.0 + s2e - D * S2 / (Ep * Ep * Ep * rt)) - 1.0;
-    double pn = p - f / fp;
-    if (!(pn == pn)) { *p_out = pn; return -it; }
+    T Ep = E + p;
+    T s2e = S2 / (Ep * Ep);
+    T rt = sqrt(one - s2e);
+    T f = gf * (Ep - S2 / Ep - D * rt) - p;
+    T fp = gf * (one + s2e - D * S2 / (Ep * Ep * Ep * rt)) - one;
+    T pn = p - f / fp;
+    if (!(val(pn) == val(pn))) { *p_out = pn; return -it; }
     if (pn <= p_lo) {
-      pn = 0.5 * (p + p_lo);  // safeguard step: never counts as convergence
-    } else if (std::fabs(pn - p) <= tol * pn) {
+      pn = T(0.5) * (p + p_lo);  // safeguard step: never counts as convergence
+    } else if (fabs(pn - p) <= T(tol) * pn) {
       *p_out = pn;
       return it;
     }
@@ -997,6 +997,55 @@ void srhd_invariants(const double* q, double* x) {
   x[0] = S / E;
   x[1] = D / E;
   x[2] = std::log(E / D);
+}
+
+// Per-voxel quantities of the conserved state q = (D, S_x, S_y, S_z, tau) that the recovery
+// uses: E = tau + D, S^2, the bracket's lower end p_lo = max(0, |S| - E) and the cold seed
+// max((1 + 1e-8) p_lo + 1e-300, (Gamma - 1) tau).
+template <class T>
+struct C2pSetup {
+  T D, E, S2, p_lo, cold;
+};
+
+template <class T>
+C2pSetup<T> c2p_setup(double Gamma, const T* q) {
+  C2pSetup<T> c;
+  c.D = q[0];
+  c.E = q[4] + q[0];
+  c.S2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  const T S = sqrt(c.S2);
+  c.p_lo = fmax(T(0.0), S - c.E);
+  c.cold = fmax(T(1.0 + 1e-8) * c.p_lo + T(1e-300), T(Gamma - 1.0) * q[4]);
+  return c;
+}
+
+// Newton from seed s1, then (if have2 and s1 failed) from s2; on a double failure the pressure
+// is `keep`.  Writes (rho, v_x, v_y, v_z, p) with v = S/(E + p), W = 1/sqrt(1 - v^2),
+// rho = D/W, and the total iterations; returns the status 0 / 1 / 2.
+template <class T>
+uint8_t c2p_solve(double Gamma, const T* q, const C2pSetup<T>& c, T s1, T s2, bool have2, T keep, double tol,
+                  int max_iter, T* w, int* total_out) {
+  T p;
+  int it1 = srhd_newton<T>(Gamma, c.D, c.S2, c.E, c.p_lo, s1, tol, max_iter, &p);
+  int total = it1 > 0 ? it1 : -it1;
+  uint8_t st = 0;
+  if (it1 <= 0) {
+    int it2 = have2 ? srhd_newton<T>(Gamma, c.D, c.S2, c.E, c.p_lo, s2, tol, max_iter, &p) : -0;
+    total += it2 > 0 ? it2 : -it2;
+    if (have2 && it2 > 0) st = 1;
+    else { st = 2; p = keep; }
+  }
+  const T Ep = c.E + p;
+  T v[3] = {q[1] / Ep, q[2] / Ep, q[3] / Ep};
+  T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  T W = T(1.0) / sqrt(T(1.0) - v2);
+  w[0] = c.D / W;
+  w[1] = v[0];
+  w[2] = v[1];
+  w[3] = v[2];
+  w[4] = p;
+  *total_out = total;
+  return st;
 }
 
 }  // namespace
@@ -1154,11 +1203,7 @@ int or_con2prim(const double* cons, double* prim, int64_t n, int64_t stride, con
   for (int64_t i = 0; i < n; ++i) {
     double q[5];
     for (int v = 0; v < 5; ++v) q[v] = cons[v * stride + i];
-    const double D = q[0], E = q[4] + q[0];
-    const double S2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    const double S = std::sqrt(S2);
-    const double p_lo = std::max(0.0, S - E);
-    const double cold = std::max((1.0 + 1e-8) * p_lo + 1e-300, (Gamma - 1.0) * q[4]);
+    const C2pSetup<double> c = c2p_setup<double>(Gamma, q);
     double s1, s2;
     bool have2;
     if (mlp) {
@@ -1167,39 +1212,65 @@ int or_con2prim(const double* cons, double* prim, int64_t n, int64_t stride, con
       float x[3], h1[32], h2[32];
       for (int j = 0; j < 3; ++j) x[j] = (float)((xd[j] - (double)mlp[MLP_NW + j]) / (double)mlp[MLP_NW + 3 + j]);
       float y = mlp_forward<float>(mlp, x, h1, h2);
-      double ps = E * std::exp((double)y);
-      double lo = p_lo * (1.0 + 1e-12);
-      s1 = ps > lo ? ps : cold;
-      s2 = p_prev ? p_prev[i] : cold;
+      double ps = c.E * std::exp((double)y);
+      double lo = c.p_lo * (1.0 + 1e-12);
+      s1 = ps > lo ? ps : c.cold;
+      s2 = p_prev ? p_prev[i] : c.cold;
       have2 = true;
     } else {
-      s1 = p_prev ? p_prev[i] : cold;
-      s2 = cold;
+      s1 = p_prev ? p_prev[i] : c.cold;
+      s2 = c.cold;
       have2 = (p_prev != nullptr);
     }
-    double p;
-    int it1 = srhd_newton(Gamma, D, S2, E, p_lo, s1, tol, max_iter, &p);
-    int total = it1 > 0 ? it1 : -it1;
-    uint8_t st = 0;
-    if (it1 <= 0) {
-      int it2 = have2 ? srhd_newton(Gamma, D, S2, E, p_lo, s2, tol, max_iter, &p) : -0;
-      total += it2 > 0 ? it2 : -it2;
-      if (have2 && it2 > 0) st = 1;
-      else { st = 2; p = p_prev ? p_prev[i] : cold; ++fails; }
-    }
-    const double Ep = E + p;
-    double v[3] = {q[1] / Ep, q[2] / Ep, q[3] / Ep};
-    double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-    double W = 1.0 / std::sqrt(1.0 - v2);
-    prim[0 * stride + i] = D / W;
-    prim[1 * stride + i] = v[0];
-    prim[2 * stride + i] = v[1];
-    prim[3 * stride + i] = v[2];
-    prim[4 * stride + i] = p;
+    double w[5];
+    int total = 0;
+    const uint8_t st = c2p_solve<double>(Gamma, q, c, s1, s2, have2, p_prev ? p_prev[i] : c.cold, tol, max_iter, w,
+                                         &total);
+    if (st == 2) ++fails;
+    for (int v = 0; v < 5; ++v) prim[v * stride + i] = w[v];
     if (status) status[i] = st;
     if (iters) iters[i] = total;
   }
   return fails;
+}
+
+// Exact FP64 operation count (counting build) of the recovery of n voxels with the plain seed
+// (p_prev, else the cold seed): the same setup, Newton iterations and recovery as or_con2prim.
+// *iters_out receives the total number of Newton iterations.
+long long or_count_con2prim(const double* cons, int64_t n, int64_t stride, const double* p_prev, double tol,
+                            int max_iter, double Gamma, long long* iters_out) {
+  g_flops = 0;
+  long long it_sum = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    Counted q[5];
+    for (int v = 0; v < 5; ++v) q[v] = Counted(cons[v * stride + i]);
+    const C2pSetup<Counted> c = c2p_setup<Counted>(Gamma, q);
+    const Counted s1 = p_prev ? Counted(p_prev[i]) : c.cold;
+    Counted w[5];
+    int total = 0;
+    c2p_solve<Counted>(Gamma, q, c, s1, c.cold, p_prev != nullptr, s1, tol, max_iter, w, &total);
+    it_sum += total;
+  }
+  if (iters_out) *iters_out = it_sum;
+  return g_flops;
+}
+
+// Exact FP64 operation count of the maximum characteristic speed of n voxels (flat arrays,
+// variable v of voxel i at v * stride + i): derived quantities and the speed in every direction.
+long long or_count_max_speed(int pde, int dim, const double* q, const double* mat, int64_t n, int64_t stride,
+                             const double* prm, int nprm) {
+  const Params P = make_params(pde, prm, nprm);
+  const PdeInfo I = pde_info(pde);
+  g_flops = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    Counted u[64], m[8], W[MAXW];
+    for (int v = 0; v < I.N; ++v) u[v] = Counted(q[v * stride + i]);
+    for (int v = 0; v < I.M; ++v) m[v] = Counted(mat[v * stride + i]);
+    prims(pde, P, u, m, W);
+    Counted lam(0.0);
+    for (int d = 0; d < dim; ++d) lam = fmax(lam, speed(pde, P, d, u, m, W));
+  }
+  return g_flops;
 }
 
 // Inputs of the MLP (z-scored with mean/std in the weight vector) for n voxels.

@@ -87,6 +87,41 @@ def test_stored_table_is_what_the_oracle_counts_now():
     spec = importlib.util.spec_from_file_location("count_flops", os.path.join(ROOT, "oracle", "count_flops.py"))
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
-    fresh = json.loads(json.dumps(mod.compute(), sort_keys=True))
+    table = mod.compute()
+    table.update(mod.con2prim_counts())
+    fresh = json.loads(json.dumps(table, sort_keys=True))
     with open(os.path.join(ROOT, "oracle", "flop_counts.json")) as f:
         assert json.load(f) == fresh
+
+
+# SRHD con2prim, counted by hand from the oracle's formulas (add, sub, mul, div, sqrt = 1):
+#   setup     E = tau + D (1); |S|^2 (3 mul + 2 add); |S| (1); |S| - E (1);
+#             cold seed (1 + 1e-8) p_lo + 1e-300 and (Gamma - 1) tau (3)          = 11
+#   recovery  E + p (1); v = S/(E + p) (3); v^2 (5); W = 1/sqrt(1 - v^2) (3); rho = D/W (1) = 13
+#   iteration y = E + p (1); S^2/y^2 (2); sqrt(1 - .) (2); f (S^2/y, y - ., D rt, -, gf *, - p: 6);
+#             f' (1 + ., D S^2, y^3 rt (3), /, -, gf *, - 1: 9); p - f/f' (2);
+#             |p_new - p| <= tol p_new (2)                                             = 24
+#   speeds    derived quantities: v^2 (5), rho h = rho + Gamma p/(Gamma - 1) (4),
+#             cs^2 = Gamma p/(rho h) (2) = 11; per direction cs (1), 1 - v^2 cs^2 (2),
+#             v_d (1 - cs^2) (2), cs sqrt((1 - v^2)(1 - v^2 cs^2 - v_d^2 (1 - cs^2))) (10),
+#             (a +- r)/den (4) = 19                                                    = 11 + 3 x 19
+C2P_HAND = {"c2p/srhd3d/voxel": 11 + 13, "c2p/srhd3d/newton_iteration": 24, "speed/srhd3d/voxel": 11 + 3 * 19}
+
+
+@pytest.mark.parametrize("key", sorted(C2P_HAND))
+def test_con2prim_counts_are_the_hand_counts(key):
+    with open(os.path.join(ROOT, "oracle", "flop_counts.json")) as f:
+        assert json.load(f)[key]["flops_per_voxel"] == C2P_HAND[key]
+
+
+def test_con2prim_count_of_known_iterations(orc):
+    """At rest the cold seed (Gamma - 1) tau is the root, so Newton stops after one iteration:
+    the counted work of n such voxels is n x (24 + 24)."""
+    n = 64
+    prim = np.zeros((5, n))
+    prim[0] = np.linspace(0.2, 3.0, n)
+    prim[4] = np.linspace(0.1, 5.0, n)
+    cons = orc.prim2con(5, prim, n)
+    fl, it = orc.count_con2prim(cons, n)
+    assert it == n
+    assert fl == n * (C2P_HAND["c2p/srhd3d/voxel"] + C2P_HAND["c2p/srhd3d/newton_iteration"])
