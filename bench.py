@@ -93,6 +93,10 @@ def parse_args():
     ap.add_argument("--no-con2prim", action="store_true", help="skip the con2prim seed comparison")
     ap.add_argument("--no-aoas", action="store_true", help="skip the AoAoS gather/scatter measurement")
     ap.add_argument("--no-offload", action="store_true", help="skip the offload-mode measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload only: skip the per-configuration entries (C1, C3-C5, MUSCL, coupled)")
+    ap.add_argument("--config-cpu-seconds", type=float, default=3.0,
+                    help="budget of the oracle CPU baseline of each per-configuration entry")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (JSON lines): reuse a previous choice, else time and append")
     ap.add_argument("--scale", type=int, default=1,
@@ -166,10 +170,10 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload_config(name, w, mesh):
+def workload_config(name, w, mesh, inner=None):
     spec = WORKLOADS[name]
     return {"workload": name, "description": spec["desc"], "voxels": mesh.nvox, "patches": int(mesh.K),
-            "time_steps_per_step": spec["inner"], "cfl": spec["cfl"], "cuda_graph": True,
+            "time_steps_per_step": spec["inner"] if inner is None else inner, "cfl": spec["cfl"], "cuda_graph": True,
             "time_integrator": {1: "forward Euler", 4: "classical RK4"}.get(
                 spec["rk"], "SSP-RK3, stage-sum (Butcher) form: acc holds the raw face-flux sums"
                 if spec["scheme"] == 0 else "SSP-RK3, Shu-Osher form"),
@@ -616,28 +620,100 @@ def measure_two_offload_problems(torch, dh, plan, mesh, spec, w, arena_init, U1,
             "total_over_compute_1_step_concurrent": par_ms / (2 * compute_ms_per_step)}
 
 
-def our_arm(args, rank, world, local_rank):
-    import torch
-    from paper_2608_19273_gb300 import dh
-    if not torch.cuda.is_available():
-        raise RuntimeError("bench.py needs a CUDA GPU: there is no CPU fallback")
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    name = args.workload
+# Settings of the per-configuration entries of the default line (`configs`): time steps per
+# graph replay, warm-up and timed replays (every state array is larger than L2 except C1's).
+CONFIGS = {
+    "euler2d": dict(label="C1", inner=10, warmup=3, steps=20),
+    "wave3d": dict(label="C3", inner=10, warmup=3, steps=3),
+    "srhd3d": dict(label="C4", inner=10, warmup=3, steps=3),
+    "gw59": dict(label="C5", inner=1, warmup=3, steps=3),
+    "euler3d_muscl": dict(label="C2, second order (MUSCL-minmod)", inner=10, warmup=3, steps=3),
+    "euler3d_amr2": dict(label="C2-like, two coupled refinement levels", inner=20, warmup=3, steps=3),
+}
+
+
+def flop_table():
+    with open(FLOPS_FILE) as fh:
+        return json.load(fh)
+
+
+def hbm_peak():
+    hbm, src = 6800.0, "fallback"
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        with open(mp) as fh:
+            hbm, src = float(json.load(fh).get("hbm_gbs", hbm)), "measured"
+    return hbm, src
+
+
+def offload_blocks(torch, mesh, nq, halo, seed):
+    """Page-locked host AoAoS blocks (one per patch, halo included, back to back in a shuffled
+    order in one buffer): (host buffer, block addresses, device pointer table).  The buffer is
+    zeroed only where the blocks have halo entries (nothing else leaves entries unwritten)."""
+    lens = [(int(pt["p"]) + 2 * halo) ** mesh.dim * nq for pt in mesh.patches]
+    order = np.random.default_rng(seed).permutation(len(lens))
+    starts = np.zeros(len(lens), dtype=np.int64)
+    pos = 0
+    for k in order:
+        starts[k] = pos
+        pos += lens[k]
+    hbuf = torch.empty(pos, dtype=torch.float64, pin_memory=True)
+    if halo > 0:
+        hbuf.zero_()
+    addrs = [hbuf.data_ptr() + 8 * int(starts[k]) for k in range(len(lens))]
+    table = torch.tensor(addrs, dtype=torch.int64, device="cuda")
+    return hbuf, addrs, table
+
+
+def measure_e2e(torch, dh, plan, mesh, spec, w, arena_init, U1, U2, ACC, stream, inner, calls):
+    """End to end through the library's host-buffer entry point: the state lives in page-locked
+    host AoAoS blocks (the paper's layout, Sec. II-B); every call of dh_offload_run gathers all
+    quantities from them over NVLink-C2C, advances `inner` time steps on the GPU and scatters
+    the evolved quantities back into them (paper Sec. III-C/D).  GW59 uses blocks without halo
+    (aos_halo 0) so that its page-locked copy stays at 14.6 GB."""
+    nq = plan.nq + plan.nm
+    halo = 0 if spec["pde"] == synth.PDE_GW59 else w.halo
+    hbuf, addrs, table = offload_blocks(torch, mesh, nq, halo, synth.SEED_BASE + 17)
+    arena = arena_init.clone()
+    dh.dh_scatter_aoas(plan, arena, table, nq, halo, stream)  # the initial state into the host blocks
+    dh.dh_offload_bind(plan, addrs, nq, halo)
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+    nq_back = nq if spec["pde"] == synth.PDE_SRHD3D else plan.nq
+    run = lambda: dh.dh_offload_run(plan, spec["scheme"], spec["rk"], inner, arena, U1, U2, ACC, dt, lam,
+                                    spec["cfl"], 0.1, nq_back, stream)
+    run()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(calls):
+        run()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    finite = bool(torch.isfinite(hbuf).all().item())
+    del hbuf, table, arena
+    return {"value": mesh.nvox * inner * calls / (ms * 1e-3), "unit": UNIT,
+            "h2d_bytes_per_step": int(8 * nq * mesh.nvox), "d2h_bytes_per_step": int(8 * nq_back * mesh.nvox),
+            "api": f"dh_offload_run: gather from page-locked host AoAoS blocks (aos_halo {halo}) over NVLink-C2C, "
+                   f"{inner} time steps, scatter back, per call",
+            "calls": calls, "time_steps_per_call": inner, "ms_per_call": ms / calls, "host_blocks_finite": finite}
+
+
+def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps, inner, e2e_calls, headline):
+    """Build, autotune, capture and time one workload (a graph of `inner` time steps, `warmup`
+    untimed and `steps` timed replays); roofline of its dominant kernel, end-to-end rate through
+    the host-buffer entry point.  Returns (line fields, objects kept for the headline's extras)."""
     spec = WORKLOADS[name]
-    dev = torch.cuda.current_device()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     w = synth.workload(name, scale=args.scale)
     mesh = w.mesh
     h, h_mat, kind = host_inputs(name, w)
-    stream = torch.cuda.Stream()
     srhd = name == "srhd3d"
+    dev = torch.cuda.current_device()
     with torch.cuda.stream(stream):
         plan = dh.Plan(spec["pde"], mesh.dim, mesh.patches, w.halo, mesh.var_stride, w.params)
         d_h = torch.from_numpy(h).to("cuda")
+        del h
         if kind == "prim":
             Q = torch.empty_like(d_h)
             dh.dh_prim2con(plan, d_h, Q, stream)
@@ -656,7 +732,6 @@ def our_arm(args, rank, world, local_rank):
         M_init = mat.clone() if mat is not None else None
         dh.max_wave_speed(plan, Q, mat, lam, stream)
         lam_init = lam.clone()
-        # autotune the stage kernel variant on this workload (U1 is scratch here)
         dh.dh_cfl_dt(plan, lam, spec["cfl"], dt, stream)
         if spec["scheme"] == 2:
             tune = {"note": "one kernel variant (no candidates)"}
@@ -672,12 +747,10 @@ def our_arm(args, rank, world, local_rank):
         if mat is not None:
             mat.copy_(M_init)
         stream.synchronize()
-        inner = spec["inner"]
         dh.dh_graph_capture(plan, spec["scheme"], spec["rk"], inner, Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1,
                             True, stream)
         n_kernels, n_timed = dh.dh_graph_info(plan)
-        peak = measure_fp64_peak(torch, dh, stream, sms)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             dh.dh_graph_launch(plan, stream)
         stream.synchronize()
         if dist:
@@ -688,7 +761,7 @@ def our_arm(args, rank, world, local_rank):
         time.sleep(0.3)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             dh.dh_graph_launch(plan, stream)
         e1.record(stream)
         e1.synchronize()
@@ -700,85 +773,134 @@ def our_arm(args, rank, world, local_rank):
             ms = max_over_ranks(ms, dist, device="cuda")
             dist.barrier()
         finite = bool(torch.isfinite(Q).all().item())
-
-        # end-to-end through the public API with host buffers: every step copies the
-        # state (and material/primitive arena) in from pinned host memory, replays the
-        # graph, and copies the resulting state back
-        h_in = torch.empty(Q.shape, dtype=torch.float64, pin_memory=True)
-        h_in.copy_(Q_init)
-        h_m = None
-        if mat is not None:
-            h_m = torch.empty(mat.shape, dtype=torch.float64, pin_memory=True)
-            h_m.copy_(M_init)
-        h_out = torch.empty_like(h_in, pin_memory=True)
-        n_e2e = max(2, args.steps // 2)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(n_e2e):
-            Q.copy_(h_in, non_blocking=True)
-            if mat is not None:
-                mat.copy_(h_m, non_blocking=True)
-            dh.max_wave_speed(plan, Q, mat, lam, stream)
-            dh.dh_graph_launch(plan, stream)
-            h_out.copy_(Q, non_blocking=True)
-        f1.record(stream)
-        f1.synchronize()
-        e2e_ms = f0.elapsed_time(f1)
-        h2d = int(Q.numel() * 8 + (mat.numel() * 8 if mat is not None else 0))
-
-        offload = None
-        if rank == 0 and not args.no_offload and spec["pde"] != synth.PDE_GW59:
-            a0 = Q_init if M_init is None else torch.cat([Q_init, M_init])
-            offload = measure_offload(torch, dh, plan, mesh, spec, w, a0.contiguous(), U1, U2, ACC, stream, inner,
-                                      ms / args.steps / inner)
+        it_mean = None
+        if srhd:
+            # Newton iterations of a recovery as the step runs it (the evolved state, seeded by
+            # the pressure of the previous stage input), for the whole-step operation count
+            its = torch.empty(mesh.var_stride, dtype=torch.int32, device="cuda")
+            its.zero_()
+            dh.con2prim(plan, Q, U1, mat[4], None, 1e-12, 50, None, its, None, stream)
+            stream.synchronize()
+            it_mean = float(its.double().sum().item()) / mesh.nvox
+        a0 = Q_init if M_init is None else torch.cat([Q_init, M_init])
+        e2e = measure_e2e(torch, dh, plan, mesh, spec, w, a0.contiguous(), U1, U2, ACC, stream, inner, e2e_calls)
 
     nvox = mesh.nvox
-    value = whole_job_rate(world, nvox, inner * args.steps, ms)
-    flops_vs = json.load(open(FLOPS_FILE))[spec["flops"]]["flops_per_voxel"]
+    table = flop_table()
+    flops_vs = table[spec["flops"]]["flops_per_voxel"]
     stage_sum_s = float(stage_ms.sum()) * 1e-3
     ach = flops_vs * nvox * inner / stage_sum_s / 1e12
-    stage_share = float(stage_ms.sum()) / (ms / args.steps)
-    hbm = 6701.5
-    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(mp):
-        hbm = float(json.load(open(mp)).get("hbm_gbs", hbm))
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(name, w, mesh), parallelism="replicas" if world > 1 else "single-gpu",
-                       scale=args.scale),
-        "roofline": {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                     "frac": ach / peak, "traffic": measured_traffic(name, nvox),
-                     "peak_source": "FP64 FMA peak measured live on this GPU (dh_probe_dfma, 2 FLOP per FMA)",
-                     "flops_per_voxel_step": flops_vs,
-                     "timed_launches": int(n_timed), "stage_ms_mean": float(stage_ms.mean()),
-                     "stage_share_of_step": stage_share,
-                     "hbm": {"bytes_per_voxel_step": spec["bytes"], "peak_gbs": hbm,
-                             "achieved_gbs": spec["bytes"] * nvox * inner / stage_sum_s / 1e9,
-                             "frac": spec["bytes"] * nvox * inner / stage_sum_s / 1e9 / hbm}},
-        "e2e": {"value": world * nvox * inner * n_e2e / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": int(Q.numel() * 8)},
-        "gpu_launches": int(n_kernels * args.steps),
-        "autotune": tune,
-        "offload": offload,
-        "clocks": clocks,
-        "state_finite": finite,
-    }
-    del Q, U1, U2, ACC, Q_init, M_init, mat
+    hbm, hbm_src = hbm_peak()
+    roof = {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": measured_traffic(name, nvox),
+            "peak_source": "FP64 FMA peak measured live on this GPU (dh_probe_dfma, 2 FLOP per FMA)",
+            "flops_per_voxel_step": flops_vs, "timed_launches": int(n_timed),
+            "stage_ms_mean": float(stage_ms.mean()),
+            "stage_share_of_step": float(stage_ms.sum()) / (ms / steps),
+            "hbm": {"bytes_per_voxel_step": spec["bytes"], "peak_gbs": hbm, "peak_source": hbm_src,
+                    "achieved_gbs": spec["bytes"] * nvox * inner / stage_sum_s / 1e9,
+                    "frac": spec["bytes"] * nvox * inner / stage_sum_s / 1e9 / hbm}}
+    out = {"value": whole_job_rate(world, nvox, inner * steps, ms), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "warmup": warmup, "config": workload_config(name, w, mesh, inner),
+           "roofline": roof, "e2e": e2e, "gpu_launches": int(n_kernels * steps), "autotune": tune,
+           "clocks": clocks, "state_finite": finite}
+    if srhd:
+        # the whole SSP-RK3 step: three recoveries (the step start's and those of stages 2 and
+        # 3), the step start's wave speed and the three FV stages, all in the timed graph
+        c2p = table["c2p/srhd3d/voxel"]["flops_per_voxel"] + it_mean * table["c2p/srhd3d/newton_iteration"][
+            "flops_per_voxel"]
+        whole = flops_vs + 3 * c2p + table["speed/srhd3d/voxel"]["flops_per_voxel"]
+        step_s = ms * 1e-3 / (steps * inner)
+        ach_w = whole * nvox / step_s / 1e12
+        out["roofline_stage"] = roof
+        out["roofline"] = {"bound": "alu", "kernel": "whole SSP-RK3 step: con2prim (k_con2prim_patches) x 3, "
+                                                      "wave speed, CFL dt, k_fv_stage<SRHD> x 3",
+                           "achieved": ach_w, "peak": peak, "unit": "TFLOP/s", "frac": ach_w / peak,
+                           "traffic": None, "peak_source": roof["peak_source"],
+                           "flops_per_voxel_step": whole,
+                           "flops_breakdown": {"fv_stages": flops_vs, "con2prim_per_call": c2p,
+                                               "con2prim_calls": 3, "newton_iterations_mean": it_mean,
+                                               "wave_speed": table["speed/srhd3d/voxel"]["flops_per_voxel"]},
+                           "hbm": {"bytes_per_voxel_step": spec["bytes"], "peak_gbs": hbm,
+                                   "achieved_gbs": spec["bytes"] * nvox / step_s / 1e9,
+                                   "frac": spec["bytes"] * nvox / step_s / 1e9 / hbm}}
+    keep = None
+    if headline:
+        keep = dict(plan=plan, mesh=mesh, spec=spec, w=w, Q_init=Q_init, M_init=M_init, U1=U1, U2=U2, ACC=ACC)
+    else:
+        plan.close()
+    del Q, U1, U2, ACC, mat
+    return out, keep
+
+
+def our_arm(args, rank, world, local_rank):
+    import torch
+    from paper_2608_19273_gb300 import dh
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU: there is no CPU fallback")
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    name = args.workload
+    spec = WORKLOADS[name]
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.Stream()
+    peak = measure_fp64_peak(torch, dh, stream, sms)
+    inner = spec["inner"]
+    main_, keep = run_workload(torch, dh, name, args, stream, world, dist, peak, args.warmup, args.steps, inner,
+                               max(3, args.steps // 4), headline=True)
+    plan, mesh, w = keep["plan"], keep["mesh"], keep["w"]
+    offload = None
+    if rank == 0 and not args.no_offload and spec["pde"] != synth.PDE_GW59:
+        with torch.cuda.stream(stream):
+            Q_init, M_init = keep["Q_init"], keep["M_init"]
+            a0 = Q_init if M_init is None else torch.cat([Q_init, M_init])
+            offload = measure_offload(torch, dh, plan, mesh, spec, w, a0.contiguous(), keep["U1"], keep["U2"],
+                                      keep["ACC"], stream, inner, main_["ms_per_step"] / inner)
+    keep.clear()
     torch.cuda.empty_cache()
+    hbm, _ = hbm_peak()
+    line = {
+        "metric": METRIC, "value": main_["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(main_["config"], parallelism="replicas" if world > 1 else "single-gpu", scale=args.scale),
+        "roofline": main_["roofline"], "e2e": main_["e2e"], "gpu_launches": main_["gpu_launches"],
+        "autotune": main_["autotune"], "offload": offload, "clocks": main_["clocks"],
+        "state_finite": main_["state_finite"],
+    }
+    if "roofline_stage" in main_:
+        line["roofline_stage"] = main_["roofline_stage"]
     if rank == 0 and not args.no_aoas:
         ao = measure_aoas(torch, dh, plan, mesh, plan.nq + plan.nm, w.halo, stream)
         ao["gather_frac"] = ao["gather_gbs"] / hbm
         ao["scatter_frac"] = ao["scatter_gbs"] / hbm
         line["aoas"] = ao
     plan.close()
+    torch.cuda.empty_cache()
     if rank == 0 and name in ("euler3d", "srhd3d") and not args.no_con2prim:
         line["con2prim"] = con2prim_compare(torch, dh, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample, _ = oracle_sample(name, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    # every other configuration: same measurement with fewer replays, each with its own oracle sample
+    if name == "euler3d" and not args.no_configs:
+        configs = {}
+        for cname, cs in CONFIGS.items():
+            out, _ = run_workload(torch, dh, cname, args, stream, world, dist, peak, cs["warmup"], cs["steps"],
+                                  cs["inner"], 2, headline=False)
+            torch.cuda.empty_cache()
+            out["config"]["label"] = cs["label"]
+            if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                rate, cores, sample, _ = oracle_sample(cname, args.config_cpu_seconds)
+                out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                       "sample": sample}
+            configs[cname] = out
+        line["configs"] = configs
+        line["gpu_launches_configs"] = int(sum(c["gpu_launches"] for c in configs.values()))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -266,7 +266,11 @@ dh_status dh_scatter_aoas(dh_plan* plan, const double* arena, double* const* aos
  * dh_offload_run: gather all nq quantities into `arena` (an nq-variable device
  *   arena: qs = arena, mat = arena + N*var_stride); if cfl > 0 take the wave
  *   speed of the gathered state; n_steps x dh_rk_step (same scheme, rk, cfl,
- *   sigma and buffer rules; u1/u2/acc are N-variable device arenas); scatter
+ *   sigma and buffer rules; u1/u2/acc are N-variable device arenas), launched
+ *   as a graph captured by dh_graph_capture would run them (for n_steps > 1
+ *   SSP-RK3 FV steps of the Euler systems hand the derived quantities of each
+ *   stage result to the next stage, in two arenas the plan allocates once);
+ *   scatter
  *   quantities 0..nq_back-1 of every interior voxel back into the blocks
  *   (nq_back = N returns the evolved state; N + M also the material).
  *   Asynchronous on `stream`; the blocks hold the result once it completes. */

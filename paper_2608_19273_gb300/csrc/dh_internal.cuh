@@ -160,6 +160,11 @@ dh_status amr_couple(dh_plan* plan, const double* qs, const double* mat, double*
 dh_status aoas_move(dh_plan* plan, bool gather, const double* const* blocks, int nq, int v0, int nv, int halo,
                     double* arena, cudaStream_t s);
 
+// n_steps whole Runge-Kutta steps launched eagerly, with the same hand-over of derived
+// quantities between stages that a captured multi-step graph uses (same kernels, same results).
+dh_status rk_steps(dh_plan* plan, int scheme, int rk, int n_steps, double* q, double* u1, double* u2, double* acc,
+                   const double* mat, double* dt, double* lam, double cfl, double sigma, cudaStream_t s);
+
 dh_status launch_fd_stage(dh_plan* plan, const double* qs, const double* q0, double* out, double* acc,
                           const double* mat, const double* dt_dev, double a, double b, double g, double d,
                           double sigma, double* lam_out, cudaStream_t stream);

@@ -144,8 +144,9 @@ dh_status dh_offload_run(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_st
     st = max_wave_speed(plan, arena, mat, lam_dev, stream);
     if (st != DH_OK) return st;
   }
-  for (int i = 0; i < n_steps; ++i) {
-    st = dh_rk_step(plan, scheme, rk, arena, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, stream);
+  // the steps as a captured graph would run them (derived quantities handed between stages)
+  if (n_steps > 0) {
+    st = rk_steps(plan, scheme, rk, n_steps, arena, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, s);
     if (st != DH_OK) return st;
   }
   nvtxRangePushA("dh offload scatter");

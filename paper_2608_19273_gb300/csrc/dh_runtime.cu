@@ -158,6 +158,36 @@ static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* 
   return DH_OK;
 }
 
+// Whether n consecutive steps hand the derived quantities W of each stage result to the next
+// stage (SSP-RK3 FV steps of the Euler systems with a device-side CFL step).
+static bool w_reuse(dh_plan* plan, int scheme, int rk, int n_steps, double cfl) {
+  return scheme == 0 && rk == 3 && cfl > 0 && n_steps > 1 &&
+         (plan->pde == DH_PDE_EULER2D || plan->pde == DH_PDE_EULER3D);
+}
+
+// The plan's two W arenas (allocated once, on first use, and kept by the plan).
+static dh_status w_chain(dh_plan* plan, int n_steps, WChain& wc) {
+  const size_t nw = (size_t)(plan->dim + 3) * (size_t)plan->var_stride;
+  if (!plan->d_w) DH_TRY(cuda_error(cudaMalloc(&plan->d_w, 2 * sizeof(double) * nw), "W arenas"));
+  wc.on = true;
+  wc.next = 0;
+  wc.total = 3 * n_steps;
+  wc.buf[0] = plan->d_w;
+  wc.buf[1] = plan->d_w + nw;
+  return DH_OK;
+}
+
+dh_status rk_steps(dh_plan* plan, int scheme, int rk, int n_steps, double* q, double* u1, double* u2, double* acc,
+                   const double* mat, double* dt, double* lam, double cfl, double sigma, cudaStream_t s) {
+  DH_TRY(check_rk(plan, scheme, rk, q, u1, u2, acc, mat, dt, lam, cfl));
+  Timer T{plan, false, s};
+  WChain wc;
+  if (w_reuse(plan, scheme, rk, n_steps, cfl)) DH_TRY(w_chain(plan, n_steps, wc));
+  for (int i = 0; i < n_steps; ++i)
+    DH_TRY(rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt, lam, cfl, sigma, T, s, wc.on ? &wc : nullptr));
+  return DH_OK;
+}
+
 }  // namespace dh
 
 using namespace dh;
@@ -207,21 +237,13 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
     }
   }
   // hand the derived quantities of the state from one step to the next (SSP-RK3 FV, Euler)
-  const bool reuse = scheme == 0 && rk == 3 && cfl > 0 && n_steps > 1 &&
-                     (plan->pde == DH_PDE_EULER2D || plan->pde == DH_PDE_EULER3D);
-  const size_t nw = (size_t)(plan->dim + 3) * (size_t)plan->var_stride;
-  if (reuse && !plan->d_w)
-    DH_TRY(cuda_error(cudaMalloc(&plan->d_w, 2 * sizeof(double) * nw), "dh_graph_capture: W arenas"));
   WChain wc;
-  wc.on = reuse;
-  wc.total = 3 * n_steps;
-  wc.buf[0] = plan->d_w;
-  wc.buf[1] = plan->d_w ? plan->d_w + nw : nullptr;
+  if (w_reuse(plan, scheme, rk, n_steps, cfl)) DH_TRY(w_chain(plan, n_steps, wc));
   DH_TRY(cuda_error(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"));
   Timer T{plan, timing != 0, s};
   dh_status st = DH_OK;
   for (int i = 0; i < n_steps && st == DH_OK; ++i)
-    st = rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s, &wc);
+    st = rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s, wc.on ? &wc : nullptr);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &graph);
   if (st != DH_OK) { if (graph) cudaGraphDestroy(graph); return st; }
