@@ -354,8 +354,14 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  * caller's buffers (one stage out = qs + dt L(qs), `reps` launches each after a
  * warm-up, CUDA events on `stream`) and keeps the fastest in the plan:
  *   FV (scheme 0): halo ring computed before or after the mid-plane barrier
- *                  x register cap (1 or 2 CTAs per SM) x z-march in whole
- *                  patches or in chunks of <= 16 planes (8 candidates);
+ *                  x register cap (1 or 2 CTAs per SM) x grid (one CTA per
+ *                  tile, or persistent: SMs x resident CTAs taking tiles from an
+ *                  atomic queue) x tile shape (16x16 columns; 32x8 columns for
+ *                  32^3 patches; 8x8 columns grouped four to a CTA -- shapes
+ *                  that change nothing for the plan's patch sizes are skipped)
+ *                  x z-march in whole patches or in chunks of <= 16 planes;
+ *                  the persistent grid and the 32x8 columns with the register
+ *                  cap only (12 to 32 candidates);
  *   FD (scheme 1): register cap x shared-memory staging by plain loads or by
  *                  TMA tensor copies (2 candidates, or 6 with TMA -- 4 for
  *                  GW59; TMA only when every level is a run of back-to-back
@@ -365,14 +371,33 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  * file the choice is first looked up
  * there (one JSON object per line, keyed by GPU name, PDE, scheme and patch-size
  * histogram) and, when timed, appended to it.  choice_out (optional, 4 ints):
- * fv_var, fv_zs, fd_var, 1 if taken from the cache.  times_out (optional, 8
- * floats): ms per launch of each candidate. */
+ * fv_var, fv_zs, fd_var, 1 if taken from the cache.  times_out (optional,
+ * DH_TUNE_MAX_CANDIDATES floats): ms per launch of each candidate, in the order
+ * tile shape, grid, z-march, then fv_var bits 0-1 (unused entries untouched). */
+#define DH_TUNE_MAX_CANDIDATES 64
 dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* out, const double* mat,
                       const double* dt_dev, int32_t reps, const char* cache_path, int32_t* choice_out,
                       float* times_out, void* stream);
-/* Select a variant directly: fv_var 0..3 (bit 0: ring before the barrier,
- * bit 1: two CTAs per SM), fv_zs 0..1 (tile list 1: z-chunks of <= 16 planes, and a
- * thin last wave filled with half-height chunks of the cheapest columns), fd_var
+/* Autotuner over whole time steps: as dh_autotune (same candidates, cache and
+ * outputs; cache key marked with the step kind), but every timed call runs
+ * n_steps time steps exactly as dh_rk_step, dh_offload_run and a captured
+ * graph run them -- for SSP-RK3 FV steps of the Euler systems with acc and
+ * cfl > 0 the stage-sum form with the derived quantities handed from stage to
+ * stage -- so that the choice fits the kernels a graph replays.  Same buffer
+ * rules as dh_rk_step.  q (and for SRHD3D the primitive arena mat) is advanced
+ * by (1 + reps) x n_steps steps per candidate: pass scratch copies.  lam_dev
+ * must hold the wave speed of q on entry when cfl > 0. */
+dh_status dh_autotune_steps(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_steps, double* q, double* u1,
+                            double* u2, double* acc, const double* mat, double* dt_dev, double* lam_dev, double cfl,
+                            double sigma_ko, int32_t reps, const char* cache_path, int32_t* choice_out,
+                            float* times_out, void* stream);
+/* Select a variant directly: fv_var 0..23 (bit 0: ring before the barrier,
+ * bit 1: two CTAs per SM, bit 2: persistent grid with a tile queue, bits 3-4:
+ * tile shape 0 = 16x16 columns for p % 16 == 0 and 8x8 columns grouped four to a
+ * CTA otherwise, 1 = as 0 but 32x8 columns for p % 32 == 0, 2 = 8x8 columns
+ * grouped four to a CTA for every patch; bit 2 and tile shape 1 need bit 1,
+ * DH_EINVAL otherwise), fv_zs 0..1 (z-chunks of <= 16 planes,
+ * and a thin last wave filled with half-height chunks of the cheapest columns), fd_var
  * 0, 2, 4 or 6 (bit 1: two CTAs per SM; bit 2: TMA staging, which needs every
  * run of equal-size patches to be stored back to back with its face
  * neighbours inside the run; DH_EUNSUPPORTED otherwise), or, for systems of
@@ -381,12 +406,13 @@ dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* o
 dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var);
 
 /* Error flags raised on the device by the plan's kernels (bit 0: a bounded
- * wait for a TMA copy gave up, the tile was skipped).  Synchronous; clear != 0
- * resets them. */
+ * wait for a TMA copy gave up: the FD stage skipped the tile, the FV stage
+ * finished the tile on stale data -- either way the launch's results are
+ * invalid).  Synchronous; clear != 0 resets them. */
 dh_status dh_plan_errors(dh_plan* plan, uint32_t* flags, int32_t clear);
 
-/* Test hooks (0 in normal use).  Bit 0: the TMA-staged FD stage arms its
- * barriers but issues no copy, so that its bounded waits run out and the
+/* Test hooks (0 in normal use).  Bit 0: the TMA-staged FD and FV stages arm
+ * their barriers but issue no copy, so that their bounded waits run out and the
  * error flag path can be exercised without any fault. */
 dh_status dh_plan_set_debug(dh_plan* plan, int32_t flags);
 
@@ -408,7 +434,7 @@ dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void*
  * allocator).  The paper has no counterpart: it is a deployment variant of
  * patch_update_fv.  It takes the plan-creation arguments (host patch table,
  * K, var_stride, params) together with the stage arguments of
- * patch_update_fv, and keeps the patch table, the work list and the two
+ * patch_update_fv, and keeps the patch table, the work list and the
  * reduction slots in one file-scope device array of 1,310,976 bytes that
  * every GPU loading the library holds until exit.  Limits: K <= 8192 patches
  * and at most 16384 tile work items (a 16x16 column of a patch, or four 8x8

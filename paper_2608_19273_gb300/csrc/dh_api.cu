@@ -279,11 +279,12 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     }
   }
   finish_params(P);
-  // Tile work lists: 16x16 columns for p % 16 == 0, groups of four 8x8 columns
-  // (same p) otherwise; largest work first.  List 1 also splits the z-march of
-  // the 16x16 columns into chunks of at most 16 planes (more, shorter CTAs), and
-  // fills a thin last wave (two CTAs resident per SM) by splitting the cheapest
-  // full columns into two half-height chunks, which then come last.
+  // Tile work lists, largest work first (see dh_plan::d_wl): 16x16 columns for p % 16 == 0
+  // (tile set 1: 32x8 columns for p % 32 == 0; tile set 2: none), groups of four 8x8
+  // columns of equal p otherwise.  With zs = 1 columns of more than 16 planes march in
+  // chunks of at most 16 planes (more, shorter CTAs), and a thin last wave (two CTAs
+  // resident per SM) is filled by splitting the cheapest full columns into two
+  // half-height chunks, which then come last.
   int n_sm = 152;
   {
     int d = 0;
@@ -291,27 +292,30 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
       n_sm = 152;
     cudaGetLastError();
   }
-  std::vector<Work> lists[2];
-  for (int zs = 0; zs < 2; ++zs) {
-    std::vector<Work>& work = lists[zs];
+  std::vector<Work> lists[dh_plan::NWL];
+  for (int li = 0; li < dh_plan::NWL; ++li) {
+    const int tile = li / 2, zs = li % 2;
+    std::vector<Work>& work = lists[li];
     std::vector<std::vector<std::pair<int, std::pair<int, int>>>> pending(257);
     for (int k = 0; k < K; ++k) {
       const int p = patches[k].p, pz = dim == 3 ? p : 1;
-      if (p % 16 == 0) {
-        const int chunk = (zs == 1 && pz > 16) ? 16 : pz;
-        for (int zz = 0; zz < pz; zz += chunk)
-          for (int yy = 0; yy < p; yy += 16)
-            for (int xx = 0; xx < p; xx += 16) {
-              Work w{};
-              w.cls = 0; w.pz = std::min(chunk, pz - zz); w.z0 = zz;
-              for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
-              w.patch[0] = k; w.x0[0] = (int16_t)xx; w.y0[0] = (int16_t)yy;
-              work.push_back(w);
-            }
-      } else {
+      const int cls = (tile == 1 && p % 32 == 0) ? 2 : (tile != 2 && p % 16 == 0) ? 0 : 1;
+      if (cls == 1) {
         for (int yy = 0; yy < p; yy += 8)
           for (int xx = 0; xx < p; xx += 8) pending[p].push_back({k, {xx, yy}});
+        continue;
       }
+      const int tx = cls == 2 ? 32 : 16, ty = cls == 2 ? 8 : 16;
+      const int chunk = (zs == 1 && pz > 16) ? 16 : pz;
+      for (int zz = 0; zz < pz; zz += chunk)
+        for (int yy = 0; yy < p; yy += ty)
+          for (int xx = 0; xx < p; xx += tx) {
+            Work w{};
+            w.cls = cls; w.pz = std::min(chunk, pz - zz); w.z0 = zz;
+            for (int i = 0; i < 4; ++i) { w.patch[i] = -1; w.x0[i] = 0; w.y0[i] = 0; }
+            w.patch[0] = k; w.x0[0] = (int16_t)xx; w.y0[0] = (int16_t)yy;
+            work.push_back(w);
+          }
     }
     for (int p = 8; p <= 256; p += 8) {
       auto& v = pending[p];
@@ -328,7 +332,7 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     auto cost = [](const Work& w) {
       int ng = 0;
       for (int j = 0; j < 4; ++j) ng += w.patch[j] >= 0;
-      return (long long)(w.cls == 0 ? 256 : 64 * ng) * w.pz;
+      return (long long)(w.cls == 1 ? 64 * ng : 256) * w.pz;
     };
     std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
     if (zs == 1 && dim == 3) {
@@ -337,7 +341,7 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
       std::vector<Work> halves;
       for (int i = (int)work.size() - 1; i >= 0 && m > 0; --i) {
         Work& w = work[i];
-        if (w.cls != 0 || w.pz < 16) continue;
+        if (w.cls == 1 || w.pz < 16) continue;
         Work upper = w;
         w.pz = w.pz / 2;
         upper.pz = upper.pz - w.pz;
@@ -348,11 +352,9 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
       work.insert(work.end(), halves.begin(), halves.end());
       std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
     }
-    for (const Work& w : work) plan->has_cls[w.cls] = true;
-    plan->n_work_z[zs] = (int)work.size();
+    for (const Work& w : work) plan->wl_cls[li][w.cls] = true;
+    plan->n_wl[li] = (int)work.size();
   }
-  plan->h_work = lists[0];
-  plan->n_work = (int)lists[0].size();
 
   // FD tiles: 8x8x4 blocks (p is a multiple of 8)
   std::vector<FdWork> fdw;
@@ -394,17 +396,16 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&plan->num_sms, cudaDevAttrMultiProcessorCount, plan->device);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_patches, sizeof(dh_patch) * K);
   if (e == cudaSuccess) e = cudaMemcpy(plan->d_patches, patches, sizeof(dh_patch) * K, cudaMemcpyHostToDevice);
-  for (int zs = 0; zs < 2 && e == cudaSuccess; ++zs) {
-    e = cudaMalloc(&plan->d_work_z[zs], sizeof(Work) * std::max<size_t>(1, lists[zs].size()));
-    if (e == cudaSuccess && !lists[zs].empty())
-      e = cudaMemcpy(plan->d_work_z[zs], lists[zs].data(), sizeof(Work) * lists[zs].size(), cudaMemcpyHostToDevice);
+  for (int li = 0; li < dh_plan::NWL && e == cudaSuccess; ++li) {
+    e = cudaMalloc(&plan->d_wl[li], sizeof(Work) * std::max<size_t>(1, lists[li].size()));
+    if (e == cudaSuccess && !lists[li].empty())
+      e = cudaMemcpy(plan->d_wl[li], lists[li].data(), sizeof(Work) * lists[li].size(), cudaMemcpyHostToDevice);
   }
-  plan->d_work = plan->d_work_z[0];
   if (e == cudaSuccess && !fdw.empty()) e = cudaMalloc(&plan->d_fdwork, sizeof(FdWork) * fdw.size());
   if (e == cudaSuccess && !fdw.empty())
     e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, 4 * sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, 4 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_red, dh_plan::NRED * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(plan->d_red, 0, dh_plan::NRED * sizeof(unsigned long long));
   if (e == cudaSuccess) {
     dh_status ast = amr_build(plan, patches, K, dim);
     if (ast != DH_OK) { dh_plan_destroy(plan); return ast; }
@@ -432,8 +433,8 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
 dh_status dh_plan_destroy(dh_plan* plan) {
   if (!plan) return DH_OK;
   if (plan->d_patches) cudaFree(plan->d_patches);
-  for (int zs = 0; zs < 2; ++zs)
-    if (plan->d_work_z[zs]) cudaFree(plan->d_work_z[zs]);
+  for (int li = 0; li < dh_plan::NWL; ++li)
+    if (plan->d_wl[li]) cudaFree(plan->d_wl[li]);
   if (plan->d_red) cudaFree(plan->d_red);
   if (plan->d_fdwork) cudaFree(plan->d_fdwork);
   if (plan->d_lvl) cudaFree(plan->d_lvl);

@@ -29,7 +29,7 @@ struct DevParams {
 // One CTA's worth of FV/FD work: up to 4 groups, each a (TX x TY) column of
 // one patch that the CTA marches through all z-planes of that patch.
 struct Work {
-  int32_t cls;    // tile class: 0 = 16x16 columns, 1 group; 1 = 8x8 columns, 4 groups
+  int32_t cls;    // tile class: 0 = one 16x16 column; 1 = four 8x8 columns; 2 = one 32x8 column
   int32_t pz;     // planes to march (p in 3D, 1 in 2D) ...
   int32_t z0;     // ... starting at this plane of the patch
   int32_t patch[4];
@@ -69,16 +69,21 @@ struct dh_plan {
   dh::DevParams params{};
   std::vector<dh_patch> h_patches;
   dh_patch* d_patches = nullptr;
-  // FV / FD tile work list (cost-descending)
-  std::vector<dh::Work> h_work;
-  dh::Work* d_work = nullptr;
-  int n_work = 0;
-  // work lists without / with the z-split of 16x16 columns into chunks of <= 16 planes
-  dh::Work* d_work_z[2] = {nullptr, nullptr};
-  int n_work_z[2] = {0, 0};
-  // kernel variants chosen by the autotuner
+  // FV tile work lists (cost-descending), one per tile set and z-split, list 2 * tile + zs:
+  //   tile set 0: 16x16 columns for p % 16 == 0, groups of four 8x8 columns otherwise;
+  //            1: as 0, but 32x8 columns for p % 32 == 0;
+  //            2: groups of four 8x8 columns for every patch (64 threads per column);
+  //   zs 1: columns of more than 16 planes march in chunks of <= 16 planes, and a thin
+  //         last wave is filled with half-height chunks.
+  static constexpr int NWL = 6;
+  dh::Work* d_wl[NWL] = {};
+  int n_wl[NWL] = {};
+  bool wl_cls[NWL][3] = {};  // tile classes present in each list
+  // kernel variants chosen by the autotuner.  fv_var bits 0-1: halo ring before the
+  // mid-plane barrier, register cap for two CTAs per SM; bit 2: persistent grid with a tile
+  // queue; bits 3-4: tile set
   int fv_var = 2, fv_zs = 0, fd_var = 0;
-  bool has_cls[2] = {false, false};
+  int fv_list() const { return 2 * ((fv_var >> 3) & 3) + fv_zs; }
   // FD tile list (8x8x4 tiles)
   dh::FdWork* d_fdwork = nullptr;
   int n_fdwork = 0;
@@ -115,7 +120,9 @@ struct dh_plan {
   char* stage_host = nullptr;
   int debug_flags = 0;    // test hooks (bit 0: TMA barriers armed but no copy issued)
   // scratch: [0] running max (bit pattern of a non-negative double), [1] CTA ticket counter,
-  // [2] error flags (bit 0: a bounded TMA wait gave up), [3] unused
+  // [2] error flags (bit 0: a bounded TMA wait gave up), [3] tile queue of a persistent FV
+  // launch (two 32-bit words: next tile, CTAs done), [4..7] unused
+  static constexpr int NRED = 8;
   unsigned long long* d_red = nullptr;
   int num_sms = 0;
   // con2prim settings used by dh_rk_step for SRHD3D

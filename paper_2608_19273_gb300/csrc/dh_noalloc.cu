@@ -42,6 +42,7 @@ constexpr size_t NA_SCRATCH_BYTES = NA_RED_BYTES + NA_PATCH_BYTES + NA_WORK_BYTE
 // the size the header states (72-byte patch records, 44-byte work items)
 static_assert(sizeof(dh_patch) == 72 && sizeof(Work) == 44, "record sizes changed: update the stated size");
 static_assert(NA_SCRATCH_BYTES == 1310976, "scratch size changed: update the header");
+static_assert(dh_plan::NRED * sizeof(unsigned long long) <= NA_RED_BYTES, "reduction slots do not fit");
 
 static __device__ __align__(256) unsigned char g_na_scratch[NA_SCRATCH_BYTES];
 
@@ -161,7 +162,7 @@ extern "C" dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_
   std::memcpy(g_na_patches, patches, sizeof(dh_patch) * K);
   e = cudaMemcpyAsync(d_patches, g_na_patches, sizeof(dh_patch) * K, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_work, g_na_work, sizeof(Work) * nw, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(red, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(red, 0, dh_plan::NRED * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_error(e, "patch_update_fv_noalloc: table upload");
 
   // A plan on the stack pointing into the static array: the stage launch path
@@ -175,13 +176,12 @@ extern "C" dh_status patch_update_fv_noalloc(int32_t pde, int32_t dim, const dh_
   if (params && n_params > 0 && (pde == DH_PDE_EULER2D || pde == DH_PDE_EULER3D)) P.gamma = params[0];
   finish_params(P);
   view.d_patches = d_patches;
-  view.d_work = d_work;
-  view.n_work = nw;
-  view.d_work_z[0] = d_work;
-  view.n_work_z[0] = nw;
+  view.d_wl[0] = d_work;
+  view.n_wl[0] = nw;
+  view.fv_var = 2;  // one CTA per tile, register cap for two CTAs per SM, tile set 0
   view.fv_zs = 0;
-  view.has_cls[0] = has_cls[0];
-  view.has_cls[1] = has_cls[1];
+  view.wl_cls[0][0] = has_cls[0];
+  view.wl_cls[0][1] = has_cls[1];
   view.d_red = red;
   return launch_fv_stage(&view, qs, q0, out, acc, mat, dt_dev, a, b, g, d, lam_out_dev, s);
 }

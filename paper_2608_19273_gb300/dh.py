@@ -26,7 +26,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fv_muscl", "patch_update_fd_ko",
            "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_bind_staged", "dh_offload_run", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_autotune_steps", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
 
@@ -63,6 +63,8 @@ def lib():
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
         L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
         L.dh_autotune.argtypes = [vp, i32, vp, vp, vp, vp, i32, ctypes.c_char_p, vp, vp, vp]
+        L.dh_autotune_steps.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, ctypes.c_char_p,
+                                        vp, vp, vp]
         L.dh_plan_set_variant.argtypes = [vp, i32, i32, i32]
         L.dh_plan_errors.argtypes = [vp, vp, i32]
         L.dh_plan_set_debug.argtypes = [vp, i32]
@@ -346,10 +348,24 @@ def dh_probe_dfma(out_dev, n_threads, iters, stream=None):
 def dh_autotune(plan, scheme, qs, out, mat, dt_dev, reps=3, cache_path=None, stream=None):
     """Pick the fastest kernel variant for this plan; returns (fv_var, fv_zs, fd_var, from_cache, times_ms)."""
     choice = (ctypes.c_int32 * 4)()
-    times = (ctypes.c_float * 8)()
+    times = (ctypes.c_float * 64)()  # DH_TUNE_MAX_CANDIDATES
     _check(lib().dh_autotune(plan.handle, int(scheme), _ptr(qs, "qs"), _ptr(out, "out"), _ptr(mat, "mat"),
                              _ptr(dt_dev, "dt"), int(reps), None if cache_path is None else cache_path.encode(),
                              choice, times, _stream(stream)), "dh_autotune")
+    return choice[0], choice[1], choice[2], bool(choice[3]), [float(t) for t in times]
+
+
+def dh_autotune_steps(plan, scheme, rk, n_steps, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko=0.1, reps=2,
+                      cache_path=None, stream=None):
+    """Pick the fastest kernel variant over whole time steps (q, mat are advanced: pass scratch copies);
+    returns (fv_var, fv_zs, fd_var, from_cache, times_ms)."""
+    choice = (ctypes.c_int32 * 4)()
+    times = (ctypes.c_float * 64)()  # DH_TUNE_MAX_CANDIDATES
+    _check(lib().dh_autotune_steps(plan.handle, int(scheme), int(rk), int(n_steps), _ptr(q, "q"), _ptr(u1, "u1"),
+                                   _ptr(u2, "u2"), _ptr(acc, "acc"), _ptr(mat, "mat"), _ptr(dt_dev, "dt"),
+                                   _ptr(lam_dev, "lam"), float(cfl), float(sigma_ko), int(reps),
+                                   None if cache_path is None else cache_path.encode(), choice, times,
+                                   _stream(stream)), "dh_autotune_steps")
     return choice[0], choice[1], choice[2], bool(choice[3]), [float(t) for t in times]
 
 
