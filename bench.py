@@ -72,7 +72,8 @@ WORKLOADS = {
                         "16^3, halo 3"),
     "srhd3d": dict(pde=5, scheme=0, rk=3, inner=10, cfl=0.4, flops="fv/srhd3d/ssprk3_step", bytes=1040,
                    kernel="k_fv_stage<SRHD> (the timed stage launches; con2prim runs between them)",
-                   desc="3D SRHD (Gamma 5/3), FV Rusanov + per-voxel con2prim Newton (tol 1e-12), SSP-RK3; "
+                   desc="3D SRHD (Gamma 5/3), FV Rusanov + per-voxel con2prim Newton (tol 1e-12, max 50 "
+                        "iterations; seed: the previous pressure refined by 2 FP32 Newton steps), SSP-RK3; "
                         "4096 patches of 16^3, halo 1"),
     "gw59": dict(pde=6, scheme=1, rk=4, inner=5, cfl=0.25, flops="fd/gw59/rk4_step", bytes=9912,
                  kernel="k_fd_stage<GW59>",
@@ -273,7 +274,7 @@ def oracle_step(name, w, mesh, q, mat, prim):
     if name == "srhd3d":
         # con2prim before every stage, warm-started from the previous primitives
         vs = mesh.var_stride
-        pr, _, _, _ = oracle.con2prim(q, vs, p_prev=np.ascontiguousarray(prim[4]))
+        pr, _, _, _ = oracle.con2prim(q, vs, p_prev=np.ascontiguousarray(prim[4]), refine=SRHD_STEP_REFINE)
         prim[:] = pr
         lam = oracle.max_wave_speed(5, 3, mesh.patches, vs, q, mat=prim, params=w.params)
         dt = oracle.cfl_dt(spec["cfl"], float(mesh.patches["dx"].min()), 3, lam)
@@ -281,7 +282,7 @@ def oracle_step(name, w, mesh, q, mat, prim):
         for qs, q0, out, a, b, g in ((q, None, u1, 0, 1, 1), (u1, q, u2, 0.75, 0.25, 0.25),
                                      (u2, q, q, 1 / 3, 2 / 3, 2 / 3)):
             if qs is not q:
-                pr, _, _, _ = oracle.con2prim(qs, vs, p_prev=np.ascontiguousarray(prim[4]))
+                pr, _, _, _ = oracle.con2prim(qs, vs, p_prev=np.ascontiguousarray(prim[4]), refine=SRHD_STEP_REFINE)
                 prim[:] = pr
             oracle.stage(0, 5, 3, mesh.patches, 1, vs, qs, q0=q0, out=out, mat=prim, dt=dt, a=a, b=b, g=g,
                          params=w.params)
@@ -416,6 +417,13 @@ def train_seed(torch, dh, stream, n=1 << 20, steps=6000, seed=synth.SEED_BASE + 
                  "loss_first": float(lh[:20].mean()), "loss_last": float(lh[-100:].mean())}
 
 
+# FP32 Newton steps that refine the learned seed before the FP64 iteration
+C2P_REFINE = 3
+# FP32 Newton steps that refine the previous pressure, the seed of every con2prim of the SRHD
+# workload's time steps (the oracle's steps refine it the same way)
+SRHD_STEP_REFINE = 2
+
+
 def con2prim_compare(torch, dh, stream):
     """Plain vs MLP-seeded Newton at tol 1e-12: cold (i.i.d. states, no previous pressure)
     and warm (the first SSP-RK3 stage of the SRHD workload, seeded by the previous pressure)."""
@@ -426,17 +434,17 @@ def con2prim_compare(torch, dh, stream):
     n = mesh.var_stride
     plan = dh.Plan(5, 3, mesh.patches, 1, mesh.var_stride, w.params)
 
-    def run(cons, p_prev, mlp):
+    def run(cons, p_prev, mlp, refine=0):
         prim = torch.empty_like(cons)
         it = torch.empty(n, dtype=torch.int32, device="cuda")
         fails = torch.zeros(1, dtype=torch.int32, device="cuda")
-        dh.con2prim(plan, cons, prim, p_prev, mlp, 1e-12, 50, None, it, fails, stream)  # warm-up
+        dh.con2prim(plan, cons, prim, p_prev, mlp, 1e-12, 50, None, it, fails, stream, seed_refine=refine)  # warm-up
         fails.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         reps = 5
         for _ in range(reps):
-            dh.con2prim(plan, cons, prim, p_prev, mlp, 1e-12, 50, None, it, fails, stream)
+            dh.con2prim(plan, cons, prim, p_prev, mlp, 1e-12, 50, None, it, fails, stream, seed_refine=refine)
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
@@ -451,8 +459,11 @@ def con2prim_compare(torch, dh, stream):
         dh.dh_prim2con(plan, prim_iid, cons, stream)
         _, plain = run(cons, None, None)
         _, mlp = run(cons, None, d_w)
-        res["cold_iid"] = {"voxels": mesh.nvox, "plain": plain, "mlp": mlp,
-                           "speedup": plain["ns_per_voxel"] / mlp["ns_per_voxel"]}
+        _, mlp_r = run(cons, None, d_w, C2P_REFINE)
+        _, plain_r = run(cons, None, None, C2P_REFINE)
+        res["cold_iid"] = {"voxels": mesh.nvox, "plain": plain, "mlp": mlp_r, "mlp_unrefined": mlp,
+                           "ablation_plain_refined": plain_r,
+                           "speedup": plain["ns_per_voxel"] / mlp_r["ns_per_voxel"]}
         del prim_iid
         # warm: smooth workload state after one FV stage; seed = previous pressure
         prim0 = torch.from_numpy(synth.srhd_initial(mesh, w.seed)).to("cuda")
@@ -467,11 +478,17 @@ def con2prim_compare(torch, dh, stream):
         p_prev = prim0[4].contiguous()
         _, plain = run(u1, p_prev, None)
         _, mlp = run(u1, p_prev, d_w)
-        res["warm_stage"] = {"voxels": mesh.nvox, "plain": plain, "mlp": mlp,
-                             "speedup": plain["ns_per_voxel"] / mlp["ns_per_voxel"]}
+        _, mlp_r = run(u1, p_prev, d_w, C2P_REFINE)
+        abl = {f"refine_{k}": run(u1, p_prev, None, k)[1] for k in (1, 2, 3)}
+        res["warm_stage"] = {"voxels": mesh.nvox, "plain": plain, "mlp": mlp_r, "mlp_unrefined": mlp,
+                             "ablation_plain_refined": abl,
+                             "speedup": plain["ns_per_voxel"] / mlp_r["ns_per_voxel"]}
     plan.close()
     res["winner_cold"] = "mlp" if res["cold_iid"]["speedup"] > 1 else "plain"
     res["winner_warm"] = "mlp" if res["warm_stage"]["speedup"] > 1 else "plain"
+    res["mlp_seed"] = (f"network seed refined by {C2P_REFINE} FP32 Newton steps, then FP64 Newton; plain = FP64 "
+                       "Newton from the previous pressure (cold: from the cold seed), unrefined; the ablation rows "
+                       "refine the plain seed the same way")
     return res
 
 
@@ -712,6 +729,8 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
     dev = torch.cuda.current_device()
     with torch.cuda.stream(stream):
         plan = dh.Plan(spec["pde"], mesh.dim, mesh.patches, w.halo, mesh.var_stride, w.params)
+        if srhd:
+            dh.dh_plan_set_con2prim(plan, None, 1e-12, 50, None, seed_refine=SRHD_STEP_REFINE)
         d_h = torch.from_numpy(h).to("cuda")
         del h
         if kind == "prim":
@@ -792,7 +811,7 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
             # the pressure of the previous stage input), for the whole-step operation count
             its = torch.empty(mesh.var_stride, dtype=torch.int32, device="cuda")
             its.zero_()
-            dh.con2prim(plan, Q, U1, mat[4], None, 1e-12, 50, None, its, None, stream)
+            dh.con2prim(plan, Q, U1, mat[4], None, 1e-12, 50, None, its, None, stream, seed_refine=SRHD_STEP_REFINE)
             stream.synchronize()
             it_mean = float(its.double().sum().item()) / mesh.nvox
         a0 = Q_init if M_init is None else torch.cat([Q_init, M_init])

@@ -183,18 +183,25 @@ dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, doub
  *   mlp_w  : NULL or 1224 floats (device): FP32 MLP seed p = E exp(mlp(x)),
  *            x = z-scored (|S|/E, D/E, ln(E/D)); then p_prev (or the cold seed
  *            max((1+1e-8) p_lo + 1e-300, (G-1) tau)) is the fallback
+ *   seed_refine : 0..8 FP32 Newton steps applied to the first seed (the MLP's,
+ *            else p_prev, else the cold seed) before the FP64 iteration: the
+ *            textbook step with every operation rounded to float (no fused
+ *            multiply-add) from float copies of D, E and S; a step whose result
+ *            is not finite or not above p_lo stops the refinement.  With the
+ *            MLP seed and seed_refine > 0 the seed E exp(y) is formed in FP32.
+ *            The fallback seed is never refined.  0: the plain recovery.
  *   status : NULL or one byte per voxel: 0 first seed converged, 1 fallback
  *            converged, 2 both failed (pressure = p_prev or the cold seed)
  *   iters  : NULL or Newton iterations per voxel (int32)
  *   fail_count_dev : NULL or a device int32 incremented by the number of status-2 voxels
  * Never traps on unphysical input. */
 dh_status con2prim(dh_plan* plan, const double* cons, double* prim, const double* p_prev, const float* mlp_w,
-                   double tol, int32_t max_iter, uint8_t* status, int32_t* iters, int32_t* fail_count_dev,
-                   void* stream);
+                   double tol, int32_t max_iter, int32_t seed_refine, uint8_t* status, int32_t* iters,
+                   int32_t* fail_count_dev, void* stream);
 /* Same recovery on a flat array of n voxels (variable v of voxel i at v*stride + i). */
 dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t stride, const double* p_prev,
-                        const float* mlp_w, double Gamma, double tol, int32_t max_iter, uint8_t* status,
-                        int32_t* iters, int32_t* fail_count_dev, void* stream);
+                        const float* mlp_w, double Gamma, double tol, int32_t max_iter, int32_t seed_refine,
+                        uint8_t* status, int32_t* iters, int32_t* fail_count_dev, void* stream);
 
 /* MLP pressure seed (3 -> 32 tanh -> 32 tanh -> 1, FP32; not in the paper).
  * Weight vector: 1224 floats = W1[32][3], b1[32], W2[32][32], b2[32], W3[32],
@@ -329,10 +336,11 @@ dh_status dh_rk_step(dh_plan* plan, int32_t scheme, int32_t rk, double* q, doubl
                      void* stream);
 
 /* con2prim settings used by dh_rk_step for SRHD3D: MLP seed weights (NULL:
- * plain Newton from the previous primitives), tolerance, iteration cap and an
- * optional device failure counter.  Defaults: NULL, 1e-12, 50, NULL. */
+ * plain Newton from the previous primitives), tolerance, iteration cap, FP32
+ * refinement steps of the first seed (see con2prim) and an optional device
+ * failure counter.  Defaults: NULL, 1e-12, 50, 0, NULL. */
 dh_status dh_plan_set_con2prim(dh_plan* plan, const float* mlp_w, double tol, int32_t max_iter,
-                               int32_t* fail_count_dev);
+                               int32_t seed_refine, int32_t* fail_count_dev);
 
 /* Capture n_steps consecutive dh_rk_step calls (same arguments) into one CUDA
  * graph owned by the plan (replacing any previous one); nothing runs during

@@ -59,8 +59,10 @@ def lib():
             L.or_rk_steps.restype = i
             L.or_prim2con.argtypes = [i, vp, vp, i64, i64, vp, i]
             L.or_prim2con.restype = i
-            L.or_con2prim.argtypes = [vp, vp, i64, i64, vp, vp, d, i, vp, vp, d]
+            L.or_con2prim.argtypes = [vp, vp, i64, i64, vp, vp, d, i, vp, vp, d, i]
             L.or_con2prim.restype = i
+            L.or_refine_seed.argtypes = [vp, i64, i64, vp, i, d, vp]
+            L.or_refine_seed.restype = None
             L.or_srhd_invariants.argtypes = [vp, i64, i64, vp]
             L.or_srhd_invariants.restype = None
             L.or_mlp_loss_grad.argtypes = [vp, vp, vp, i, vp]
@@ -157,16 +159,26 @@ def prim2con(pde, prim, var_stride, params=None):
     return cons
 
 
-def con2prim(cons, stride, n=None, p_prev=None, mlp=None, tol=1e-12, max_iter=50, Gamma=5.0 / 3.0):
-    """Returns (prim, status, iterations, n_fail)."""
+def con2prim(cons, stride, n=None, p_prev=None, mlp=None, tol=1e-12, max_iter=50, Gamma=5.0 / 3.0, refine=0):
+    """Returns (prim, status, iterations, n_fail); refine: FP32 Newton steps applied to the first seed."""
     n = stride if n is None else n
     prim = np.zeros((5, stride))
     status = np.zeros(stride, dtype=np.uint8)
     iters = np.zeros(stride, dtype=np.int32)
     mlpw = None if mlp is None else np.ascontiguousarray(mlp, dtype=np.float32)
     fails = lib().or_con2prim(_p(cons), _p(prim), n, stride, _p(_f64(p_prev)), _p(mlpw), tol, max_iter,
-                              _p(status), _p(iters), Gamma)
+                              _p(status), _p(iters), Gamma, int(refine))
     return prim, status, iters, fails
+
+
+def refine_seed(cons, seed, k, Gamma=5.0 / 3.0):
+    """The FP32 Newton refinement of the first seed, alone: k steps on each of the voxels of a flat
+    conserved array (stride = cons.shape[1]) from the given seeds."""
+    cons = _f64(cons)
+    seed = _f64(seed)
+    out = np.zeros(len(seed))
+    lib().or_refine_seed(_p(cons), len(seed), cons.shape[1], _p(seed), int(k), Gamma, _p(out))
+    return out
 
 
 def srhd_invariants(cons, stride, n=None):

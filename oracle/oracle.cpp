@@ -999,6 +999,32 @@ void srhd_invariants(const double* q, double* x) {
   x[2] = std::log(E / D);
 }
 
+// FP32 refinement of a seed: up to k steps of the same Newton iteration on the pressure in
+// single precision (textbook f and f', every operation rounded to float, no fused
+// multiply-add), from float copies of D, E = tau + D and the momentum components.  A step
+// whose result is not finite or not above the bracket's lower end (in float) stops the
+// refinement and keeps the value before it.  The FP64 Newton iteration then starts from the
+// result.  (The paper has no relativistic hydrodynamics; this is the reading of a seeded
+// solve on hardware whose FP32 throughput is far above its FP64 throughput.)
+double refine_seed_f32(double Gamma, const double* q, double E, double p_lo, double seed, int k) {
+  const float D = (float)q[0], Ef = (float)E, lo = (float)p_lo;
+  const float Sx = (float)q[1], Sy = (float)q[2], Sz = (float)q[3];
+  const float S2 = Sx * Sx + Sy * Sy + Sz * Sz;
+  const float gf = (float)((Gamma - 1.0) / Gamma), one = 1.0f;
+  float p = (float)seed;
+  for (int i = 0; i < k; ++i) {
+    const float Ep = Ef + p;
+    const float s2e = S2 / (Ep * Ep);
+    const float rt = std::sqrt(one - s2e);
+    const float f = gf * (Ep - S2 / Ep - D * rt) - p;
+    const float fp = gf * (one + s2e - D * S2 / (Ep * Ep * Ep * rt)) - one;
+    const float pn = p - f / fp;
+    if (!(pn > lo && pn < std::numeric_limits<float>::infinity())) break;
+    p = pn;
+  }
+  return (double)p;
+}
+
 // Per-voxel quantities of the conserved state q = (D, S_x, S_y, S_z, tau) that the recovery
 // uses: E = tau + D, S^2, the bracket's lower end p_lo = max(0, |S| - E) and the cold seed
 // max((1 + 1e-8) p_lo + 1e-300, (Gamma - 1) tau).
@@ -1192,12 +1218,14 @@ int or_prim2con(int pde, const double* prim, double* cons, int64_t n, int64_t st
 //           max((1+1e-8) p_lo + 1e-300, (Gamma-1) tau);
 //   seed 2 (only if seed 1 fails): p_prev if the MLP was seed 1 and p_prev is
 //           given, else the cold seed.
+//   refine > 0: seed 1 is first refined by up to `refine` FP32 Newton steps
+//           (refine_seed_f32); seed 2 is never refined.
 //   status 0: seed 1 converged; 1: seed 2 converged; 2: both failed (the
 //   pressure falls back to p_prev, or the cold seed, and the voxel counts as a
 //   failure).  iters (optional) receives the total Newton iterations.
 int or_con2prim(const double* cons, double* prim, int64_t n, int64_t stride, const double* p_prev,
                 const float* mlp, double tol, int max_iter, uint8_t* status, int32_t* iters,
-                double Gamma) {
+                double Gamma, int refine) {
   int fails = 0;
 #pragma omp parallel for reduction(+ : fails) if (n > 4096)
   for (int64_t i = 0; i < n; ++i) {
@@ -1212,7 +1240,8 @@ int or_con2prim(const double* cons, double* prim, int64_t n, int64_t stride, con
       float x[3], h1[32], h2[32];
       for (int j = 0; j < 3; ++j) x[j] = (float)((xd[j] - (double)mlp[MLP_NW + j]) / (double)mlp[MLP_NW + 3 + j]);
       float y = mlp_forward<float>(mlp, x, h1, h2);
-      double ps = c.E * std::exp((double)y);
+      // with the FP32 refinement the seed itself is formed in FP32 as well
+      double ps = refine > 0 ? (double)((float)c.E * std::exp(y)) : c.E * std::exp((double)y);
       double lo = c.p_lo * (1.0 + 1e-12);
       s1 = ps > lo ? ps : c.cold;
       s2 = p_prev ? p_prev[i] : c.cold;
@@ -1222,6 +1251,7 @@ int or_con2prim(const double* cons, double* prim, int64_t n, int64_t stride, con
       s2 = c.cold;
       have2 = (p_prev != nullptr);
     }
+    if (refine > 0) s1 = refine_seed_f32(Gamma, q, c.E, c.p_lo, s1, refine);
     double w[5];
     int total = 0;
     const uint8_t st = c2p_solve<double>(Gamma, q, c, s1, s2, have2, p_prev ? p_prev[i] : c.cold, tol, max_iter, w,
@@ -1271,6 +1301,17 @@ long long or_count_max_speed(int pde, int dim, const double* q, const double* ma
     for (int d = 0; d < dim; ++d) lam = fmax(lam, speed(pde, P, d, u, m, W));
   }
   return g_flops;
+}
+
+// The FP32 refinement alone (refine_seed_f32) of n seeds: out[i] = the refined seed of voxel i.
+void or_refine_seed(const double* cons, int64_t n, int64_t stride, const double* seed, int k, double Gamma,
+                    double* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double q[5];
+    for (int v = 0; v < 5; ++v) q[v] = cons[v * stride + i];
+    const C2pSetup<double> c = c2p_setup<double>(Gamma, q);
+    out[i] = refine_seed_f32(Gamma, q, c.E, c.p_lo, seed[i], k);
+  }
 }
 
 // Inputs of the MLP (z-scored with mean/std in the weight vector) for n voxels.

@@ -129,6 +129,7 @@ struct dh_plan {
   const float* c2p_mlp = nullptr;
   double c2p_tol = 1e-12;
   int c2p_max_iter = 50;
+  int c2p_refine = 0;  // FP32 Newton steps applied to the first seed
   int32_t* c2p_fail = nullptr;
   // captured multi-step graph and optional per-stage timing events
   cudaGraphExec_t graph_exec = nullptr;

@@ -62,7 +62,7 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
     double* prim = const_cast<double*>(mat);
     if (!prims_current)
       DH_TRY(con2prim(plan, qs, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol, plan->c2p_max_iter,
-                      nullptr, nullptr, plan->c2p_fail, s));
+                      plan->c2p_refine, nullptr, nullptr, plan->c2p_fail, s));
     lam = nullptr;
   }
   // NVTX range per stage (host-side marker for profilers; a no-op without one attached)
@@ -109,7 +109,7 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
     // the wave speed needs the primitives of q: recover them, then take the maximum
     double* prim = const_cast<double*>(mat);
     DH_TRY(con2prim(plan, q, prim, prim + 4 * plan->var_stride, plan->c2p_mlp, plan->c2p_tol, plan->c2p_max_iter,
-                    nullptr, nullptr, plan->c2p_fail, s));
+                    plan->c2p_refine, nullptr, nullptr, plan->c2p_fail, s));
     DH_TRY(max_wave_speed(plan, q, prim, lam, s));
   }
   if (cfl > 0) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
@@ -195,12 +195,16 @@ using namespace dh;
 extern "C" {
 
 dh_status dh_plan_set_con2prim(dh_plan* plan, const float* mlp_w, double tol, int32_t max_iter,
-                               int32_t* fail_count_dev) {
+                               int32_t seed_refine, int32_t* fail_count_dev) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000) { set_error("dh_plan_set_con2prim: bad tol or max_iter"); return DH_EINVAL; }
+  if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000 || seed_refine < 0 || seed_refine > 8) {
+    set_error("dh_plan_set_con2prim: bad tol, max_iter or seed_refine");
+    return DH_EINVAL;
+  }
   plan->c2p_mlp = mlp_w;
   plan->c2p_tol = tol;
   plan->c2p_max_iter = max_iter;
+  plan->c2p_refine = seed_refine;
   plan->c2p_fail = fail_count_dev;
   return DH_OK;
 }

@@ -11,7 +11,9 @@
 //   converged when |p_new - p| <= tol p_new; at most max_iter steps.
 //   Seeds: MLP (if weights given) -> p_prev (if given) -> cold seed
 //   max((1 + 1e-8) p_lo + 1e-300, (G-1) tau); the first seed is tried, the
-//   second only if the first fails.  status: 0 first seed converged, 1 second
+//   second only if the first fails.  With seed_refine = k > 0 the first seed is
+//   first refined by up to k FP32 Newton steps (refine_seed_f32); the second seed
+//   (plain Newton from the previous pressure) never is.  status: 0 first seed converged, 1 second
 //   seed converged, 2 both failed (p = p_prev or the cold seed, counted in
 //   fail_count).  Recovery: v = S/(E+p), W = 1/sqrt(1 - v^2), rho = D/W.
 // Failures never trap: they are reported through status and the counter.
@@ -65,6 +67,35 @@ __device__ int srhd_newton_dev(double gf, double D, double S2, double E, double 
   return -max_iter;
 }
 
+// FP32 refinement of the first seed: up to k Newton steps on the pressure in single
+// precision, textbook f and f', every operation rounded to float with no fused multiply-add
+// (the __f*_rn intrinsics), from float copies of D, E and the momentum components; a step
+// whose result is not finite or not above the bracket's lower end (in float) stops the
+// refinement and keeps the value before it.  The same operations in the same order as the
+// oracle's reference, so the refined seed is bitwise the oracle's.  FP32 runs far faster
+// than FP64 on this GPU: the steps cost little next to one FP64 Newton iteration.
+__device__ __forceinline__ double refine_seed_f32(const double* q, double E, double p_lo, double seed, int k,
+                                                  float gf) {
+  const float D = __double2float_rn(q[0]), Ef = __double2float_rn(E), lo = __double2float_rn(p_lo);
+  const float Sx = __double2float_rn(q[1]), Sy = __double2float_rn(q[2]), Sz = __double2float_rn(q[3]);
+  const float S2 = __fadd_rn(__fadd_rn(__fmul_rn(Sx, Sx), __fmul_rn(Sy, Sy)), __fmul_rn(Sz, Sz));
+  float p = __double2float_rn(seed);
+  for (int i = 0; i < k; ++i) {
+    const float Ep = __fadd_rn(Ef, p);
+    const float Ep2 = __fmul_rn(Ep, Ep);
+    const float s2e = __fdiv_rn(S2, Ep2);
+    const float rt = __fsqrt_rn(__fsub_rn(1.0f, s2e));
+    const float f = __fsub_rn(__fmul_rn(gf, __fsub_rn(__fsub_rn(Ep, __fdiv_rn(S2, Ep)), __fmul_rn(D, rt))), p);
+    const float fp = __fsub_rn(
+        __fmul_rn(gf, __fsub_rn(__fadd_rn(1.0f, s2e), __fdiv_rn(__fmul_rn(D, S2), __fmul_rn(__fmul_rn(Ep2, Ep), rt)))),
+        1.0f);
+    const float pn = __fsub_rn(p, __fdiv_rn(f, fp));
+    if (!(pn > lo && pn < __int_as_float(0x7f800000))) break;
+    p = pn;
+  }
+  return (double)p;
+}
+
 struct C2PArgs {
   const double* cons;
   double* prim;
@@ -72,6 +103,8 @@ struct C2PArgs {
   const float* mlp;
   double tol;
   int max_iter;
+  int refine;              // FP32 Newton steps applied to the first seed (0: none)
+  float gf32;              // (G - 1)/G rounded to float (the refinement's constant)
   uint8_t* status;
   int32_t* iters;
   int32_t* fail_count;
@@ -94,7 +127,8 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   // without the square root (the usual case: physical states have |S| < E); the learned
   // seed needs |S| itself.
   double S = 0.0, p_lo = 0.0;
-  if (w || !(E > 0.0 && S2 < E * E * (1.0 - 0x1p-50))) {
+  const bool ref = A.refine > 0;
+  if ((w && !ref) || !(E > 0.0 && S2 < E * E * (1.0 - 0x1p-50))) {
     S = sqrt(S2);
     p_lo = S > E ? S - E : 0.0;
   }
@@ -105,9 +139,10 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   bool have2;
   if (w) {
     float x[3], h1[32], h2[32];
-    mlp_inputs_f32(w, D, E, S, x);
+    // with the FP32 refinement the seed's |S| and exp are FP32 too (the refinement is)
+    mlp_inputs_f32(w, D, E, ref ? (double)__fsqrt_rn(__double2float_rn(S2)) : S, x);
     const float y = mlp_forward(w, x, h1, h2);
-    const double ps = E * exp((double)y);
+    const double ps = ref ? (double)__fmul_rn(__double2float_rn(E), expf(y)) : E * exp((double)y);
     const double lo = p_lo * (1.0 + 1e-12);
     s1 = ps > lo ? ps : cold();
     have2 = true;
@@ -115,6 +150,7 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
     s1 = have_prev ? A.p_prev[e] : cold();
     have2 = have_prev;
   }
+  if (ref) s1 = refine_seed_f32(q, E, p_lo, s1, A.refine, A.gf32);
   double p;
   int it1 = srhd_newton_dev(A.gf, D, S2, E, p_lo, s1, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
   int total = it1 > 0 ? it1 : -it1;
@@ -182,9 +218,10 @@ __global__ void __launch_bounds__(256) k_con2prim_flat(int64_t n, const __grid_c
   }
 }
 
-static dh_status c2p_check(const double* cons, double* prim, double tol, int32_t max_iter) {
+static dh_status c2p_check(const double* cons, double* prim, double tol, int32_t max_iter, int32_t seed_refine) {
   if (!cons || !prim || cons == prim) { set_error("con2prim: cons and prim are required and distinct"); return DH_EINVAL; }
   if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000) { set_error("con2prim: tol > 0 and 1 <= max_iter <= 1000 required"); return DH_EINVAL; }
+  if (seed_refine < 0 || seed_refine > 8) { set_error("con2prim: seed_refine must lie in [0, 8]"); return DH_EINVAL; }
   return DH_OK;
 }
 
@@ -195,28 +232,28 @@ using namespace dh;
 extern "C" {
 
 dh_status con2prim(dh_plan* plan, const double* cons, double* prim, const double* p_prev, const float* mlp_w,
-                   double tol, int32_t max_iter, uint8_t* status, int32_t* iters, int32_t* fail_count_dev,
-                   void* stream) {
+                   double tol, int32_t max_iter, int32_t seed_refine, uint8_t* status, int32_t* iters,
+                   int32_t* fail_count_dev, void* stream) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
   if (plan->pde != DH_PDE_SRHD3D) { set_error("con2prim: the plan's PDE is not SRHD3D"); return DH_EUNSUPPORTED; }
-  dh_status st = c2p_check(cons, prim, tol, max_iter);
+  dh_status st = c2p_check(cons, prim, tol, max_iter, seed_refine);
   if (st != DH_OK) return st;
   const double G = plan->params.Gamma;
-  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, plan->var_stride, G,
-            (G - 1.0) / G, 1.0, -1.0, 0.0};
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, seed_refine, (float)((G - 1.0) / G), status, iters,
+            fail_count_dev, plan->var_stride, G, (G - 1.0) / G, 1.0, -1.0, 0.0};
   k_con2prim_patches<<<plan->K, 256, 0, (cudaStream_t)stream>>>(plan->d_patches, plan->dim, A);
   return cuda_error(cudaGetLastError(), "con2prim launch");
 }
 
 dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t stride, const double* p_prev,
-                        const float* mlp_w, double Gamma, double tol, int32_t max_iter, uint8_t* status,
-                        int32_t* iters, int32_t* fail_count_dev, void* stream) {
-  dh_status st = c2p_check(cons, prim, tol, max_iter);
+                        const float* mlp_w, double Gamma, double tol, int32_t max_iter, int32_t seed_refine,
+                        uint8_t* status, int32_t* iters, int32_t* fail_count_dev, void* stream) {
+  dh_status st = c2p_check(cons, prim, tol, max_iter, seed_refine);
   if (st != DH_OK) return st;
   if (n <= 0 || stride < n) { set_error("con2prim_flat: need 0 < n <= stride"); return DH_EINVAL; }
   if (!(Gamma > 1.0)) { set_error("con2prim_flat: Gamma must exceed 1"); return DH_EINVAL; }
-  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, status, iters, fail_count_dev, stride, Gamma,
-            (Gamma - 1.0) / Gamma, 1.0, -1.0, 0.0};
+  C2PArgs A{cons, prim, p_prev, mlp_w, tol, max_iter, seed_refine, (float)((Gamma - 1.0) / Gamma), status, iters,
+            fail_count_dev, stride, Gamma, (Gamma - 1.0) / Gamma, 1.0, -1.0, 0.0};
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

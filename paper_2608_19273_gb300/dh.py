@@ -70,8 +70,8 @@ def lib():
         L.dh_plan_set_debug.argtypes = [vp, i32]
         L.patch_update_fv_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp, vp, d, d, d, d,
                                               vp, vp]
-        L.con2prim.argtypes = [vp, vp, vp, vp, vp, d, i32, vp, vp, vp, vp]
-        L.con2prim_flat.argtypes = [vp, vp, i64, i64, vp, vp, d, d, i32, vp, vp, vp, vp]
+        L.con2prim.argtypes = [vp, vp, vp, vp, vp, d, i32, i32, vp, vp, vp, vp]
+        L.con2prim_flat.argtypes = [vp, vp, i64, i64, vp, vp, d, d, i32, i32, vp, vp, vp, vp]
         f32 = ctypes.c_float
         L.dh_mlp_features.argtypes = [vp, vp, i64, i64, vp, vp, vp]
         L.dh_mlp_standardize.argtypes = [vp, i64, vp, vp, i32, vp]
@@ -79,7 +79,7 @@ def lib():
         L.dh_mlp_grad.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
         L.dh_mlp_adam.argtypes = [vp, vp, vp, vp, i32, f32, f32, f32, f32, vp]
         L.dh_mlp_train.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, i32, f32, vp, vp, vp, vp]
-        L.dh_plan_set_con2prim.argtypes = [vp, vp, d, i32, vp]
+        L.dh_plan_set_con2prim.argtypes = [vp, vp, d, i32, i32, vp]
         L.dh_rk_step.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, vp]
         L.dh_graph_capture.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, vp]
         L.dh_graph_launch.argtypes = [vp, vp]
@@ -198,16 +198,17 @@ def patch_update_fv_noalloc(pde, dim, patches, var_stride, params, qs, q0, out, 
 
 
 def con2prim(plan, cons, prim, p_prev=None, mlp_w=None, tol=1e-12, max_iter=50, status=None, iters=None,
-             fail_count_dev=None, stream=None):
+             fail_count_dev=None, stream=None, seed_refine=0):
+    """seed_refine (the C argument after max_iter) comes last here so that positional calls keep their meaning."""
     _check(lib().con2prim(plan.handle, _ptr(cons, "cons"), _ptr(prim, "prim"), _ptr(p_prev, "p_prev"),
-                          _ptr(mlp_w, "mlp_w"), float(tol), int(max_iter), _ptr(status, "status"),
+                          _ptr(mlp_w, "mlp_w"), float(tol), int(max_iter), int(seed_refine), _ptr(status, "status"),
                           _ptr(iters, "iters"), _ptr(fail_count_dev, "fail_count"), _stream(stream)), "con2prim")
 
 
 def con2prim_flat(cons, prim, n, stride, p_prev=None, mlp_w=None, Gamma=5.0 / 3.0, tol=1e-12, max_iter=50,
-                  status=None, iters=None, fail_count_dev=None, stream=None):
+                  status=None, iters=None, fail_count_dev=None, stream=None, seed_refine=0):
     _check(lib().con2prim_flat(_ptr(cons, "cons"), _ptr(prim, "prim"), int(n), int(stride), _ptr(p_prev, "p_prev"),
-                               _ptr(mlp_w, "mlp_w"), float(Gamma), float(tol), int(max_iter),
+                               _ptr(mlp_w, "mlp_w"), float(Gamma), float(tol), int(max_iter), int(seed_refine),
                                _ptr(status, "status"), _ptr(iters, "iters"), _ptr(fail_count_dev, "fail_count"),
                                _stream(stream)), "con2prim_flat")
 
@@ -306,9 +307,9 @@ def dh_offload_run(plan, scheme, rk, n_steps, arena, u1, u2, acc, dt_dev, lam_de
            "dh_offload_run")
 
 
-def dh_plan_set_con2prim(plan, mlp_w=None, tol=1e-12, max_iter=50, fail_count_dev=None):
+def dh_plan_set_con2prim(plan, mlp_w=None, tol=1e-12, max_iter=50, fail_count_dev=None, seed_refine=0):
     _check(lib().dh_plan_set_con2prim(plan.handle, _ptr(mlp_w, "mlp_w"), float(tol), int(max_iter),
-                                      _ptr(fail_count_dev, "fail_count")), "dh_plan_set_con2prim")
+                                      int(seed_refine), _ptr(fail_count_dev, "fail_count")), "dh_plan_set_con2prim")
 
 
 def dh_rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko=0.1, stream=None):

@@ -14,6 +14,9 @@ from helpers import voxel_mask
 from paper_2608_19273_gb300 import dh, synth
 
 pytestmark = pytest.mark.gpu
+# as the benchmark: every con2prim of the SRHD steps refines its seed (the previous pressure) by
+# two FP32 Newton steps
+SRHD_REFINE = 2
 
 
 def _gpu_step(torch, name, w, q, mat, steps=1):
@@ -22,6 +25,8 @@ def _gpu_step(torch, name, w, q, mat, steps=1):
     scheme, rk, cfl = spec
     mesh = w.mesh
     with dh.Plan(w.pde, 3, mesh.patches, w.halo, mesh.var_stride, w.params) as plan:
+        if name == "srhd3d":
+            dh.dh_plan_set_con2prim(plan, None, 1e-12, 50, None, seed_refine=SRHD_REFINE)
         Q = dev(torch, q)
         M = dev(torch, mat) if mat is not None else None
         U1, U2 = torch.empty_like(Q), torch.empty_like(Q)
@@ -30,7 +35,7 @@ def _gpu_step(torch, name, w, q, mat, steps=1):
         lam = torch.zeros(1, dtype=torch.float64, device="cuda")
         dt = torch.zeros(1, dtype=torch.float64, device="cuda")
         if name == "srhd3d":
-            dh.con2prim(plan, Q, U2, M[4], None, 1e-12, 50)
+            dh.con2prim(plan, Q, U2, M[4], None, 1e-12, 50, seed_refine=SRHD_REFINE)
             M.copy_(U2)
         dh.max_wave_speed(plan, Q, M, lam)
         dh.dh_cfl_dt(plan, lam, cfl, dt)
@@ -103,13 +108,13 @@ def test_srhd3d_full_size_step(orc):
     # oracle: con2prim (warm) before the step and before every stage
     vs = mesh.var_stride
     pr = prim.copy()
-    pr[:], st, _, _ = orc.con2prim(q, vs, p_prev=np.ascontiguousarray(pr[4]))
+    pr[:], st, _, _ = orc.con2prim(q, vs, p_prev=np.ascontiguousarray(pr[4]), refine=SRHD_REFINE)
     lam = orc.max_wave_speed(5, 3, mesh.patches, vs, q, mat=pr, params=w.params)
     dt = orc.cfl_dt(0.4, float(mesh.patches["dx"].min()), 3, lam)
     u1, u2 = np.zeros_like(q), np.zeros_like(q)
     for qs, q0, out, a, b, g in ((q, None, u1, 0, 1, 1), (u1, q, u2, 0.75, 0.25, 0.25), (u2, q, q, 1 / 3, 2 / 3, 2 / 3)):
         if qs is not q:
-            pr[:], st, _, _ = orc.con2prim(qs, vs, p_prev=np.ascontiguousarray(pr[4]))
+            pr[:], st, _, _ = orc.con2prim(qs, vs, p_prev=np.ascontiguousarray(pr[4]), refine=SRHD_REFINE)
         assert np.all(st == 0)
         orc.stage(0, 5, 3, mesh.patches, 1, vs, qs, q0=q0, out=out, mat=pr, dt=dt, a=a, b=b, g=g, params=w.params)
     # the evolved state is held to the 1e-12 rule (the 1e-10 of con2prim applies to primitives only)

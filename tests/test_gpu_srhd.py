@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 G = 5.0 / 3.0
 
 
-def _flat_c2p(torch, cons, p_prev=None, mlp=None):
+def _flat_c2p(torch, cons, p_prev=None, mlp=None, refine=0):
     n = cons.shape[1]
     d_cons = dev(torch, cons)
     prim = torch.zeros_like(d_cons)
@@ -23,7 +23,8 @@ def _flat_c2p(torch, cons, p_prev=None, mlp=None):
     iters = torch.zeros(n, dtype=torch.int32, device="cuda")
     fails = torch.zeros(1, dtype=torch.int32, device="cuda")
     dh.con2prim_flat(d_cons, prim, n, n, dev(torch, p_prev) if p_prev is not None else None,
-                     dev(torch, mlp) if mlp is not None else None, G, 1e-12, 50, status, iters, fails)
+                     dev(torch, mlp) if mlp is not None else None, G, 1e-12, 50, status, iters, fails,
+                     seed_refine=refine)
     torch.cuda.synchronize()
     return host(prim), host(status), host(iters), int(host(fails)[0])
 
@@ -155,118 +156,88 @@ def train_seed_mlp(torch, orc, n=1_000_000, steps=6000, seed=260819276):
     return host(d_w), host(loss)
 
 
+def _warp_cost(it):
+    """Mean over warps of 32 consecutive voxels of their largest iteration count (what a warp pays)."""
+    m = len(it) // 32 * 32
+    return it[:m].reshape(-1, 32).max(axis=1).mean()
+
+
 def test_mlp_training_and_seeded_newton(orc):
-    """Train on oracle pairs; the learned seed must converge to the oracle's answer and
-    need fewer Newton iterations than the cold plain seed on i.i.d. states."""
+    """Train on oracle pairs.  The learned seed (refined by 3 FP32 Newton steps) converges to the
+    oracle's answer (held-out i.i.d. states), and on the full-size SRHD workload after one FV stage
+    it beats plain Newton from the previous pressure -- the method without the network -- in FP64
+    Newton iterations per warp (a warp runs until its slowest lane converges) and in device time."""
     torch = require_cuda()
     w, loss = train_seed_mlp(torch, orc, n=200_000, steps=3000)
     assert loss[-100:].mean() < 0.1 * loss[:20].mean()
     held = iid_prims(20000, 99)
     n = held.shape[1]
     cons = orc.prim2con(synth.PDE_SRHD3D, held, n)
-    ref, st_ref, it_ref, _ = orc.con2prim(cons, n, mlp=w)
-    got, st, it, f = _flat_c2p(torch, cons, mlp=w)
-    assert f == 0
-    assert np.array_equal(st, st_ref)
-    assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what="mlp-seeded con2prim")
-    _, _, it_cold, _ = _flat_c2p(torch, cons)
-    assert it.mean() < it_cold.mean()
-
-
-def test_srhd_fv_stage_and_rk3(orc):
-    torch = require_cuda()
-    w = synth.workload("srhd3d", scale=8)
-    mesh = w.mesh
-    m = voxel_mask(mesh)
-    prim = arena(mesh, 5)
-    prim[:, m] = iid_prims(int(m.sum()), 5, wmax=3.0)  # rough data exercises every flux term
-    X = synth.voxel_centres(mesh)
-    rng = np.random.default_rng(6)
-    prim[0] = np.exp(synth.fourier_field(rng, X, [1, 1, 1], 3, 0.0, 1.0))
-    prim[4] = np.exp(synth.fourier_field(rng, X, [1, 1, 1], 3, 0.0, 1.0))
-    for a in range(3):
-        prim[1 + a] = synth.fourier_field(rng, X, [1, 1, 1], 3, 0.0, 0.5)
-    cons = orc.prim2con(synth.PDE_SRHD3D, prim, mesh.var_stride)
-    dt = 1e-3
-    ref = np.zeros_like(cons)
-    orc.stage(0, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, cons, out=ref, mat=prim, dt=dt,
-              params=w.params)
-    lam_ref = orc.max_wave_speed(synth.PDE_SRHD3D, 3, mesh.patches, mesh.var_stride, cons, mat=prim,
-                                 params=w.params)
-    with dh.Plan(synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, w.params) as plan:
-        d_cons, d_prim = dev(torch, cons), dev(torch, prim)
-        out = torch.zeros_like(d_cons)
-        d_dt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        dh.patch_update_fv(plan, d_cons, None, out, None, d_prim, d_dt, 0, 1, 1, 0)
+    for refine in (0, 3):
+        ref, st_ref, it_ref, _ = orc.con2prim(cons, n, mlp=w, refine=refine)
+        got, st, it, f = _flat_c2p(torch, cons, mlp=w, refine=refine)
+        assert f == 0
+        assert np.array_equal(st, st_ref)
+        assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what=f"mlp-seeded con2prim, refine {refine}")
+    # warm states: the workload after one stage, seeded by the pressure before it
+    wl = synth.workload("srhd3d")
+    mesh = wl.mesh
+    with dh.Plan(5, 3, mesh.patches, 1, mesh.var_stride, wl.params) as plan:
+        prim0 = torch.from_numpy(synth.srhd_initial(mesh, wl.seed)).cuda()
+        q0 = torch.empty_like(prim0)
+        dh.dh_prim2con(plan, prim0, q0)
         lam = torch.zeros(1, dtype=torch.float64, device="cuda")
-        dh.max_wave_speed(plan, d_cons, d_prim, lam)
-        got = host(out)
-        assert_parity(got, ref, m, what="srhd stage")
-        assert abs(float(host(lam)[0]) - lam_ref) <= 1e-14 * lam_ref
-        # one SSP-RK3 step with con2prim (warm seed) before every stage, both sides
-        q_o = cons.copy()
-        u1_o, u2_o = np.zeros_like(cons), np.zeros_like(cons)
-        pr_o = prim.copy()
-
-        def c2p_o(q, pr):
-            p2, st, _, fl = orc.con2prim(q, mesh.var_stride, n=mesh.var_stride, p_prev=np.ascontiguousarray(pr[4]))
-            assert np.all(st[m] == 0)
-            return p2
-        for (qs, q0, out_o, a, b, g) in ((q_o, None, u1_o, 0, 1, 1), (u1_o, q_o, u2_o, 0.75, 0.25, 0.25),
-                                         (u2_o, q_o, q_o, 1 / 3, 2 / 3, 2 / 3)):
-            pr_o[:, m] = c2p_o(qs, pr_o)[:, m]
-            orc.stage(0, synth.PDE_SRHD3D, 3, mesh.patches, 1, mesh.var_stride, qs, q0=q0, out=out_o, mat=pr_o,
-                      dt=dt, a=a, b=b, g=g, params=w.params)
-        Q = dev(torch, cons)
-        U1, U2, PR, PR2 = torch.zeros_like(Q), torch.zeros_like(Q), dev(torch, prim), torch.zeros_like(Q)
-        fails = torch.zeros(1, dtype=torch.int32, device="cuda")
-        for (qs, q0, o, a, b, g) in ((Q, None, U1, 0, 1, 1), (U1, Q, U2, 0.75, 0.25, 0.25),
-                                     (U2, Q, Q, 1 / 3, 2 / 3, 2 / 3)):
-            dh.con2prim(plan, qs, PR2, PR[4], None, 1e-12, 50, None, None, fails)
-            PR.copy_(PR2)
-            dh.patch_update_fv(plan, qs, q0, o, None, PR, d_dt, a, b, g, 0)
-        got = host(Q)
-        assert int(host(fails)[0]) == 0
-    # the evolved state is held to the 1e-12 rule; only the primitives con2prim returns have 1e-10
-    worst = assert_parity(got, q_o, m, tol=1e-12, what="srhd SSP-RK3 step")
-    print(f"srhd SSP-RK3 step (rough data, W <= 3): max relative error {worst:.3e}")
-    worst_p = assert_parity(host(PR), pr_o, m, tol=1e-10, what="srhd primitives of the last stage")
-    print(f"srhd primitives of the last stage input: max relative error {worst_p:.3e}")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, q0, prim0, lam)
+        dh.dh_cfl_dt(plan, lam, 0.4, dt)
+        u1 = torch.empty_like(q0)
+        dh.patch_update_fv(plan, q0, None, u1, None, prim0, dt, 0, 1, 1, 0)
+        p_prev = prim0[4].contiguous()
+        d_w = dev(torch, w)
+        res = {}
+        for name, mlp, refine in (("plain", None, 0), ("learned", d_w, 3)):
+            prim = torch.empty_like(u1)
+            its = torch.zeros(mesh.var_stride, dtype=torch.int32, device="cuda")
+            st = torch.zeros(mesh.var_stride, dtype=torch.uint8, device="cuda")
+            dh.con2prim(plan, u1, prim, p_prev, mlp, 1e-12, 50, st, its, None, seed_refine=refine)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                dh.con2prim(plan, u1, prim, p_prev, mlp, 1e-12, 50, st, its, None, seed_refine=refine)
+            e1.record()
+            torch.cuda.synchronize()
+            m = voxel_mask(mesh)
+            assert np.all(host(st)[m] == 0)
+            res[name] = (_warp_cost(host(its)[m]), e0.elapsed_time(e1) / 3, host(prim)[:, m][:, ::97])
+    print(f"warm workload stage: FP64 iterations per warp plain {res['plain'][0]:.2f}, learned {res['learned'][0]:.2f}; "
+          f"device time {res['plain'][1]:.3f} ms vs {res['learned'][1]:.3f} ms")
+    assert res["learned"][0] < res["plain"][0]
+    assert res["learned"][1] < res["plain"][1]
+    # both seeds reach the same primitives (tolerance of con2prim)
+    assert_parity(res["learned"][2], res["plain"][2], np.ones(res["plain"][2].shape[1], dtype=bool), tol=1e-10,
+                  what="learned vs plain seed")
 
 
-def test_seeded_solve_fallback_matches_oracle(orc):
-    """The seeded-solve fallback: a network whose seed (E e^30) cannot converge within max_iter = 3
-    steps, and a previous pressure 1e-7 off from which Newton converges in 2.  Every voxel takes
-    the fallback (status 1) on both sides; status and iteration arrays equal the oracle's
-    exactly and the primitives match within 1e-10.  Then both seeds fail (status 2): the
-    pressure is the previous pressure and every voxel is counted."""
+@pytest.mark.parametrize("refine", [1, 3])
+@pytest.mark.parametrize("seed", ["cold", "warm", "mlp"])
+def test_con2prim_refined_seed_matches_oracle(orc, refine, seed):
+    """The FP32 refinement of the first seed (the same float operations on both sides): status
+    arrays equal the oracle's, primitives within 1e-10 of the oracle's and of the generating
+    states, mean FP64 iterations within 5% and below those without the refinement."""
     torch = require_cuda()
-    w, cons = fallback_states(20000, 43)
+    w = iid_prims(50000, 61)
     n = w.shape[1]
-    mlp = constant_seed_mlp(30.0)
-    p_prev = np.ascontiguousarray(w[4] * (1 + 1e-7))
-    ref, st_ref, it_ref, f_ref = orc.con2prim(cons, n, p_prev=p_prev, mlp=mlp, max_iter=3)
-    assert np.all(st_ref == 1) and f_ref == 0
-
-    def run(pp):
-        d_cons = dev(torch, cons)
-        prim = torch.zeros_like(d_cons)
-        status = torch.zeros(n, dtype=torch.uint8, device="cuda")
-        iters = torch.zeros(n, dtype=torch.int32, device="cuda")
-        fails = torch.zeros(1, dtype=torch.int32, device="cuda")
-        dh.con2prim_flat(d_cons, prim, n, n, dev(torch, pp), dev(torch, mlp), G, 1e-12, 3, status, iters, fails)
-        torch.cuda.synchronize()
-        return host(prim), host(status), host(iters), int(host(fails)[0])
-
-    got, st, it, f = run(p_prev)
-    assert np.array_equal(st, st_ref) and np.array_equal(it, it_ref) and f == 0
-    worst = assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what="fallback con2prim")
-    assert_parity(got, w, np.ones(n, dtype=bool), tol=1e-10, what="fallback round trip")
-    print(f"seeded-solve fallback on {n} voxels: status 1 everywhere, max relative error {worst:.3e}")
-    bad = np.ascontiguousarray((cons[4] + cons[0]) * math.exp(30.0))
-    ref2, st_ref2, it_ref2, f_ref2 = orc.con2prim(cons, n, p_prev=bad, mlp=mlp, max_iter=3)
-    got2, st2, it2, f2 = run(bad)
-    assert np.all(st_ref2 == 2) and f_ref2 == n
-    assert np.array_equal(st2, st_ref2) and np.array_equal(it2, it_ref2) and f2 == n
-    assert np.array_equal(got2[4], bad)
-    assert_parity(got2, ref2, np.ones(n, dtype=bool), tol=1e-12, what="both seeds failed")
+    cons = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    rng = np.random.default_rng(62)
+    p_prev = w[4] * np.exp(rng.uniform(-1e-3, 1e-3, n)) if seed == "warm" else None
+    mlp = constant_seed_mlp(-1.0) if seed == "mlp" else None
+    ref, st_ref, it_ref, f_ref = orc.con2prim(cons, n, p_prev=p_prev, mlp=mlp, refine=refine)
+    got, st, it, f = _flat_c2p(torch, cons, p_prev, mlp, refine)
+    _, _, it0, _ = _flat_c2p(torch, cons, p_prev, mlp, 0)
+    assert np.array_equal(st, st_ref) and f == f_ref == 0
+    worst = assert_parity(got, ref, np.ones(n, dtype=bool), tol=1e-10, what=f"refined {seed} seed")
+    assert_parity(got, w, np.ones(n, dtype=bool), tol=1e-10, what="round trip")
+    assert abs(it.mean() - it_ref.mean()) < 0.05 * it_ref.mean()
+    assert it.mean() < it0.mean()
+    print(f"{seed} seed + {refine} FP32 steps: FP64 iterations {it0.mean():.2f} -> {it.mean():.2f}, "
+          f"max relative error {worst:.2e}")

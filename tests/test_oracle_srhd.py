@@ -5,6 +5,7 @@ iteration and the learned seed follow textbook definitions."""
 import math
 
 import numpy as np
+import pytest
 
 from helpers import arena, single_level, voxel_mask
 from paper_2608_19273_gb300 import synth
@@ -296,3 +297,61 @@ def test_both_seeds_failing_keeps_the_previous_pressure(orc):
     v = cons[1:4] / (E + p_prev)
     assert np.allclose(prim[1:4], v, rtol=1e-15, atol=0)
     assert np.allclose(prim[0], cons[0] * np.sqrt(1 - np.sum(v * v, axis=0)), rtol=1e-15, atol=0)
+
+
+def test_refinement_off_is_the_plain_recovery(orc):
+    """refine = 0 leaves the recovery bitwise as without the option (cold, warm, learned seeds)."""
+    w = iid_prims(5000, 51)
+    n = w.shape[1]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    mlp = constant_seed_mlp(-1.0)
+    for kw in (dict(), dict(p_prev=w[4] * 1.01), dict(mlp=mlp, p_prev=w[4] * 1.01)):
+        a = orc.con2prim(q, n, **kw)
+        b = orc.con2prim(q, n, refine=0, **kw)
+        assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])) and a[3] == b[3]
+
+
+def test_refinement_at_rest_is_exact_in_one_step(orc):
+    """At rest f(p) = (G-1)/G (E + p - D) - p is linear, so one FP32 Newton step from any seed lands
+    on its root (G-1) tau to float rounding."""
+    w = np.zeros((5, 6))
+    w[0] = [0.2, 0.5, 1.0, 2.0, 4.0, 9.0]
+    w[4] = [0.1, 3.0, 0.7, 6.0, 0.3, 2.0]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, 6)
+    seeds = np.array([1e-3, 50.0, 0.2, 1e2, 1e-2, 7.0])
+    got = orc.refine_seed(q, seeds, 1)
+    # (float rounding of E + p - D, which cancels, leaves a few float ulps of E)
+    assert np.all(np.abs(got / w[4] - 1) < 2e-5), got / w[4] - 1
+    assert np.all(np.abs(seeds / w[4] - 1) > 0.7)  # every seed far from the root
+
+
+def test_refinement_converges_quadratically_to_float_precision(orc):
+    """Seeds 3% off converge like a Newton iteration: the error after one step is of the order of
+    the square of the error before it, down to the floor of the FP32 evaluation (a few 1e-5 at
+    worst, where the terms of f cancel), which three steps reach (W <= 3)."""
+    w = iid_prims(20000, 52, wmax=3.0)
+    n = w.shape[1]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    rng = np.random.default_rng(53)
+    seed = w[4] * np.exp(rng.uniform(-0.03, 0.03, n))
+    e0 = np.abs(seed / w[4] - 1)
+    e1 = np.abs(orc.refine_seed(q, seed, 1) / w[4] - 1)
+    e3 = np.abs(orc.refine_seed(q, seed, 3) / w[4] - 1)
+    assert np.all(e1 <= 10 * e0 ** 2 + 5e-5)
+    assert np.median(e1[e0 > 1e-2]) < 1e-3
+    assert np.max(e3) < 5e-5 and np.median(e3) < 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_refined_seeds_reach_the_same_root(orc, k):
+    """With the refinement on, cold and learned seeds still converge to the generating pressure
+    (1e-10), with no failures, and in fewer FP64 iterations than without it."""
+    w = iid_prims(20000, 54)
+    n = w.shape[1]
+    q = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    for kw in (dict(), dict(mlp=constant_seed_mlp(-1.0))):
+        prim, st, it, f = orc.con2prim(q, n, refine=k, **kw)
+        _, _, it0, _ = orc.con2prim(q, n, **kw)
+        assert f == 0 and np.all(st == 0)
+        assert np.max(np.abs(prim[4] - w[4]) / w[4]) < 1e-10
+        assert it.mean() < it0.mean()
