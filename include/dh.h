@@ -366,10 +366,12 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  *                  tile, or persistent: SMs x resident CTAs taking tiles from an
  *                  atomic queue) x tile shape (16x16 columns; 32x8 columns for
  *                  32^3 patches; 8x8 columns grouped four to a CTA -- shapes
- *                  that change nothing for the plan's patch sizes are skipped)
+ *                  that change nothing for the plan's patch sizes are skipped;
+ *                  one 8x8 column per 64-thread CTA) x TMA staging of the column
+ *                  planes (3D Euler)
  *                  x z-march in whole patches or in chunks of <= 16 planes;
  *                  the persistent grid and the 32x8 columns with the register
- *                  cap only (12 to 32 candidates);
+ *                  cap only (20 to 48 candidates);
  *   FD (scheme 1): register cap x shared-memory staging by plain loads or by
  *                  TMA tensor copies (2 candidates, or 6 with TMA -- 4 for
  *                  GW59; TMA only when every level is a run of back-to-back
@@ -403,8 +405,10 @@ dh_status dh_autotune_steps(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n
  * bit 1: two CTAs per SM, bit 2: persistent grid with a tile queue, bits 3-4:
  * tile shape 0 = 16x16 columns for p % 16 == 0 and 8x8 columns grouped four to a
  * CTA otherwise, 1 = as 0 but 32x8 columns for p % 32 == 0, 2 = 8x8 columns
- * grouped four to a CTA for every patch; bit 2 and tile shape 1 need bit 1,
- * DH_EINVAL otherwise), fv_zs 0..1 (z-chunks of <= 16 planes,
+ * grouped four to a CTA for every patch, 3 = one 8x8 column per 64-thread CTA
+ * (small problems); bit 5: TMA-staged column planes (3D Euler); bit 2, tile
+ * shape 1 and bit 5 need bit 1, bit 5 excludes bit 2 and tile shapes 2 and 3,
+ * tile shape 3 excludes bit 2; DH_EINVAL otherwise), fv_zs 0..1 (z-chunks of <= 16 planes,
  * and a thin last wave filled with half-height chunks of the cheapest columns), fd_var
  * 0, 2, 4 or 6 (bit 1: two CTAs per SM; bit 2: TMA staging, which needs every
  * run of equal-size patches to be stored back to back with its face

@@ -299,13 +299,13 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     std::vector<std::vector<std::pair<int, std::pair<int, int>>>> pending(257);
     for (int k = 0; k < K; ++k) {
       const int p = patches[k].p, pz = dim == 3 ? p : 1;
-      const int cls = (tile == 1 && p % 32 == 0) ? 2 : (tile != 2 && p % 16 == 0) ? 0 : 1;
+      const int cls = tile == 3 ? 3 : (tile == 1 && p % 32 == 0) ? 2 : (tile != 2 && p % 16 == 0) ? 0 : 1;
       if (cls == 1) {
         for (int yy = 0; yy < p; yy += 8)
           for (int xx = 0; xx < p; xx += 8) pending[p].push_back({k, {xx, yy}});
         continue;
       }
-      const int tx = cls == 2 ? 32 : 16, ty = cls == 2 ? 8 : 16;
+      const int tx = cls == 2 ? 32 : (cls == 3 ? 8 : 16), ty = cls == 2 ? 8 : (cls == 3 ? 8 : 16);
       const int chunk = (zs == 1 && pz > 16) ? 16 : pz;
       for (int zz = 0; zz < pz; zz += chunk)
         for (int yy = 0; yy < p; yy += ty)
@@ -332,16 +332,16 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     auto cost = [](const Work& w) {
       int ng = 0;
       for (int j = 0; j < 4; ++j) ng += w.patch[j] >= 0;
-      return (long long)(w.cls == 1 ? 64 * ng : 256) * w.pz;
+      return (long long)(w.cls == 1 ? 64 * ng : (w.cls == 3 ? 64 : 256)) * w.pz;
     };
     std::stable_sort(work.begin(), work.end(), [&](const Work& a, const Work& b) { return cost(a) > cost(b); });
     if (zs == 1 && dim == 3) {
-      const long long R = 2LL * n_sm;
+      const long long R = (tile == 3 ? 8LL : 2LL) * n_sm;  // resident CTAs per wave
       long long m = (R - (long long)work.size() % R) % R;
       std::vector<Work> halves;
       for (int i = (int)work.size() - 1; i >= 0 && m > 0; --i) {
         Work& w = work[i];
-        if (w.cls == 1 || w.pz < 16) continue;
+        if (w.cls == 1 || w.pz < 16) continue;  // (16-plane columns split into two chunks of 8)
         Work upper = w;
         w.pz = w.pz / 2;
         upper.pz = upper.pz - w.pz;

@@ -25,6 +25,10 @@ dh_status launch_fv_stage(dh_plan* plan, const double* qs, const double* q0, dou
   A.qs = qs; A.q0 = q0; A.out = out; A.acc = acc; A.mat = mat; A.dt_dev = dt_dev;
   A.a = a; A.b = b; A.g = g; A.d = d;
   A.lam_out = lam_out;
+  // a multi-step sequence asks the last stage of a step to compute the next step's dt
+  A.dt_next = lam_out ? plan->dt_fold : nullptr;
+  A.cfl = plan->dt_fold_cfl;
+  A.dx_dim = plan->dx_min / plan->dim;
   A.red = plan->d_red;
   A.oct = plan->coupled ? plan->d_amr_oct : nullptr;
   A.w_in = w_in;

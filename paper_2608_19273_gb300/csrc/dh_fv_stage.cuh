@@ -57,6 +57,10 @@ struct FvArgs {
   const double* dt_dev;
   double a, b, g, d;
   double* lam_out;
+  // with lam_out: the last CTA also writes the next time step's dt = cfl dx_dim / lambda
+  // (the CFL rule, same expression as dh_cfl_dt), NULL otherwise
+  double* dt_next;
+  double cfl, dx_dim;
   unsigned long long* red;
   unsigned int* queue;  // persistent launch: tile queue head and exit count (two words), else NULL
   int n_work;           // tiles in the work list
@@ -193,7 +197,7 @@ struct FvTile {
   static_assert(!TMA || ((8 * ST_INT) % 128 == 0 && (8 * ST_XS) % 128 == 0 && (8 * ST_YS) % 128 == 0),
                 "TMA destinations must stay 128-byte aligned");
   static constexpr size_t SMEM = SMEM_BASE + (TMA ? 2 * (size_t)ST_BYTES + 128 : 0);
-  static_assert(NT == 256, "tile classes use 256 threads");
+  static_assert(NT == 256 || NT == 64, "tile classes use 256 threads, or 64 (one 8x8 column)");
 
   struct Smem {
     double *Q, *Fx, *Fy, *Lx, *Ly, *Hx, *Hy, *Dx, *Dy;
@@ -629,7 +633,8 @@ static __device__ __forceinline__ double warp_max(double v) {
 }
 
 // Block-wide max, then one atomicMax per CTA and last-CTA publication.
-static __device__ void publish_lambda(double lam, double* lam_out, unsigned long long* red) {
+static __device__ void publish_lambda(double lam, double* lam_out, unsigned long long* red, double* dt_next = nullptr,
+                                      double cfl = 0.0, double dx_dim = 0.0) {
   __shared__ double wmax[32];
   __shared__ bool last;
   lam = warp_max(lam);
@@ -648,7 +653,10 @@ static __device__ void publish_lambda(double lam, double* lam_out, unsigned long
   if (last && threadIdx.x == 0) {
     __threadfence();
     const unsigned long long bits = atomicAdd(red, 0ull);
-    *lam_out = __longlong_as_double((long long)bits);
+    const double lmax = __longlong_as_double((long long)bits);
+    *lam_out = lmax;
+    // every CTA read dt before taking its ticket, so the last one may overwrite it
+    if (dt_next) *dt_next = cfl * dx_dim / lmax;
     red[0] = 0ull;
     red[1] = 0ull;
     __threadfence();
@@ -731,7 +739,40 @@ __global__ void __launch_bounds__(256, (VAR & 2) ? 2 : 1)
   } else {
     fv_run_tile<PDE, EARLY, WM, T32, TMA>(A, A.work[blockIdx.x], smem, lam, &M, bars, &abort_flag);
   }
-  if (A.lam_out) publish_lambda(lam, A.lam_out, A.red);
+  if (A.lam_out) publish_lambda(lam, A.lam_out, A.red, A.dt_next, A.cfl, A.dx_dim);
+}
+
+// Tile set 3: one 8x8 column per 64-thread CTA (small problems: four times the CTAs of the
+// 256-thread tiles, so that more SMs share the FP64 work).
+template <class PDE, int VAR>
+__global__ void __launch_bounds__(64, (VAR & 2) ? 8 : 1) k_fv_stage64(const __grid_constant__ FvArgs A) {
+  extern __shared__ __align__(128) double smem[];
+  constexpr bool EARLY = (VAR & 1) != 0;
+  constexpr int WM = (VAR >> 2) & 3;
+  double lam = 0.0;
+  FvTile<PDE, 8, 8, 1, EARLY, WM>::run(A, A.work[blockIdx.x], smem, lam);
+  if (A.lam_out) publish_lambda(lam, A.lam_out, A.red, A.dt_next, A.cfl, A.dx_dim);
+}
+
+template <class PDE, int VAR>
+static dh_status launch_var64(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
+  constexpr bool EARLY = (VAR & 1) != 0;
+  constexpr int WM = (VAR >> 2) & 3;
+  constexpr size_t smem = FvTile<PDE, 8, 8, 1, EARLY, WM>::SMEM;
+  static int configured_device = -1;
+  if (configured_device != plan->device) {
+    cudaError_t e = cudaFuncSetAttribute(k_fv_stage64<PDE, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv_stage64)");
+    configured_device = plan->device;
+  }
+  const int li = plan->fv_list();
+  FvArgs B = A;
+  B.work = plan->d_wl[li];
+  B.n_work = plan->n_wl[li];
+  B.queue = nullptr;
+  if (B.n_work <= 0) return DH_OK;
+  k_fv_stage64<PDE, VAR><<<B.n_work, 64, smem, stream>>>(B);
+  return cuda_error(cudaGetLastError(), "k_fv_stage64 launch");
 }
 
 template <class PDE, int VAR>
@@ -791,6 +832,18 @@ static dh_status launch_wm(dh_plan* plan, const FvArgs& A, cudaStream_t stream) 
     if constexpr (std::is_same<PDE, PdeEuler3>::value) return fv_launch_euler3_tma(plan, A, WM, stream);
     set_error("k_fv_stage: the TMA-staged variant exists for 3D Euler only");
     return DH_EUNSUPPORTED;
+  }
+  if (((v >> 3) & 3) == 3) {
+    if (v & 4) {
+      set_error("k_fv_stage: tile set 3 runs one CTA per column (no persistent grid)");
+      return DH_EUNSUPPORTED;
+    }
+    switch (v & 3) {
+      case 0: return launch_var64<PDE, 0 | W>(plan, A, stream);
+      case 1: return launch_var64<PDE, 1 | W>(plan, A, stream);
+      case 2: return launch_var64<PDE, 2 | W>(plan, A, stream);
+      default: return launch_var64<PDE, 3 | W>(plan, A, stream);
+    }
   }
   const int ext = ((v & 4) ? 16 : 0) | ((((v >> 3) & 3) == 1) ? 32 : 0);
   if (ext && !(v & 2)) {

@@ -29,7 +29,8 @@ struct DevParams {
 // One CTA's worth of FV/FD work: up to 4 groups, each a (TX x TY) column of
 // one patch that the CTA marches through all z-planes of that patch.
 struct Work {
-  int32_t cls;    // tile class: 0 = one 16x16 column; 1 = four 8x8 columns; 2 = one 32x8 column
+  int32_t cls;    // tile class: 0 = one 16x16 column; 1 = four 8x8 columns; 2 = one 32x8 column;
+                  // 3 = one 8x8 column (a 64-thread CTA)
   int32_t pz;     // planes to march (p in 3D, 1 in 2D) ...
   int32_t z0;     // ... starting at this plane of the patch
   int32_t patch[4];
@@ -73,12 +74,13 @@ struct dh_plan {
   //   tile set 0: 16x16 columns for p % 16 == 0, groups of four 8x8 columns otherwise;
   //            1: as 0, but 32x8 columns for p % 32 == 0;
   //            2: groups of four 8x8 columns for every patch (64 threads per column);
+  //            3: one 8x8 column per 64-thread CTA for every patch (small problems: more CTAs);
   //   zs 1: columns of more than 16 planes march in chunks of <= 16 planes, and a thin
   //         last wave is filled with half-height chunks.
-  static constexpr int NWL = 6;
+  static constexpr int NWL = 8;
   dh::Work* d_wl[NWL] = {};
   int n_wl[NWL] = {};
-  bool wl_cls[NWL][3] = {};  // tile classes present in each list
+  bool wl_cls[NWL][4] = {};  // tile classes present in each list
   // kernel variants chosen by the autotuner.  fv_var bits 0-1: halo ring before the
   // mid-plane barrier, register cap for two CTAs per SM; bit 2: persistent grid with a tile
   // queue; bits 3-4: tile set
@@ -125,6 +127,10 @@ struct dh_plan {
   static constexpr int NRED = 8;
   unsigned long long* d_red = nullptr;
   int num_sms = 0;
+  // set by the runtime around the last FV stage of a time step whose successor's dt that
+  // stage computes in its lambda epilogue (multi-step sequences), NULL otherwise
+  double* dt_fold = nullptr;
+  double dt_fold_cfl = 0.0;
   // con2prim settings used by dh_rk_step for SRHD3D
   const float* c2p_mlp = nullptr;
   double c2p_tol = 1e-12;

@@ -9,6 +9,7 @@
 // memory and is recomputed on the device from the maximum wave speed that the
 // last stage of the previous step produced, so a graph of many steps replays
 // without any host round trip.
+#include <algorithm>
 #include <cstring>
 
 #include <nvtx3/nvToolsExt.h>
@@ -96,12 +97,35 @@ static dh_status stage_call(dh_plan* plan, int scheme, const double* qs, const d
   return T.end();
 }
 
+// Whether the last FV stage of a step can compute the next step's dt in its lambda epilogue:
+// its kernel publishes the wave speed of the step's result itself (not on coupled levels, where
+// the speed is taken after the coupling, nor for SRHD, whose speed comes from the primitives).
+static bool dt_foldable(const dh_plan* plan, int scheme, double cfl) {
+  return scheme == 0 && cfl > 0 && !plan->coupled && plan->pde != DH_PDE_SRHD3D;
+}
+
+// Sets the plan's fold request for the duration of one stage call.
+struct FoldScope {
+  dh_plan* plan;
+  FoldScope(dh_plan* p, double* dt, double cfl) : plan(p) {
+    plan->dt_fold = dt;
+    plan->dt_fold_cfl = cfl;
+  }
+  ~FoldScope() { plan->dt_fold = nullptr; }
+};
+
 // One time step.  bufs: q (state, in/out), u1, u2 (stage buffers), acc (RK4).
+// In a sequence of steps: cfl_done -- the previous step's last stage already computed this
+// step's dt; fold -- this step's last stage computes the next step's dt; fe_dst -- forward
+// Euler writes the new state there (the caller alternates buffers) instead of into u1 and
+// copying it back to q.
 static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u1, double* u2, double* acc,
                          const double* mat, double* dt, double* lam, double cfl, double sigma, Timer& T,
-                         cudaStream_t s, WChain* wc = nullptr) {
+                         cudaStream_t s, WChain* wc = nullptr, bool cfl_done = false, bool fold = false,
+                         double* fe_dst = nullptr) {
   const size_t bytes = sizeof(double) * (size_t)plan->nq * (size_t)plan->var_stride;
   double* lam_last = cfl > 0 ? lam : nullptr;
+  double* const fold_dt = fold ? dt : nullptr;
   // SRHD: with a CFL step the primitives of q are recovered here for the wave speed and
   // then serve the first stage as well
   const bool srhd_cur = cfl > 0 && plan->pde == DH_PDE_SRHD3D;
@@ -112,20 +136,26 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
                     plan->c2p_refine, nullptr, nullptr, plan->c2p_fail, s));
     DH_TRY(max_wave_speed(plan, q, prim, lam, s));
   }
-  if (cfl > 0) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
+  if (cfl > 0 && !cfl_done) DH_TRY(dh_cfl_dt(plan, lam, cfl, dt, s));
   if (rk == 1) {
-    DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s, nullptr,
-                      srhd_cur));
-    DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
+    double* dst = fe_dst ? fe_dst : u1;
+    {
+      FoldScope f(plan, fold_dt, cfl);
+      DH_TRY(stage_call(plan, scheme, q, nullptr, dst, nullptr, mat, dt, 0, 1, 1, 0, sigma, lam_last, T, s, nullptr,
+                        srhd_cur));
+    }
+    if (!fe_dst) DH_TRY(cuda_error(cudaMemcpyAsync(q, u1, bytes, cudaMemcpyDeviceToDevice, s), "copy u1 -> q"));
   } else if (rk == 3 && scheme == 0 && acc) {
     // the stage-sum form of the same scheme: acc carries the raw face-flux sum of the earlier stages
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, acc, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc, srhd_cur, 1));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 0, 0, 0.25, 0, sigma, nullptr, T, s, wc, false, 2));
+    FoldScope f(plan, fold_dt, cfl);
     DH_TRY(stage_call(plan, scheme, u2, q, q, acc, mat, dt, 0, 0, 2.0 / 3.0, 1.0 / 6.0, sigma, lam_last, T, s, wc,
                       false, 3));
   } else if (rk == 3) {
     DH_TRY(stage_call(plan, scheme, q, nullptr, u1, nullptr, mat, dt, 0, 1, 1, 0, sigma, nullptr, T, s, wc, srhd_cur));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, nullptr, mat, dt, 0.75, 0.25, 0.25, 0, sigma, nullptr, T, s, wc));
+    FoldScope f(plan, fold_dt, cfl);
     DH_TRY(stage_call(plan, scheme, u2, q, q, nullptr, mat, dt, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0, sigma, lam_last,
                       T, s, wc));
   } else if (rk == 4) {
@@ -134,11 +164,40 @@ static dh_status rk_step(dh_plan* plan, int scheme, int rk, double* q, double* u
                       srhd_cur));
     DH_TRY(stage_call(plan, scheme, u1, q, u2, acc, mat, dt, 1, 0, 0.5, 1.0 / 3.0, sigma, nullptr, T, s));
     DH_TRY(stage_call(plan, scheme, u2, q, u1, acc, mat, dt, 1, 0, 1.0, 1.0 / 3.0, sigma, nullptr, T, s));
-    DH_TRY(stage_call(plan, scheme, u1, nullptr, nullptr, acc, mat, dt, 0, 0, 0, 1.0 / 6.0, sigma, lam_last, T, s));
+    {
+      FoldScope f(plan, fold_dt, cfl);
+      DH_TRY(stage_call(plan, scheme, u1, nullptr, nullptr, acc, mat, dt, 0, 0, 0, 1.0 / 6.0, sigma, lam_last, T, s));
+    }
     DH_TRY(cuda_error(cudaMemcpyAsync(q, acc, bytes, cudaMemcpyDeviceToDevice, s), "copy acc -> q"));
   } else {
     set_error("dh_rk_step: rk must be 1, 3 or 4");
     return DH_EINVAL;
+  }
+  return DH_OK;
+}
+
+// n_steps consecutive steps: from the second step on, each step's dt is computed by the
+// previous step's last stage (where foldable), and forward Euler alternates between q and u1
+// instead of copying every step's result back to q (one copy at the end if n_steps is odd).
+static dh_status rk_sequence(dh_plan* plan, int scheme, int rk, int n_steps, double* q, double* u1, double* u2,
+                             double* acc, const double* mat, double* dt, double* lam, double cfl, double sigma,
+                             Timer& T, cudaStream_t s, WChain* wc) {
+  const bool fold = dt_foldable(plan, scheme, cfl);
+  const bool pingpong = rk == 1 && n_steps > 1;
+  double* cur = q;
+  double* oth = u1;
+  for (int i = 0; i < n_steps; ++i) {
+    const bool done = fold && i > 0, next = fold && i + 1 < n_steps;
+    if (pingpong) {
+      DH_TRY(rk_step(plan, scheme, rk, cur, oth, u2, acc, mat, dt, lam, cfl, sigma, T, s, nullptr, done, next, oth));
+      std::swap(cur, oth);
+    } else {
+      DH_TRY(rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt, lam, cfl, sigma, T, s, wc, done, next));
+    }
+  }
+  if (cur != q) {
+    const size_t bytes = sizeof(double) * (size_t)plan->nq * (size_t)plan->var_stride;
+    DH_TRY(cuda_error(cudaMemcpyAsync(q, cur, bytes, cudaMemcpyDeviceToDevice, s), "copy result -> q"));
   }
   return DH_OK;
 }
@@ -183,9 +242,7 @@ dh_status rk_steps(dh_plan* plan, int scheme, int rk, int n_steps, double* q, do
   Timer T{plan, false, s};
   WChain wc;
   if (w_reuse(plan, scheme, rk, n_steps, cfl)) DH_TRY(w_chain(plan, n_steps, wc));
-  for (int i = 0; i < n_steps; ++i)
-    DH_TRY(rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt, lam, cfl, sigma, T, s, wc.on ? &wc : nullptr));
-  return DH_OK;
+  return rk_sequence(plan, scheme, rk, n_steps, q, u1, u2, acc, mat, dt, lam, cfl, sigma, T, s, wc.on ? &wc : nullptr);
 }
 
 }  // namespace dh
@@ -245,9 +302,8 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
   if (w_reuse(plan, scheme, rk, n_steps, cfl)) DH_TRY(w_chain(plan, n_steps, wc));
   DH_TRY(cuda_error(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture"));
   Timer T{plan, timing != 0, s};
-  dh_status st = DH_OK;
-  for (int i = 0; i < n_steps && st == DH_OK; ++i)
-    st = rk_step(plan, scheme, rk, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s, wc.on ? &wc : nullptr);
+  dh_status st = rk_sequence(plan, scheme, rk, n_steps, q, u1, u2, acc, mat, dt_dev, lam_dev, cfl, sigma_ko, T, s,
+                             wc.on ? &wc : nullptr);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &graph);
   if (st != DH_OK) { if (graph) cudaGraphDestroy(graph); return st; }
@@ -269,7 +325,10 @@ dh_status dh_graph_capture(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n_
       cpl += plan->amr_restrict_off[l + 1] > plan->amr_restrict_off[l];
   }
   const int cpl_lam = plan->coupled && scheme == 0 && cfl > 0 && !srhd;
-  plan->graph_kernels = n_steps * (nst * (1 + srhd + cpl) + (cfl > 0 ? 1 + srhd + cpl_lam : 0));
+  // the CFL step: one launch per step, or only the first step's where later steps take their dt
+  // from the previous step's last stage
+  const int cfl_steps = cfl > 0 ? (dt_foldable(plan, scheme, cfl) ? 1 : n_steps) : 0;
+  plan->graph_kernels = n_steps * nst * (1 + srhd + cpl) + cfl_steps * (1 + srhd + cpl_lam);
   return DH_OK;
 }
 

@@ -9,9 +9,9 @@
 //             x grid: one CTA per tile, or persistent (SMs x resident CTAs taking tiles
 //               from an atomic queue)
 //             x tile shape: 16x16 columns (256 threads per column), 32x8 columns for
-//               32^3 patches, or 8x8 columns (64 threads) grouped four to a CTA
-//               (up to four patches per CTA) -- tile sets that give the same list as
-//               the first one are skipped
+//               32^3 patches, 8x8 columns (64 threads) grouped four to a CTA (up to
+//               four patches per CTA) -- tile sets that give the same list as the
+//               first one are skipped -- or one 8x8 column per 64-thread CTA
 //             x z-march of whole patches or chunks of <= 16 planes
 //             x loads: plain (L2-prefetched) or, for 3D Euler, TMA tensor copies of every
 //               column plane and its ring strips into a double-buffered shared ring
@@ -88,6 +88,9 @@ static int tune_candidates(const dh_plan* plan, int scheme, Cand* cands) {
             cands[nc++] = {vv | (pers << 2) | (tile << 3), zz, plan->fd_var};
           }
     }
+    // one 8x8 column per 64-thread CTA (every kernel form)
+    for (int zz = 0; zz < 2; ++zz)
+      for (int vv = 0; vv < 4; ++vv) cands[nc++] = {vv | (3 << 3), zz, plan->fd_var};
     // TMA staging of the column planes (3D Euler), with the register cap, one CTA per tile
     if (fv_tma_ok(plan))
       for (int tile = 0; tile < 2; ++tile) {
@@ -178,12 +181,13 @@ dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int3
   const bool fd_ok = fd_var == 0 || fd_var == 2 || fd_var == 4 || fd_var == 6 ||
                      ((fd_var == 12 || fd_var == 20) && plan->pde != DH_PDE_GW59);
   const int tile = (fv_var >> 3) & 3;
-  const bool fv_ok = fv_var >= 0 && fv_var <= 63 && tile <= 2 &&
+  const bool fv_ok = fv_var >= 0 && fv_var <= 63 &&
                      (!((fv_var & 4) || tile == 1 || (fv_var & 32)) || (fv_var & 2)) &&
-                     (!(fv_var & 32) || (!(fv_var & 4) && tile <= 1));
+                     (!(fv_var & 32) || (!(fv_var & 4) && tile <= 1)) && (tile != 3 || !(fv_var & 4));
   if (!fv_ok || fv_zs < 0 || fv_zs > 1 || !fd_ok) {
-    set_error("dh_plan_set_variant: fv_var in 0..63 (tile set <= 2; bit 2, tile set 1 and bit 5 need bit 1; bit 5 "
-              "excludes bit 2 and tile set 2), fv_zs in 0..1, fd_var in {0, 2, 4, 6} (and 12, 20 except for GW59)");
+    set_error("dh_plan_set_variant: fv_var in 0..63 (bit 2, tile set 1 and bit 5 need bit 1; bit 5 excludes bit 2 "
+              "and tile sets 2, 3; tile set 3 excludes bit 2), fv_zs in 0..1, fd_var in {0, 2, 4, 6} (and 12, 20 "
+              "except for GW59)");
     return DH_EINVAL;
   }
   if ((fv_var & 32) && !fv_tma_ok(plan)) {

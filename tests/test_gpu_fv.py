@@ -262,3 +262,41 @@ def test_stage_sum_form_rejects_aliased_acc():
         dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
         with pytest.raises(dh.DhError):
             dh.dh_rk_step(plan, FV, 3, Q, U1, U2, U1, None, dt, None, 0.0, 0.0)
+
+
+@pytest.mark.parametrize("fv_var", [0, 3, 24, 27])
+@pytest.mark.parametrize("n_steps", [10, 9])
+def test_euler2d_graph_steps_fold_dt_and_alternate_buffers(orc, fv_var, n_steps):
+    """The 2D workload as a captured graph of forward-Euler steps: the steps alternate between the
+    state and the stage buffer (one copy at the end when their number is odd), and from the second
+    step on each step's dt is written by the previous step's stage in its lambda epilogue (one CFL
+    launch per graph).  Result and every step's dt against the oracle, with 16x16 columns and with
+    one 8x8 column per 64-thread CTA; the graph holds n_steps + 1 kernel launches."""
+    torch = require_cuda()
+    w = synth.workload("euler2d")
+    mesh = w.mesh
+    q = _euler_cons(orc, mesh, w.seed, synth.PDE_EULER2D)
+    ref = q.copy()
+    dts = orc.rk_steps(FV, 2, 2, mesh.patches, 1, mesh.var_stride, ref, rk=1, steps=2 * n_steps, cfl=0.4)
+    with dh.Plan(2, 2, mesh.patches, 1, mesh.var_stride) as plan:
+        dh.dh_plan_set_variant(plan, fv_var, 0, 0)
+        Q = dev(torch, q)
+        U1 = torch.empty_like(Q)
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, Q, None, lam)
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        dh.dh_graph_capture(plan, FV, 1, n_steps, Q, U1, None, None, None, dt, lam, 0.4, 0.0, 0, s)
+        n_kernels, _ = dh.dh_graph_info(plan)
+        assert n_kernels == n_steps + 1
+        dh.dh_graph_launch(plan, s)
+        s.synchronize()
+        dt_mid = float(host(dt)[0])
+        dh.dh_graph_launch(plan, s)
+        s.synchronize()
+        got, dt_last = host(Q), float(host(dt)[0])
+    # dt_dev holds the dt of the last step taken (the graph's last step does not fold)
+    assert abs(dt_mid - dts[n_steps - 1]) <= 1e-15 * dts[n_steps - 1]
+    assert abs(dt_last - dts[-1]) <= 1e-15 * dts[-1]
+    assert_parity(got, ref, voxel_mask(mesh), what=f"euler2d graph, {2 * n_steps} steps, variant {fv_var}")

@@ -13,6 +13,8 @@ pytestmark = pytest.mark.gpu
 # every valid FV variant: bits 0-1 kernel form, bit 2 persistent grid, bits 3-4 tile shape (the
 # persistent grid and 32x8 columns come with the register cap, bit 1)
 FV_VARIANTS = [v for v in range(24) if (v >> 3) <= 2 and (v & 2 or not (v & 4 or (v >> 3) == 1))]
+# one 8x8 column per 64-thread CTA (tile set 3), every kernel form, no persistent grid
+FV_VARIANTS += [24, 25, 26, 27]
 # TMA staging of the column planes (bit 5; 3D Euler): register cap, one CTA per tile, tile shape 0 or 1
 FV_TMA_VARIANTS = [34, 35, 42, 43]
 
@@ -79,12 +81,13 @@ def test_autotune_picks_and_caches(orc, tmp_path):
         assert not cached and v in FV_VARIANTS + FV_TMA_VARIANTS and z in (0, 1)
         timed = [t for t in times if t > 0]
         # candidate order: tile shape, grid, z-march, kernel form (bits 0-1); the mix has 32^3
-        # and 16^3 patches, so all three tile shapes are candidates (32), then the TMA-staged
-        # variants (8)
+        # and 16^3 patches, so all three tile shapes are candidates (32), then one 8x8 column
+        # per 64-thread CTA (8), then the TMA-staged variants (8)
         order = [(vv | (pers << 2) | (tile << 3), zz) for tile in range(3) for pers in range(2) for zz in range(2)
                  for vv in range(4) if not ((pers or tile == 1) and not vv & 2)]
+        order += [(24 | vv, zz) for zz in range(2) for vv in range(4)]
         order += [(32 | vv | (tile << 3), zz) for tile in range(2) for zz in range(2) for vv in (2, 3)]
-        assert len(order) == 40 and len(timed) == len(order)
+        assert len(order) == 48 and len(timed) == len(order)
         assert min(timed) == timed[order.index((v, z))]
     with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
         v2, z2, f2, cached2, _ = dh.dh_autotune(plan, 0, qs, out, None, d_dt, reps=2, cache_path=cache)
@@ -136,7 +139,7 @@ def test_variant_rules_rejected(orc):
     require_cuda()
     mesh = synth.euler3d_amr_mesh(scale=8)
     with dh.Plan(3, 3, mesh.patches, 1, mesh.var_stride) as plan:
-        for bad in (4, 5, 8, 9, 24, 31, 32, 33, 38, 50, 64):
+        for bad in (4, 5, 8, 9, 28, 31, 32, 33, 38, 50, 58, 64):
             with pytest.raises(dh.DhError):
                 dh.dh_plan_set_variant(plan, bad, 0, 0)
     # the TMA-staged variant is 3D Euler only
@@ -146,7 +149,7 @@ def test_variant_rules_rejected(orc):
             dh.dh_plan_set_variant(plan, 34, 0, 0)
 
 
-@pytest.mark.parametrize("fv_var", [2 | 4, 2 | 8, 3 | 4 | 8, 2 | 16, 3 | 4 | 16])
+@pytest.mark.parametrize("fv_var", [2 | 4, 2 | 8, 3 | 4 | 8, 2 | 16, 3 | 4 | 16, 24, 3 | 24])
 @pytest.mark.parametrize("pde", [synth.PDE_EULER3D, synth.PDE_SRHD3D, synth.PDE_EULER2D])
 def test_new_fv_variants_in_captured_graph_steps(orc, fv_var, pde):
     """Persistent grids and the new tile shapes over whole time steps: three SSP-RK3 steps in a
@@ -280,7 +283,7 @@ def test_autotune_steps_picks_a_variant_of_the_step_path(orc, tmp_path):
         v, z, f, cached, times = dh.dh_autotune_steps(plan, 0, 3, 1, Qt, U1, U2, R, None, dt, lam_t, 0.4, 0.1, reps=1,
                                                       cache_path=cache)
         assert not cached and v in FV_VARIANTS + FV_TMA_VARIANTS
-        assert len([x for x in times if x > 0]) == 40
+        assert len([x for x in times if x > 0]) == 48
         # the stage tuner's cache entry (other key) is not taken for the step tuner, and vice versa
         v2, z2, _, cached2, _ = dh.dh_autotune_steps(plan, 0, 3, 1, Qt, U1, U2, R, None, dt, lam_t, 0.4, 0.1,
                                                      reps=1, cache_path=cache)
