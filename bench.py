@@ -752,21 +752,21 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
         dh.max_wave_speed(plan, Q, mat, lam, stream)
         lam_init = lam.clone()
         dh.dh_cfl_dt(plan, lam, spec["cfl"], dt, stream)
-        if spec["scheme"] == 2:
-            tune = {"note": "one kernel variant (no candidates)"}
-        elif spec["scheme"] == 0:
+        if spec["scheme"] in (0, 2):
             # FV: tune whole time steps as the graph runs them (stage-sum form, derived quantities
             # handed between stages), on scratch copies of the state
             Qt = Q.clone()
             Mt = mat.clone() if mat is not None else None
             lam_t = lam.clone()
             # (two steps per call: the hand-over of derived quantities starts with the second stage)
-            tv, tz, tf, cached, ttimes = dh.dh_autotune_steps(plan, 0, spec["rk"], 2, Qt, U1, U2, ACC, Mt, dt, lam_t,
+            tv, tz, tf, cached, ttimes = dh.dh_autotune_steps(plan, spec["scheme"], spec["rk"], 2, Qt, U1, U2, ACC, Mt,
+                                                              dt, lam_t,
                                                               spec["cfl"], 0.1, reps=2, cache_path=args.tune_cache,
                                                               stream=stream)
             del Qt, Mt, lam_t
-            tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf, "from_cache": cached, "timed": "two time steps per call",
-                    "candidate_ms": [round(t, 4) for t in ttimes if t > 0]}
+            tune = ({"fv2_var": tv} if spec["scheme"] == 2 else {"fv_var": tv, "fv_zs": tz, "fd_var": tf})
+            tune.update({"from_cache": cached, "timed": "two time steps per call",
+                         "candidate_ms": [round(t, 4) for t in ttimes if t > 0]})
         else:
             tv, tz, tf, cached, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3,
                                                         cache_path=args.tune_cache, stream=stream)

@@ -372,6 +372,7 @@ dh_status dh_graph_stage_times(dh_plan* plan, float* ms_out, int32_t n);
  *                  x z-march in whole patches or in chunks of <= 16 planes;
  *                  the persistent grid and the 32x8 columns with the register
  *                  cap only (20 to 48 candidates);
+ *   FV2 (scheme 2): the three variants of dh_plan_set_variant_muscl;
  *   FD (scheme 1): register cap x shared-memory staging by plain loads or by
  *                  TMA tensor copies (2 candidates, or 6 with TMA -- 4 for
  *                  GW59; TMA only when every level is a run of back-to-back
@@ -416,6 +417,16 @@ dh_status dh_autotune_steps(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n
  * at most five variables (not GW59), 12 / 20: TMA staging with register caps
  * for three / four CTAs per SM. */
 dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int32_t fd_var);
+
+/* Variant of the second-order FV stage (patch_update_fv_muscl), also chosen by
+ * dh_autotune / dh_autotune_steps with scheme 2 (choice_out[0] is then fv2_var):
+ *   0 (default) z-march: a CTA marches a 16x16 column (four 8x8 columns of 8^3
+ *     patches) through the patch, keeping the z states of its voxels in
+ *     registers and exchanging x/y states through shared memory;
+ *   1 the same in chunks of at most 16 planes;
+ *   2 8x8x4 tiles staged with their two-voxel face halos.
+ * Every variant gives the same results (the same operations in the same order). */
+dh_status dh_plan_set_variant_muscl(dh_plan* plan, int32_t fv2_var);
 
 /* Error flags raised on the device by the plan's kernels (bit 0: a bounded
  * wait for a TMA copy gave up: the FD stage skipped the tile, the FV stage

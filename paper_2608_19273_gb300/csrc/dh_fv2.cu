@@ -98,6 +98,14 @@ __device__ __forceinline__ void m_slot(int s, int& x, int& y, int& z) {
   z = side == 0 ? -MH + h : MZ + h;
 }
 
+// Asynchronous 8-byte copy global -> shared (no register round trip) and the wait for all of
+// this thread's copies.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // minmod on the integer pipe: 0 if the signs differ, else the argument of smaller magnitude.
 __device__ __forceinline__ double minmod(double a, double b) {
   const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
@@ -271,6 +279,332 @@ struct Fv2Tile {
   }
 };
 
+// ------------------------------------------------------------- z-marching variant
+// A CTA owns a (TX x TY) column of one patch (or four 8x8 columns of up to four 8^3 patches)
+// and marches it through the patch's z-planes, one voxel per thread and plane:
+//   * z: each thread keeps its column's states in registers -- the states of planes zk and
+//     zk+1, the limited slope of plane zk and the z face below plane zk -- so every z slope,
+//     z face state and z face flux is computed once (two extra states per column end);
+//   * x, y: plane zk and a two-voxel ring around the column sit in a double-buffered plane
+//     buffer in shared memory; each thread forms its x (then y) slope and its two face states,
+//     keeps the + state in registers and publishes the - state; after a barrier it forms the
+//     Rusanov flux of its + face from its own + state and its neighbour's - state; the ring
+//     threads form the inward states of the voxels next to the column (the last warps, so the
+//     extra work is whole warps);
+//   * the ring of the next plane is loaded into registers at the top of an iteration and
+//     stored into the other plane buffer at its end.
+// Five barriers per plane.  Same arithmetic, in the same order, as the tile kernel: results
+// agree bitwise.
+template <class PDE, int TX, int TY, int G>
+struct Fv2March {
+  static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW;
+  static constexpr int NT = TX * TY * G;
+  static_assert(NT == 256, "one voxel per thread and plane, 256 threads");
+  static constexpr int R2 = 4 * TY + 4 * TX;           // ring slots per group: two deep on every side
+  static constexpr int PS = NT + G * R2;                // plane-buffer slots
+  static constexpr int RX = 2 * G * TY, RY = 2 * G * TX;  // ring voxels with a state per direction
+  static constexpr int LM = TX > TY ? TX : TY;
+  static constexpr int NS = NT + G * LM;                // faces: interior + one ring per group
+  static constexpr int NSS = NS + G * LM;               // states: interior, ring after, ring before
+  static constexpr int NST = 2 * N + 1;                 // a face state: F (N), lambda, u (N)
+  static constexpr size_t SMEM = sizeof(double) * (2 * (size_t)NV * PS + (size_t)NST * NSS + (size_t)N * NS);
+
+  __device__ static int xring(int g, int side, int h, int j) { return NT + g * R2 + (side * 2 + h) * TY + j; }
+  __device__ static int yring(int g, int side, int h, int j) { return NT + g * R2 + 4 * TY + (side * 2 + h) * TX + j; }
+
+  // Face state of q (N + M values) with slope sig along d at offset h (+-1/2): u, derived
+  // quantities, flux F_d and speed.
+  __device__ static void state(const DevParams& P, int d, const double* q, const double* sig, double h, double* F,
+                               double& lam, double* u) {
+    double W[NW > 0 ? NW : 1];
+#pragma unroll
+    for (int v = 0; v < N; ++v) u[v] = fma(h, sig[v], q[v]);
+#pragma unroll
+    for (int v = N; v < NV; ++v) u[v] = q[v];
+    PDE::prims(u, P, W);
+    PDE::flux(d, u, W, P, F);
+    lam = PDE::speed(d, u, W, P);
+  }
+  __device__ static void publish(double* SS, int slot, const double* F, double lam, const double* u) {
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      SS[v * NSS + slot] = F[v];
+      SS[(N + 1 + v) * NSS + slot] = u[v];
+    }
+    SS[N * NSS + slot] = lam;
+  }
+  // Twice the Rusanov flux from the left state (registers) and the published right state.
+  __device__ static void face_lr(const DevParams& P, const double* FL, double lL, const double* uL, const double* SS,
+                                 int slot, double* H) {
+    const double s = max_nn(lL, SS[N * NSS + slot]);
+#pragma unroll
+    for (int v = 0; v < N; ++v)
+      H[v] = fma(-s, SUB(P, SS[(N + 1 + v) * NSS + slot], uL[v]), ADD(P, FL[v], SS[v * NSS + slot]));
+  }
+  // Twice the Rusanov flux of two published states.
+  __device__ static void face_ss(const DevParams& P, const double* SS, int ls, int rs, double* H) {
+    const double s = max_nn(SS[N * NSS + ls], SS[N * NSS + rs]);
+#pragma unroll
+    for (int v = 0; v < N; ++v)
+      H[v] = fma(-s, SUB(P, SS[(N + 1 + v) * NSS + rs], SS[(N + 1 + v) * NSS + ls]),
+                 ADD(P, SS[v * NSS + ls], SS[v * NSS + rs]));
+  }
+  // Twice the Rusanov flux of two states in registers.
+  __device__ static void face_rr(const DevParams& P, const double* FL, double lL, const double* uL, const double* FR,
+                                 double lR, const double* uR, double* H) {
+    const double s = max_nn(lL, lR);
+#pragma unroll
+    for (int v = 0; v < N; ++v) H[v] = fma(-s, SUB(P, uR[v], uL[v]), ADD(P, FL[v], FR[v]));
+  }
+  __device__ static void slope(const double* qm, const double* q0, const double* qp, const DevParams& P, double* sig) {
+#pragma unroll
+    for (int v = 0; v < N; ++v) sig[v] = minmod(SUB(P, q0[v], qm[v]), SUB(P, qp[v], q0[v]));
+  }
+  __device__ static void load(const Fv2Args& A, int64_t e, double* q) {
+#pragma unroll
+    for (int v = 0; v < N; ++v) q[v] = __ldg(A.qs + (int64_t)v * A.vs + e);
+#pragma unroll
+    for (int v = 0; v < PDE::M; ++v) q[N + v] = __ldg(A.mat + (int64_t)v * A.vs + e);
+  }
+  __device__ static void read_slot(const double* Qp, int slot, double* q) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) q[v] = Qp[v * PS + slot];
+  }
+  // Ring slot r (t < G * R2) of plane z: its patch-relative position.
+  __device__ static bool ring_pos(const Work& w, int r, int& g, int& x, int& y, int& slot) {
+    g = r / R2;
+    const int rr = r % R2;
+    if (w.patch[g] < 0) return false;
+    const int x0 = w.x0[g], y0 = w.y0[g];
+    if (rr < 4 * TY) {
+      const int side = rr / (2 * TY), h = (rr / TY) % 2, j = rr % TY;
+      x = side == 0 ? x0 - 1 - h : x0 + TX + h;
+      y = y0 + j;
+      slot = xring(g, side, h, j);
+    } else {
+      const int r2 = rr - 4 * TY;
+      const int side = r2 / (2 * TX), h = (r2 / TX) % 2, j = r2 % TX;
+      x = x0 + j;
+      y = side == 0 ? y0 - 1 - h : y0 + TY + h;
+      slot = yring(g, side, h, j);
+    }
+    return true;
+  }
+
+  __device__ static void run(const Fv2Args& A, const Work& w, double* smem, double& lam_thread) {
+    double* Qb[2] = {smem, smem + NV * PS};
+    double* SS = smem + 2 * NV * PS;
+    double* HS = SS + NST * NSS;
+    const DevParams& P = A.P;
+    const int t = threadIdx.x;
+    const int g = t / (TX * TY), lxy = t % (TX * TY), lx = lxy % TX, ly = lxy / TX;
+    const int k = w.patch[g];
+    const bool act = k >= 0;
+    const int kk = act ? k : w.patch[0];
+    const dh_patch pt = A.patches[kk];
+    const int p = pt.p, pz = w.pz, z0 = w.z0;
+    const int x = (act ? w.x0[g] : 0) + lx, y = (act ? w.y0[g] : 0) + ly;
+    const int own = t;
+    __shared__ double s_cL;
+    if (t == 0) s_cL = -0.5 / pt.dx;  // one IEEE division per CTA
+    const bool ringt = t < G * R2;
+    int rg = 0, rx_ = 0, ry_ = 0, rslot = 0;
+    const bool rok = ringt && ring_pos(w, t, rg, rx_, ry_, rslot);
+    // x / y ring states: the last warps
+    const int hx = t - (NT - RX), hy = t - (NT - RX - RY);
+    // ---- prologue: the column's planes z0-2 .. z0+1 and plane z0 with its ring
+    double Qc[NV], Qn[NV], sc[N], Hzm[N];
+    {
+      double Qa[NV], Qb2[NV], sa[N];
+      if (act) {
+        load(A, m_vox(A.patches, k, p, x, y, z0 - 2), Qa);
+        load(A, m_vox(A.patches, k, p, x, y, z0 - 1), Qb2);
+        load(A, m_vox(A.patches, k, p, x, y, z0), Qc);
+        load(A, m_vox(A.patches, k, p, x, y, z0 + 1), Qn);
+        slope(Qa, Qb2, Qc, P, sa);
+        slope(Qb2, Qc, Qn, P, sc);
+        double FL[N], FR[N], uL[NV], uR[NV], lL, lR;
+        state(P, 2, Qb2, sa, P.half, FL, lL, uL);
+        state(P, 2, Qc, sc, -P.half, FR, lR, uR);
+        face_rr(P, FL, lL, uL, FR, lR, uR, Hzm);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Qb[0][v * PS + own] = Qc[v];
+      }
+      if (rok) {
+        double q[NV];
+        load(A, m_vox(A.patches, w.patch[rg], p, rx_, ry_, z0), q);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Qb[0][v * PS + rslot] = q[v];
+      }
+    }
+    __syncthreads();
+    for (int kz = 0; kz < pz; ++kz) {
+      const int zk = z0 + kz;
+      const double* Qp = Qb[kz & 1];
+      // next loads: the column's plane zk+2 into registers, and the ring of plane zk+1 straight
+      // into the other plane buffer (asynchronous copies, waited for at the end of the iteration;
+      // that buffer's last readers finished before the previous iteration's final barrier)
+      double Qnn[NV];
+      if (act) load(A, m_vox(A.patches, k, p, x, y, zk + 2), Qnn);
+      const bool more = kz + 1 < pz;
+      if (rok && more) {
+        double* Qo = Qb[(kz + 1) & 1];
+        const int64_t e = m_vox(A.patches, w.patch[rg], p, rx_, ry_, zk + 1);
+#pragma unroll
+        for (int v = 0; v < N; ++v) cp_async8(Qo + v * PS + rslot, A.qs + (int64_t)v * A.vs + e);
+#pragma unroll
+        for (int v = 0; v < PDE::M; ++v) cp_async8(Qo + (N + v) * PS + rslot, A.mat + (int64_t)v * A.vs + e);
+      }
+      double sum[N];
+#pragma unroll
+      for (int v = 0; v < N; ++v) sum[v] = 0.0;
+#pragma unroll 1
+      for (int d = 0; d < 2; ++d) {
+        const int T = d == 0 ? TX : TY;
+        const int a = d == 0 ? lx : ly;
+        const int mslot = a > 0 ? own - (d == 0 ? 1 : TX) : (d == 0 ? xring(g, 0, 0, ly) : yring(g, 0, 0, lx));
+        const int pslot = a < T - 1 ? own + (d == 0 ? 1 : TX) : (d == 0 ? xring(g, 1, 0, ly) : yring(g, 1, 0, lx));
+        // phase 1: own slope and states (- published, + kept); ring voxels' inward states
+        double FP[N], uP[NV], lP = 0.0;
+        if (act) {
+          double qm[NV], qp[NV], sig[N], FM[N], uM[NV], lM;
+          read_slot(Qp, mslot, qm);
+          read_slot(Qp, pslot, qp);
+          slope(qm, Qc, qp, P, sig);
+          state(P, d, Qc, sig, -P.half, FM, lM, uM);
+          publish(SS, own, FM, lM, uM);
+          state(P, d, Qc, sig, P.half, FP, lP, uP);
+        }
+        // ring: (hr < half) the voxel before the column (its + state and the face into the
+        // column), (else) the voxel after it (its - state)
+        const int hr = d == 0 ? hx : hy;
+        const int RR = d == 0 ? RX : RY;
+        const int LEN = d == 0 ? TY : TX;  // ring voxels per side and group
+        int rgr = 0, rj = 0, rside = 0;
+        bool ract = false;
+        if (hr >= 0 && hr < RR) {
+          rgr = hr / (2 * LEN);
+          rside = (hr / LEN) % 2;
+          rj = hr % LEN;
+          ract = w.patch[rgr] >= 0;
+          if (ract) {
+            const int ci = rgr * TX * TY + (d == 0 ? rj * TX : rj);  // first interior voxel of the row / column
+            const int ce = rgr * TX * TY + (d == 0 ? rj * TX + TX - 1 : (TY - 1) * TX + rj);  // last one
+            double q0[NV], qa[NV], qb[NV], sig[N];
+            if (rside == 0) {
+              read_slot(Qp, d == 0 ? xring(rgr, 0, 1, rj) : yring(rgr, 0, 1, rj), qa);
+              read_slot(Qp, d == 0 ? xring(rgr, 0, 0, rj) : yring(rgr, 0, 0, rj), q0);
+              read_slot(Qp, ci, qb);
+              slope(qa, q0, qb, P, sig);
+              double FQ[N], uQ[NV], lQ;
+              state(P, d, q0, sig, P.half, FQ, lQ, uQ);
+              publish(SS, NS + rgr * LEN + rj, FQ, lQ, uQ);
+            } else {
+              read_slot(Qp, ce, qa);
+              read_slot(Qp, d == 0 ? xring(rgr, 1, 0, rj) : yring(rgr, 1, 0, rj), q0);
+              read_slot(Qp, d == 0 ? xring(rgr, 1, 1, rj) : yring(rgr, 1, 1, rj), qb);
+              slope(qa, q0, qb, P, sig);
+              double FM[N], uM[NV], lM;
+              state(P, d, q0, sig, -P.half, FM, lM, uM);
+              publish(SS, NT + rgr * LEN + rj, FM, lM, uM);
+            }
+          }
+        }
+        __syncthreads();
+        // phase 2: the + face of every voxel (right state: the neighbour's - state); the face
+        // into the column from the ring voxel before it
+        if (act) {
+          const int rs = a < T - 1 ? own + (d == 0 ? 1 : TX) : NT + g * LEN + (d == 0 ? ly : lx);
+          double Hown[N];
+          face_lr(P, FP, lP, uP, SS, rs, Hown);
+#pragma unroll
+          for (int v = 0; v < N; ++v) HS[v * NS + own] = Hown[v];
+        }
+        if (ract && rside == 0) {
+          const int ci = rgr * TX * TY + (d == 0 ? rj * TX : rj);
+          double Hb[N];
+          face_ss(P, SS, NS + rgr * LEN + rj, ci, Hb);
+#pragma unroll
+          for (int v = 0; v < N; ++v) HS[v * NS + NT + rgr * LEN + rj] = Hb[v];
+        }
+        __syncthreads();
+        // phase 3: difference of this voxel's two faces along d
+        if (act) {
+          const int ms = a > 0 ? own - (d == 0 ? 1 : TX) : NT + g * LEN + (d == 0 ? ly : lx);
+#pragma unroll
+          for (int v = 0; v < N; ++v) sum[v] = ADD(P, sum[v], SUB(P, HS[v * NS + own], HS[v * NS + ms]));
+        }
+      }
+      if (act) {
+        // z: slope of plane zk+1, the states on both sides of the face zk+1/2 and its flux
+        double sn[N], Hzp[N];
+        slope(Qc, Qn, Qnn, P, sn);
+        {
+          double FL[N], FR[N], uL[NV], uR[NV], lL, lR;
+          state(P, 2, Qc, sc, P.half, FL, lL, uL);
+          state(P, 2, Qn, sn, -P.half, FR, lR, uR);
+          face_rr(P, FL, lL, uL, FR, lR, uR, Hzp);
+        }
+#pragma unroll
+        for (int v = 0; v < N; ++v) sum[v] = ADD(P, sum[v], SUB(P, Hzp[v], Hzm[v]));
+        // update of plane zk
+        const double dt = *A.dt_dev;
+        const double cL = s_cL;
+        const double gdt = A.g * dt, ddt = A.d * dt;
+        const bool b1 = A.b == 1.0;
+        const int64_t e = pt.offset + ((int64_t)zk * p + y) * p + x;
+        double Sv[N], res[NV];
+        if (PDE::SRC) {
+          double W[NW > 0 ? NW : 1];
+          PDE::prims(Qc, P, W);
+          PDE::source(Qc, W, P, Sv);
+        }
+        const dh_patch& mp = A.patches[k];
+        const int64_t ek = mp.offset + ((int64_t)zk * p + y) * p + x;
+        (void)e;
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          const int64_t ev = (int64_t)v * A.vs + ek;
+          if (A.out) {
+            double base = b1 ? Qc[v] : MUL(P, A.b, Qc[v]);
+            if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
+            res[v] = PDE::SRC ? fma(gdt, fma(cL, sum[v], Sv[v]), base) : fma(MUL(P, gdt, cL), sum[v], base);
+          }
+          if (A.acc) {
+            const double r = PDE::SRC ? fma(ddt, fma(cL, sum[v], Sv[v]), A.acc[ev])
+                                      : fma(MUL(P, ddt, cL), sum[v], A.acc[ev]);
+            A.acc[ev] = r;
+            if (!A.out) res[v] = r;
+          }
+          if (A.out) A.out[ev] = res[v];
+        }
+        if (A.lam_out) {
+#pragma unroll
+          for (int v = N; v < NV; ++v) res[v] = Qc[v];
+          double W[NW > 0 ? NW : 1];
+          PDE::prims(res, P, W);
+          const double l = max_nn(max_nn(PDE::speed(0, res, W, P), PDE::speed(1, res, W, P)), PDE::speed(2, res, W, P));
+          lam_thread = max_nn(lam_thread, l);
+        }
+        // march one plane on
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { Qc[v] = Qn[v]; Qn[v] = Qnn[v]; }
+#pragma unroll
+        for (int v = 0; v < N; ++v) { sc[v] = sn[v]; Hzm[v] = Hzp[v]; }
+      }
+      if (more) {
+        double* Qo = Qb[(kz + 1) & 1];
+        if (act) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Qo[v * PS + own] = Qc[v];
+        }
+        cp_async_wait_all();
+        __syncthreads();
+      }
+    }
+  }
+};
+
 __device__ void m_publish_lambda(double lam, double* lam_out, unsigned long long* red) {
   __shared__ double wmax[MNT / 32];
   __shared__ bool last;
@@ -296,6 +630,16 @@ __device__ void m_publish_lambda(double lam, double* lam_out, unsigned long long
 }
 
 template <class PDE>
+__global__ void __launch_bounds__(256, 2) k_fv2_march(const __grid_constant__ Fv2Args A, const Work* work) {
+  extern __shared__ __align__(16) double m_smem[];
+  const Work w = work[blockIdx.x];
+  double lam = 0.0;
+  if (w.cls == 0) Fv2March<PDE, 16, 16, 1>::run(A, w, m_smem, lam);
+  else Fv2March<PDE, 8, 8, 4>::run(A, w, m_smem, lam);
+  if (A.lam_out) m_publish_lambda(lam, A.lam_out, A.red);
+}
+
+template <class PDE>
 __global__ void __launch_bounds__(MNT, 2) k_fv2_stage(const __grid_constant__ Fv2Args A) {
   extern __shared__ __align__(16) double m_smem[];
   const FdWork w = A.work[blockIdx.x];
@@ -305,7 +649,27 @@ __global__ void __launch_bounds__(MNT, 2) k_fv2_stage(const __grid_constant__ Fv
 }
 
 template <class PDE>
+dh_status m_launch_march(dh_plan* plan, const Fv2Args& A, cudaStream_t s) {
+  // the FV work lists of tile set 0: 16x16 columns, four 8x8 columns of 8^3 patches (zs: z-chunks)
+  const int li = (plan->fv2_var & 1) ? 1 : 0;
+  const bool* cls = plan->wl_cls[li];
+  const size_t smem = std::max(cls[0] ? Fv2March<PDE, 16, 16, 1>::SMEM : (size_t)0,
+                               cls[1] ? Fv2March<PDE, 8, 8, 4>::SMEM : (size_t)0);
+  static int configured_device = -1;
+  if (configured_device != plan->device) {
+    cudaError_t e = cudaFuncSetAttribute(k_fv2_march<PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max(Fv2March<PDE, 16, 16, 1>::SMEM, Fv2March<PDE, 8, 8, 4>::SMEM));
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv2_march)");
+    configured_device = plan->device;
+  }
+  if (plan->n_wl[li] <= 0) return DH_OK;
+  k_fv2_march<PDE><<<plan->n_wl[li], 256, smem, s>>>(A, plan->d_wl[li]);
+  return cuda_error(cudaGetLastError(), "k_fv2_march launch");
+}
+
+template <class PDE>
 dh_status m_launch(dh_plan* plan, const Fv2Args& A, cudaStream_t s) {
+  if (plan->fv2_var != 2) return m_launch_march<PDE>(plan, A, s);
   static int configured_device = -1;
   if (configured_device != plan->device) {
     cudaError_t e = cudaFuncSetAttribute(k_fv2_stage<PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,

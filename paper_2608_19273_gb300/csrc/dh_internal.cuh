@@ -86,6 +86,9 @@ struct dh_plan {
   // queue; bits 3-4: tile set
   int fv_var = 2, fv_zs = 0, fd_var = 0;
   int fv_list() const { return 2 * ((fv_var >> 3) & 3) + fv_zs; }
+  // second-order FV stage: 0 = z-march of whole patches, 1 = z-march in chunks of <= 16 planes
+  // (both on the work lists of tile set 0), 2 = 8x8x4 tiles
+  int fv2_var = 0;
   // FD tile list (8x8x4 tiles)
   dh::FdWork* d_fdwork = nullptr;
   int n_fdwork = 0;

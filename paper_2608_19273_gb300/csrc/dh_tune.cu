@@ -15,6 +15,8 @@
 //             x z-march of whole patches or chunks of <= 16 planes
 //             x loads: plain (L2-prefetched) or, for 3D Euler, TMA tensor copies of every
 //               column plane and its ring strips into a double-buffered shared ring
+//   second-order FV stage: z-march of whole patches or in chunks of <= 16 planes, or the 8x8x4
+//             tile kernel;
 //   FD stage: register cap (1 or 2 CTAs per SM) x staging (plain loads or TMA);
 //             with TMA staging of one group (systems of <= 5 variables) also
 //             caps for 3 and 4 CTAs per SM
@@ -71,6 +73,11 @@ struct Cand {
 
 static int tune_candidates(const dh_plan* plan, int scheme, Cand* cands) {
   int nc = 0;
+  if (scheme == 2) {
+    // second-order FV: z-march of whole patches, z-march in chunks of <= 16 planes, 8x8x4 tiles
+    for (int v = 0; v < 3; ++v) cands[nc++] = {v, plan->fv_zs, plan->fd_var};
+    return nc;
+  }
   if (scheme == 0) {
     // a tile set is a candidate only where it changes the work list
     bool has32 = false, has16 = false;
@@ -121,7 +128,7 @@ static dh_status tune_run(dh_plan* plan, int scheme, const std::string& key, int
   if (!cache_path) cache_path = std::getenv("DH_TUNE_CACHE");  // NULL and unset: no cache
   int v = 0, z = 0, f = 0;
   if (cache_path && cache_lookup(cache_path, key, &v, &z, &f)) {
-    dh_status st = dh_plan_set_variant(plan, v, z, f);
+    dh_status st = scheme == 2 ? dh_plan_set_variant_muscl(plan, v) : dh_plan_set_variant(plan, v, z, f);
     if (st == DH_OK && choice_out) { choice_out[0] = v; choice_out[1] = z; choice_out[2] = f; choice_out[3] = 1; }
     return st;
   }
@@ -135,10 +142,17 @@ static dh_status tune_run(dh_plan* plan, int scheme, const std::string& key, int
   float best = 1e30f;
   int bi = 0;
   dh_status st = DH_OK;
+  auto apply = [&](const Cand& c) {
+    if (scheme == 2) {
+      plan->fv2_var = c.v;
+    } else {
+      plan->fv_var = c.v;
+      plan->fv_zs = c.z;
+      plan->fd_var = c.f;
+    }
+  };
   for (int i = 0; i < nc && st == DH_OK; ++i) {
-    plan->fv_var = cands[i].v;
-    plan->fv_zs = cands[i].z;
-    plan->fd_var = cands[i].f;
+    apply(cands[i]);
     st = launch();  // warm-up (also sets the kernel's shared-memory attribute)
     if (st != DH_OK) break;
     cudaEventRecord(e0, s);
@@ -155,9 +169,7 @@ static dh_status tune_run(dh_plan* plan, int scheme, const std::string& key, int
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != DH_OK) return st;
-  plan->fv_var = cands[bi].v;
-  plan->fv_zs = cands[bi].z;
-  plan->fd_var = cands[bi].f;
+  apply(cands[bi]);
   if (choice_out) { choice_out[0] = cands[bi].v; choice_out[1] = cands[bi].z; choice_out[2] = cands[bi].f; choice_out[3] = 0; }
   if (cache_path) {
     FILE* fo = fopen(cache_path, "a");
@@ -205,16 +217,24 @@ dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int3
   return DH_OK;
 }
 
+dh_status dh_plan_set_variant_muscl(dh_plan* plan, int32_t fv2_var) {
+  if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
+  if (fv2_var < 0 || fv2_var > 2) { set_error("dh_plan_set_variant_muscl: fv2_var in 0..2"); return DH_EINVAL; }
+  plan->fv2_var = fv2_var;
+  return DH_OK;
+}
+
 dh_status dh_autotune(dh_plan* plan, int32_t scheme, const double* qs, double* out, const double* mat,
                       const double* dt_dev, int32_t reps, const char* cache_path, int32_t* choice_out,
                       float* times_out, void* stream) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (scheme != 0 && scheme != 1) { set_error("dh_autotune: scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
+  if (scheme < 0 || scheme > 2) { set_error("dh_autotune: scheme must be 0 (FV), 1 (FD) or 2 (FV, MUSCL)"); return DH_EINVAL; }
   if (!qs || !out || !dt_dev || reps < 1 || reps > 1000) { set_error("dh_autotune: bad arguments"); return DH_EINVAL; }
   cudaStream_t s = (cudaStream_t)stream;
   auto launch = [&]() {
-    return scheme == 0 ? patch_update_fv(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, nullptr, s)
-                       : patch_update_fd_ko(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, 0.1, nullptr, s);
+    return scheme == 0   ? patch_update_fv(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, nullptr, s)
+           : scheme == 2 ? patch_update_fv_muscl(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, nullptr, s)
+                         : patch_update_fd_ko(plan, qs, nullptr, out, nullptr, mat, dt_dev, 0, 1, 1, 0, 0.1, nullptr, s);
   };
   return tune_run(plan, scheme, tune_key(plan, scheme), reps, cache_path, choice_out, times_out, s, launch);
 }
@@ -224,7 +244,10 @@ dh_status dh_autotune_steps(dh_plan* plan, int32_t scheme, int32_t rk, int32_t n
                             double sigma_ko, int32_t reps, const char* cache_path, int32_t* choice_out,
                             float* times_out, void* stream) {
   if (!plan) { set_error("plan is NULL"); return DH_EINVAL; }
-  if (scheme != 0 && scheme != 1) { set_error("dh_autotune_steps: scheme must be 0 (FV) or 1 (FD)"); return DH_EINVAL; }
+  if (scheme < 0 || scheme > 2) {
+    set_error("dh_autotune_steps: scheme must be 0 (FV), 1 (FD) or 2 (FV, MUSCL)");
+    return DH_EINVAL;
+  }
   if (n_steps < 1 || n_steps > 1000 || reps < 1 || reps > 1000) {
     set_error("dh_autotune_steps: n_steps and reps must lie in [1, 1000]");
     return DH_EINVAL;

@@ -26,7 +26,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fv_muscl", "patch_update_fd_ko",
            "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_bind_staged", "dh_offload_run", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_autotune_steps", "dh_plan_set_variant", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_autotune", "dh_autotune_steps", "dh_plan_set_variant", "dh_plan_set_variant_muscl", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
 
@@ -66,6 +66,7 @@ def lib():
         L.dh_autotune_steps.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, ctypes.c_char_p,
                                         vp, vp, vp]
         L.dh_plan_set_variant.argtypes = [vp, i32, i32, i32]
+        L.dh_plan_set_variant_muscl.argtypes = [vp, i32]
         L.dh_plan_errors.argtypes = [vp, vp, i32]
         L.dh_plan_set_debug.argtypes = [vp, i32]
         L.patch_update_fv_noalloc.argtypes = [i32, i32, vp, i32, i64, vp, i32, vp, vp, vp, vp, vp, vp, d, d, d, d,
@@ -372,6 +373,10 @@ def dh_autotune_steps(plan, scheme, rk, n_steps, q, u1, u2, acc, mat, dt_dev, la
 
 def dh_plan_set_variant(plan, fv_var, fv_zs, fd_var):
     _check(lib().dh_plan_set_variant(plan.handle, int(fv_var), int(fv_zs), int(fd_var)), "dh_plan_set_variant")
+
+
+def dh_plan_set_variant_muscl(plan, fv2_var):
+    _check(lib().dh_plan_set_variant_muscl(plan.handle, int(fv2_var)), "dh_plan_set_variant_muscl")
 
 
 def dh_plan_errors(plan, clear=True):

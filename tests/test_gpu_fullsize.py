@@ -39,8 +39,7 @@ def _gpu_step(torch, name, w, q, mat, steps=1):
             M.copy_(U2)
         dh.max_wave_speed(plan, Q, M, lam)
         dh.dh_cfl_dt(plan, lam, cfl, dt)
-        if scheme != 2:
-            dh.dh_autotune(plan, scheme, Q, U1, M, dt, reps=1)
+        dh.dh_autotune(plan, scheme, Q, U1, M, dt, reps=1)
         for _ in range(steps):
             dh.dh_rk_step(plan, scheme, rk, Q, U1, U2, ACC, M, dt, lam, cfl, 0.1)
         torch.cuda.synchronize()

@@ -13,9 +13,11 @@ pytestmark = pytest.mark.gpu
 FV2 = 2
 
 
+@pytest.mark.parametrize("fv2_var", [0, 1, 2])
 @pytest.mark.parametrize("scale", [8, 4])
 @pytest.mark.parametrize("coef", [(0.0, 1.0, 1.0), (0.75, 0.25, 0.25), (1 / 3, 2 / 3, 2 / 3)])
-def test_euler3d_muscl_stage(orc, scale, coef):
+def test_euler3d_muscl_stage(orc, scale, coef, fv2_var):
+    """Every variant of the stage (z-march of whole patches / of 16-plane chunks, 8x8x4 tiles)."""
     torch = require_cuda()
     mesh = synth.euler3d_amr_mesh(scale=scale)
     q0 = orc.prim2con(3, synth.euler_prims(mesh, 61), mesh.var_stride)
@@ -26,6 +28,7 @@ def test_euler3d_muscl_stage(orc, scale, coef):
     lam_ref = orc.stage(FV2, 3, 3, mesh.patches, 2, mesh.var_stride, qs, q0=q0 if a else None, out=ref, dt=dt,
                         a=a, b=b, g=g, want_lam=True)
     with dh.Plan(3, 3, mesh.patches, 2, mesh.var_stride) as plan:
+        dh.dh_plan_set_variant_muscl(plan, fv2_var)
         out = torch.zeros(qs.shape, dtype=torch.float64, device="cuda")
         d_dt = torch.tensor([dt], dtype=torch.float64, device="cuda")
         lam = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -36,7 +39,8 @@ def test_euler3d_muscl_stage(orc, scale, coef):
     assert_parity(got, ref, voxel_mask(mesh), what=f"muscl stage {coef}")
 
 
-def test_advection_muscl_stage_with_material_field(orc):
+@pytest.mark.parametrize("fv2_var", [0, 2])
+def test_advection_muscl_stage_with_material_field(orc, fv2_var):
     """ADV_FLUX with a velocity field that varies in space (material M = 3) and rough data."""
     torch = require_cuda()
     mesh = single_level((2, 3, 2), 8, 1.0 / 32)
@@ -53,6 +57,7 @@ def test_advection_muscl_stage_with_material_field(orc):
     orc.stage(FV2, synth.PDE_ADV_FLUX, 3, mesh.patches, 2, mesh.var_stride, q, out=ref_out, acc=ref_acc, mat=mat,
               dt=2e-3, a=0, b=1, g=0.5, d=1 / 6)
     with dh.Plan(synth.PDE_ADV_FLUX, 3, mesh.patches, 2, mesh.var_stride) as plan:
+        dh.dh_plan_set_variant_muscl(plan, fv2_var)
         out = torch.zeros(q.shape, dtype=torch.float64, device="cuda")
         acc = dev(torch, acc0)
         d_dt = torch.tensor([2e-3], dtype=torch.float64, device="cuda")
@@ -111,3 +116,27 @@ def test_muscl_rejects_bad_plans():
     with dh.Plan(2, 2, m2.patches, 2, m2.var_stride) as plan:        # 2D is not supported
         with pytest.raises(dh.DhError):
             dh.patch_update_fv_muscl(plan, q2, None, torch.zeros_like(q2), None, None, d_dt, 0, 1, 1, 0)
+
+
+def test_muscl_variants_agree_bitwise(orc):
+    """The z-march and the tile kernel perform the same operations in the same order: their
+    results (and lambda) are bitwise equal on rough data."""
+    torch = require_cuda()
+    mesh = synth.euler3d_amr_mesh(scale=4)
+    rng = np.random.default_rng(64)
+    prim = synth.euler_prims(mesh, 65)
+    prim[0] *= np.exp(0.3 * rng.normal(size=prim[0].shape))
+    prim[4] *= np.exp(0.3 * rng.normal(size=prim[4].shape))
+    q = orc.prim2con(3, prim, mesh.var_stride)
+    outs = []
+    with dh.Plan(3, 3, mesh.patches, 2, mesh.var_stride) as plan:
+        for v in (0, 1, 2):
+            dh.dh_plan_set_variant_muscl(plan, v)
+            out = torch.zeros(q.shape, dtype=torch.float64, device="cuda")
+            lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+            d_dt = torch.tensor([1e-3], dtype=torch.float64, device="cuda")
+            dh.patch_update_fv_muscl(plan, dev(torch, q), None, out, None, None, d_dt, 0, 1, 1, 0, lam)
+            outs.append((host(out), float(host(lam)[0])))
+    m = voxel_mask(mesh)
+    for o, l in outs[1:]:
+        assert np.array_equal(o[:, m], outs[0][0][:, m]) and l == outs[0][1]
