@@ -106,9 +106,11 @@ def parse_args():
 
 
 # sources of each workload's dominant kernel (besides the shared headers)
+_FV = ["dh_fv.cu", "dh_fv_stage.cuh", "dh_tma.cuh"]
 KERNEL_SOURCES = {
-    "euler3d": ["dh_fv.cu"], "euler2d": ["dh_fv.cu"], "euler3d_amr2": ["dh_fv.cu", "dh_amr.cu"],
-    "euler3d_muscl": ["dh_fv2.cu"], "srhd3d": ["dh_fv.cu"],
+    "euler3d": _FV + ["dh_fv_euler3.cu", "dh_fv_euler3_tma.cu"], "euler2d": _FV + ["dh_fv_euler2.cu"],
+    "euler3d_amr2": _FV + ["dh_fv_euler3.cu", "dh_fv_euler3_tma.cu", "dh_amr.cu"],
+    "euler3d_muscl": ["dh_fv2.cu"], "srhd3d": _FV + ["dh_fv_srhd.cu"],
     "wave3d": ["dh_fd.cu"], "gw59": ["dh_fd.cu"],
 }
 
@@ -752,9 +754,9 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
         dh.max_wave_speed(plan, Q, mat, lam, stream)
         lam_init = lam.clone()
         dh.dh_cfl_dt(plan, lam, spec["cfl"], dt, stream)
-        if spec["scheme"] in (0, 2):
-            # FV: tune whole time steps as the graph runs them (stage-sum form, derived quantities
-            # handed between stages), on scratch copies of the state
+        if spec["scheme"] == 0 and spec["pde"] in (synth.PDE_EULER2D, synth.PDE_EULER3D):
+            # FV, Euler: tune whole time steps as the graph runs them (stage-sum form, derived
+            # quantities handed between stages), on scratch copies of the state
             Qt = Q.clone()
             Mt = mat.clone() if mat is not None else None
             lam_t = lam.clone()
@@ -768,10 +770,14 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
             tune.update({"from_cache": cached, "timed": "two time steps per call",
                          "candidate_ms": [round(t, 4) for t in ttimes if t > 0]})
         else:
+            # the other stages hand nothing from stage to stage: one stage per call, on the same state
+            # for every candidate (for SRHD the steps' con2prim work would vary from candidate to
+            # candidate as the state advanced)
             tv, tz, tf, cached, ttimes = dh.dh_autotune(plan, spec["scheme"], Q, U1, mat, dt, reps=3,
                                                         cache_path=args.tune_cache, stream=stream)
-            tune = {"fv_var": tv, "fv_zs": tz, "fd_var": tf, "from_cache": cached, "timed": "one stage per call",
-                    "candidate_ms": [round(t, 4) for t in ttimes if t > 0]}
+            tune = ({"fv2_var": tv} if spec["scheme"] == 2 else {"fv_var": tv, "fv_zs": tz, "fd_var": tf})
+            tune.update({"from_cache": cached, "timed": "one stage per call",
+                         "candidate_ms": [round(t, 4) for t in ttimes if t > 0]})
         # eager warm-up step (sets kernel attributes outside of capture), then reset
         dh.dh_rk_step(plan, spec["scheme"], spec["rk"], Q, U1, U2, ACC, mat, dt, lam, spec["cfl"], 0.1, stream)
         Q.copy_(Q_init)
