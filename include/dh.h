@@ -420,11 +420,11 @@ dh_status dh_plan_set_variant(dh_plan* plan, int32_t fv_var, int32_t fv_zs, int3
 
 /* Variant of the second-order FV stage (patch_update_fv_muscl), also chosen by
  * dh_autotune / dh_autotune_steps with scheme 2 (choice_out[0] is then fv2_var):
- *   0 (default) z-march: a CTA marches a 16x16 column (four 8x8 columns of 8^3
+ *   0 z-march: a CTA marches a 16x16 column (four 8x8 columns of 8^3
  *     patches) through the patch, keeping the z states of its voxels in
  *     registers and exchanging x/y states through shared memory;
  *   1 the same in chunks of at most 16 planes;
- *   2 8x8x4 tiles staged with their two-voxel face halos.
+ *   2 (default) 8x8x4 tiles staged with their two-voxel face halos.
  * Every variant gives the same results (the same operations in the same order). */
 dh_status dh_plan_set_variant_muscl(dh_plan* plan, int32_t fv2_var);
 
