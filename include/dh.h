@@ -184,12 +184,18 @@ dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, doub
  *            x = z-scored (|S|/E, D/E, ln(E/D)); then p_prev (or the cold seed
  *            max((1+1e-8) p_lo + 1e-300, (G-1) tau)) is the fallback
  *   seed_refine : 0..8 FP32 Newton steps applied to the first seed (the MLP's,
- *            else p_prev, else the cold seed) before the FP64 iteration: the
- *            textbook step with every operation rounded to float (no fused
- *            multiply-add) from float copies of D, E and S; a step whose result
- *            is not finite or not above p_lo stops the refinement.  With the
- *            MLP seed and seed_refine > 0 the seed E exp(y) is formed in FP32.
- *            The fallback seed is never refined.  0: the plain recovery.
+ *            else p_prev, else the cold seed) before the FP64 iteration.  The
+ *            step uses A = E^2 - S^2 and B = tau (tau + 2 D) - S^2, formed once
+ *            in FP64 with fused multiply-adds (S^2 = fma(S_x, S_x, fma(S_y, S_y,
+ *            S_z S_z))); with y = E + p, t = p (E + y), q = sqrt(A + t) and
+ *            q - D = (B + t)/(q + D) (no cancellation), p <- p - y (y f)/(y^2 f')
+ *            with y f = gf q (q - D) - p y, y^2 f' = gf S^2 (q - D)/q + (gf - 1) y^2,
+ *            gf = (G-1)/G; every FP32 operation rounded to float, no fused
+ *            multiply-add; a step whose result is not finite or not above p_lo
+ *            stops the refinement.  The refined seed lies within about 1e-6 of
+ *            the root, so the FP64 iteration usually stops after two steps.
+ *            With the MLP seed and seed_refine > 0 the seed E exp(y) is formed in
+ *            FP32.  The fallback seed is never refined.  0: the plain recovery.
  *   status : NULL or one byte per voxel: 0 first seed converged, 1 fallback
  *            converged, 2 both failed (pressure = p_prev or the cold seed)
  *   iters  : NULL or Newton iterations per voxel (int32)

@@ -999,26 +999,33 @@ void srhd_invariants(const double* q, double* x) {
   x[2] = std::log(E / D);
 }
 
-// FP32 refinement of a seed: up to k steps of the same Newton iteration on the pressure in
-// single precision (textbook f and f', every operation rounded to float, no fused
-// multiply-add), from float copies of D, E = tau + D and the momentum components.  A step
-// whose result is not finite or not above the bracket's lower end (in float) stops the
-// refinement and keeps the value before it.  The FP64 Newton iteration then starts from the
-// result.  (The paper has no relativistic hydrodynamics; this is the reading of a seeded
-// solve on hardware whose FP32 throughput is far above its FP64 throughput.)
+// FP32 refinement of a seed: up to k Newton steps on the pressure in single precision.  The
+// textbook f cancels badly in FP32 (1 - S^2/(E+p)^2 at high Lorentz factors, rho h - rho for
+// cold gas), so the step is written with two invariants formed once in FP64 with fused
+// multiply-adds, A = E^2 - S^2 and B = tau (tau + 2 D) - S^2 (= A - D^2), where
+// S^2 = fma(S_x, S_x, fma(S_y, S_y, S_z S_z)).  With y = E + p and t = p (E + y) = y^2 - E^2:
+// q = sqrt(y^2 - S^2) = sqrt(A + t) and q - D = (q^2 - D^2)/(q + D) = (B + t)/(q + D) are
+// sums of positive terms, y f = gf q (q - D) - p y and y^2 f' = gf S^2 (q - D)/q + (gf - 1) y^2
+// (gf = (Gamma - 1)/Gamma), and p <- p - y (y f)/(y^2 f').  Every FP32 operation is rounded to
+// float, no fused multiply-add, on float copies of A, B, E, D and S^2.  A step whose result is
+// not finite or not above the bracket's lower end (in float) stops the refinement and keeps the
+// value before it.  The FP64 Newton iteration then starts from the result.  (The paper has no
+// relativistic hydrodynamics; this is the reading of a seeded solve on hardware whose FP32
+// throughput is far above its FP64 throughput.)
 double refine_seed_f32(double Gamma, const double* q, double E, double p_lo, double seed, int k) {
-  const float D = (float)q[0], Ef = (float)E, lo = (float)p_lo;
-  const float Sx = (float)q[1], Sy = (float)q[2], Sz = (float)q[3];
-  const float S2 = Sx * Sx + Sy * Sy + Sz * Sz;
-  const float gf = (float)((Gamma - 1.0) / Gamma), one = 1.0f;
+  const double S2 = std::fma(q[1], q[1], std::fma(q[2], q[2], q[3] * q[3]));
+  const double A = std::fma(E, E, -S2), B = std::fma(q[4], std::fma(2.0, q[0], q[4]), -S2);
+  const float Af = (float)A, Bf = (float)B, Ef = (float)E, Df = (float)q[0], S2f = (float)S2, lo = (float)p_lo;
+  const float gf = (float)((Gamma - 1.0) / Gamma), gm = gf - 1.0f;
   float p = (float)seed;
   for (int i = 0; i < k; ++i) {
-    const float Ep = Ef + p;
-    const float s2e = S2 / (Ep * Ep);
-    const float rt = std::sqrt(one - s2e);
-    const float f = gf * (Ep - S2 / Ep - D * rt) - p;
-    const float fp = gf * (one + s2e - D * S2 / (Ep * Ep * Ep * rt)) - one;
-    const float pn = p - f / fp;
+    const float y = Ef + p;
+    const float t = p * (Ef + y);
+    const float qq = std::sqrt(Af + t);
+    const float qmD = (Bf + t) / (qq + Df);
+    const float yf = gf * qq * qmD - p * y;
+    const float den = gf * S2f * qmD / qq + gm * y * y;
+    const float pn = p - y * yf / den;
     if (!(pn > lo && pn < std::numeric_limits<float>::infinity())) break;
     p = pn;
   }

@@ -68,28 +68,36 @@ __device__ int srhd_newton_dev(double gf, double D, double S2, double E, double 
 }
 
 // FP32 refinement of the first seed: up to k Newton steps on the pressure in single
-// precision, textbook f and f', every operation rounded to float with no fused multiply-add
-// (the __f*_rn intrinsics), from float copies of D, E and the momentum components; a step
-// whose result is not finite or not above the bracket's lower end (in float) stops the
-// refinement and keeps the value before it.  The same operations in the same order as the
-// oracle's reference, so the refined seed is bitwise the oracle's.  FP32 runs far faster
-// than FP64 on this GPU: the steps cost little next to one FP64 Newton iteration.
-__device__ __forceinline__ double refine_seed_f32(const double* q, double E, double p_lo, double seed, int k,
-                                                  float gf) {
-  const float D = __double2float_rn(q[0]), Ef = __double2float_rn(E), lo = __double2float_rn(p_lo);
-  const float Sx = __double2float_rn(q[1]), Sy = __double2float_rn(q[2]), Sz = __double2float_rn(q[3]);
-  const float S2 = __fadd_rn(__fadd_rn(__fmul_rn(Sx, Sx), __fmul_rn(Sy, Sy)), __fmul_rn(Sz, Sz));
+// precision.  The terms of the textbook f cancel in FP32 for fast flows (1 - S^2/(E+p)^2 is
+// 0.01 at W = 10) and for cold gas (the rest mass D against rho h W), which leaves seeds a few
+// 1e-5 off; the step is therefore formed from two invariants taken once in FP64 with fused
+// multiply-adds, A = E^2 - S^2 and B = tau (tau + 2 D) - S^2 = A - D^2, in which nothing
+// cancels during the iteration: with y = E + p and t = p (E + y) = y^2 - E^2,
+//   q = sqrt(y^2 - S^2) = sqrt(A + t),  q - D = (q^2 - D^2)/(q + D) = (B + t)/(q + D),
+//   y f = gf q (q - D) - p y,  y^2 f' = gf S^2 (q - D)/q + (gf - 1) y^2  (the FP64 step's form),
+//   p <- p - y (y f)/(y^2 f').
+// Every FP32 operation is IEEE-rounded with no fused multiply-add (the __f*_rn intrinsics) on
+// float copies of A, B, E, D and S^2; a step whose result is not finite or not above the
+// bracket's lower end (in float) stops the refinement and keeps the value before it.  The same
+// operations in the same order as the oracle's reference, so the refined seed is bitwise the
+// oracle's; the seeds land within about 1e-6 of the root, from which two FP64 Newton steps meet
+// the 1e-12 rule.  FP32 runs far faster than FP64 on this GPU: the steps cost little next to
+// one FP64 Newton iteration.
+__device__ __forceinline__ double refine_seed_f32(const double* q, double E, double S2, double p_lo, double seed,
+                                                  int k, float gf) {
+  const double A = __fma_rn(E, E, -S2), B = __fma_rn(q[4], __fma_rn(2.0, q[0], q[4]), -S2);
+  const float Af = __double2float_rn(A), Bf = __double2float_rn(B), Ef = __double2float_rn(E);
+  const float Df = __double2float_rn(q[0]), S2f = __double2float_rn(S2), lo = __double2float_rn(p_lo);
+  const float gm = __fsub_rn(gf, 1.0f);
   float p = __double2float_rn(seed);
   for (int i = 0; i < k; ++i) {
-    const float Ep = __fadd_rn(Ef, p);
-    const float Ep2 = __fmul_rn(Ep, Ep);
-    const float s2e = __fdiv_rn(S2, Ep2);
-    const float rt = __fsqrt_rn(__fsub_rn(1.0f, s2e));
-    const float f = __fsub_rn(__fmul_rn(gf, __fsub_rn(__fsub_rn(Ep, __fdiv_rn(S2, Ep)), __fmul_rn(D, rt))), p);
-    const float fp = __fsub_rn(
-        __fmul_rn(gf, __fsub_rn(__fadd_rn(1.0f, s2e), __fdiv_rn(__fmul_rn(D, S2), __fmul_rn(__fmul_rn(Ep2, Ep), rt)))),
-        1.0f);
-    const float pn = __fsub_rn(p, __fdiv_rn(f, fp));
+    const float y = __fadd_rn(Ef, p);
+    const float t = __fmul_rn(p, __fadd_rn(Ef, y));
+    const float qq = __fsqrt_rn(__fadd_rn(Af, t));
+    const float qmD = __fdiv_rn(__fadd_rn(Bf, t), __fadd_rn(qq, Df));
+    const float yf = __fsub_rn(__fmul_rn(__fmul_rn(gf, qq), qmD), __fmul_rn(p, y));
+    const float den = __fadd_rn(__fdiv_rn(__fmul_rn(__fmul_rn(gf, S2f), qmD), qq), __fmul_rn(__fmul_rn(gm, y), y));
+    const float pn = __fsub_rn(p, __fdiv_rn(__fmul_rn(y, yf), den));
     if (!(pn > lo && pn < __int_as_float(0x7f800000))) break;
     p = pn;
   }
@@ -150,7 +158,7 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
     s1 = have_prev ? A.p_prev[e] : cold();
     have2 = have_prev;
   }
-  if (ref) s1 = refine_seed_f32(q, E, p_lo, s1, A.refine, A.gf32);
+  if (ref) s1 = refine_seed_f32(q, E, S2, p_lo, s1, A.refine, A.gf32);
   double p;
   int it1 = srhd_newton_dev(A.gf, D, S2, E, p_lo, s1, A.tol, A.max_iter, A.one, A.mone, A.zero, &p);
   int total = it1 > 0 ? it1 : -it1;
