@@ -450,6 +450,14 @@ dh_status dh_plan_set_debug(dh_plan* plan, int32_t flags);
  * can bound the reciprocal's error.  All three arrays are device arrays of n. */
 dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n, void* stream);
 
+/* Diagnostic: the integer-pipe conversions of the recovery's FP32 seed paths
+ * against the hardware conversions.  For n doubles x and n floats g (device
+ * arrays): f_int[i] / f_hw[i] = x[i] rounded to float by bit operations / by
+ * the hardware; d_int[i] / d_hw[i] = g[i] widened to double likewise.  The
+ * pairs are bitwise equal (NaNs aside) by construction. */
+dh_status dh_check_convert(const double* x, float* f_int, float* f_hw, const float* g, double* d_int, double* d_hw,
+                           int64_t n, void* stream);
+
 /* Diagnostic: FP64 FMA throughput probe used to measure the FP64 roofline
  * peak on the running GPU.  Launches n_threads (a multiple of 256) threads;
  * each runs 8 independent chains of `iters` fused multiply-adds

@@ -92,13 +92,20 @@ def con2prim_counts(n=20000, seed=5):
     assert round(A) * rows[2][0] + round(B) * rows[2][1] == rhs[2]
     speed = oracle.count_max_speed(synth.PDE_SRHD3D, 3, cons, prim, n)
     assert speed % n == 0
+    # derived quantities and the speed of one direction: the kernel evaluates only the direction
+    # of the largest |v_d|, whose speed is the largest (the speed increases with |v_d|)
+    speed1 = oracle.count_max_speed(synth.PDE_SRHD3D, 1, cons, prim, n)
+    assert speed1 % n == 0
     return {"c2p/srhd3d/voxel": {"flops_per_voxel": int(round(A)),
                                  "note": "setup and recovery of one voxel, plain seed, without the Newton iterations"},
             "c2p/srhd3d/newton_iteration": {"flops_per_voxel": int(round(B)),
                                             "note": "one Newton iteration on the pressure (no safeguard step)"},
             "speed/srhd3d/voxel": {"flops_per_voxel": speed // n,
                                    "note": "derived quantities and the speeds of all three directions, from the "
-                                           "primitives"}}
+                                           "primitives"},
+            "speed/srhd3d/voxel_one_direction": {"flops_per_voxel": speed1 // n,
+                                                 "note": "derived quantities and the speed of one direction, "
+                                                         "from the primitives"}}
 
 
 def main():

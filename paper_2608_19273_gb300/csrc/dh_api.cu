@@ -63,9 +63,7 @@ __global__ void __launch_bounds__(256) k_max_speed(const dh_patch* __restrict__ 
 #pragma unroll
     for (int v = 0; v < PDE::M; ++v) u[PDE::N + v] = mat[v * vs + e];
     PDE::prims(u, P, W);
-    double l = fmax(PDE::speed(0, u, W, P), PDE::speed(1, u, W, P));
-    if (dim == 3) l = fmax(l, PDE::speed(2, u, W, P));
-    lam = fmax(lam, l);
+    lam = fmax(lam, max_speed_dirs<PDE>(u, W, P, dim));
   }
   lam = warp_max_d(lam);
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lam;
@@ -103,9 +101,7 @@ __global__ void __launch_bounds__(256) k_max_speed_w(const dh_patch* __restrict_
     const int64_t e = pt.offset + i;
 #pragma unroll
     for (int v = 0; v < PDE::NW; ++v) W[v] = w[v * vs + e];
-    double l = fmax(PDE::speed(0, nullptr, W, P), PDE::speed(1, nullptr, W, P));
-    if (dim == 3) l = fmax(l, PDE::speed(2, nullptr, W, P));
-    lam = fmax(lam, l);
+    lam = fmax(lam, max_speed_dirs<PDE>(nullptr, W, P, dim));
   }
   lam = warp_max_d(lam);
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = lam;

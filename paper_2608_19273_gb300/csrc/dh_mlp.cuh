@@ -32,13 +32,46 @@ __device__ __forceinline__ void mlp_normalize(const float* w, const double* xd, 
   for (int j = 0; j < 3; ++j) x[j] = (float)((xd[j] - (double)w[MLP_MEAN + j]) / (double)w[MLP_STD + j]);
 }
 
+// Conversions between FP64 and FP32 on the integer pipes.  On this GPU the hardware
+// conversions run on the FP64 pipe at the FP64 rate (measured: a double -> float -> double
+// round trip costs as much as two FMAs and does not overlap with FMAs), so the FP32 seed
+// paths convert with bit operations.  Both give IEEE round-to-nearest-even results, so they
+// are bitwise the hardware conversions (tested over all exponent ranges); operands whose
+// float result would be zero, subnormal, infinite or NaN take the hardware path (a call, so
+// that it never executes on the common path).
+static __device__ __noinline__ float f32_rn_slow(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double f64_of_f32_slow(float f) { return (double)f; }
+
+// double -> float, round to nearest even: the 52-bit fraction keeps its top 23 bits and rounds
+// on the remaining 29 (a carry out of the fraction moves into the exponent, and past the largest
+// finite float into infinity, as IEEE rounding does).
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 896;  // float biased exponent (1023 - 127 = 896)
+  if (e < 1 || e > 254) return f32_rn_slow(x);
+  const unsigned frac = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  const unsigned up = (rem + (frac & 1u)) > 0x10000000u ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | (((unsigned)e << 23) + frac + up));
+}
+
+// float -> double (exact): exponent rebiased, fraction shifted into place.
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return f64_of_f32_slow(f);
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // z-scored FP32 network input formed in FP32 from D, E = tau + D and |S|
 // (the seed path of con2prim: the network is FP32, so its inputs need no FP64
 // divides or logarithm on the FP64 pipe).
 __device__ __forceinline__ void mlp_inputs_f32(const float* w, double D, double E, double S, float* x) {
-  const float rE = 1.0f / (float)E;
-  const float dE = (float)D * rE;
-  const float raw[3] = {(float)S * rE, dE, -logf(dE)};  // |S|/E, D/E, ln(E/D)
+  const float rE = 1.0f / f32_rn(E);
+  const float dE = f32_rn(D) * rE;
+  const float raw[3] = {f32_rn(S) * rE, dE, -logf(dE)};  // |S|/E, D/E, ln(E/D)
 #pragma unroll
   for (int j = 0; j < 3; ++j) x[j] = (raw[j] - w[MLP_MEAN + j]) / w[MLP_STD + j];
 }

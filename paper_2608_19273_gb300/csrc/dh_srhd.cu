@@ -86,10 +86,12 @@ __device__ int srhd_newton_dev(double gf, double D, double S2, double E, double 
 __device__ __forceinline__ double refine_seed_f32(const double* q, double E, double S2, double p_lo, double seed,
                                                   int k, float gf) {
   const double A = __fma_rn(E, E, -S2), B = __fma_rn(q[4], __fma_rn(2.0, q[0], q[4]), -S2);
-  const float Af = __double2float_rn(A), Bf = __double2float_rn(B), Ef = __double2float_rn(E);
-  const float Df = __double2float_rn(q[0]), S2f = __double2float_rn(S2), lo = __double2float_rn(p_lo);
+  // the conversions run on the integer pipes (f32_rn: the hardware's rounding, bit for bit)
+  const float Af = f32_rn(A), Bf = f32_rn(B), Ef = f32_rn(E);
+  const float Df = f32_rn(q[0]), S2f = f32_rn(S2);
+  const float lo = __double_as_longlong(p_lo) == 0 ? 0.0f : f32_rn(p_lo);
   const float gm = __fsub_rn(gf, 1.0f);
-  float p = __double2float_rn(seed);
+  float p = f32_rn(seed);
   for (int i = 0; i < k; ++i) {
     const float y = __fadd_rn(Ef, p);
     const float t = __fmul_rn(p, __fadd_rn(Ef, y));
@@ -101,7 +103,7 @@ __device__ __forceinline__ double refine_seed_f32(const double* q, double E, dou
     if (!(pn > lo && pn < __int_as_float(0x7f800000))) break;
     p = pn;
   }
-  return (double)p;
+  return f64_of_f32(p);
 }
 
 struct C2PArgs {
@@ -148,9 +150,9 @@ __device__ __forceinline__ int c2p_voxel(const C2PArgs& A, const float* w, int64
   if (w) {
     float x[3], h1[32], h2[32];
     // with the FP32 refinement the seed's |S| and exp are FP32 too (the refinement is)
-    mlp_inputs_f32(w, D, E, ref ? (double)__fsqrt_rn(__double2float_rn(S2)) : S, x);
+    mlp_inputs_f32(w, D, E, ref ? f64_of_f32(__fsqrt_rn(f32_rn(S2))) : S, x);
     const float y = mlp_forward(w, x, h1, h2);
-    const double ps = ref ? (double)__fmul_rn(__double2float_rn(E), expf(y)) : E * exp((double)y);
+    const double ps = ref ? f64_of_f32(__fmul_rn(f32_rn(E), expf(y))) : E * exp((double)y);
     const double lo = p_lo * (1.0 + 1e-12);
     s1 = ps > lo ? ps : cold();
     have2 = true;
@@ -226,6 +228,17 @@ __global__ void __launch_bounds__(256) k_con2prim_flat(int64_t n, const __grid_c
   }
 }
 
+// Diagnostic of the integer-pipe conversions against the hardware's.
+__global__ void k_check_convert(const double* x, float* f_int, float* f_hw, const float* g, double* d_int,
+                                double* d_hw, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  f_int[i] = f32_rn(x[i]);
+  f_hw[i] = __double2float_rn(x[i]);
+  d_int[i] = f64_of_f32(g[i]);
+  d_hw[i] = (double)g[i];
+}
+
 static dh_status c2p_check(const double* cons, double* prim, double tol, int32_t max_iter, int32_t seed_refine) {
   if (!cons || !prim || cons == prim) { set_error("con2prim: cons and prim are required and distinct"); return DH_EINVAL; }
   if (!(tol > 0.0) || max_iter < 1 || max_iter > 1000) { set_error("con2prim: tol > 0 and 1 <= max_iter <= 1000 required"); return DH_EINVAL; }
@@ -269,6 +282,16 @@ dh_status con2prim_flat(const double* cons, double* prim, int64_t n, int64_t str
   const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 8);
   k_con2prim_flat<<<grid, 256, 0, (cudaStream_t)stream>>>(n, A);
   return cuda_error(cudaGetLastError(), "con2prim_flat launch");
+}
+
+dh_status dh_check_convert(const double* x, float* f_int, float* f_hw, const float* g, double* d_int, double* d_hw,
+                           int64_t n, void* stream) {
+  if (!x || !f_int || !f_hw || !g || !d_int || !d_hw || n <= 0 || n > (1ll << 40)) {
+    set_error("dh_check_convert: bad arguments");
+    return DH_EINVAL;
+  }
+  k_check_convert<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, f_int, f_hw, g, d_int, d_hw, n);
+  return cuda_error(cudaGetLastError(), "dh_check_convert launch");
 }
 
 }  // extern "C"

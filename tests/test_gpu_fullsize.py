@@ -16,7 +16,7 @@ from paper_2608_19273_gb300 import dh, synth
 pytestmark = pytest.mark.gpu
 # as the benchmark: every con2prim of the SRHD steps refines its seed (the previous pressure) by
 # two FP32 Newton steps
-SRHD_REFINE = 2
+SRHD_REFINE = 3
 
 
 def _gpu_step(torch, name, w, q, mat, steps=1):

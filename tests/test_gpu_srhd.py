@@ -241,3 +241,64 @@ def test_con2prim_refined_seed_matches_oracle(orc, refine, seed):
     assert it.mean() < it0.mean()
     print(f"{seed} seed + {refine} FP32 steps: FP64 iterations {it0.mean():.2f} -> {it.mean():.2f}, "
           f"max relative error {worst:.2e}")
+
+
+@pytest.mark.gpu
+def test_integer_pipe_conversions_match_hardware():
+    """The seed paths convert between FP64 and FP32 with bit operations (the hardware conversions
+    run on the FP64 pipe); the results must be the hardware's bit for bit: random bit patterns
+    over every exponent, exact ties between adjacent floats (round half to even) and their
+    neighbours one double ulp away, the edges of the float range, and every float class."""
+    torch = require_cuda()
+    rng = np.random.default_rng(71)
+    n = 1 << 20
+    parts = [rng.integers(0, 2 ** 64, n, dtype=np.uint64, endpoint=False).view(np.float64)]
+    # doubles within the float exponent range
+    e = rng.integers(1023 - 130, 1023 + 130, n, dtype=np.uint64)
+    m = rng.integers(0, 2 ** 52, n, dtype=np.uint64)
+    s = rng.integers(0, 2, n, dtype=np.uint64)
+    parts.append(((s << np.uint64(63)) | (e << np.uint64(52)) | m).view(np.float64))
+    # ties between adjacent floats and one double ulp either side
+    f = rng.standard_normal(n).astype(np.float32) * np.float32(2.0) ** rng.integers(-120, 120, n).astype(np.float32)
+    f = f[np.isfinite(f) & (f != 0)]
+    tie = (f.astype(np.float64) + np.nextafter(f, np.float32(np.inf)).astype(np.float64)) / 2.0
+    parts += [tie, np.nextafter(tie, np.inf), np.nextafter(tie, -np.inf)]
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028234663852886e38, 3.4028235677973366e38,
+                        3.402823669209385e38, 1.1754943508222875e-38, 1.1754942e-38, 1.4e-45, 7e-46, 1e-300,
+                        1e300, 1.0, -1.0, 0.1, 2.0 ** -126, 2.0 ** -127, 2.0 ** 127, 2.0 ** 128])
+    parts.append(special)
+    x = np.ascontiguousarray(np.concatenate(parts))
+    g = rng.integers(0, 2 ** 32, len(x), dtype=np.uint64).astype(np.uint32).view(np.float32)
+    g[: 8] = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.4e-45, 1.1754942e-38, 3.4028235e38], dtype=np.float32)
+    dx = torch.from_numpy(x).cuda()
+    dg = torch.from_numpy(np.ascontiguousarray(g)).cuda()
+    fi, fh = (torch.empty(len(x), dtype=torch.float32, device="cuda") for _ in range(2))
+    di, dh_ = (torch.empty(len(x), dtype=torch.float64, device="cuda") for _ in range(2))
+    dh.dh_check_convert(dx, fi, fh, dg, di, dh_)
+    torch.cuda.synchronize()
+    fi, fh, di, dh_ = (t.cpu().numpy() for t in (fi, fh, di, dh_))
+    nan_f = np.isnan(fi) & np.isnan(fh)
+    assert np.all((fi.view(np.uint32) == fh.view(np.uint32)) | nan_f)
+    assert np.all((fh.view(np.uint32) == x.astype(np.float32).view(np.uint32)) | nan_f)  # IEEE RN
+    nan_d = np.isnan(di) & np.isnan(dh_)
+    assert np.all((di.view(np.uint64) == dh_.view(np.uint64)) | nan_d)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("seed,wmax", [(81, 10.0), (82, 10.0), (83, 1.5), (84, 3.0)])
+def test_srhd_max_wave_speed_matches_oracle(orc, seed, wmax):
+    """max_wave_speed for SRHD evaluates only the direction of the largest |v_d| (the speed grows
+    with |v_d|); the maximum over the mesh must equal the oracle's three-direction maximum to one
+    unit in the last place, on i.i.d. states of several Lorentz factor ranges."""
+    torch = require_cuda()
+    mesh = single_level(4, 16, 1.0 / 64)
+    n = mesh.var_stride
+    w = iid_prims(n, seed, wmax=wmax)
+    params = synth.workload("srhd3d").params
+    q = orc.prim2con(synth.PDE_SRHD3D, w, n)
+    ref = orc.max_wave_speed(synth.PDE_SRHD3D, 3, mesh.patches, n, q, mat=w, params=params)
+    with dh.Plan(synth.PDE_SRHD3D, 3, mesh.patches, 1, n, params) as plan:
+        lam = torch.zeros(1, dtype=torch.float64, device="cuda")
+        dh.max_wave_speed(plan, dev(torch, q), dev(torch, w), lam)
+        got = float(host(lam)[0])
+    assert abs(got - ref) <= 2.3e-16 * ref, (got, ref)
