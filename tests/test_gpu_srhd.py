@@ -293,7 +293,7 @@ def test_srhd_max_wave_speed_matches_oracle(orc, seed, wmax):
     with |v_d|); the maximum over the mesh must equal the oracle's three-direction maximum to one
     unit in the last place, on i.i.d. states of several Lorentz factor ranges."""
     torch = require_cuda()
-    mesh = single_level(4, 16, 1.0 / 64)
+    mesh = single_level((4, 4, 4), 16, 1.0 / 64)
     n = mesh.var_stride
     w = iid_prims(n, seed, wmax=wmax)
     params = synth.workload("srhd3d").params
