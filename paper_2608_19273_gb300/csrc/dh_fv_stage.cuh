@@ -77,6 +77,26 @@ struct FvArgs {
   DevParams P;
 };
 
+// The stage's arithmetic constants as register values.  On GB300 an FP64 FMA whose operands
+// are all registers issues at 2.0 per clock per SM, while DADD, DMUL and any FP64 instruction
+// with a constant-bank operand (a kernel parameter or a literal) issue at 1.68 (measured), so
+// the constants that the adds, subtractions and products written as FMAs use (1, -1, 0, 1/2)
+// and the gas constants are copied into registers once per thread: a shuffle hides their
+// values from the compiler, which would otherwise fold them back into constant-bank operands.
+__device__ __forceinline__ double opaque_reg(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ FvArgs with_reg_params(const FvArgs& A) {
+  FvArgs L = A;
+  L.P.one = opaque_reg(A.P.one);
+  L.P.mone = opaque_reg(A.P.mone);
+  L.P.zero = opaque_reg(A.P.zero);
+  L.P.half = opaque_reg(A.P.half);
+  L.P.gamma = opaque_reg(A.P.gamma);
+  L.P.gm1 = opaque_reg(A.P.gm1);
+  L.P.Gamma = opaque_reg(A.P.Gamma);
+  L.P.Gq = opaque_reg(A.P.Gq);
+  return L;
+}
+
 // Tensor maps of the TMA-staged variant, per arena level of back-to-back patches: boxes of
 // one z-plane of a 16x16 or 32x8 column and of its four ring strips (x strips two voxels
 // wide, so that every copy starts on a 16-byte boundary).  Other variants get an empty struct.
@@ -730,14 +750,15 @@ __global__ void __launch_bounds__(256, (VAR & 2) ? 2 : 1)
     __syncthreads();
   }
   double lam = 0.0;
+  const FvArgs R = with_reg_params(A);
   if constexpr (PERS) {
     for (int t = fv_next_item(A.queue); t < A.n_work; t = fv_next_item(A.queue)) {
-      fv_run_tile<PDE, EARLY, WM, T32, false>(A, A.work[t], smem, lam, nullptr, nullptr, nullptr);
+      fv_run_tile<PDE, EARLY, WM, T32, false>(R, A.work[t], smem, lam, nullptr, nullptr, nullptr);
       __syncthreads();  // the next tile reuses the shared memory
     }
     fv_queue_exit(A.queue);
   } else {
-    fv_run_tile<PDE, EARLY, WM, T32, TMA>(A, A.work[blockIdx.x], smem, lam, &M, bars, &abort_flag);
+    fv_run_tile<PDE, EARLY, WM, T32, TMA>(R, A.work[blockIdx.x], smem, lam, &M, bars, &abort_flag);
   }
   if (A.lam_out) publish_lambda(lam, A.lam_out, A.red, A.dt_next, A.cfl, A.dx_dim);
 }
@@ -750,7 +771,8 @@ __global__ void __launch_bounds__(64, (VAR & 2) ? 8 : 1) k_fv_stage64(const __gr
   constexpr bool EARLY = (VAR & 1) != 0;
   constexpr int WM = (VAR >> 2) & 3;
   double lam = 0.0;
-  FvTile<PDE, 8, 8, 1, EARLY, WM>::run(A, A.work[blockIdx.x], smem, lam);
+  const FvArgs R = with_reg_params(A);
+  FvTile<PDE, 8, 8, 1, EARLY, WM>::run(R, A.work[blockIdx.x], smem, lam);
   if (A.lam_out) publish_lambda(lam, A.lam_out, A.red, A.dt_next, A.cfl, A.dx_dim);
 }
 
