@@ -18,14 +18,17 @@ __device__ __forceinline__ double sel3(int d, double a, double b, double c) {
   return d == 0 ? a : (d == 1 ? b : c);
 }
 
-// In isolation GB300 issues FP64 fused multiply-adds at 1.9 per clock per SM
-// but plain adds and multiplies at 1.6.  The FV stage therefore writes its
-// adds, subtractions and products as FMAs whose extra operand is 1, -1 or 0
-// taken from the kernel parameters (values the compiler cannot see, so it
-// cannot turn them back into DADD/DMUL); measured on the full stage this is
-// 1% faster (the FD stage keeps plain operations: there it was 7% slower).
-// The results are bitwise those of a + b, a - b and a * b (a product that is
-// -0 comes out as +0).
+// GB300 issues FP64 fused multiply-adds with register operands at 2.0 per
+// clock per SM, but DADD, DMUL and FP64 instructions with a constant-bank
+// operand (a kernel parameter or a literal) at 1.68 (measured).  The FV stage
+// therefore writes its adds, subtractions and products as FMAs whose extra
+// operand is 1, -1 or 0 from its parameters (values the compiler cannot see,
+// so it cannot turn them back into DADD/DMUL), and its kernels copy those
+// parameters into registers once per thread (a shuffle hides them from the
+// compiler, which would fold them into constant-bank operands).  The FD stage
+// keeps plain operations (the FMA form with constant-bank operands measured 7%
+// slower there).  The results are bitwise those of a + b, a - b and a * b (a
+// product that is -0 comes out as +0).
 __device__ __forceinline__ double ADD(const DevParams& P, double a, double b) { return fma(a, P.one, b); }
 __device__ __forceinline__ double SUB(const DevParams& P, double a, double b) { return fma(b, P.mone, a); }
 __device__ __forceinline__ double MUL(const DevParams& P, double a, double b) { return fma(a, b, P.zero); }
