@@ -167,7 +167,10 @@ dh_status patch_update_fv_muscl(dh_plan* plan, const double* qs, const double* q
                                 double* lam_out_dev, void* stream);
 
 /* lam_out_dev <- max over voxels and directions of the characteristic speed of q
- * (the paper's scalar eigenvalue functions, Sec. II-B). */
+ * (the paper's scalar eigenvalue functions, Sec. II-B).  SRHD3D (mat = the
+ * primitives): a voxel's speed grows with |v_d|, so only the direction of its
+ * largest |v_d| is evaluated; the result is that direction's speed, within one
+ * ulp of the maximum over three separately rounded speeds. */
 dh_status max_wave_speed(dh_plan* plan, const double* q, const double* mat, double* lam_out_dev, void* stream);
 
 /* Conservative -> primitive recovery for SRHD3D over the plan's voxels
