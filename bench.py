@@ -840,6 +840,16 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
     table = flop_table()
     flops_vs = table[spec["flops"]]["flops_per_voxel"]
     stage_sum_s = float(stage_ms.sum()) * 1e-3
+    # The event records around every stage launch cost time of their own (about 4 us per launch):
+    # where the per-stage times add up to more than the replay without them, the replay's time per
+    # stage launch (which still includes the gaps between launches, and the step's one CFL kernel
+    # where there is one) is the smaller, and closer, bound on the stage kernel's duration.
+    step_s = ms * 1e-3 / steps
+    duration_source = "per-stage CUDA events in a graph replay"
+    if stage_sum_s > step_s:
+        stage_sum_s = step_s
+        duration_source = ("CUDA events around the timed replays / stage launches (the replay holds only the "
+                           "stage launches and at most one CFL kernel; per-stage event records would add their own time)")
     ach = flops_vs * nvox * inner / stage_sum_s / 1e12
     hbm, hbm_src = hbm_peak()
     roof = {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
@@ -848,6 +858,7 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
             "flops_per_voxel_step": flops_vs, "timed_launches": int(n_timed),
             "stage_ms_mean": float(stage_ms.mean()),
             "stage_share_of_step": float(stage_ms.sum()) / (ms / steps),
+            "duration_source": duration_source,
             "hbm": {"bytes_per_voxel_step": spec["bytes"], "peak_gbs": hbm, "peak_source": hbm_src,
                     "achieved_gbs": spec["bytes"] * nvox * inner / stage_sum_s / 1e9,
                     "frac": spec["bytes"] * nvox * inner / stage_sum_s / 1e9 / hbm}}
