@@ -842,14 +842,14 @@ def run_workload(torch, dh, name, args, stream, world, dist, peak, warmup, steps
     stage_sum_s = float(stage_ms.sum()) * 1e-3
     # The event records around every stage launch cost time of their own (about 4 us per launch):
     # where the per-stage times add up to more than the replay without them, the replay's time per
-    # stage launch (which still includes the gaps between launches, and the step's one CFL kernel
-    # where there is one) is the smaller, and closer, bound on the stage kernel's duration.
+    # stage launch (which still includes the gaps between launches and the steps' CFL kernels,
+    # where there are any) is the smaller, and closer, bound on the stage kernel's duration.
     step_s = ms * 1e-3 / steps
     duration_source = "per-stage CUDA events in a graph replay"
     if stage_sum_s > step_s:
         stage_sum_s = step_s
         duration_source = ("CUDA events around the timed replays / stage launches (the replay holds only the "
-                           "stage launches and at most one CFL kernel; per-stage event records would add their own time)")
+                           "stage launches and the steps' CFL kernels; per-stage event records would add their own time)")
     ach = flops_vs * nvox * inner / stage_sum_s / 1e12
     hbm, hbm_src = hbm_peak()
     roof = {"bound": "alu", "kernel": spec["kernel"], "achieved": ach, "peak": peak, "unit": "TFLOP/s",
