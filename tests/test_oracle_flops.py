@@ -105,7 +105,9 @@ def test_stored_table_is_what_the_oracle_counts_now():
 #             cs^2 = Gamma p/(rho h) (2) = 11; per direction cs (1), 1 - v^2 cs^2 (2),
 #             v_d (1 - cs^2) (2), cs sqrt((1 - v^2)(1 - v^2 cs^2 - v_d^2 (1 - cs^2))) (10),
 #             (a +- r)/den (4) = 19                                                    = 11 + 3 x 19
-C2P_HAND = {"c2p/srhd3d/voxel": 11 + 13, "c2p/srhd3d/newton_iteration": 24, "speed/srhd3d/voxel": 11 + 3 * 19}
+#             (one direction, what the kernel evaluates: the largest |v_d|)           = 11 + 19
+C2P_HAND = {"c2p/srhd3d/voxel": 11 + 13, "c2p/srhd3d/newton_iteration": 24, "speed/srhd3d/voxel": 11 + 3 * 19,
+            "speed/srhd3d/voxel_one_direction": 11 + 19}
 
 
 @pytest.mark.parametrize("key", sorted(C2P_HAND))
