@@ -26,8 +26,8 @@ __device__ __forceinline__ double sel3(int d, double a, double b, double c) {
 // so it cannot turn them back into DADD/DMUL), and its kernels copy those
 // parameters into registers once per thread (a shuffle hides them from the
 // compiler, which would fold them into constant-bank operands).  The FD stage
-// keeps plain operations (the FMA form with constant-bank operands measured 7%
-// slower there).  The results are bitwise those of a + b, a - b and a * b (a
+// keeps plain operations (the FMA form measured 7% slower there with
+// constant-bank operands, and no faster with register operands).  The results are bitwise those of a + b, a - b and a * b (a
 // product that is -0 comes out as +0).
 __device__ __forceinline__ double ADD(const DevParams& P, double a, double b) { return fma(a, P.one, b); }
 __device__ __forceinline__ double SUB(const DevParams& P, double a, double b) { return fma(b, P.mone, a); }
