@@ -102,7 +102,14 @@ typedef struct dh_plan dh_plan;
  *   params     : PDE parameters (host, may be NULL for defaults):
  *                EULER*: [gamma=1.4]  SRHD3D: [Gamma=5/3]  WAVE3D: [damping=0.1]
  *                GW59: [kappa=0.1, C_ab (121 values, row-major)]
- * Patch sizes: every p must be a multiple of 8.  A face neighbour has the
+ * Patch sizes: 2 <= p <= 256.  Plans whose sizes are all multiples of 8 run
+ * every stage kernel; other plans (the paper's typical 3^3 and 6^3 cells,
+ * Sec. IV) run the first-order FV stage (patch_update_fv, dh_rk_step and the
+ * graphs with scheme 0) through a generic kernel -- whole small patches packed
+ * up to eight to a CTA, boxes of 8x8x4 (2D: 16x16) voxels of larger ones --
+ * and refuse the FD4, MUSCL and coupled-level paths (DH_EUNSUPPORTED, or
+ * DH_EINVAL at plan creation for coupled tables); the autotuner has nothing to
+ * choose for them.  A face neighbour has the
  * same p, dx and level, or -- coupled refinement levels -- is one level
  * coarser with the same p and twice the dx; every patch above the coarsest
  * level present must then cover one octant of a patch one level coarser (its

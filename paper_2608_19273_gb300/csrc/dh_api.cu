@@ -205,6 +205,60 @@ __global__ void k_check_recip(const double* x, double* y_nr, double* y_div, int6
 
 static inline int pt_nbr(const dh_patch* patches, int k, int f) { return patches[k].nbr[f]; }
 
+// Work list of the generic FV stage (k_fv_any; see dh_fv_any.cuh): patches of equal p and dx
+// packed whole, up to eight to a CTA, where a patch fits (at most 256 voxels, and the groups'
+// boxes with their face halo at most 640 cells); boxes of 8x8x4 (3D) or 16x16 (2D) voxels of
+// larger patches otherwise.  Largest work first.
+static std::vector<AnyWork> any_work(const dh_patch* patches, int K, int dim) {
+  constexpr int NT = 256, SLOTS = 640;
+  std::vector<AnyWork> out;
+  std::vector<int> order(K);
+  for (int k = 0; k < K; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return patches[a].p != patches[b].p ? patches[a].p > patches[b].p : patches[a].dx < patches[b].dx;
+  });
+  auto blank = [] {
+    AnyWork w{};
+    for (int i = 0; i < 8; ++i) w.patch[i] = -1;
+    return w;
+  };
+  size_t i = 0;
+  while (i < order.size()) {
+    const int k = order[i], p = patches[k].p;
+    const int pz = dim == 3 ? p : 1;
+    const int nvox = p * p * pz, cells = (p + 2) * (p + 2) * (dim == 3 ? p + 2 : 1);
+    const int G = std::min({8, NT / nvox, SLOTS / cells});
+    if (G >= 1) {
+      AnyWork w = blank();
+      w.bx = (int8_t)p; w.by = (int8_t)p; w.bz = (int8_t)pz;
+      int ng = 0;
+      while (ng < G && i < order.size() && patches[order[i]].p == p && patches[order[i]].dx == patches[k].dx)
+        w.patch[ng++] = order[i++];
+      w.ng = (int8_t)ng;
+      out.push_back(w);
+      continue;
+    }
+    const int tx = dim == 3 ? 8 : 16, ty = tx, tz = dim == 3 ? 4 : 1;
+    for (int z0 = 0; z0 < pz; z0 += tz)
+      for (int y0 = 0; y0 < p; y0 += ty)
+        for (int x0 = 0; x0 < p; x0 += tx) {
+          AnyWork w = blank();
+          w.patch[0] = k;
+          w.x0 = (int16_t)x0; w.y0 = (int16_t)y0; w.z0 = (int16_t)z0;
+          w.bx = (int8_t)std::min(tx, p - x0);
+          w.by = (int8_t)std::min(ty, p - y0);
+          w.bz = (int8_t)std::min(tz, pz - z0);
+          w.ng = 1;
+          out.push_back(w);
+        }
+    ++i;
+  }
+  std::stable_sort(out.begin(), out.end(), [](const AnyWork& a, const AnyWork& b) {
+    return a.ng * a.bx * a.by * a.bz > b.ng * b.bx * b.by * b.bz;
+  });
+  return out;
+}
+
 static dh_status check_plan(const dh_plan* plan) {
   if (!plan) {
     set_error("plan is NULL");
@@ -233,9 +287,11 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   if (halo < 1 || halo > 8) { set_error("dh_plan_create: halo %d out of range [1, 8]", halo); return DH_EINVAL; }
   if (var_stride <= 0 || var_stride % 32 != 0) { set_error("dh_plan_create: var_stride %lld must be a positive multiple of 32", (long long)var_stride); return DH_EINVAL; }
   if (n_params < 0 || (n_params > 0 && !params)) { set_error("dh_plan_create: bad params"); return DH_EINVAL; }
+  bool generic = false;
+  for (int k = 0; k < K; ++k) generic = generic || patches[k].p % 8 != 0;
   for (int k = 0; k < K; ++k) {
     const dh_patch& pt = patches[k];
-    if (pt.p < 8 || pt.p % 8 != 0 || pt.p > 256) { set_error("patch %d: p = %d must be a multiple of 8 in [8, 256]", k, pt.p); return DH_EINVAL; }
+    if (pt.p < 2 || pt.p > 256) { set_error("patch %d: p = %d must lie in [2, 256]", k, pt.p); return DH_EINVAL; }
     if (pt.p < halo) { set_error("patch %d: p = %d smaller than the halo %d", k, pt.p, halo); return DH_EINVAL; }
     if (!(pt.dx > 0.0)) { set_error("patch %d: dx must be positive", k); return DH_EINVAL; }
     const int64_t n = dim == 3 ? (int64_t)pt.p * pt.p * pt.p : (int64_t)pt.p * pt.p;
@@ -248,6 +304,10 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
       if (nb < 0 || nb >= K) { set_error("patch %d: neighbour %d = %d out of range", k, f, nb); return DH_EINVAL; }
       const bool same = patches[nb].p == pt.p && patches[nb].dx == pt.dx && patches[nb].level == pt.level;
       const bool coarser = patches[nb].p == pt.p && patches[nb].dx == 2.0 * pt.dx && patches[nb].level == pt.level - 1;
+      if (coarser && generic) {
+        set_error("patch %d: coupled refinement levels need patch sizes that are multiples of 8", k);
+        return DH_EINVAL;
+      }
       if (!same && !coarser) {
         set_error("patch %d: neighbour %d (patch %d) must have the same p, dx and level, or be one level coarser "
                   "with the same p and twice the dx", k, f, nb);
@@ -289,7 +349,7 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     cudaGetLastError();
   }
   std::vector<Work> lists[dh_plan::NWL];
-  for (int li = 0; li < dh_plan::NWL; ++li) {
+  for (int li = 0; li < dh_plan::NWL && !generic; ++li) {
     const int tile = li / 2, zs = li % 2;
     std::vector<Work>& work = lists[li];
     std::vector<std::vector<std::pair<int, std::pair<int, int>>>> pending(257);
@@ -354,7 +414,7 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
 
   // FD tiles: 8x8x4 blocks (p is a multiple of 8)
   std::vector<FdWork> fdw;
-  if (dim == 3) {
+  if (dim == 3 && !generic) {
     for (int k = 0; k < K; ++k) {
       const int p = patches[k].p;
       for (int zz = 0; zz < p; zz += 4)
@@ -364,10 +424,18 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   }
   plan->n_fdwork = (int)fdw.size();
 
+  // Generic FV work (patch sizes not all multiples of 8): whole patches packed up to eight to a
+  // CTA where a patch and its face halo fit (p^3 <= 256 voxels and (p+2)^3 cells in 3D), else
+  // boxes of 8x8x4 (3D) or 16x16 (2D) voxels, smaller at a patch's upper ends.
+  std::vector<AnyWork> anyw;
+  plan->fv_generic = generic;
+  if (generic) anyw = any_work(patches, K, dim);
+  plan->n_any = (int)anyw.size();
+
   // Levels for TMA staging (see dh_internal.cuh).
   std::vector<int2> lvl(K);
   {
-    bool ok = dim == 3;
+    bool ok = dim == 3 && !generic;
     int nl = 0;
     for (int k = 0; k < K && ok;) {
       int e = k + 1;
@@ -397,6 +465,9 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
     if (e == cudaSuccess && !lists[li].empty())
       e = cudaMemcpy(plan->d_wl[li], lists[li].data(), sizeof(Work) * lists[li].size(), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess && !anyw.empty()) e = cudaMalloc(&plan->d_any, sizeof(AnyWork) * anyw.size());
+  if (e == cudaSuccess && !anyw.empty())
+    e = cudaMemcpy(plan->d_any, anyw.data(), sizeof(AnyWork) * anyw.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !fdw.empty()) e = cudaMalloc(&plan->d_fdwork, sizeof(FdWork) * fdw.size());
   if (e == cudaSuccess && !fdw.empty())
     e = cudaMemcpy(plan->d_fdwork, fdw.data(), sizeof(FdWork) * fdw.size(), cudaMemcpyHostToDevice);
@@ -433,6 +504,7 @@ dh_status dh_plan_destroy(dh_plan* plan) {
     if (plan->d_wl[li]) cudaFree(plan->d_wl[li]);
   if (plan->d_red) cudaFree(plan->d_red);
   if (plan->d_fdwork) cudaFree(plan->d_fdwork);
+  if (plan->d_any) cudaFree(plan->d_any);
   if (plan->d_lvl) cudaFree(plan->d_lvl);
   if (plan->d_aunits) cudaFree(plan->d_aunits);
   if (plan->d_offload) cudaFree(plan->d_offload);
@@ -483,6 +555,7 @@ dh_status patch_update_fd_ko(dh_plan* plan, const double* qs, const double* q0, 
                              double sigma_ko, double* lam_out_dev, void* stream) {
   dh_status st = check_plan(plan);
   if (st != DH_OK) return st;
+  if (plan->fv_generic) { set_error("patch_update_fd_ko: needs patch sizes that are multiples of 8"); return DH_EUNSUPPORTED; }
   if (!qs || !dt_dev) { set_error("patch_update_fd_ko: qs and dt_dev are required"); return DH_EINVAL; }
   if (!out && !acc) { set_error("patch_update_fd_ko: nothing to write (out and acc are NULL)"); return DH_EINVAL; }
   if (plan->nm > 0 && !mat) { set_error("patch_update_fd_ko: PDE needs the material arena"); return DH_EINVAL; }
@@ -500,6 +573,7 @@ dh_status patch_update_fv_muscl(dh_plan* plan, const double* qs, const double* q
                                 double* lam_out_dev, void* stream) {
   dh_status st = check_plan(plan);
   if (st != DH_OK) return st;
+  if (plan->fv_generic) { set_error("patch_update_fv_muscl: needs patch sizes that are multiples of 8"); return DH_EUNSUPPORTED; }
   if (!qs || !dt_dev) { set_error("patch_update_fv_muscl: qs and dt_dev are required"); return DH_EINVAL; }
   if (!out && !acc) { set_error("patch_update_fv_muscl: nothing to write (out and acc are NULL)"); return DH_EINVAL; }
   if (plan->nm > 0 && !mat) { set_error("patch_update_fv_muscl: PDE needs the material arena"); return DH_EINVAL; }

@@ -1,0 +1,239 @@
+// First-order FV stage for plans with patch sizes that are not multiples of 8 (the paper's
+// typical 3^3 and 6^3 cells, Sec. IV): the same operator as the z-marching stage (Rusanov face
+// flux and non-conservative product of Sec. II-A Eq. 3, the stage combination and the lambda
+// epilogue), in a simpler tiling that fits any p.
+//
+// A CTA of 256 threads takes one work item: up to eight whole small patches of equal p (each
+// patch a group, p^3 <= 256 voxels in 3D, p^2 <= 256 in 2D) or one box of one larger patch
+// (8x8x4 voxels in 3D, 16x16 in 2D, smaller at the patch's upper ends).  One voxel per thread.
+//   1. Every cell of the box and its one-voxel face halo (edges and corners are never read) is
+//      loaded into shared memory with its derived quantities W (read from the W arena of the
+//      stage input, or computed).
+//   2. Per direction d: every cell of a line along d (the box and the two halo layers) forms its
+//      flux F_d and speed lambda_d into shared memory; after a barrier every voxel forms the
+//      Rusanov fluxes of its two d faces (each interior face twice, once from each side: simpler
+//      than a face array, and this path is for small or odd patches) and adds their difference.
+//   3. The stage combination, W of the result and lambda of the result as in the marching stage.
+// Shared memory: ANY_SLOTS cells x (N + M quantities, W, F_d, lambda_d).
+#pragma once
+
+namespace dh {
+
+constexpr int ANY_NT = 256;     // threads per CTA
+constexpr int ANY_SLOTS = 640;  // box cells (all groups) per CTA
+
+template <class PDE>
+struct FvAny {
+  static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW > 0 ? PDE::NW : 1, DIM = PDE::DIM;
+  static constexpr size_t SMEM = sizeof(double) * (size_t)ANY_SLOTS * (NV + NW + N + 1);
+
+  template <int WM>
+  __device__ static void run(const FvArgs& A, const AnyWork& w, double* smem, double& lam_thread) {
+    double* Q = smem;                 // [NV][ANY_SLOTS]
+    double* Wc = Q + NV * ANY_SLOTS;  // [NW][ANY_SLOTS]
+    double* F = Wc + NW * ANY_SLOTS;  // [N][ANY_SLOTS], one direction at a time
+    double* L = F + N * ANY_SLOTS;    // [ANY_SLOTS]
+    const DevParams& P = A.P;
+    const int bx = w.bx, by = w.by, bz = DIM == 3 ? w.bz : 1, ng = w.ng;
+    const int SX = bx + 2, SY = by + 2, SZ = DIM == 3 ? bz + 2 : 1;
+    const int SG = SX * SY * SZ;  // cells per group
+    const int nvg = bx * by * bz;  // voxels per group
+    const int tid = threadIdx.x;
+    const int g = tid / nvg, li = tid % nvg;
+    const bool act = g < ng;
+    const int lx = li % bx, ly = (li / bx) % by, lz = li / (bx * by);
+    const int p = A.patches[w.patch[0]].p;  // every group of an item has the same p
+    const double dt = *A.dt_dev;             // read before the lambda epilogue may rewrite it
+    const double gdt = A.g * dt, ddt = A.d * dt;
+
+    // 1. the box and its face halo, with W
+    for (int s = tid; s < ng * SG; s += ANY_NT) {
+      const int gg = s / SG, r = s % SG;
+      const int cx = r % SX - 1, cy = (r / SX) % SY - 1, cz = DIM == 3 ? r / (SX * SY) - 1 : 0;
+      const int outside = (cx < 0 || cx >= bx) + (cy < 0 || cy >= by) + (DIM == 3 && (cz < 0 || cz >= bz));
+      if (outside > 1) continue;
+      const int k = w.patch[gg];
+      const int64_t e = vox_index(A.patches, nullptr, k, p, w.x0 + cx, w.y0 + cy, DIM == 3 ? w.z0 + cz : 0);
+      double q[NV], W[NW];
+#pragma unroll
+      for (int v = 0; v < N; ++v) q[v] = __ldg(A.qs + v * A.vs + e);
+#pragma unroll
+      for (int v = 0; v < PDE::M; ++v) q[N + v] = __ldg(A.mat + v * A.vs + e);
+      if (WM & 1) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) W[i] = __ldg(A.w_in + i * A.vs + e);
+      } else {
+        PDE::prims(q, P, W);
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Q[v * ANY_SLOTS + s] = q[v];
+#pragma unroll
+      for (int i = 0; i < NW; ++i) Wc[i * ANY_SLOTS + s] = W[i];
+    }
+    __syncthreads();
+
+    // 2. per direction: line fluxes and speeds, then this voxel's two faces
+    const int me = g * SG + ((DIM == 3 ? lz + 1 : 0) * SY + (ly + 1)) * SX + (lx + 1);
+    double sum[N], dsum[N];
+#pragma unroll
+    for (int v = 0; v < N; ++v) { sum[v] = 0.0; dsum[v] = 0.0; }
+#pragma unroll 1
+    for (int d = 0; d < DIM; ++d) {
+      for (int s = tid; s < ng * SG; s += ANY_NT) {
+        const int r = s % SG;
+        const int cx = r % SX - 1, cy = (r / SX) % SY - 1, cz = DIM == 3 ? r / (SX * SY) - 1 : 0;
+        const bool inx = cx >= 0 && cx < bx, iny = cy >= 0 && cy < by, inz = DIM == 2 || (cz >= 0 && cz < bz);
+        const bool line = d == 0 ? (iny && inz) : (d == 1 ? (inx && inz) : (inx && iny));
+        if (!line) continue;
+        double q[NV], W[NW], Fd[N];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) q[v] = Q[v * ANY_SLOTS + s];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) W[i] = Wc[i * ANY_SLOTS + s];
+        if (PDE::FLUX) {
+          PDE::flux(d, q, W, P, Fd);
+#pragma unroll
+          for (int v = 0; v < N; ++v) F[v * ANY_SLOTS + s] = Fd[v];
+        }
+        L[s] = PDE::speed(d, q, W, P);
+      }
+      __syncthreads();
+      if (act) {
+        const int st = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
+        const int cm = me - st, cp = me + st;
+        const double sm = max_nn(L[cm], L[me]), sp = max_nn(L[me], L[cp]);
+        double dqm[N], dqp[N];
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          const double qm = Q[v * ANY_SLOTS + cm], qc = Q[v * ANY_SLOTS + me], qp = Q[v * ANY_SLOTS + cp];
+          dqm[v] = SUB(P, qc, qm);
+          dqp[v] = SUB(P, qp, qc);
+          double hm, hp;
+          if (PDE::FLUX) {
+            hm = fma(-sm, dqm[v], ADD(P, F[v * ANY_SLOTS + cm], F[v * ANY_SLOTS + me]));
+            hp = fma(-sp, dqp[v], ADD(P, F[v * ANY_SLOTS + me], F[v * ANY_SLOTS + cp]));
+          } else {
+            hm = MUL(P, -sm, dqm[v]);
+            hp = MUL(P, -sp, dqp[v]);
+          }
+          sum[v] = ADD(P, sum[v], SUB(P, hp, hm));
+        }
+        if (PDE::NCP) {
+          double qbm[NV], qbp[NV], Dm[N], Dp[N];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const double qc = Q[v * ANY_SLOTS + me];
+            qbm[v] = MUL(P, 0.5, ADD(P, Q[v * ANY_SLOTS + cm], qc));
+            qbp[v] = MUL(P, 0.5, ADD(P, qc, Q[v * ANY_SLOTS + cp]));
+          }
+          PDE::ncp(d, qbm, dqm, P, Dm);
+          PDE::ncp(d, qbp, dqp, P, Dp);
+#pragma unroll
+          for (int v = 0; v < N; ++v) dsum[v] = ADD(P, dsum[v], ADD(P, Dp[v], Dm[v]));
+        }
+      }
+      __syncthreads();  // the next direction rewrites F and L
+    }
+
+    // 3. stage combination, W and lambda of the result
+    if (!act) return;
+    const int k = w.patch[g];
+    const double cL = -0.5 / A.patches[k].dx;  // faces hold twice the flux
+    const double cS = gdt * cL, cA = ddt * cL;
+    const bool b1 = A.b == 1.0;
+    const int x = w.x0 + lx, y = w.y0 + ly, z = DIM == 3 ? w.z0 + lz : 0;
+    const int64_t e = A.patches[k].offset + ((int64_t)z * p + y) * p + x;
+    double Qk[NV], Sv[N], res[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Qk[v] = Q[v * ANY_SLOTS + me];
+    if (PDE::SRC) {
+      double Wk[NW];
+      PDE::prims(Qk, P, Wk);
+      PDE::source(Qk, Wk, P, Sv);
+    }
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+      const double s = PDE::NCP ? ADD(P, sum[v], dsum[v]) : sum[v];
+      const int64_t ev = v * A.vs + e;
+      if (!PDE::SRC && A.form != 0) {
+        double o;
+        if (A.form == 1) {
+          o = fma(cS, s, Qk[v]);
+          A.acc[ev] = s;
+        } else if (A.form == 2) {
+          const double t = ADD(P, A.acc[ev], s);
+          o = fma(cS, t, __ldg(A.q0 + ev));
+          A.acc[ev] = t;
+        } else {
+          o = fma(cS, s, fma(cA, A.acc[ev], __ldg(A.q0 + ev)));
+        }
+        res[v] = o;
+        A.out[ev] = o;
+        continue;
+      }
+      if (A.out) {
+        double base = b1 ? Qk[v] : MUL(P, A.b, Qk[v]);
+        if (A.q0) base = fma(A.a, __ldg(A.q0 + ev), base);
+        res[v] = PDE::SRC ? fma(gdt, fma(cL, s, Sv[v]), base) : fma(cS, s, base);
+      }
+      if (A.acc) {
+        const double r = PDE::SRC ? fma(ddt, fma(cL, s, Sv[v]), A.acc[ev]) : fma(cA, s, A.acc[ev]);
+        A.acc[ev] = r;
+        if (!A.out) res[v] = r;
+      }
+      if (A.out) A.out[ev] = res[v];
+    }
+    if (A.lam_out || (WM & 2)) {
+#pragma unroll
+      for (int v = N; v < NV; ++v) res[v] = Qk[v];
+      double Wr[NW];
+      PDE::prims(res, P, Wr);
+      if (WM & 2) {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) A.w_out[i * A.vs + e] = Wr[i];
+      }
+      if (A.lam_out) {
+        double l = max_nn(PDE::speed(0, res, Wr, P), PDE::speed(1, res, Wr, P));
+        if (DIM == 3) l = max_nn(l, PDE::speed(2, res, Wr, P));
+        lam_thread = max_nn(lam_thread, l);
+      }
+    }
+  }
+};
+
+template <class PDE, int WM>
+__global__ void __launch_bounds__(ANY_NT) k_fv_any(const __grid_constant__ FvArgs A, const AnyWork* __restrict__ work) {
+  extern __shared__ __align__(16) double smem[];
+  double lam = 0.0;
+  FvAny<PDE>::template run<WM>(A, work[blockIdx.x], smem, lam);
+  if (A.lam_out) publish_lambda(lam, A.lam_out, A.red, A.dt_next, A.cfl, A.dx_dim);
+}
+
+template <class PDE, int WM>
+static dh_status launch_any_wm(dh_plan* plan, const FvArgs& A, cudaStream_t stream) {
+  constexpr size_t smem = FvAny<PDE>::SMEM;
+  static int configured_device = -1;
+  if (configured_device != plan->device) {
+    cudaError_t e = cudaFuncSetAttribute(k_fv_any<PDE, WM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(k_fv_any)");
+    configured_device = plan->device;
+  }
+  if (plan->n_any <= 0) return DH_OK;
+  k_fv_any<PDE, WM><<<plan->n_any, ANY_NT, smem, stream>>>(A, plan->d_any);
+  return cuda_error(cudaGetLastError(), "k_fv_any launch");
+}
+
+template <class PDE>
+static dh_status launch_any(dh_plan* plan, const FvArgs& A, int wmode, cudaStream_t stream) {
+  if constexpr (std::is_same<PDE, PdeEuler2>::value || std::is_same<PDE, PdeEuler3>::value) {
+    switch (wmode & 3) {
+      case 1: return launch_any_wm<PDE, 1>(plan, A, stream);
+      case 2: return launch_any_wm<PDE, 2>(plan, A, stream);
+      case 3: return launch_any_wm<PDE, 3>(plan, A, stream);
+      default: break;
+    }
+  }
+  return launch_any_wm<PDE, 0>(plan, A, stream);
+}
+
+}  // namespace dh

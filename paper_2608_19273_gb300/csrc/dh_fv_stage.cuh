@@ -886,10 +886,18 @@ static dh_status launch_wm(dh_plan* plan, const FvArgs& A, cudaStream_t stream) 
   }
 }
 
+}  // namespace dh
+
+#include "dh_fv_any.cuh"
+
+namespace dh {
+
 // W reuse is compiled for the Euler systems only (the systems whose derived
-// quantities cost a reciprocal and a square root per voxel).
+// quantities cost a reciprocal and a square root per voxel).  Plans whose patch sizes are
+// not all multiples of 8 run the generic stage.
 template <class PDE>
 static dh_status fv_launch_pde(dh_plan* plan, const FvArgs& A, int wmode, cudaStream_t stream) {
+  if (plan->fv_generic) return launch_any<PDE>(plan, A, wmode, stream);
   if constexpr (std::is_same<PDE, PdeEuler2>::value || std::is_same<PDE, PdeEuler3>::value) {
     switch (wmode & 3) {
       case 1: return launch_wm<PDE, 1>(plan, A, stream);

@@ -26,6 +26,15 @@ struct DevParams {
   double C[121];  // GW59 coupling matrix, row-major
 };
 
+// One CTA's worth of work of the FV stage for patch sizes that are not multiples of 8: up to
+// eight whole patches of equal p (ng groups, origin 0) or one box of one patch (ng = 1) of
+// bx x by x bz voxels from (x0, y0, z0).
+struct AnyWork {
+  int32_t patch[8];
+  int16_t x0, y0, z0;
+  int8_t bx, by, bz, ng;
+};
+
 // One CTA's worth of FV/FD work: up to 4 groups, each a (TX x TY) column of
 // one patch that the CTA marches through all z-planes of that patch.
 struct Work {
@@ -92,6 +101,11 @@ struct dh_plan {
   // FD tile list (8x8x4 tiles)
   dh::FdWork* d_fdwork = nullptr;
   int n_fdwork = 0;
+  // Patch sizes that are not all multiples of 8: the FV stage runs k_fv_any over d_any (the
+  // FD, MUSCL and coupled-level paths, whose tiles need multiples of 8, refuse such plans).
+  bool fv_generic = false;
+  dh::AnyWork* d_any = nullptr;
+  int n_any = 0;
   // levels for the TMA staging of the FD stage: maximal runs of patches of equal p
   // stored back to back (offset step p^3) whose face neighbours lie in the same run
   bool tma_ok = false;

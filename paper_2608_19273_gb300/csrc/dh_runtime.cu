@@ -214,6 +214,10 @@ static dh_status check_rk(dh_plan* plan, int scheme, int rk, double* q, double* 
   if (acc && (acc == q || acc == u1 || acc == u2)) { set_error("dh_rk_step: acc aliases a state buffer"); return DH_EINVAL; }
   if (plan->pde == DH_PDE_SRHD3D && !mat) { set_error("dh_rk_step: SRHD3D needs the primitive arena as mat"); return DH_EINVAL; }
   if (rk != 1 && rk != 3 && rk != 4) { set_error("dh_rk_step: rk must be 1, 3 or 4"); return DH_EINVAL; }
+  if (plan->fv_generic && scheme != 0) {
+    set_error("dh_rk_step: FD and MUSCL stages need patch sizes that are multiples of 8");
+    return DH_EUNSUPPORTED;
+  }
   return DH_OK;
 }
 

@@ -125,6 +125,16 @@ static int tune_candidates(const dh_plan* plan, int scheme, Cand* cands) {
 template <class Launch>
 static dh_status tune_run(dh_plan* plan, int scheme, const std::string& key, int reps, const char* cache_path,
                           int32_t* choice_out, float* times_out, cudaStream_t s, Launch launch) {
+  if (plan->fv_generic) {
+    // patch sizes that are not all multiples of 8: one FV kernel (no variants); FD and MUSCL
+    // refuse such plans
+    if (scheme != 0) {
+      set_error("dh_autotune: FD and MUSCL stages need patch sizes that are multiples of 8");
+      return DH_EUNSUPPORTED;
+    }
+    if (choice_out) { choice_out[0] = plan->fv_var; choice_out[1] = plan->fv_zs; choice_out[2] = plan->fd_var; choice_out[3] = 0; }
+    return DH_OK;
+  }
   if (!cache_path) cache_path = std::getenv("DH_TUNE_CACHE");  // NULL and unset: no cache
   int v = 0, z = 0, f = 0;
   if (cache_path && cache_lookup(cache_path, key, &v, &z, &f)) {

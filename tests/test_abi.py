@@ -46,7 +46,8 @@ def _create(patches, pde=3, dim=3, halo=1, vs=None):
 
 
 @pytest.mark.parametrize("mutate,code", [
-    (lambda P: P.__setitem__("p", 12), dh.DH_EINVAL),         # not a multiple of 8
+    (lambda P: P.__setitem__("p", 300), dh.DH_EINVAL),        # p outside [2, 256]
+    (lambda P: P.__setitem__("p", 1), dh.DH_EINVAL),          # p outside [2, 256]
     (lambda P: P["nbr"].__setitem__((0, 1), 99), dh.DH_EINVAL),  # neighbour out of range
     (lambda P: P.__setitem__("offset", P["offset"] + 3), dh.DH_EINVAL),  # misaligned block
     (lambda P: P["dx"].__setitem__(0, -1.0), dh.DH_EINVAL),   # negative spacing
@@ -179,3 +180,13 @@ def test_noalloc_rejects_coupled_levels(libdh):
     mesh = synth.coupled_mesh(4, 8, 1.0 / 32, 1, 2, dim=3)
     assert _noalloc(mesh.patches.copy(), mesh.var_stride) == dh.DH_EINVAL
     assert b"neighbour" in dh.lib().dh_last_error()
+
+
+def test_coupled_levels_need_multiples_of_8(libdh):
+    """Patch sizes that are not multiples of 8 run the generic FV stage, which has no coupling of
+    refinement levels: a coupled table of such patches is refused before any device call."""
+    mesh = synth.coupled_mesh(4, 16, 1.0 / 64, 1, 2)
+    P = mesh.patches.copy()
+    P["p"] = 12
+    assert _create(P, vs=mesh.var_stride) == dh.DH_EINVAL
+    assert b"multiples of 8" in dh.lib().dh_last_error()
