@@ -291,6 +291,8 @@ def workload(name, scale=1):
     euler3d_amr2 : 3D Euler on two coupled refinement levels: 8^3 coarse patches of 16^3 (dx 1/128) and
                    the block of coarse lattice [2, 6)^3 refined into 8^3 patches of 16^3 (dx 1/256);
                    FV Rusanov with prolongation, reflux and restriction, SSP-RK3, CFL 0.4.
+    euler3d_p6 : 3D Euler on the paper's typical 6^3 cells: 32 x 32 x 16 patches of 6^3 (dx 1/192,
+                 3,538,944 voxels), FV Rusanov (the generic stage), SSP-RK3, CFL 0.4.
     """
     if name == "euler2d":
         return Workload(name, PDE_EULER2D, SCHEME_FV, euler2d_mesh(), 1, 1, 10, 0.4, 0.0, SEED_BASE + 0)
@@ -301,6 +303,11 @@ def workload(name, scale=1):
         s_ = scale
         return Workload(name, PDE_EULER3D, SCHEME_FV, coupled_mesh(8 // s_, 16, 1.0 / 128, 2 // s_, 4 // s_), 1, 3,
                         20, 0.4, 0.0, SEED_BASE + 6)
+    if name == "euler3d_p6":
+        s_ = scale
+        return Workload(name, PDE_EULER3D, SCHEME_FV, make_mesh([Level((32 // s_, 32 // s_, 16 // s_), 6,
+                                                                       1.0 / 192, 0)], dim=3), 1, 3, 20, 0.4, 0.0,
+                        SEED_BASE + 7)
     if name == "euler3d_muscl":
         return Workload(name, PDE_EULER3D, SCHEME_FV2, euler3d_amr_mesh(scale), 2, 3, 20, 0.4, 0.0,
                         SEED_BASE + 1)

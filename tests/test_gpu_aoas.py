@@ -27,6 +27,13 @@ def mesh_for(case):
         return synth.make_mesh([synth.Level((2, 2, 2), 24, 1.0 / 48, 0)], dim=3)
     if case == "p256_2d":
         return synth.make_mesh([synth.Level((2, 1, 1), 256, 1.0 / 512, 0)], dim=2)
+    if case == "p3_cube":    # patch sizes that are not multiples of 8 (the paper's 3^3 and 6^3 cells)
+        return synth.make_mesh([synth.Level((4, 4, 4), 3, 1.0 / 12, 0)], dim=3)
+    if case == "p6_p13_mix":
+        return synth.make_mesh([synth.Level((3, 3, 3), 6, 1.0 / 18, 0), synth.Level((2, 1, 1), 13, 1.0 / 26, 1)],
+                               dim=3)
+    if case == "p5_2d":
+        return synth.make_mesh([synth.Level((3, 3, 1), 5, 1.0 / 15, 0)], dim=2)
     raise KeyError(case)
 
 
@@ -79,7 +86,9 @@ def run_case(torch, mesh, nq, halo, seed, separate=True):
 
 @pytest.mark.parametrize("case,nq,halo", [("euler3d_s4", 5, 0), ("euler3d_s4", 5, 1), ("gw59_s8", 59, 3),
                                           ("euler2d", 4, 1), ("p8_cube", 256, 2), ("p24_cube", 1, 0),
-                                          ("p24_cube", 10, 1), ("p8_cube", 23, 8), ("p256_2d", 3, 8)])
+                                          ("p24_cube", 10, 1), ("p8_cube", 23, 8), ("p256_2d", 3, 8),
+                                          ("p3_cube", 5, 1), ("p3_cube", 7, 3), ("p6_p13_mix", 5, 1),
+                                          ("p6_p13_mix", 59, 2), ("p5_2d", 4, 1)])
 def test_gather_scatter_bit_exact(case, nq, halo):
     torch = require_cuda()
     run_case(torch, mesh_for(case), nq, halo, seed=2608 + nq + 17 * halo)

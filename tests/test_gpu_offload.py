@@ -55,9 +55,12 @@ def run_offload(torch, plan, mesh, views, nq, halo, n_q, scheme, rk, steps, cfl,
 
 
 @pytest.mark.parametrize("staged", [False, True])
-def test_offload_euler3d_ssprk3(orc, staged):
+@pytest.mark.parametrize("mesh_kind", ["amr_mix", "p6"])
+def test_offload_euler3d_ssprk3(orc, staged, mesh_kind):
     torch = require_cuda()
-    mesh = synth.euler3d_amr_mesh(scale=4)
+    # the AMR mix, or 6^3 patches (the paper's typical cells; the generic FV stage)
+    mesh = (synth.euler3d_amr_mesh(scale=4) if mesh_kind == "amr_mix"
+            else synth.make_mesh([synth.Level((4, 4, 3), 6, 1.0 / 24, 0)], dim=3))
     q = orc.prim2con(3, synth.euler_prims(mesh, 41), mesh.var_stride)
     halo = 1
     blocks = blocks_from_arena(mesh, q, 5, halo, 7)
