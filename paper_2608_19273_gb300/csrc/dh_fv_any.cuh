@@ -11,10 +11,11 @@
 //      stage input, or computed).
 //   2. Per direction d: every cell of a line along d (the box and the two halo layers) forms its
 //      flux F_d and speed lambda_d into shared memory; after a barrier every voxel forms the
-//      Rusanov fluxes of its two d faces (each interior face twice, once from each side: simpler
-//      than a face array, and this path is for small or odd patches) and adds their difference.
+//      Rusanov flux of its -d face (the last voxel of a line also its +d face) into a face array
+//      indexed by the cell on the face's + side; after another barrier every voxel adds the
+//      difference of its two faces.  Every face is formed once.
 //   3. The stage combination, W of the result and lambda of the result as in the marching stage.
-// Shared memory: ANY_SLOTS cells x (N + M quantities, W, F_d, lambda_d).
+// Shared memory: ANY_SLOTS cells x (N + M quantities, W, F_d, lambda_d, the face values of d).
 #pragma once
 
 namespace dh {
@@ -25,7 +26,8 @@ constexpr int ANY_SLOTS = 640;  // box cells (all groups) per CTA
 template <class PDE>
 struct FvAny {
   static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW > 0 ? PDE::NW : 1, DIM = PDE::DIM;
-  static constexpr size_t SMEM = sizeof(double) * (size_t)ANY_SLOTS * (NV + NW + N + 1);
+  static constexpr int NF = PDE::NCP ? 2 : 1;  // face arrays: flux (and non-conservative product)
+  static constexpr size_t SMEM = sizeof(double) * (size_t)ANY_SLOTS * (NV + NW + N + 1 + NF * N);
 
   template <int WM>
   __device__ static void run(const FvArgs& A, const AnyWork& w, double* smem, double& lam_thread) {
@@ -33,6 +35,8 @@ struct FvAny {
     double* Wc = Q + NV * ANY_SLOTS;  // [NW][ANY_SLOTS]
     double* F = Wc + NW * ANY_SLOTS;  // [N][ANY_SLOTS], one direction at a time
     double* L = F + N * ANY_SLOTS;    // [ANY_SLOTS]
+    double* H = L + ANY_SLOTS;        // [N][ANY_SLOTS]: face values, at the cell on the face's + side
+    double* Dn = H + N * ANY_SLOTS;   // [N][ANY_SLOTS]: non-conservative products (NCP systems)
     const DevParams& P = A.P;
     const int bx = w.bx, by = w.by, bz = DIM == 3 ? w.bz : 1, ng = w.ng;
     const int SX = bx + 2, SY = by + 2, SZ = DIM == 3 ? bz + 2 : 1;
@@ -98,41 +102,46 @@ struct FvAny {
         L[s] = PDE::speed(d, q, W, P);
       }
       __syncthreads();
-      if (act) {
+      // every face along d once, spread over the threads: face pos of a line lies between the
+      // cells at pos - 1 and pos (pos = 0 and pos = b_d take a halo cell); stored at the + cell
+      {
         const int st = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
-        const int cm = me - st, cp = me + st;
-        const double sm = max_nn(L[cm], L[me]), sp = max_nn(L[me], L[cp]);
-        double dqm[N], dqp[N];
+        const int bd = d == 0 ? bx : (d == 1 ? by : bz), ba = d == 0 ? by : bx;  // ba: first other axis
+        const int FG = (nvg / bd) * (bd + 1);  // faces per group
+        for (int fi = tid; fi < ng * FG; fi += ANY_NT) {
+          const int gg = fi / FG, r = fi % FG, pos = r % (bd + 1), line = r / (bd + 1);
+          const int a0 = line % ba, a1 = line / ba;  // the two other coordinates, in axis order
+          const int cx = d == 0 ? pos : a0, cy = d == 1 ? pos : (d == 0 ? a0 : a1), cz = d == 2 ? pos : a1;
+          const int cR = gg * SG + ((DIM == 3 ? cz + 1 : 0) * SY + (cy + 1)) * SX + (cx + 1), cLf = cR - st;
+          const double sf = max_nn(L[cLf], L[cR]);
+          double dq[N];
 #pragma unroll
-        for (int v = 0; v < N; ++v) {
-          const double qm = Q[v * ANY_SLOTS + cm], qc = Q[v * ANY_SLOTS + me], qp = Q[v * ANY_SLOTS + cp];
-          dqm[v] = SUB(P, qc, qm);
-          dqp[v] = SUB(P, qp, qc);
-          double hm, hp;
-          if (PDE::FLUX) {
-            hm = fma(-sm, dqm[v], ADD(P, F[v * ANY_SLOTS + cm], F[v * ANY_SLOTS + me]));
-            hp = fma(-sp, dqp[v], ADD(P, F[v * ANY_SLOTS + me], F[v * ANY_SLOTS + cp]));
-          } else {
-            hm = MUL(P, -sm, dqm[v]);
-            hp = MUL(P, -sp, dqp[v]);
+          for (int v = 0; v < N; ++v) {
+            dq[v] = SUB(P, Q[v * ANY_SLOTS + cR], Q[v * ANY_SLOTS + cLf]);
+            H[v * ANY_SLOTS + cR] = PDE::FLUX ? fma(-sf, dq[v], ADD(P, F[v * ANY_SLOTS + cLf], F[v * ANY_SLOTS + cR]))
+                                              : MUL(P, -sf, dq[v]);
           }
-          sum[v] = ADD(P, sum[v], SUB(P, hp, hm));
-        }
-        if (PDE::NCP) {
-          double qbm[NV], qbp[NV], Dm[N], Dp[N];
+          if (PDE::NCP) {
+            double qb[NV], Dv[N];
 #pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const double qc = Q[v * ANY_SLOTS + me];
-            qbm[v] = MUL(P, 0.5, ADD(P, Q[v * ANY_SLOTS + cm], qc));
-            qbp[v] = MUL(P, 0.5, ADD(P, qc, Q[v * ANY_SLOTS + cp]));
+            for (int v = 0; v < NV; ++v) qb[v] = MUL(P, 0.5, ADD(P, Q[v * ANY_SLOTS + cLf], Q[v * ANY_SLOTS + cR]));
+            PDE::ncp(d, qb, dq, P, Dv);
+#pragma unroll
+            for (int v = 0; v < N; ++v) Dn[v * ANY_SLOTS + cR] = Dv[v];
           }
-          PDE::ncp(d, qbm, dqm, P, Dm);
-          PDE::ncp(d, qbp, dqp, P, Dp);
-#pragma unroll
-          for (int v = 0; v < N; ++v) dsum[v] = ADD(P, dsum[v], ADD(P, Dp[v], Dm[v]));
         }
       }
-      __syncthreads();  // the next direction rewrites F and L
+      __syncthreads();
+      if (act) {
+        const int cp = me + (d == 0 ? 1 : (d == 1 ? SX : SX * SY));
+#pragma unroll
+        for (int v = 0; v < N; ++v) {
+          sum[v] = ADD(P, sum[v], SUB(P, H[v * ANY_SLOTS + cp], H[v * ANY_SLOTS + me]));
+          if (PDE::NCP) dsum[v] = ADD(P, dsum[v], ADD(P, Dn[v * ANY_SLOTS + cp], Dn[v * ANY_SLOTS + me]));
+        }
+      }
+      // (the next direction writes F and L first, which no thread reads any more, then -- after a
+      // barrier -- H)
     }
 
     // 3. stage combination, W and lambda of the result
