@@ -23,6 +23,17 @@ namespace dh {
 constexpr int ANY_NT = 256;     // threads per CTA
 constexpr int ANY_SLOTS = 640;  // box cells (all groups) per CTA
 
+// Integer division by a run-time divisor without the integer divide sequence: for
+// 0 <= n < 2^15 and 1 <= d < 2^24, (n + 1/2)/d is never an integer and lies at least 1/(2n + 1)
+// (relative) from one, while (n + 1/2) * fl(1/d) in float errs by at most 2^-23 (relative):
+// truncation gives floor(n/d) exactly.  Every cell, face and group index here is below 2^10.
+struct ADiv {
+  int d;
+  float r;
+  __device__ explicit ADiv(int d_) : d(d_), r(1.0f / (float)d_) {}  // IEEE-rounded quotient
+  __device__ int q(int n) const { return (int)(((float)n + 0.5f) * r); }
+};
+
 template <class PDE>
 struct FvAny {
   static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW > 0 ? PDE::NW : 1, DIM = PDE::DIM;
@@ -42,18 +53,27 @@ struct FvAny {
     const int SX = bx + 2, SY = by + 2, SZ = DIM == 3 ? bz + 2 : 1;
     const int SG = SX * SY * SZ;  // cells per group
     const int nvg = bx * by * bz;  // voxels per group
+    const ADiv dSG(SG), dSX(SX), dSXY(SX * SY);
     const int tid = threadIdx.x;
     const int g = tid / nvg, li = tid % nvg;
     const bool act = g < ng;
     const int lx = li % bx, ly = (li / bx) % by, lz = li / (bx * by);
+    // cell s -> (group, cx, cy, cz), cx in [-1, bx] etc.
+    auto cell = [&](int s, int& gg, int& cx, int& cy, int& cz) {
+      gg = dSG.q(s);
+      const int r = s - gg * SG, rz = DIM == 3 ? dSXY.q(r) : 0, rxy = r - rz * SX * SY, ry = dSX.q(rxy);
+      cx = rxy - ry * SX - 1;
+      cy = ry - 1;
+      cz = DIM == 3 ? rz - 1 : 0;
+    };
     const int p = A.patches[w.patch[0]].p;  // every group of an item has the same p
     const double dt = *A.dt_dev;             // read before the lambda epilogue may rewrite it
     const double gdt = A.g * dt, ddt = A.d * dt;
 
     // 1. the box and its face halo, with W
     for (int s = tid; s < ng * SG; s += ANY_NT) {
-      const int gg = s / SG, r = s % SG;
-      const int cx = r % SX - 1, cy = (r / SX) % SY - 1, cz = DIM == 3 ? r / (SX * SY) - 1 : 0;
+      int gg, cx, cy, cz;
+      cell(s, gg, cx, cy, cz);
       const int outside = (cx < 0 || cx >= bx) + (cy < 0 || cy >= by) + (DIM == 3 && (cz < 0 || cz >= bz));
       if (outside > 1) continue;
       const int k = w.patch[gg];
@@ -84,8 +104,8 @@ struct FvAny {
 #pragma unroll 1
     for (int d = 0; d < DIM; ++d) {
       for (int s = tid; s < ng * SG; s += ANY_NT) {
-        const int r = s % SG;
-        const int cx = r % SX - 1, cy = (r / SX) % SY - 1, cz = DIM == 3 ? r / (SX * SY) - 1 : 0;
+        int gg, cx, cy, cz;
+        cell(s, gg, cx, cy, cz);
         const bool inx = cx >= 0 && cx < bx, iny = cy >= 0 && cy < by, inz = DIM == 2 || (cz >= 0 && cz < bz);
         const bool line = d == 0 ? (iny && inz) : (d == 1 ? (inx && inz) : (inx && iny));
         if (!line) continue;
@@ -108,9 +128,10 @@ struct FvAny {
         const int st = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
         const int bd = d == 0 ? bx : (d == 1 ? by : bz), ba = d == 0 ? by : bx;  // ba: first other axis
         const int FG = (nvg / bd) * (bd + 1);  // faces per group
+        const ADiv dFG(FG), dB1(bd + 1), dBa(ba);
         for (int fi = tid; fi < ng * FG; fi += ANY_NT) {
-          const int gg = fi / FG, r = fi % FG, pos = r % (bd + 1), line = r / (bd + 1);
-          const int a0 = line % ba, a1 = line / ba;  // the two other coordinates, in axis order
+          const int gg = dFG.q(fi), r = fi - gg * FG, line = dB1.q(r), pos = r - line * (bd + 1);
+          const int a1 = dBa.q(line), a0 = line - a1 * ba;  // the two other coordinates, in axis order
           const int cx = d == 0 ? pos : a0, cy = d == 1 ? pos : (d == 0 ? a0 : a1), cz = d == 2 ? pos : a1;
           const int cR = gg * SG + ((DIM == 3 ? cz + 1 : 0) * SY + (cy + 1)) * SX + (cx + 1), cLf = cR - st;
           const double sf = max_nn(L[cLf], L[cR]);
