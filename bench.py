@@ -68,6 +68,10 @@ WORKLOADS = {
                        desc="3D Euler on the paper's typical 6^3 cells: 32x32x16 patches of 6^3 (16,384 cells of "
                             "216 voxels), FV Rusanov through the generic stage (whole patches packed to a CTA), "
                             "SSP-RK3; halo 1"),
+    "euler3d_p3": dict(pde=3, scheme=0, rk=3, inner=20, cfl=0.4, flops="fv/euler3d/ssprk3_step", bytes=320,
+                       kernel="k_fv_any<Euler3D>",
+                       desc="3D Euler on 3^3 cells: 64x64x32 patches of 3^3 (131,072 cells of 27 voxels), FV "
+                            "Rusanov through the generic stage, SSP-RK3; halo 1"),
     "euler2d": dict(pde=2, scheme=0, rk=1, inner=10, cfl=0.4, flops="fv/euler2d/fe_step", bytes=128,
                     kernel="k_fv_stage<Euler2D>",
                     desc="2D Euler (4 vars), FV Rusanov, forward Euler; 64 patches of 16^2, halo 1"),
@@ -117,6 +121,7 @@ KERNEL_SOURCES = {
     "euler3d_amr2": _FV + ["dh_fv_euler3.cu", "dh_fv_euler3_tma.cu", "dh_amr.cu"],
     "euler3d_muscl": ["dh_fv2.cu"], "srhd3d": _FV + ["dh_fv_srhd.cu"],
     "euler3d_p6": _FV + ["dh_fv_euler3.cu", "dh_fv_any.cuh"],
+    "euler3d_p3": _FV + ["dh_fv_euler3.cu", "dh_fv_any.cuh"],
     "wave3d": ["dh_fd.cu"], "gw59": ["dh_fd.cu"],
 }
 
@@ -195,7 +200,7 @@ def workload_config(name, w, mesh, inner=None):
 def host_inputs(name, w):
     """(prim or cons on host, material on host or None, kind) of the workload."""
     mesh = w.mesh
-    if name in ("euler3d", "euler2d", "euler3d_muscl", "euler3d_p6"):
+    if name in ("euler3d", "euler2d", "euler3d_muscl", "euler3d_p6", "euler3d_p3"):
         return synth.euler_prims(mesh, w.seed), None, "prim"
     if name == "euler3d_amr2":
         return synth.euler_prims_coupled(mesh, w.seed), None, "prim"
@@ -305,7 +310,7 @@ def oracle_sample(name, budget_s):
     import oracle
     cores = oracle.num_threads(0)
     scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
-             "gw59": 4, "euler3d_p6": 1}[name]
+             "gw59": 4, "euler3d_p6": 1, "euler3d_p3": 1}[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)
@@ -343,7 +348,7 @@ def reference_arm(args, rank, world):
     # the host's cores
     cores = oracle.num_threads(len(os.sched_getaffinity(0)) if world > 1 else 0)
     scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
-             "gw59": 4, "euler3d_p6": 1}[name]
+             "gw59": 4, "euler3d_p6": 1, "euler3d_p3": 1}[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)

@@ -205,12 +205,25 @@ __global__ void k_check_recip(const double* x, double* y_nr, double* y_div, int6
 
 static inline int pt_nbr(const dh_patch* patches, int k, int f) { return patches[k].nbr[f]; }
 
-// Work list of the generic FV stage (k_fv_any; see dh_fv_any.cuh): patches of equal p and dx
-// packed whole, up to eight to a CTA, where a patch fits (at most 256 voxels, and the groups'
-// boxes with their face halo at most 640 cells); boxes of 8x8x4 (3D) or 16x16 (2D) voxels of
-// larger patches otherwise.  Largest work first.
+// Work list of the generic FV stage (k_fv_any; see dh_fv_any.cuh).  An item's shape: ng groups
+// of bx x by x bz voxels; its limits: at most 256 voxels, 512 box cells with the face halo, 320
+// line cells and 256 faces of one direction.
+static bool any_fits(int bx, int by, int bz, int ng, int dim) {
+  const int ez = dim == 3 ? 2 : 0;
+  if (ng < 1 || ng > 8 || bx < 1 || by < 1 || bz < 1 || (dim == 2 && bz != 1)) return false;
+  if (ng * bx * by * bz > 256 || ng * (bx + 2) * (by + 2) * (bz + ez) > 512) return false;
+  for (int d = 0; d < dim; ++d) {
+    const int lines = (bx + 2 * (d == 0)) * (by + 2 * (d == 1)) * (bz + 2 * (d == 2));
+    const int faces = (bx + (d == 0)) * (by + (d == 1)) * (bz + (d == 2));
+    if (ng * lines > 320 || ng * faces > 256) return false;
+  }
+  return true;
+}
+
+// Patches of equal p and dx packed whole, up to eight to an item, where that fits; 2x2x2 blocks of
+// face-adjacent 3^3 patches as one 6^3 box; boxes of the larger patches otherwise, of the tile
+// shape that needs the fewest boxes.  Largest work first.
 static std::vector<AnyWork> any_work(const dh_patch* patches, int K, int dim) {
-  constexpr int NT = 256, SLOTS = 640;
   std::vector<AnyWork> out;
   std::vector<int> order(K);
   for (int k = 0; k < K; ++k) order[k] = k;
@@ -222,12 +235,38 @@ static std::vector<AnyWork> any_work(const dh_patch* patches, int K, int dim) {
     for (int i = 0; i < 8; ++i) w.patch[i] = -1;
     return w;
   };
+  // 3D patches of 3^3: 2x2x2 blocks of face-adjacent patches form one 6^3 box (216 voxels, 512
+  // cells), so that the halos between the block's members are ordinary box cells
+  std::vector<char> used(K, 0);
+  if (dim == 3) {
+    for (int a = 0; a < K; ++a) {
+      if (used[a] || patches[a].p != 3) continue;
+      const int b = patches[a].nbr[1], c = patches[a].nbr[3], e = patches[a].nbr[5];
+      const int d = patches[c].nbr[1], f = patches[e].nbr[1], g = patches[e].nbr[3], h = patches[g].nbr[1];
+      const int m[8] = {a, b, c, d, e, f, g, h};
+      // every member distinct, unused, 3^3 at a's dx, and linked both ways to its three partners
+      bool ok = true;
+      for (int x = 0; x < 8 && ok; ++x) {
+        ok = !used[m[x]] && patches[m[x]].p == 3 && patches[m[x]].dx == patches[a].dx;
+        for (int y = 0; y < x && ok; ++y) ok = m[x] != m[y];
+        for (int ax = 0; ax < 3 && ok; ++ax) ok = patches[m[x]].nbr[2 * ax + !((x >> ax) & 1)] == m[x ^ (1 << ax)];
+      }
+      if (!ok) continue;
+      AnyWork w = blank();
+      for (int x = 0; x < 8; ++x) { w.patch[x] = m[x]; used[m[x]] = 1; }
+      w.bx = 6; w.by = 6; w.bz = 6; w.ng = 1; w.mp = 3;
+      out.push_back(w);
+    }
+  }
+  order.erase(std::remove_if(order.begin(), order.end(), [&](int k) { return used[k] != 0; }), order.end());
+  static const int tiles3[][3] = {{6, 6, 6}, {8, 8, 3}, {7, 7, 4}, {8, 6, 4}, {6, 8, 4}};
+  static const int tiles2[][3] = {{16, 15, 1}, {15, 16, 1}, {16, 8, 1}, {8, 16, 1}};
   size_t i = 0;
   while (i < order.size()) {
     const int k = order[i], p = patches[k].p;
     const int pz = dim == 3 ? p : 1;
-    const int nvox = p * p * pz, cells = (p + 2) * (p + 2) * (dim == 3 ? p + 2 : 1);
-    const int G = std::min({8, NT / nvox, SLOTS / cells});
+    int G = 8;
+    while (G >= 1 && !any_fits(p, p, pz, G, dim)) --G;
     if (G >= 1) {
       AnyWork w = blank();
       w.bx = (int8_t)p; w.by = (int8_t)p; w.bz = (int8_t)pz;
@@ -238,7 +277,16 @@ static std::vector<AnyWork> any_work(const dh_patch* patches, int K, int dim) {
       out.push_back(w);
       continue;
     }
-    const int tx = dim == 3 ? 8 : 16, ty = tx, tz = dim == 3 ? 4 : 1;
+    const int(*tl)[3] = dim == 3 ? tiles3 : tiles2;
+    const int nt = dim == 3 ? 5 : 4;
+    int best = 0;
+    long best_n = -1;
+    for (int t = 0; t < nt; ++t) {
+      const long n = (long)((p + tl[t][0] - 1) / tl[t][0]) * ((p + tl[t][1] - 1) / tl[t][1]) *
+                     ((pz + tl[t][2] - 1) / tl[t][2]);
+      if (best_n < 0 || n < best_n) { best_n = n; best = t; }
+    }
+    const int tx = tl[best][0], ty = tl[best][1], tz = tl[best][2];
     for (int z0 = 0; z0 < pz; z0 += tz)
       for (int y0 = 0; y0 < p; y0 += ty)
         for (int x0 = 0; x0 < p; x0 += tx) {
@@ -424,12 +472,19 @@ dh_status dh_plan_create(dh_plan** out, int32_t pde, int32_t dim, const dh_patch
   }
   plan->n_fdwork = (int)fdw.size();
 
-  // Generic FV work (patch sizes not all multiples of 8): whole patches packed up to eight to a
-  // CTA where a patch and its face halo fit (p^3 <= 256 voxels and (p+2)^3 cells in 3D), else
-  // boxes of 8x8x4 (3D) or 16x16 (2D) voxels, smaller at a patch's upper ends.
+  // Generic FV work (patch sizes not all multiples of 8): every item within the kernel's shared-
+  // memory limits, checked here once more since the kernel indexes its arrays without checks.
   std::vector<AnyWork> anyw;
   plan->fv_generic = generic;
-  if (generic) anyw = any_work(patches, K, dim);
+  if (generic) {
+    anyw = any_work(patches, K, dim);
+    for (const AnyWork& w : anyw)
+      if (!any_fits(w.bx, w.by, w.bz, w.ng, dim)) {
+        set_error("generic FV work item %dx%dx%d x %d exceeds the kernel's limits", w.bx, w.by, w.bz, w.ng);
+        delete plan;
+        return DH_EINVAL;
+      }
+  }
   plan->n_any = (int)anyw.size();
 
   // Levels for TMA staging (see dh_internal.cuh).

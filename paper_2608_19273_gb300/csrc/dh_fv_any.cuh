@@ -4,24 +4,29 @@
 // epilogue), in a simpler tiling that fits any p.
 //
 // A CTA of 256 threads takes one work item: up to eight whole small patches of equal p (each
-// patch a group, p^3 <= 256 voxels in 3D, p^2 <= 256 in 2D) or one box of one larger patch
-// (8x8x4 voxels in 3D, 16x16 in 2D, smaller at the patch's upper ends).  One voxel per thread.
+// patch a group), a 2x2x2 block of face-adjacent 3^3 patches as one 6^3 box, or one box of a
+// larger patch (6x6x6, 7x7x4 or 8x8x3 voxels in 3D, 16x15 or 15x16 in 2D, smaller at the patch's
+// upper ends).  One voxel per thread.  Every item keeps within the limits below (checked on the
+// host when the plan is made).
 //   1. Every cell of the box and its one-voxel face halo (edges and corners are never read) is
 //      loaded into shared memory with its derived quantities W (read from the W arena of the
 //      stage input, or computed).
-//   2. Per direction d: every cell of a line along d (the box and the two halo layers) forms its
-//      flux F_d and speed lambda_d into shared memory; after a barrier every voxel forms the
-//      Rusanov flux of its -d face (the last voxel of a line also its +d face) into a face array
-//      indexed by the cell on the face's + side; after another barrier every voxel adds the
-//      difference of its two faces.  Every face is formed once.
+//   2. Per direction d: every line cell of d (the box and its two halo layers across d) forms
+//      its flux F_d and speed lambda_d into the line arrays; after a barrier every face along d
+//      is formed once (one per thread) into the face arrays; after another barrier every voxel
+//      adds the difference of its two faces.
 //   3. The stage combination, W of the result and lambda of the result as in the marching stage.
-// Shared memory: ANY_SLOTS cells x (N + M quantities, W, F_d, lambda_d, the face values of d).
+// Shared memory: box cells x (N + M quantities, W), line cells x (F_d, lambda_d), faces x (the
+// face values, and the non-conservative products of NCP systems); 70.7 KB for the Euler
+// equations in 3D, three CTAs per SM.
 #pragma once
 
 namespace dh {
 
-constexpr int ANY_NT = 256;     // threads per CTA
-constexpr int ANY_SLOTS = 640;  // box cells (all groups) per CTA
+constexpr int ANY_NT = 256;      // threads per CTA; voxels per item at most
+constexpr int ANY_SLOTS = 512;   // box cells with halo (all groups) per item
+constexpr int ANY_LINES = 320;   // line cells of one direction per item
+constexpr int ANY_FACES = 256;   // faces of one direction per item (one per thread)
 
 // Integer division by a run-time divisor without the integer divide sequence: for
 // 0 <= n < 2^15 and 1 <= d < 2^24, (n + 1/2)/d is never an integer and lies at least 1/(2n + 1)
@@ -38,16 +43,17 @@ template <class PDE>
 struct FvAny {
   static constexpr int N = PDE::N, NV = PDE::N + PDE::M, NW = PDE::NW > 0 ? PDE::NW : 1, DIM = PDE::DIM;
   static constexpr int NF = PDE::NCP ? 2 : 1;  // face arrays: flux (and non-conservative product)
-  static constexpr size_t SMEM = sizeof(double) * (size_t)ANY_SLOTS * (NV + NW + N + 1 + NF * N);
+  static constexpr size_t SMEM =
+      sizeof(double) * ((size_t)ANY_SLOTS * (NV + NW) + (size_t)ANY_LINES * (N + 1) + (size_t)ANY_FACES * NF * N);
 
   template <int WM>
   __device__ static void run(const FvArgs& A, const AnyWork& w, double* smem, double& lam_thread) {
-    double* Q = smem;                 // [NV][ANY_SLOTS]
+    double* Q = smem;                 // [NV][ANY_SLOTS]: box cells
     double* Wc = Q + NV * ANY_SLOTS;  // [NW][ANY_SLOTS]
-    double* F = Wc + NW * ANY_SLOTS;  // [N][ANY_SLOTS], one direction at a time
-    double* L = F + N * ANY_SLOTS;    // [ANY_SLOTS]
-    double* H = L + ANY_SLOTS;        // [N][ANY_SLOTS]: face values, at the cell on the face's + side
-    double* Dn = H + N * ANY_SLOTS;   // [N][ANY_SLOTS]: non-conservative products (NCP systems)
+    double* F = Wc + NW * ANY_SLOTS;  // [N][ANY_LINES]: line cells of one direction
+    double* L = F + N * ANY_LINES;    // [ANY_LINES]
+    double* H = L + ANY_LINES;        // [N][ANY_FACES]: face values of one direction
+    double* Dn = H + N * ANY_FACES;   // [N][ANY_FACES]: non-conservative products (NCP systems)
     const DevParams& P = A.P;
     const int bx = w.bx, by = w.by, bz = DIM == 3 ? w.bz : 1, ng = w.ng;
     const int SX = bx + 2, SY = by + 2, SZ = DIM == 3 ? bz + 2 : 1;
@@ -66,7 +72,7 @@ struct FvAny {
       cy = ry - 1;
       cz = DIM == 3 ? rz - 1 : 0;
     };
-    const int p = A.patches[w.patch[0]].p;  // every group of an item has the same p
+    const int p = A.patches[w.patch[0]].p;  // every group or block member of an item has the same p
     const double dt = *A.dt_dev;             // read before the lambda epilogue may rewrite it
     const double gdt = A.g * dt, ddt = A.d * dt;
 
@@ -76,8 +82,16 @@ struct FvAny {
       cell(s, gg, cx, cy, cz);
       const int outside = (cx < 0 || cx >= bx) + (cy < 0 || cy >= by) + (DIM == 3 && (cz < 0 || cz >= bz));
       if (outside > 1) continue;
-      const int k = w.patch[gg];
-      const int64_t e = vox_index(A.patches, nullptr, k, p, w.x0 + cx, w.y0 + cy, DIM == 3 ? w.z0 + cz : 0);
+      int64_t e;
+      if (w.mp > 0) {
+        // a 2x2x2 block of mp^3 patches: the member holding the cell, and the cell's
+        // coordinates in it (at most one outside [0, mp): a face neighbour of that member)
+        const int mx = cx >= w.mp, my = cy >= w.mp, mz = cz >= w.mp;
+        e = vox_index(A.patches, nullptr, __ldg(w.patch + mx + 2 * my + 4 * mz), w.mp, cx - mx * w.mp,
+                      cy - my * w.mp, cz - mz * w.mp);
+      } else {
+        e = vox_index(A.patches, nullptr, __ldg(w.patch + gg), p, w.x0 + cx, w.y0 + cy, DIM == 3 ? w.z0 + cz : 0);
+      }
       double q[NV], W[NW];
 #pragma unroll
       for (int v = 0; v < N; ++v) q[v] = __ldg(A.qs + v * A.vs + e);
@@ -103,13 +117,15 @@ struct FvAny {
     for (int v = 0; v < N; ++v) { sum[v] = 0.0; dsum[v] = 0.0; }
 #pragma unroll 1
     for (int d = 0; d < DIM; ++d) {
-      for (int s = tid; s < ng * SG; s += ANY_NT) {
-        int gg, cx, cy, cz;
-        cell(s, gg, cx, cy, cz);
-        const bool inx = cx >= 0 && cx < bx, iny = cy >= 0 && cy < by, inz = DIM == 2 || (cz >= 0 && cz < bz);
-        const bool line = d == 0 ? (iny && inz) : (d == 1 ? (inx && inz) : (inx && iny));
-        if (!line) continue;
-        double q[NV], W[NW], Fd[N];
+      // the line cells of d (the box and its two halo layers across d) of every group, x fastest
+      const int LX = bx + 2 * (d == 0), LY = by + 2 * (d == 1), LZ = DIM == 3 ? bz + 2 * (d == 2) : 1;
+      const int LG = LX * LY * LZ;
+      const ADiv dLG(LG), dLX(LX), dLY(LY);
+      for (int j = tid; j < ng * LG; j += ANY_NT) {
+        const int gg = dLG.q(j), r = j - gg * LG, t = dLX.q(r), hi = dLY.q(t);
+        const int cx = r - t * LX - (d == 0), cy = t - hi * LY - (d == 1), cz = hi - (d == 2);
+        const int s = gg * SG + ((DIM == 3 ? cz + 1 : 0) * SY + (cy + 1)) * SX + (cx + 1);
+        double q[NV], W[NW], Fd[N];  // line arrays at j
 #pragma unroll
         for (int v = 0; v < NV; ++v) q[v] = Q[v * ANY_SLOTS + s];
 #pragma unroll
@@ -117,29 +133,34 @@ struct FvAny {
         if (PDE::FLUX) {
           PDE::flux(d, q, W, P, Fd);
 #pragma unroll
-          for (int v = 0; v < N; ++v) F[v * ANY_SLOTS + s] = Fd[v];
+          for (int v = 0; v < N; ++v) F[v * ANY_LINES + j] = Fd[v];
         }
-        L[s] = PDE::speed(d, q, W, P);
+        L[j] = PDE::speed(d, q, W, P);
       }
       __syncthreads();
-      // every face along d once, spread over the threads: face pos of a line lies between the
-      // cells at pos - 1 and pos (pos = 0 and pos = b_d take a halo cell); stored at the + cell
+      // every face along d once, one per thread, in x-fastest order (consecutive threads touch
+      // consecutive cells: no shared-memory bank conflicts in any direction).  The face grid is
+      // the voxel grid with one more layer along d: the face at c_d = pos lies between the cells
+      // at pos - 1 and pos (pos = 0 and pos = b_d take a halo cell).
+      const int FX = bx + (d == 0), FY = by + (d == 1), FZ = DIM == 3 ? bz + (d == 2) : 1;
+      const int FG = FX * FY * FZ;  // faces per group
       {
-        const int st = d == 0 ? 1 : (d == 1 ? SX : SX * SY);
-        const int bd = d == 0 ? bx : (d == 1 ? by : bz), ba = d == 0 ? by : bx;  // ba: first other axis
-        const int FG = (nvg / bd) * (bd + 1);  // faces per group
-        const ADiv dFG(FG), dB1(bd + 1), dBa(ba);
-        for (int fi = tid; fi < ng * FG; fi += ANY_NT) {
-          const int gg = dFG.q(fi), r = fi - gg * FG, line = dB1.q(r), pos = r - line * (bd + 1);
-          const int a1 = dBa.q(line), a0 = line - a1 * ba;  // the two other coordinates, in axis order
-          const int cx = d == 0 ? pos : a0, cy = d == 1 ? pos : (d == 0 ? a0 : a1), cz = d == 2 ? pos : a1;
+        const int st = d == 0 ? 1 : (d == 1 ? SX : SX * SY), lst = d == 0 ? 1 : (d == 1 ? LX : LX * LY);
+        const ADiv dFG(FG), dFX(FX), dFY(FY);
+        const int fi = tid;
+        if (fi < ng * FG) {
+          const int gg = dFG.q(fi), r = fi - gg * FG, t = dFX.q(r), cz = dFY.q(t);
+          const int cx = r - t * FX, cy = t - cz * FY;
           const int cR = gg * SG + ((DIM == 3 ? cz + 1 : 0) * SY + (cy + 1)) * SX + (cx + 1), cLf = cR - st;
-          const double sf = max_nn(L[cLf], L[cR]);
+          // the same two cells in the line arrays (line coordinates are shifted by one along d)
+          const int jR = gg * LG + ((DIM == 3 ? cz + (d == 2) : 0) * LY + (cy + (d == 1))) * LX + (cx + (d == 0));
+          const int jL = jR - lst;
+          const double sf = max_nn(L[jL], L[jR]);
           double dq[N];
 #pragma unroll
           for (int v = 0; v < N; ++v) {
             dq[v] = SUB(P, Q[v * ANY_SLOTS + cR], Q[v * ANY_SLOTS + cLf]);
-            H[v * ANY_SLOTS + cR] = PDE::FLUX ? fma(-sf, dq[v], ADD(P, F[v * ANY_SLOTS + cLf], F[v * ANY_SLOTS + cR]))
+            H[v * ANY_FACES + fi] = PDE::FLUX ? fma(-sf, dq[v], ADD(P, F[v * ANY_LINES + jL], F[v * ANY_LINES + jR]))
                                               : MUL(P, -sf, dq[v]);
           }
           if (PDE::NCP) {
@@ -148,17 +169,19 @@ struct FvAny {
             for (int v = 0; v < NV; ++v) qb[v] = MUL(P, 0.5, ADD(P, Q[v * ANY_SLOTS + cLf], Q[v * ANY_SLOTS + cR]));
             PDE::ncp(d, qb, dq, P, Dv);
 #pragma unroll
-            for (int v = 0; v < N; ++v) Dn[v * ANY_SLOTS + cR] = Dv[v];
+            for (int v = 0; v < N; ++v) Dn[v * ANY_FACES + fi] = Dv[v];
           }
         }
       }
       __syncthreads();
       if (act) {
-        const int cp = me + (d == 0 ? 1 : (d == 1 ? SX : SX * SY));
+        // this voxel's two faces along d: face coordinates pos = l_d and l_d + 1
+        const int fm = g * FG + ((DIM == 3 ? lz : 0) * FY + ly) * FX + lx;
+        const int fp = fm + (d == 0 ? 1 : (d == 1 ? FX : FX * FY));
 #pragma unroll
         for (int v = 0; v < N; ++v) {
-          sum[v] = ADD(P, sum[v], SUB(P, H[v * ANY_SLOTS + cp], H[v * ANY_SLOTS + me]));
-          if (PDE::NCP) dsum[v] = ADD(P, dsum[v], ADD(P, Dn[v * ANY_SLOTS + cp], Dn[v * ANY_SLOTS + me]));
+          sum[v] = ADD(P, sum[v], SUB(P, H[v * ANY_FACES + fp], H[v * ANY_FACES + fm]));
+          if (PDE::NCP) dsum[v] = ADD(P, dsum[v], ADD(P, Dn[v * ANY_FACES + fp], Dn[v * ANY_FACES + fm]));
         }
       }
       // (the next direction writes F and L first, which no thread reads any more, then -- after a
@@ -167,12 +190,20 @@ struct FvAny {
 
     // 3. stage combination, W and lambda of the result
     if (!act) return;
-    const int k = w.patch[g];
+    int k, x, y, z;
+    if (w.mp > 0) {
+      const int mx = lx >= w.mp, my = ly >= w.mp, mz = lz >= w.mp;
+      k = __ldg(w.patch + mx + 2 * my + 4 * mz);
+      x = lx - mx * w.mp; y = ly - my * w.mp; z = lz - mz * w.mp;
+    } else {
+      k = __ldg(w.patch + g);
+      x = w.x0 + lx; y = w.y0 + ly; z = DIM == 3 ? w.z0 + lz : 0;
+    }
     const double cL = -0.5 / A.patches[k].dx;  // faces hold twice the flux
     const double cS = gdt * cL, cA = ddt * cL;
     const bool b1 = A.b == 1.0;
-    const int x = w.x0 + lx, y = w.y0 + ly, z = DIM == 3 ? w.z0 + lz : 0;
-    const int64_t e = A.patches[k].offset + ((int64_t)z * p + y) * p + x;
+    const int pk = w.mp > 0 ? w.mp : p;
+    const int64_t e = A.patches[k].offset + ((int64_t)z * pk + y) * pk + x;
     double Qk[NV], Sv[N], res[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Qk[v] = Q[v * ANY_SLOTS + me];
@@ -233,7 +264,7 @@ struct FvAny {
 
 template <class PDE, int WM>
 __global__ void __launch_bounds__(ANY_NT) k_fv_any(const __grid_constant__ FvArgs A, const AnyWork* __restrict__ work) {
-  extern __shared__ __align__(16) double smem[];
+  extern __shared__ __align__(128) double smem[];
   double lam = 0.0;
   FvAny<PDE>::template run<WM>(A, work[blockIdx.x], smem, lam);
   if (A.lam_out) publish_lambda(lam, A.lam_out, A.red, A.dt_next, A.cfl, A.dx_dim);

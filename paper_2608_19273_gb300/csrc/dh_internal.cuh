@@ -27,12 +27,14 @@ struct DevParams {
 };
 
 // One CTA's worth of work of the FV stage for patch sizes that are not multiples of 8: up to
-// eight whole patches of equal p (ng groups, origin 0) or one box of one patch (ng = 1) of
-// bx x by x bz voxels from (x0, y0, z0).
+// eight whole patches of equal p (ng groups, origin 0), one box of one patch (ng = 1) of
+// bx x by x bz voxels from (x0, y0, z0), or (mp > 0) one box made of a 2x2x2 block of face-
+// adjacent patches of mp^3 voxels (patch[mx + 2 my + 4 mz] holds block member (mx, my, mz)).
 struct AnyWork {
   int32_t patch[8];
   int16_t x0, y0, z0;
   int8_t bx, by, bz, ng;
+  int8_t mp;
 };
 
 // One CTA's worth of FV/FD work: up to 4 groups, each a (TX x TY) column of

@@ -293,6 +293,7 @@ def workload(name, scale=1):
                    FV Rusanov with prolongation, reflux and restriction, SSP-RK3, CFL 0.4.
     euler3d_p6 : 3D Euler on the paper's typical 6^3 cells: 32 x 32 x 16 patches of 6^3 (dx 1/192,
                  3,538,944 voxels), FV Rusanov (the generic stage), SSP-RK3, CFL 0.4.
+    euler3d_p3 : the same box in 3^3 cells: 64 x 64 x 32 patches of 3^3 (131,072 patches).
     """
     if name == "euler2d":
         return Workload(name, PDE_EULER2D, SCHEME_FV, euler2d_mesh(), 1, 1, 10, 0.4, 0.0, SEED_BASE + 0)
@@ -308,6 +309,11 @@ def workload(name, scale=1):
         return Workload(name, PDE_EULER3D, SCHEME_FV, make_mesh([Level((32 // s_, 32 // s_, 16 // s_), 6,
                                                                        1.0 / 192, 0)], dim=3), 1, 3, 20, 0.4, 0.0,
                         SEED_BASE + 7)
+    if name == "euler3d_p3":
+        s_ = scale
+        return Workload(name, PDE_EULER3D, SCHEME_FV, make_mesh([Level((64 // s_, 64 // s_, 32 // s_), 3,
+                                                                       1.0 / 192, 0)], dim=3), 1, 3, 20, 0.4, 0.0,
+                        SEED_BASE + 8)
     if name == "euler3d_muscl":
         return Workload(name, PDE_EULER3D, SCHEME_FV2, euler3d_amr_mesh(scale), 2, 3, 20, 0.4, 0.0,
                         SEED_BASE + 1)
