@@ -66,12 +66,13 @@ WORKLOADS = {
     "euler3d_p6": dict(pde=3, scheme=0, rk=3, inner=20, cfl=0.4, flops="fv/euler3d/ssprk3_step", bytes=320,
                        kernel="k_fv_any<Euler3D>",
                        desc="3D Euler on the paper's typical 6^3 cells: 32x32x16 patches of 6^3 (16,384 cells of "
-                            "216 voxels), FV Rusanov through the generic stage (whole patches packed to a CTA), "
+                            "216 voxels), FV Rusanov through the generic stage (one patch per CTA), "
                             "SSP-RK3; halo 1"),
     "euler3d_p3": dict(pde=3, scheme=0, rk=3, inner=20, cfl=0.4, flops="fv/euler3d/ssprk3_step", bytes=320,
                        kernel="k_fv_any<Euler3D>",
-                       desc="3D Euler on 3^3 cells: 64x64x32 patches of 3^3 (131,072 cells of 27 voxels), FV "
-                            "Rusanov through the generic stage, SSP-RK3; halo 1"),
+                       desc="3D Euler on the paper's typical 3^3 cells: 64x64x32 patches of 3^3 (131,072 cells of 27 "
+                            "voxels), FV Rusanov through the generic stage (2x2x2 blocks of patches as one 6^3 box "
+                            "per CTA), SSP-RK3; halo 1"),
     "euler2d": dict(pde=2, scheme=0, rk=1, inner=10, cfl=0.4, flops="fv/euler2d/fe_step", bytes=128,
                     kernel="k_fv_stage<Euler2D>",
                     desc="2D Euler (4 vars), FV Rusanov, forward Euler; 64 patches of 16^2, halo 1"),
@@ -660,6 +661,8 @@ CONFIGS = {
     "euler3d_muscl": dict(label="C2, second order (MUSCL-minmod)", inner=10, warmup=3, steps=3),
     "euler3d_amr2": dict(label="C2-like, two coupled refinement levels", inner=20, warmup=3, steps=3),
     "euler3d_p6": dict(label="the paper's typical 6^3 cells (generic FV stage)", inner=20, warmup=3, steps=3),
+    "euler3d_p3": dict(label="the paper's typical 3^3 cells (generic FV stage, 2x2x2 blocks of patches)", inner=20,
+                       warmup=3, steps=3),
 }
 
 

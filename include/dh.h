@@ -105,9 +105,9 @@ typedef struct dh_plan dh_plan;
  * Patch sizes: 2 <= p <= 256.  Plans whose sizes are all multiples of 8 run
  * every stage kernel; other plans (the paper's typical 3^3 and 6^3 cells,
  * Sec. IV) run the first-order FV stage (patch_update_fv, dh_rk_step and the
- * graphs with scheme 0) through a generic kernel -- whole small patches packed
- * up to eight to a CTA, boxes of 8x8x4 (2D: 16x16) voxels of larger ones --
- * and refuse the FD4, MUSCL and coupled-level paths (DH_EUNSUPPORTED, or
+ * graphs with scheme 0) through a generic kernel -- 2x2x2 blocks of
+ * face-adjacent 3^3 patches as one 6^3 box, other small patches whole (up to
+ * eight to a CTA), boxes of at most 256 voxels of larger ones -- and refuse the FD4, MUSCL and coupled-level paths (DH_EUNSUPPORTED, or
  * DH_EINVAL at plan creation for coupled tables); the autotuner has nothing to
  * choose for them.  A face neighbour has the
  * same p, dx and level, or -- coupled refinement levels -- is one level

@@ -1,7 +1,7 @@
 """GPU parity of the first-order FV stage on plans whose patch sizes are not multiples of 8 (the
-generic kernel: whole small patches packed up to eight to a CTA, boxes of larger ones with ragged
-ends) against the FP64 oracle: the paper's typical 3^3 and 6^3 cells, sizes that leave partial
-boxes (12, 20), 2D, the advection forms with a material field, SRHD, mixed sizes, whole SSP-RK3
+generic kernel: 2x2x2 blocks of 3^3 patches as 6^3 boxes, other small patches whole, boxes of
+larger ones with ragged ends) against the FP64 oracle: the paper's typical 3^3 and 6^3 cells,
+sizes that leave partial boxes (7, 12, 20), 2D, the advection forms with a material field, SRHD, mixed sizes, whole SSP-RK3
 steps with the derived-quantity hand-over and the device-side CFL step, and the refusal of the
 paths that need multiples of 8.
 
@@ -16,7 +16,10 @@ from paper_2608_19273_gb300 import dh, synth
 pytestmark = pytest.mark.gpu
 FV = 0
 
-SIZES_3D = [((4, 4, 4), 3), ((3, 3, 3), 6), ((2, 2, 2), 5), ((2, 2, 2), 12), ((2, 1, 1), 20), ((2, 2, 2), 7)]
+# 3^3: 2x2x2 blocks as 6^3 boxes (4x4x4), one block whose members are each other's periodic
+# neighbours (2x2x2), and patches that form no block (2x2x1: the z neighbour is the patch itself)
+SIZES_3D = [((4, 4, 4), 3), ((2, 2, 2), 3), ((2, 2, 1), 3), ((3, 2, 2), 4), ((3, 3, 3), 6), ((2, 2, 2), 5),
+            ((2, 2, 2), 12), ((2, 1, 1), 20), ((2, 2, 2), 7)]
 
 
 def _stage(torch, orc, mesh, pde, dim, qs, q0, mat, coef, params=None, lam=True):
