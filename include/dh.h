@@ -460,6 +460,13 @@ dh_status dh_plan_set_debug(dh_plan* plan, int32_t flags);
  * can bound the reciprocal's error.  All three arrays are device arrays of n. */
 dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n, void* stream);
 
+/* Diagnostic: for n doubles x, y_sqrt[i] and y_rsqrt[i] = the kernels' square
+ * root and reciprocal square root of x[i] (the hardware estimate refined by one
+ * third-order step for normal, finite x > 0; sqrt and rsqrt themselves for other
+ * arguments), so that a test can bound their error against correctly rounded
+ * values.  All three arrays are device arrays of n. */
+dh_status dh_check_sqrt(const double* x, double* y_sqrt, double* y_rsqrt, int64_t n, void* stream);
+
 /* Diagnostic: the integer-pipe conversions of the recovery's FP32 seed paths
  * against the hardware conversions.  For n doubles x and n floats g (device
  * arrays): f_int[i] / f_hw[i] = x[i] rounded to float by bit operations / by
@@ -486,8 +493,10 @@ dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void*
  * every GPU loading the library holds until exit.  Limits: K <= 8192 patches
  * and at most 16384 tile work items (a 16x16 column of a patch, or four 8x8
  * columns); larger inputs return DH_EINVAL.  PDEs: ADV_FLUX, ADV_NCP,
- * EULER2D, EULER3D; halo 1; every face neighbour on the same level (coupled
- * refinement levels, which dh_plan_create accepts, return DH_EINVAL here).
+ * EULER2D, EULER3D; halo 1; patch sizes multiples of 8 in [8, 256] (other
+ * sizes, which dh_plan_create accepts, return DH_EINVAL here); every face
+ * neighbour on the same level (coupled refinement levels, which
+ * dh_plan_create accepts, return DH_EINVAL here).
  * Each call copies the patch table and the work list it builds into static
  * host buffers of the library and uploads them from there with
  * cudaMemcpyAsync (staged before the call returns, so `patches` may be freed

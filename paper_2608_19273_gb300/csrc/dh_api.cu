@@ -203,6 +203,15 @@ __global__ void k_check_recip(const double* x, double* y_nr, double* y_div, int6
   }
 }
 
+// sqrt_pos and rsqrt_pos, for the accuracy test.
+__global__ void k_check_sqrt(const double* x, double* y_sqrt, double* y_rsqrt, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    y_sqrt[i] = sqrt_pos(x[i]);
+    y_rsqrt[i] = rsqrt_pos(x[i]);
+  }
+}
+
 static inline int pt_nbr(const dh_patch* patches, int k, int f) { return patches[k].nbr[f]; }
 
 // Work list of the generic FV stage (k_fv_any; see dh_fv_any.cuh).  An item's shape: ng groups
@@ -706,6 +715,12 @@ dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n
   if (!x || !y_nr || !y_div || n <= 0 || n > (1ll << 40)) { set_error("dh_check_recip: bad arguments"); return DH_EINVAL; }
   k_check_recip<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y_nr, y_div, n);
   return cuda_error(cudaGetLastError(), "dh_check_recip launch");
+}
+
+dh_status dh_check_sqrt(const double* x, double* y_sqrt, double* y_rsqrt, int64_t n, void* stream) {
+  if (!x || !y_sqrt || !y_rsqrt || n <= 0 || n > (1ll << 40)) { set_error("dh_check_sqrt: bad arguments"); return DH_EINVAL; }
+  k_check_sqrt<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y_sqrt, y_rsqrt, n);
+  return cuda_error(cudaGetLastError(), "dh_check_sqrt launch");
 }
 
 dh_status dh_probe_dfma(double* out_dev, int64_t n_threads, int32_t iters, void* stream) {

@@ -35,7 +35,8 @@ namespace dh {
 // issued as FMAs with the run-time constants one/mone/zero (GB300 runs DFMA
 // faster than DADD/DMUL; results are bitwise the same); the reciprocal is a
 // refined hardware estimate (recip_nr, one third-order step, <= 1 ulp from the
-// IEEE quotient).  A state whose y^2 - S^2 is not positive gives NaN (failure).
+// IEEE quotient), and so is the reciprocal square root (rsqrt_pos, one third-order
+// step, within two ulps).  A state whose y^2 - S^2 is not positive gives NaN (failure).
 __device__ int srhd_newton_dev(double gf, double D, double S2, double E, double p_lo, double p0, double tol,
                                int max_iter, double one, double mone, double zero, double* p_out) {
   const double gfS2 = fma(gf, S2, zero), gm1 = fma(gf, one, mone);
@@ -43,7 +44,7 @@ __device__ int srhd_newton_dev(double gf, double D, double S2, double E, double 
   for (int it = 1; it <= max_iter; ++it) {
     const double y = fma(E, one, p);
     const double d = fma(y, y, -S2);                      // q^2
-    const double iq = rsqrt(d);                           // 1/q
+    const double iq = rsqrt_pos(d);                       // 1/q
     const double q = fma(d, iq, zero);
     const double qmD = fma(D, mone, q);                   // q - D
     const double num = fma(fma(-p, y, fma(fma(gf, q, zero), qmD, zero)), y, zero);   // y^2 f

@@ -161,6 +161,35 @@ def test_newton_reciprocal_within_one_ulp():
     assert np.array_equal(b, 1.0 / x)
 
 
+def test_refined_square_root_and_reciprocal_square_root_within_two_ulps():
+    """The kernels' sqrt and 1/sqrt (hardware estimate + one third-order step of the binomial series)
+    against correctly rounded values, over the whole normal range; zero, subnormal, infinite,
+    negative and NaN arguments take sqrt and rsqrt themselves."""
+    torch = require_cuda()
+    rng = np.random.default_rng(19)
+    x = np.concatenate([np.exp(rng.uniform(-700, 700, 400000)), rng.uniform(1.0, 4.0, 100000),
+                        np.array([1.0, 2.0, 4.0, 0.25, 3.0, 2.2250738585072014e-308, 1.7976931348623157e308])])
+    d_x = dev(torch, x)
+    y_s, y_r = torch.zeros_like(d_x), torch.zeros_like(d_x)
+    dh.dh_check_sqrt(d_x, y_s, y_r)
+    s, r = host(y_s), host(y_r)
+    ulp_s = np.abs(s.view(np.int64) - np.sqrt(x).view(np.int64))
+    r_ref = (np.longdouble(1) / np.sqrt(x.astype(np.longdouble))).astype(np.float64)
+    ulp_r = np.abs(r.view(np.int64) - r_ref.view(np.int64))
+    print(f"sqrt: max {ulp_s.max()} ulp, {np.mean(ulp_s == 0):.3f} exact; 1/sqrt: max {ulp_r.max()} ulp")
+    assert ulp_s.max() <= 2 and ulp_r.max() <= 2
+    special = np.array([0.0, 5e-324, 1e-310, np.inf, -1.0, np.nan])
+    d_x = dev(torch, special)
+    y_s, y_r = torch.zeros_like(d_x), torch.zeros_like(d_x)
+    dh.dh_check_sqrt(d_x, y_s, y_r)
+    s, r = host(y_s), host(y_r)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        assert np.array_equal(s, np.sqrt(special), equal_nan=True)
+        r_ref = (np.longdouble(1) / np.sqrt(special.astype(np.longdouble))).astype(np.float64)
+    assert r[0] == np.inf and r[3] == 0.0 and np.isnan(r[4]) and np.isnan(r[5])
+    assert np.all(np.abs(r[1:3].view(np.int64) - r_ref[1:3].view(np.int64)) <= 2)
+
+
 def test_graph_hands_derived_quantities_to_the_next_step(orc):
     """Inside a multi-step SSP-RK3 graph the last stage of a step stores the derived quantities of
     its result and the next step's first stage reads them: bitwise the same state and dt as eager

@@ -49,6 +49,15 @@ def test_noalloc_rejects_oversize(orc):
     assert ei.value.status == dh.DH_EINVAL
 
 
+def test_noalloc_rejects_patch_sizes_not_multiples_of_8(orc):
+    """6^3 patches, which a plan accepts (generic stage), are refused here before any launch."""
+    require_cuda()
+    mesh = synth.make_mesh([synth.Level((2, 2, 2), 6, 1.0 / 12, 0)], dim=3)
+    with pytest.raises(dh.DhError) as ei:
+        dh.patch_update_fv_noalloc(3, 3, mesh.patches, mesh.var_stride, None, 1, None, 1, None, None, 1, 0, 1, 1, 0)
+    assert ei.value.status == dh.DH_EINVAL
+
+
 def test_noalloc_euler2d_gamma_matches_plan_path(orc):
     """2D Euler with a non-default ratio of specific heats (gamma = 5/3, passed in params) on two
     calls in a row, against the plan path with the same parameter."""
