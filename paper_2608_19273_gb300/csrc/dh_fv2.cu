@@ -204,12 +204,16 @@ struct Fv2Tile {
       const int st = d == 0 ? 1 : (d == 1 ? MBX : MBX * MBY);
       const int a = d == 0 ? tx : (d == 1 ? ty : tz);                          // along d
       const int o = d == 0 ? tz * MY + ty : (d == 1 ? tz * MX + tx : ty * MX + tx);  // across d
+      // state slot of face j (along d) of line o: x faces line by line (consecutive threads,
+      // which differ in x, then touch consecutive slots), y and z faces plane by plane (where
+      // consecutive threads differ in o); every face's two states share one slot index
+      auto slot = [&](int j, int oo) { return d == 0 ? oo * (MX + 1) + j : j * area + oo; };
       // phase 1: own states; face f lies between voxels f-1 and f along d, so this
       // voxel's + state is the left state of face a+1 and its - state the right
       // state of face a.  Halo voxels next to the tile: the + state of the voxel
       // at -1 (left state of face 0) and the - state of the voxel at T (right
       // state of face T).
-      states(A, box, me, st, d, SP, (a + 1) * area + o, SM, a * area + o);
+      states(A, box, me, st, d, SP, slot(a + 1, o), SM, slot(a, o));
       // (taken by the last warps along x and z and by warps 4 and 5 along y, so that the
       // extra work of x and y falls on different SM sub-partitions; the faces beyond 256
       // in phase 2 go to warp 0, or to warp 2 along y)
@@ -221,8 +225,8 @@ struct Fv2Tile {
         else if (d == 1) { hy = side == 0 ? -1 : MY; hx = oo % MX; hz = oo / MX; }
         else { hz = side == 0 ? -1 : MZ; hx = oo % MX; hy = oo / MX; }
         const int c = mbox(hx, hy, hz);
-        if (side == 0) states(A, box, c, st, d, SP, oo, nullptr, 0);
-        else states(A, box, c, st, d, nullptr, 0, SM, T * area + oo);
+        if (side == 0) states(A, box, c, st, d, SP, slot(0, oo), nullptr, 0);
+        else states(A, box, c, st, d, nullptr, 0, SM, slot(T, oo));
       }
       __syncthreads();
       // phase 2: every face along d once ((T + 1) * area faces over the 256 threads)
@@ -236,7 +240,7 @@ struct Fv2Tile {
       // phase 3: difference of this voxel's two faces
 #pragma unroll
       for (int v = 0; v < N; ++v)
-        sum[v] = ADD(P, sum[v], SUB(P, SP[v * MFS + (a + 1) * area + o], SP[v * MFS + a * area + o]));
+        sum[v] = ADD(P, sum[v], SUB(P, SP[v * MFS + slot(a + 1, o)], SP[v * MFS + slot(a, o)]));
       __syncthreads();
     }
     // update

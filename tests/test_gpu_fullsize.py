@@ -1,7 +1,8 @@
 """Parity at the full workload sizes, in the launch configuration the benchmark
 times (autotuned kernel variant, whole time steps through dh_rk_step).
 
-3D Euler (10.5M voxels, first and second order), the wave system (8.4M) and SRHD (16.7M) are compared
+3D Euler (10.5M voxels, first and second order; 3.5M voxels in 6^3 and in 3^3 cells), the wave system
+(8.4M) and SRHD (16.7M) are compared
 with the oracle voxel by voxel after one full time step; GW59 (31M voxels x 59
 unknowns, 14.6 GB per state) is compared on a sample of patches from every
 level after one stage (the oracle updates only the sampled patches)."""
@@ -21,7 +22,7 @@ SRHD_REFINE = 3
 
 def _gpu_step(torch, name, w, q, mat, steps=1):
     spec = {"euler3d": (0, 3, 0.4), "wave3d": (1, 4, 0.25), "srhd3d": (0, 3, 0.4), "euler3d_muscl": (2, 3, 0.4),
-            "euler3d_amr2": (0, 3, 0.4)}[name]
+            "euler3d_amr2": (0, 3, 0.4), "euler3d_p6": (0, 3, 0.4), "euler3d_p3": (0, 3, 0.4)}[name]
     scheme, rk, cfl = spec
     mesh = w.mesh
     with dh.Plan(w.pde, 3, mesh.patches, w.halo, mesh.var_stride, w.params) as plan:
@@ -56,6 +57,21 @@ def test_euler3d_full_size_step(orc):
     dts = orc.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=1, cfl=0.4)
     assert abs(dt - dts[0]) <= 1e-15 * dts[0]
     assert_parity(got, ref, voxel_mask(mesh), what="euler3d full size")
+
+
+@pytest.mark.parametrize("name", ["euler3d_p6", "euler3d_p3"])
+def test_euler3d_small_cells_full_size_steps(orc, name):
+    """The paper's typical 6^3 and 3^3 cells (3.5M voxels each) through the generic FV stage: two
+    SSP-RK3 steps in the benchmark's configuration (stage-sum form, device-side CFL step)."""
+    torch = require_cuda()
+    w = synth.workload(name)
+    mesh = w.mesh
+    q = orc.prim2con(3, synth.euler_prims(mesh, w.seed), mesh.var_stride)
+    got, dt = _gpu_step(torch, name, w, q, None, steps=2)
+    ref = q.copy()
+    dts = orc.rk_steps(0, 3, 3, mesh.patches, 1, mesh.var_stride, ref, rk=3, steps=2, cfl=0.4)
+    assert abs(dt - dts[-1]) <= 1e-15 * dts[-1]
+    assert_parity(got, ref, voxel_mask(mesh), what=f"{name} full size")
 
 
 def test_euler3d_muscl_full_size_step(orc):
