@@ -11,7 +11,7 @@
 //   1. Every cell of the box and its one-voxel face halo (edges and corners are never read) is
 //      loaded into shared memory with its derived quantities W (read from the W arena of the
 //      stage input, or computed).
-//   2. Per direction d: every line cell of d (the box and its two halo layers across d) forms
+//   2. Per direction d: every line cell of d (the box and its halo layers at both ends along d) forms
 //      its flux F_d and speed lambda_d into the line arrays; after a barrier every face along d
 //      is formed once (one per thread) into the face arrays; after another barrier every voxel
 //      adds the difference of its two faces.
@@ -117,7 +117,8 @@ struct FvAny {
     for (int v = 0; v < N; ++v) { sum[v] = 0.0; dsum[v] = 0.0; }
 #pragma unroll 1
     for (int d = 0; d < DIM; ++d) {
-      // the line cells of d (the box and its two halo layers across d) of every group, x fastest
+      // the line cells of d (the box and the halo layer at each of its ends along d) of every
+      // group, x fastest; their fluxes and speeds go to the line arrays at index j
       const int LX = bx + 2 * (d == 0), LY = by + 2 * (d == 1), LZ = DIM == 3 ? bz + 2 * (d == 2) : 1;
       const int LG = LX * LY * LZ;
       const ADiv dLG(LG), dLX(LX), dLY(LY);
@@ -125,7 +126,7 @@ struct FvAny {
         const int gg = dLG.q(j), r = j - gg * LG, t = dLX.q(r), hi = dLY.q(t);
         const int cx = r - t * LX - (d == 0), cy = t - hi * LY - (d == 1), cz = hi - (d == 2);
         const int s = gg * SG + ((DIM == 3 ? cz + 1 : 0) * SY + (cy + 1)) * SX + (cx + 1);
-        double q[NV], W[NW], Fd[N];  // line arrays at j
+        double q[NV], W[NW], Fd[N];
 #pragma unroll
         for (int v = 0; v < NV; ++v) q[v] = Q[v * ANY_SLOTS + s];
 #pragma unroll
