@@ -18,8 +18,8 @@ FV = 0
 
 # 3^3: 2x2x2 blocks as 6^3 boxes (4x4x4), one block whose members are each other's periodic
 # neighbours (2x2x2), and patches that form no block (2x2x1: the z neighbour is the patch itself)
-SIZES_3D = [((4, 4, 4), 3), ((2, 2, 2), 3), ((2, 2, 1), 3), ((3, 2, 2), 4), ((3, 3, 3), 6), ((2, 2, 2), 5),
-            ((2, 2, 2), 12), ((2, 1, 1), 20), ((2, 2, 2), 7)]
+SIZES_3D = [((4, 4, 4), 3), ((2, 2, 2), 3), ((2, 2, 1), 3), ((4, 4, 2), 2), ((3, 2, 2), 4), ((3, 3, 3), 6),
+            ((2, 2, 2), 5), ((2, 2, 2), 12), ((2, 1, 1), 20), ((2, 2, 2), 7)]
 
 
 def _stage(torch, orc, mesh, pde, dim, qs, q0, mat, coef, params=None, lam=True):
