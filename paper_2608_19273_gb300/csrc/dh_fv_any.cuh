@@ -59,29 +59,46 @@ struct FvAny {
     const int SX = bx + 2, SY = by + 2, SZ = DIM == 3 ? bz + 2 : 1;
     const int SG = SX * SY * SZ;  // cells per group
     const int nvg = bx * by * bz;  // voxels per group
-    const ADiv dSG(SG), dSX(SX), dSXY(SX * SY);
     const int tid = threadIdx.x;
     const int g = tid / nvg, li = tid % nvg;
     const bool act = g < ng;
     const int lx = li % bx, ly = (li / bx) % by, lz = li / (bx * by);
-    // cell s -> (group, cx, cy, cz), cx in [-1, bx] etc.
-    auto cell = [&](int s, int& gg, int& cx, int& cy, int& cz) {
-      gg = dSG.q(s);
-      const int r = s - gg * SG, rz = DIM == 3 ? dSXY.q(r) : 0, rxy = r - rz * SX * SY, ry = dSX.q(rxy);
-      cx = rxy - ry * SX - 1;
-      cy = ry - 1;
-      cz = DIM == 3 ? rz - 1 : 0;
-    };
     const int p = A.patches[w.patch[0]].p;  // every group or block member of an item has the same p
     const double dt = *A.dt_dev;             // read before the lambda epilogue may rewrite it
     const double gdt = A.g * dt, ddt = A.d * dt;
 
-    // 1. the box and its face halo, with W
-    for (int s = tid; s < ng * SG; s += ANY_NT) {
-      int gg, cx, cy, cz;
-      cell(s, gg, cx, cy, cz);
-      const int outside = (cx < 0 || cx >= bx) + (cy < 0 || cy >= by) + (DIM == 3 && (cz < 0 || cz >= bz));
-      if (outside > 1) continue;
+    // 1. the box and its face halo, with W: the cells that are read, enumerated group by group as
+    //    the box (x fastest), then the two halo layers across x, y and z (edges and corners are
+    //    never read and never visited)
+    const int HX = by * bz, HY = bx * bz, HZ = DIM == 3 ? bx * by : 0;
+    const int CG = nvg + 2 * (HX + HY + HZ);  // cells read per group
+    const ADiv dCG(CG), dBX(bx), dBXY(bx * by), dBY(by), dHX(HX), dHY(HY), dHZ(HZ > 0 ? HZ : 1);
+    for (int j = tid; j < ng * CG; j += ANY_NT) {
+      const int gg = dCG.q(j);
+      int r = j - gg * CG, cx, cy, cz;
+      if (r < nvg) {
+        cz = DIM == 3 ? dBXY.q(r) : 0;
+        const int rxy = r - cz * bx * by;
+        cy = dBX.q(rxy);
+        cx = rxy - cy * bx;
+      } else if ((r -= nvg) < 2 * HX) {
+        const int side = dHX.q(r), t = r - side * HX;
+        cx = side ? bx : -1;
+        cz = dBY.q(t);
+        cy = t - cz * by;
+      } else if ((r -= 2 * HX) < 2 * HY) {
+        const int side = dHY.q(r), t = r - side * HY;
+        cy = side ? by : -1;
+        cz = dBX.q(t);
+        cx = t - cz * bx;
+      } else {
+        r -= 2 * HY;
+        const int side = dHZ.q(r), t = r - side * HZ;
+        cz = side ? bz : -1;
+        cy = dBX.q(t);
+        cx = t - cy * bx;
+      }
+      const int s = gg * SG + ((DIM == 3 ? cz + 1 : 0) * SY + (cy + 1)) * SX + (cx + 1);
       int64_t e;
       if (w.mp > 0) {
         // a 2x2x2 block of mp^3 patches: the member holding the cell, and the cell's
