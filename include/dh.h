@@ -467,6 +467,19 @@ dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n
  * values.  All three arrays are device arrays of n. */
 dh_status dh_check_sqrt(const double* x, double* y_sqrt, double* y_rsqrt, int64_t n, void* stream);
 
+/* Diagnostic (host only, no CUDA call): the work list that dh_plan_create builds
+ * for the generic FV stage of a table whose patch sizes are not all multiples of
+ * 8 (one CTA per item).  *n_items receives the number of items; with items !=
+ * NULL, 16 int32 per item are written to the host array items (capacity
+ * max_items items): the patch ids patch[0..7] (-1 where unused), the box origin
+ * x0, y0, z0 inside the patch, the box extents bx, by, bz, the group count ng
+ * (whole patches of equal size packed into one item) and mp (3 for a 2x2x2 block
+ * of face-adjacent 3^3 patches run as one 6^3 box: member (mx, my, mz) is
+ * patch[mx + 2 my + 4 mz]; 0 otherwise).  The table is checked only for patch
+ * sizes in [2, 256] and neighbour ids in [0, K) (DH_EINVAL otherwise). */
+dh_status dh_generic_work_list(int32_t dim, const dh_patch* patches, int32_t K, int32_t* items, int32_t max_items,
+                               int32_t* n_items);
+
 /* Diagnostic: the integer-pipe conversions of the recovery's FP32 seed paths
  * against the hardware conversions.  For n doubles x and n floats g (device
  * arrays): f_int[i] / f_hw[i] = x[i] rounded to float by bit operations / by

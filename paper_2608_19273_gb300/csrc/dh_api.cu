@@ -717,6 +717,31 @@ dh_status dh_check_recip(const double* x, double* y_nr, double* y_div, int64_t n
   return cuda_error(cudaGetLastError(), "dh_check_recip launch");
 }
 
+dh_status dh_generic_work_list(int32_t dim, const dh_patch* patches, int32_t K, int32_t* items, int32_t max_items,
+                               int32_t* n_items) {
+  if ((dim != 2 && dim != 3) || !patches || K <= 0 || !n_items || (items && max_items < 0)) {
+    set_error("dh_generic_work_list: bad arguments");
+    return DH_EINVAL;
+  }
+  for (int k = 0; k < K; ++k) {
+    const dh_patch& pt = patches[k];
+    if (pt.p < 2 || pt.p > 256) { set_error("dh_generic_work_list: patch %d: p = %d", k, pt.p); return DH_EINVAL; }
+    for (int f = 0; f < 2 * dim; ++f)
+      if (pt.nbr[f] < 0 || pt.nbr[f] >= K) { set_error("dh_generic_work_list: patch %d: bad neighbour", k); return DH_EINVAL; }
+  }
+  const std::vector<AnyWork> w = any_work(patches, K, dim);
+  *n_items = (int32_t)w.size();
+  if (!items) return DH_OK;
+  if ((int64_t)w.size() > max_items) { set_error("dh_generic_work_list: %d items > max_items", (int)w.size()); return DH_EINVAL; }
+  for (size_t i = 0; i < w.size(); ++i) {
+    int32_t* o = items + 16 * i;
+    for (int j = 0; j < 8; ++j) o[j] = w[i].patch[j];
+    o[8] = w[i].x0; o[9] = w[i].y0; o[10] = w[i].z0;
+    o[11] = w[i].bx; o[12] = w[i].by; o[13] = w[i].bz; o[14] = w[i].ng; o[15] = w[i].mp;
+  }
+  return DH_OK;
+}
+
 dh_status dh_check_sqrt(const double* x, double* y_sqrt, double* y_rsqrt, int64_t n, void* stream) {
   if (!x || !y_sqrt || !y_rsqrt || n <= 0 || n > (1ll << 40)) { set_error("dh_check_sqrt: bad arguments"); return DH_EINVAL; }
   k_check_sqrt<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, y_sqrt, y_rsqrt, n);

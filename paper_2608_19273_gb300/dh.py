@@ -26,7 +26,7 @@ PDE_ADV_FLUX, PDE_ADV_NCP, PDE_EULER2D, PDE_EULER3D, PDE_WAVE3D, PDE_SRHD3D, PDE
 EXPORTS = ["dh_plan_create", "dh_plan_destroy", "patch_update_fv", "patch_update_fv_muscl", "patch_update_fd_ko",
            "max_wave_speed",
            "dh_cfl_dt", "dh_prim2con", "dh_gather_aoas", "dh_scatter_aoas", "dh_offload_bind", "dh_offload_bind_staged", "dh_offload_run", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch", "dh_graph_info",
-           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_check_sqrt", "dh_check_convert", "dh_autotune", "dh_autotune_steps", "dh_plan_set_variant", "dh_plan_set_variant_muscl", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
+           "dh_graph_stage_times", "dh_probe_dfma", "dh_check_recip", "dh_check_sqrt", "dh_check_convert", "dh_generic_work_list", "dh_autotune", "dh_autotune_steps", "dh_plan_set_variant", "dh_plan_set_variant_muscl", "dh_plan_errors", "dh_plan_set_debug", "patch_update_fv_noalloc", "con2prim", "con2prim_flat",
            "dh_mlp_features", "dh_mlp_standardize", "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train",
            "dh_last_error", "dh_version"]
 
@@ -63,6 +63,7 @@ def lib():
         L.dh_probe_dfma.argtypes = [vp, i64, i32, vp]
         L.dh_check_recip.argtypes = [vp, vp, vp, i64, vp]
         L.dh_check_sqrt.argtypes = [vp, vp, vp, i64, vp]
+        L.dh_generic_work_list.argtypes = [i32, vp, i32, vp, i32, vp]
         L.dh_check_convert.argtypes = [vp, vp, vp, vp, vp, vp, i64, vp]
         L.dh_autotune.argtypes = [vp, i32, vp, vp, vp, vp, i32, ctypes.c_char_p, vp, vp, vp]
         L.dh_autotune_steps.argtypes = [vp, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, d, d, i32, ctypes.c_char_p,
@@ -394,6 +395,19 @@ def dh_plan_set_debug(plan, flags):
 def dh_check_sqrt(x, y_sqrt, y_rsqrt, stream=None):
     _check(lib().dh_check_sqrt(_ptr(x, "x"), _ptr(y_sqrt, "y_sqrt"), _ptr(y_rsqrt, "y_rsqrt"), int(x.numel()),
                                _stream(stream)), "dh_check_sqrt")
+
+
+def dh_generic_work_list(dim, patches):
+    """The generic FV stage's work list of a patch table (host only): an int32 array of shape
+    (items, 16): patch[0..7], x0, y0, z0, bx, by, bz, ng, mp."""
+    patches = np.ascontiguousarray(patches, dtype=synth.PATCH_DTYPE)
+    n = ctypes.c_int32(0)
+    _check(lib().dh_generic_work_list(int(dim), patches.ctypes.data, len(patches), None, 0, ctypes.byref(n)),
+           "dh_generic_work_list")
+    out = np.zeros((n.value, 16), dtype=np.int32)
+    _check(lib().dh_generic_work_list(int(dim), patches.ctypes.data, len(patches), out.ctypes.data, n.value,
+                                      ctypes.byref(n)), "dh_generic_work_list")
+    return out
 
 
 def dh_check_recip(x, y_nr, y_div, stream=None):

@@ -131,7 +131,7 @@ ENTRY_POINTS = ["patch_update_fv", "patch_update_fd_ko", "patch_update_fv_muscl"
                 "dh_offload_run", "dh_autotune", "dh_autotune_steps", "dh_plan_set_variant", "dh_plan_set_variant_muscl", "dh_plan_errors", "dh_plan_set_debug",
                 "con2prim", "dh_plan_set_con2prim", "dh_rk_step", "dh_graph_capture", "dh_graph_launch",
                 "dh_graph_info", "dh_graph_stage_times", "con2prim_flat", "dh_mlp_features", "dh_mlp_standardize",
-                "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train", "dh_check_recip", "dh_check_sqrt", "dh_check_convert", "dh_probe_dfma",
+                "dh_mlp_forward", "dh_mlp_grad", "dh_mlp_adam", "dh_mlp_train", "dh_check_recip", "dh_check_sqrt", "dh_check_convert", "dh_generic_work_list", "dh_probe_dfma",
                 "patch_update_fv_noalloc"]
 
 
