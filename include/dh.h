@@ -107,9 +107,10 @@ typedef struct dh_plan dh_plan;
  * Sec. IV) run the first-order FV stage (patch_update_fv, dh_rk_step and the
  * graphs with scheme 0) through a generic kernel -- 2x2x2 blocks of
  * face-adjacent 3^3 patches as one 6^3 box, other small patches whole (up to
- * eight to a CTA), boxes of at most 256 voxels of larger ones -- and refuse the FD4, MUSCL and coupled-level paths (DH_EUNSUPPORTED, or
- * DH_EINVAL at plan creation for coupled tables); the autotuner has nothing to
- * choose for them.  A face neighbour has the
+ * eight to a CTA), boxes of at most 256 voxels of larger ones (see
+ * dh_generic_work_list) -- and refuse the FD4, MUSCL and coupled-level paths
+ * (DH_EUNSUPPORTED, or DH_EINVAL at plan creation for coupled tables); the
+ * autotuner has nothing to choose for them.  A face neighbour has the
  * same p, dx and level, or -- coupled refinement levels -- is one level
  * coarser with the same p and twice the dx; every patch above the coarsest
  * level present must then cover one octant of a patch one level coarser (its
