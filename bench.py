@@ -305,13 +305,18 @@ def oracle_step(name, w, mesh, q, mat, prim):
                     rk=spec["rk"], steps=1, cfl=spec["cfl"], sigma=0.1, params=w.params)
 
 
+# The oracle's CPU samples run each workload with its box scaled down by this factor per axis
+# (same patch sizes) where the whole workload would take too long on the host cores.
+ORACLE_SCALE = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
+                "gw59": 4, "euler3d_p6": 1, "euler3d_p3": 1}
+
+
 def oracle_sample(name, budget_s):
     """The oracle on a bounded sample of the workload: the full mesh when it is small enough,
     else the same patch sizes with fewer patches per level (scaled box)."""
     import oracle
     cores = oracle.num_threads(0)
-    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
-             "gw59": 4, "euler3d_p6": 1, "euler3d_p3": 1}[name]
+    scale = ORACLE_SCALE[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)
@@ -348,8 +353,7 @@ def reference_arm(args, rank, world):
     # under torchrun every rank starts with one OpenMP thread; rank 0 runs alone here, so it takes
     # the host's cores
     cores = oracle.num_threads(len(os.sched_getaffinity(0)) if world > 1 else 0)
-    scale = {"euler3d": 1, "euler3d_muscl": 2, "euler3d_amr2": 1, "euler2d": 1, "wave3d": 2, "srhd3d": 2,
-             "gw59": 4, "euler3d_p6": 1, "euler3d_p3": 1}[name]
+    scale = ORACLE_SCALE[name]
     w = synth.workload(name, scale=scale)
     mesh = w.mesh
     h, mat, kind = host_inputs(name, w)
